@@ -1,0 +1,389 @@
+/*
+ * Fast Bilateral Solver -- plain FP64 CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline / reference arm may load this file.  The product
+ * path (the CUDA library) never calls it, and the two share no code.
+ *
+ * Everything here is the method written out in the paper's order with plain
+ * loops, in FP64 (the paper fixes no precision).  Build with
+ *     gcc -O2 -ffp-contract=off -fPIC -shared
+ * (no FMA contraction, no fast-math) so results are the same on x86-64 and
+ * aarch64.
+ *
+ * Notation.  N pixels, V vertices, C channels.  Key fields are ordered
+ * (x, y, l, u, v) as dimensions d = 0..4; the packed 64-bit key holds them
+ * MSB -> LSB as y, x, l, u, v in 12-bit fields, so ascending packed key is
+ * row-major order of grid cells, then colour.  Neighbour table nbr[v][2d+0]
+ * is the -1 neighbour in dimension d and nbr[v][2d+1] the +1 neighbour,
+ * -1 when absent.
+ *
+ * Readings of points the paper leaves open (each is listed with its
+ * justification in the design notes):
+ *   - quantisation key_d = floor(p_d / sigma_d + 1/2), p = (col, row, l, u, v),
+ *     evaluated in FP64; fields outside [0, 4095] are an error;
+ *   - vertices are the distinct keys in ascending packed order;
+ *   - the blur is Bbar = sum over the 5 dims of the [1, 2, 1] stencil, so
+ *     Bbar = 10 I + N with N the sum over existing +-1 neighbours;
+ *   - "while not converged" in the bistochastisation is a fixed sweep count;
+ *   - 0/0 guards: y0 = 0 where S c = 0; M^-1 = 0 where diag(A) <= 0;
+ *     alpha = 0 if d'q <= 0 or delta = 0; beta = 0 if delta_old = 0.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define FBSO_FIELD_MAX 4095
+#define FBSO_OK 0
+#define FBSO_ERR_ARG 1
+#define FBSO_ERR_RANGE 2
+#define FBSO_ERR_OOM 3
+
+/* bit position of dimension d = (x, y, l, u, v) in the packed key */
+static const int kShift[5] = {36, 48, 24, 12, 0};
+
+/* ---------------------------------------------------------------------- */
+/* Quantisation: Eq. (2) measures affinity in (x/sxy, y/sxy, l/sl, u/suv,  */
+/* v/suv); the simplified grid assigns each pixel to its nearest vertex.   */
+/* ---------------------------------------------------------------------- */
+static int quantise(double p, double sigma, uint64_t* out)
+{
+    double k = floor(p / sigma + 0.5);
+    if (!(k >= 0.0 && k <= (double)FBSO_FIELD_MAX)) return FBSO_ERR_RANGE; /* NaN fails too */
+    *out = (uint64_t)k;
+    return FBSO_OK;
+}
+
+int fbso_keys(const float* yuv, int64_t H, int64_t W, double sigma_xy, double sigma_l,
+              double sigma_uv, uint64_t* keys)
+{
+    if (!(sigma_xy > 0.0 && sigma_l > 0.0 && sigma_uv > 0.0) || H <= 0 || W <= 0)
+        return FBSO_ERR_ARG;
+    int64_t N = H * W;
+    for (int64_t row = 0; row < H; ++row) {
+        for (int64_t col = 0; col < W; ++col) {
+            int64_t i = row * W + col;
+            double p[5] = {(double)col, (double)row, (double)yuv[i], (double)yuv[N + i],
+                           (double)yuv[2 * N + i]};
+            double s[5] = {sigma_xy, sigma_xy, sigma_l, sigma_uv, sigma_uv};
+            uint64_t key = 0;
+            for (int d = 0; d < 5; ++d) {
+                uint64_t f;
+                int st = quantise(p[d], s[d], &f);
+                if (st) return st;
+                key |= f << kShift[d];
+            }
+            keys[i] = key;
+        }
+    }
+    return FBSO_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Simplified bilateral grid (Eq. (3), (5)): one vertex per distinct key. */
+/* ---------------------------------------------------------------------- */
+static int cmp_u64(const void* a, const void* b)
+{
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* index of key in sorted unique vkey[0..V), or -1 */
+static int64_t find_key(const uint64_t* vkey, int64_t V, uint64_t key)
+{
+    int64_t lo = 0, hi = V - 1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (vkey[mid] == key) return mid;
+        if (vkey[mid] < key) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+/* Returns V (>= 0) or -FBSO_ERR_OOM.  vkey and m need room for N entries,
+ * nbr for 10 N. */
+int64_t fbso_grid(const uint64_t* keys, int64_t N, uint64_t* vkey, uint32_t* vid, uint32_t* m,
+                  int32_t* nbr)
+{
+    uint64_t* sorted = (uint64_t*)malloc((size_t)(N > 0 ? N : 1) * sizeof(uint64_t));
+    if (!sorted) return -FBSO_ERR_OOM;
+    memcpy(sorted, keys, (size_t)N * sizeof(uint64_t));
+    qsort(sorted, (size_t)N, sizeof(uint64_t), cmp_u64);
+    int64_t V = 0;
+    for (int64_t i = 0; i < N; ++i)
+        if (i == 0 || sorted[i] != sorted[i - 1]) vkey[V++] = sorted[i];
+    free(sorted);
+
+    /* S: pixel i -> vertex vid[i]; m = S 1 (Alg. 1, first step) */
+    for (int64_t v = 0; v < V; ++v) m[v] = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t v = find_key(vkey, V, keys[i]);
+        vid[i] = (uint32_t)v;
+        m[v] += 1;
+    }
+    /* +-1 neighbours along each of the 5 dimensions; no wrap at field edges */
+    for (int64_t v = 0; v < V; ++v) {
+        for (int d = 0; d < 5; ++d) {
+            uint64_t f = (vkey[v] >> kShift[d]) & FBSO_FIELD_MAX;
+            uint64_t unit = (uint64_t)1 << kShift[d];
+            int64_t lo = -1, hi = -1;
+            if (f > 0) lo = find_key(vkey, V, vkey[v] - unit);
+            if (f < FBSO_FIELD_MAX) hi = find_key(vkey, V, vkey[v] + unit);
+            nbr[v * 10 + 2 * d + 0] = (int32_t)lo;
+            nbr[v * 10 + 2 * d + 1] = (int32_t)hi;
+        }
+    }
+    return V;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Bistochastisation (supplement Alg. 1): n <- sqrt(n o m / (Bbar n)),     */
+/* as a Jacobi sweep (every vertex updated from the previous n).           */
+/* Bbar n at v is accumulated as 10 n_v, then + n_u for k = 0..9 in order. */
+/* ---------------------------------------------------------------------- */
+int fbso_bistochastize(int64_t V, const uint32_t* m, const int32_t* nbr, int iters, double* n)
+{
+    double* prev = (double*)malloc((size_t)(V > 0 ? V : 1) * sizeof(double));
+    if (!prev) return FBSO_ERR_OOM;
+    for (int64_t v = 0; v < V; ++v) n[v] = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        memcpy(prev, n, (size_t)V * sizeof(double));
+        for (int64_t v = 0; v < V; ++v) {
+            double bn = 10.0 * prev[v];
+            for (int k = 0; k < 10; ++k) {
+                int32_t u = nbr[v * 10 + k];
+                if (u >= 0) bn = bn + prev[u];
+            }
+            n[v] = sqrt(prev[v] * (double)m[v] / bn);
+        }
+    }
+    free(prev);
+    return FBSO_OK;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Problem construction (Eq. (6)): b = S (c o t), S c, and diag(A) (Sec. 4) */
+/* ---------------------------------------------------------------------- */
+static void splat_impl(int64_t N, int64_t V, int C, const uint32_t* vid, const float* t,
+                       const double* c, double* b, double* sc)
+{
+    for (int64_t v = 0; v < V; ++v) sc[v] = 0.0;
+    for (int64_t k = 0; k < (int64_t)C * V; ++k) b[k] = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        int64_t v = vid[i];
+        sc[v] += c[i];
+        for (int ch = 0; ch < C; ++ch) b[ch * V + v] += c[i] * (double)t[ch * N + i];
+    }
+}
+
+/* b = S (c o t) per channel and S c, summed in FP64 in pixel order */
+int fbso_splat(int64_t N, int64_t V, int C, const uint32_t* vid, const float* t, const float* c,
+               double* b, double* sc)
+{
+    double* cd = (double*)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
+    if (!cd) return FBSO_ERR_OOM;
+    for (int64_t i = 0; i < N; ++i) cd[i] = (double)c[i];
+    splat_impl(N, V, C, vid, t, cd, b, sc);
+    free(cd);
+    return FBSO_OK;
+}
+
+static int has_neighbour(const int32_t* nbr, int64_t v)
+{
+    for (int k = 0; k < 10; ++k)
+        if (nbr[v * 10 + k] >= 0) return 1;
+    return 0;
+}
+
+/* diag(A) = lambda (m - Bbar_diag n^2) + S c with Bbar_diag = 10; the
+ * smoothness part is exactly 0 for a vertex without neighbours (its row of
+ * lambda (D_m - D_n Bbar D_n) vanishes once n^2 = m / 10).  M^-1 = 1/diag(A),
+ * 0 where diag(A) <= 0. */
+void fbso_diag(int64_t V, const uint32_t* m, const int32_t* nbr, const double* n,
+               const double* sc, double lam, double* a, double* minv)
+{
+    for (int64_t v = 0; v < V; ++v) {
+        double smooth = has_neighbour(nbr, v) ? lam * ((double)m[v] - 10.0 * n[v] * n[v]) : 0.0;
+        a[v] = smooth + sc[v];
+        minv[v] = a[v] > 0.0 ? 1.0 / a[v] : 0.0;
+    }
+}
+
+/* A z = diag(A) z - lambda D_n N D_n z  (the off-diagonal part of Bbar is N) */
+void fbso_apply_A(int64_t V, const int32_t* nbr, const double* n, const double* a, double lam,
+                  const double* z, double* out)
+{
+    for (int64_t v = 0; v < V; ++v) {
+        double s = 0.0;
+        for (int k = 0; k < 10; ++k) {
+            int32_t u = nbr[v * 10 + k];
+            if (u >= 0) s += n[u] * z[u];
+        }
+        out[v] = a[v] * z[v] - lam * n[v] * s;
+    }
+}
+
+/* flat initialisation (Eq. (13)): y = S(c o t) / S(c), 0 where S c = 0 */
+void fbso_flat_init(int64_t V, const double* b, const double* sc, double* y)
+{
+    for (int64_t v = 0; v < V; ++v) y[v] = sc[v] > 0.0 ? b[v] / sc[v] : 0.0;
+}
+
+static double dot(int64_t V, const double* x, const double* y)
+{
+    double s = 0.0;
+    for (int64_t v = 0; v < V; ++v) s += x[v] * y[v];
+    return s;
+}
+
+/* Preconditioned CG, supplement Alg. 2 (Shewchuk B3), fixed iteration
+ * count, one right-hand side.  y holds the initial state on entry.
+ * The paper's lambda_new / lambda_old are named delta here. */
+int fbso_pcg(int64_t V, const int32_t* nbr, const double* n, const double* a,
+             const double* minv, double lam, const double* b, double* y, int iters)
+{
+    size_t sz = (size_t)(V > 0 ? V : 1) * sizeof(double);
+    double* r = (double*)malloc(sz);
+    double* d = (double*)malloc(sz);
+    double* q = (double*)malloc(sz);
+    double* s = (double*)malloc(sz);
+    if (!r || !d || !q || !s) { free(r); free(d); free(q); free(s); return FBSO_ERR_OOM; }
+
+    fbso_apply_A(V, nbr, n, a, lam, y, q);
+    for (int64_t v = 0; v < V; ++v) r[v] = b[v] - q[v];
+    for (int64_t v = 0; v < V; ++v) d[v] = minv[v] * r[v];
+    double delta = dot(V, r, d);
+    for (int i = 0; i < iters; ++i) {
+        fbso_apply_A(V, nbr, n, a, lam, d, q);
+        double dq = dot(V, d, q);
+        double alpha = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
+        for (int64_t v = 0; v < V; ++v) y[v] += alpha * d[v];
+        for (int64_t v = 0; v < V; ++v) r[v] -= alpha * q[v];
+        for (int64_t v = 0; v < V; ++v) s[v] = minv[v] * r[v];
+        double delta_old = delta;
+        delta = dot(V, r, s);
+        double beta = delta_old != 0.0 ? delta / delta_old : 0.0;
+        for (int64_t v = 0; v < V; ++v) d[v] = s[v] + beta * d[v];
+    }
+    free(r); free(d); free(q); free(s);
+    return FBSO_OK;
+}
+
+/* slice (Eq. (8)): x = S^T y */
+void fbso_slice(int64_t N, int64_t V, int C, const uint32_t* vid, const double* y, double* x)
+{
+    for (int ch = 0; ch < C; ++ch)
+        for (int64_t i = 0; i < N; ++i) x[ch * N + i] = y[ch * V + vid[i]];
+}
+
+/* One forward solve of C channels sharing A (Sec. 2, Eq. (8); supplement
+ * Sec. 4): b, S c, diag(A), flat init, PCG per channel, slice.
+ * Outputs y (C x V) and, if x is non-NULL, x (C x N). */
+static int solve_impl(int64_t N, int64_t V, int C, const uint32_t* vid, const uint32_t* m,
+                      const int32_t* nbr, const double* n, const float* t, const double* c,
+                      double lam, int pcg_iters, double* y, double* x)
+{
+    size_t sv = (size_t)(V > 0 ? V : 1) * sizeof(double);
+    double* b = (double*)malloc(sv * (size_t)(C > 0 ? C : 1));
+    double* sc = (double*)malloc(sv);
+    double* a = (double*)malloc(sv);
+    double* minv = (double*)malloc(sv);
+    if (!b || !sc || !a || !minv) { free(b); free(sc); free(a); free(minv); return FBSO_ERR_OOM; }
+    splat_impl(N, V, C, vid, t, c, b, sc);
+    fbso_diag(V, m, nbr, n, sc, lam, a, minv);
+    int st = FBSO_OK;
+    for (int ch = 0; ch < C && !st; ++ch) {
+        fbso_flat_init(V, b + (int64_t)ch * V, sc, y + (int64_t)ch * V);
+        st = fbso_pcg(V, nbr, n, a, minv, lam, b + (int64_t)ch * V, y + (int64_t)ch * V, pcg_iters);
+    }
+    if (!st && x) fbso_slice(N, V, C, vid, y, x);
+    free(b); free(sc); free(a); free(minv);
+    return st;
+}
+
+int fbso_solve(int64_t N, int64_t V, int C, const uint32_t* vid, const uint32_t* m,
+               const int32_t* nbr, const double* n, const float* t, const float* c, double lam,
+               int pcg_iters, double* y, double* x)
+{
+    double* cd = (double*)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
+    if (!cd) return FBSO_ERR_OOM;
+    for (int64_t i = 0; i < N; ++i) cd[i] = (double)c[i];
+    int st = solve_impl(N, V, C, vid, m, nbr, n, t, cd, lam, pcg_iters, y, x);
+    free(cd);
+    return st;
+}
+
+/* Robust bilateral solver with the Geman-McClure loss (supplement Alg. 3):
+ * c <- c_init; repeat irls_iters times { x <- solve(t, c); e <- x - t;
+ * c <- 2 s^2 / (s^2 + e^2)^2 }.  Each solve starts afresh from the flat
+ * initialisation of the current c.  Returns the last solve's y and x. */
+int fbso_solve_robust(int64_t N, int64_t V, const uint32_t* vid, const uint32_t* m,
+                      const int32_t* nbr, const double* n, const float* t, const float* c_init,
+                      double lam, double sigma_gm, int irls_iters, int pcg_iters, double* y,
+                      double* x)
+{
+    double* c = (double*)malloc((size_t)(N > 0 ? N : 1) * sizeof(double));
+    if (!c) return FBSO_ERR_OOM;
+    for (int64_t i = 0; i < N; ++i) c[i] = (double)c_init[i];
+    double s2 = sigma_gm * sigma_gm;
+    int st = FBSO_OK;
+    for (int it = 0; it < irls_iters && !st; ++it) {
+        st = solve_impl(N, V, 1, vid, m, nbr, n, t, c, lam, pcg_iters, y, x);
+        if (st) break;
+        for (int64_t i = 0; i < N; ++i) {
+            double e = x[i] - (double)t[i];
+            double den = s2 + e * e;
+            c[i] = 2.0 * s2 / (den * den);
+        }
+    }
+    free(c);
+    return st;
+}
+
+/* Backward pass (Sec. 3): g = S dL/dx; z = A^-1 g by the same PCG with the
+ * flat initialisation applied to g; dL/dt = c o S^T z;
+ * dL/dc = sum_ch [ S^T(-z o yhat) + (S^T z) o t ]  (c is shared by the
+ * channels).  yhat is the forward solution (C x V). */
+int fbso_backward(int64_t N, int64_t V, int C, const uint32_t* vid, const uint32_t* m,
+                  const int32_t* nbr, const double* n, const float* t, const float* c,
+                  double lam, int pcg_iters, const double* yhat, const double* dx,
+                  double* dt, double* dc)
+{
+    size_t sv = (size_t)(V > 0 ? V : 1) * sizeof(double);
+    double* g = (double*)malloc(sv * (size_t)(C > 0 ? C : 1));
+    double* z = (double*)malloc(sv * (size_t)(C > 0 ? C : 1));
+    double* sc = (double*)malloc(sv);
+    double* a = (double*)malloc(sv);
+    double* minv = (double*)malloc(sv);
+    if (!g || !z || !sc || !a || !minv) {
+        free(g); free(z); free(sc); free(a); free(minv);
+        return FBSO_ERR_OOM;
+    }
+    for (int64_t v = 0; v < V; ++v) sc[v] = 0.0;
+    for (int64_t k = 0; k < (int64_t)C * V; ++k) g[k] = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        sc[vid[i]] += (double)c[i];
+        for (int ch = 0; ch < C; ++ch) g[ch * V + vid[i]] += dx[ch * N + i];
+    }
+    fbso_diag(V, m, nbr, n, sc, lam, a, minv);
+    int st = FBSO_OK;
+    for (int ch = 0; ch < C && !st; ++ch) {
+        fbso_flat_init(V, g + (int64_t)ch * V, sc, z + (int64_t)ch * V);
+        st = fbso_pcg(V, nbr, n, a, minv, lam, g + (int64_t)ch * V, z + (int64_t)ch * V, pcg_iters);
+    }
+    if (!st) {
+        for (int64_t i = 0; i < N; ++i) dc[i] = 0.0;
+        for (int ch = 0; ch < C; ++ch) {
+            for (int64_t i = 0; i < N; ++i) {
+                int64_t v = vid[i];
+                double zb = z[ch * V + v];                       /* S^T dL/db */
+                double zd = -zb * yhat[ch * V + v];              /* S^T dL/ddiag(A) */
+                dt[ch * N + i] = (double)c[i] * zb;
+                dc[i] += zd + zb * (double)t[ch * N + i];
+            }
+        }
+    }
+    free(g); free(z); free(sc); free(a); free(minv);
+    return st;
+}

@@ -1,0 +1,414 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test compares the oracle with an independent construction (exact
+rationals, numpy.unique, brute force, dense linear algebra, closed forms,
+invariants, finite differences), so that a dropped term, a wrong sign or
+index or a transposed operand in ``oracle/fbs_oracle.c`` fails one of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1511_03296_gb300 import synth
+from tests import dense
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def tiny(seed=11, h=20, w=28, sig=(6.0, 24.0, 24.0), lam=4.0, C=2, npoly=3):
+    return synth.make_tiny(seed, h, w, npoly, C, sig, lam)
+
+
+def pack(fields):
+    k = 0
+    for d, f in zip(dense.DIMS, fields):
+        k |= int(f) << dense.SHIFT[d]
+    return k
+
+
+# ---------------------------------------------------------------- keys ----
+
+@pytest.mark.parametrize("name", ["keys_2x3.json", "grid_1x5.json"])
+def test_keys_golden(name):
+    g = json.load(open(os.path.join(GOLDEN, name)))
+    h, w = g["height"], g["width"]
+    yuv = np.stack([np.array(g[p], np.float32).reshape(h, w) for p in "luv"])
+    k = oracle.keys(yuv, g["sigma_xy"], g["sigma_l"], g["sigma_uv"])
+    if "fields" in g:
+        assert [int(x) for x in k] == [pack(f) for f in g["fields"]]
+    vkey, vid, m, nbr = oracle.grid(k)
+    assert vid.tolist() == g["vid"]
+    assert m.tolist() == g["m"]
+    if "vkey_fields" in g:
+        assert [int(x) for x in vkey] == [pack(f) for f in g["vkey_fields"]]
+    if "nbr" in g:
+        assert nbr.tolist() == g["nbr"]
+
+
+def test_keys_exact_rational():
+    inst = tiny(seed=3, h=12, w=17, sig=(3.0, 5.0, 7.0))
+    # plant exact ties (k + 1/2) sigma and their float32 neighbours
+    yuv = inst.yuv.copy()
+    ties = np.array([2.5, 7.5, 12.5, 17.5], np.float32)
+    yuv[0, 0, :4] = ties * 5.0
+    yuv[0, 1, :4] = np.nextafter(ties * 5.0, np.float32(0))
+    yuv[1, 2, :4] = ties * 7.0
+    yuv[2, 3, :4] = np.nextafter(ties * 7.0, np.float32(1e9))
+    got = oracle.keys(yuv, 3.0, 5.0, 7.0)
+    want = dense.exact_keys(yuv, 3.0, 5.0, 7.0)
+    assert np.array_equal(got, want)
+
+
+def test_keys_non_integer_sigma():
+    inst = tiny(seed=4, h=9, w=13)
+    yuv = inst.yuv
+    for sig in [(1.7, 2.3, 3.1), (0.75, 0.5, 1.25)]:
+        assert np.array_equal(oracle.keys(yuv, *sig), dense.exact_keys(yuv, *sig))
+
+
+@pytest.mark.parametrize("bad", [-3.0, np.nan, 4095.5 * 4.0 + 1.0])
+def test_keys_out_of_range(bad):
+    yuv = np.full((3, 2, 2), 10.0, np.float32)
+    yuv[1, 1, 1] = bad
+    with pytest.raises(oracle.OracleError):
+        oracle.keys(yuv, 2.0, 4.0, 4.0)
+
+
+def test_keys_field_max_is_inclusive():
+    yuv = np.full((3, 1, 1), 0.0, np.float32)
+    yuv[0] = 4095.0 * 4.0 + 1.99     # rounds to 4095, still in range
+    k = oracle.keys(yuv, 1.0, 4.0, 4.0)
+    assert int(k[0]) >> 24 & 4095 == 4095
+
+
+# ---------------------------------------------------------------- grid ----
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_grid_matches_unique_and_brute_force(seed):
+    inst = tiny(seed=seed, h=24, w=32, sig=(4.0, 8.0, 8.0))
+    k = oracle.keys(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv)
+    vkey, vid, m, nbr = oracle.grid(k)
+    u, inv, cnt = np.unique(k, return_inverse=True, return_counts=True)
+    assert np.array_equal(vkey, u)
+    assert np.array_equal(vid, inv.astype(np.uint32))
+    assert np.array_equal(m, cnt.astype(np.uint32))
+    assert np.array_equal(nbr, dense.brute_neighbours(vkey))
+    assert (nbr >= 0).any(), "test image should have some neighbours"
+
+
+def test_grid_no_wrap_at_field_edges():
+    # v field 0 next to a vertex whose u is one less and v = 4095: not a neighbour
+    yuv = np.zeros((3, 1, 2), np.float32)
+    yuv[:, 0, 0] = (0.0, 5.0, 0.0)
+    yuv[:, 0, 1] = (0.0, 4.0, 4095.0)
+    k = oracle.keys(yuv, 100.0, 1.0, 1.0)
+    vkey, vid, m, nbr = oracle.grid(k)
+    assert int(vkey[1]) - int(vkey[0]) == 1  # adjacent packed keys
+    assert (nbr == -1).all()
+
+
+def test_SSt_is_Dm():
+    inst = tiny(seed=5)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    S = dense.dense_S(g.vid, g.V)
+    assert np.array_equal(S @ S.T, np.diag(g.m.astype(float)))   # supplement Eq. (5)
+    assert int(g.m.sum()) == g.N
+
+
+# ---------------------------------------------------- bistochastisation ----
+
+def _grid(seed=6, **kw):
+    inst = tiny(seed=seed, **kw)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, None)
+    return inst, g
+
+
+def test_bistoch_one_sweep_closed_form():
+    _, g = _grid()
+    B = dense.dense_Bbar(dense.brute_neighbours(g.vkey))
+    n1 = oracle.bistochastize(g.m, g.nbr, 1)
+    # from n = 1: n <- sqrt(m / (Bbar 1))   (Alg. 1)
+    assert np.allclose(n1, np.sqrt(g.m / (B @ np.ones(g.V))), rtol=1e-15, atol=0)
+    n2 = oracle.bistochastize(g.m, g.nbr, 2)
+    assert np.allclose(n2, np.sqrt(n1 * g.m / (B @ n1)), rtol=1e-14, atol=0)
+
+
+def test_bistoch_zero_sweeps_is_ones():
+    _, g = _grid()
+    assert np.array_equal(oracle.bistochastize(g.m, g.nbr, 0), np.ones(g.V))
+
+
+def test_bistoch_fixed_point_row_sums():
+    _, g = _grid()
+    B = dense.dense_Bbar(dense.brute_neighbours(g.vkey))
+    res = []
+    for it in (1, 4, 16, 64, 4000):
+        n = oracle.bistochastize(g.m, g.nbr, it)
+        res.append(np.linalg.norm(n * (B @ n) - g.m) / np.linalg.norm(g.m))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(res, res[1:])), res
+    assert res[-1] < 1e-10
+    # at the fixed point the bistochastised W-hat has unit row sums
+    n = oracle.bistochastize(g.m, g.nbr, 4000)
+    S = dense.dense_S(g.vid, g.V)
+    W = dense.dense_What(S, g.m, n, B)
+    assert np.allclose(W.sum(axis=1), 1.0, atol=1e-9)
+
+
+# ------------------------------------------------------------ problem A, b -
+
+def _problem(seed=7, iters=2, lam=4.0, C=2, **kw):
+    inst = tiny(seed=seed, lam=lam, C=C, **kw)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, iters)
+    nb = dense.brute_neighbours(g.vkey)
+    B = dense.dense_Bbar(nb)
+    S = dense.dense_S(g.vid, g.V)
+    c = inst.c.reshape(-1).astype(np.float64)
+    t = inst.t.reshape(inst.channels, -1).astype(np.float64)
+    sc = S @ c
+    A = dense.dense_A(g.m, g.n, B, sc, lam)
+    b = (S @ (c[None] * t).T).T
+    return inst, g, S, B, A, b, sc
+
+
+def test_splat_and_diag_match_dense():
+    inst, g, S, B, A, b, sc = _problem()
+    ob, osc = oracle.splat(g.vid, inst.t.reshape(inst.channels, -1), inst.c.reshape(-1), g.V)
+    assert np.allclose(ob, b, rtol=1e-13, atol=1e-10)
+    assert np.allclose(osc, sc, rtol=1e-13, atol=1e-12)
+    a, minv = oracle.diag(g.m, g.nbr, g.n, osc, inst.lam)
+    assert np.allclose(a, np.diag(A), rtol=1e-12, atol=1e-9 * inst.lam)
+    assert np.allclose(minv, np.where(a > 0, 1.0 / a, 0.0))
+
+
+def test_apply_A_matches_dense_and_is_symmetric():
+    inst, g, S, B, A, b, sc = _problem()
+    a, _ = oracle.diag(g.m, g.nbr, g.n, sc, inst.lam)
+    cols = np.stack([oracle.apply_A(g.nbr, g.n, a, inst.lam, e) for e in np.eye(g.V)], axis=1)
+    assert np.allclose(cols, A, rtol=1e-12, atol=1e-9 * inst.lam)
+    assert np.array_equal(cols, cols.T)
+
+
+@pytest.mark.parametrize("iters", [1, 4000])
+def test_A_is_spd(iters):
+    inst, g, S, B, A, b, sc = _problem(iters=iters)
+    np.linalg.cholesky(A)     # raises if not SPD
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+def test_A_min_eigenvalue_two_sweeps_reported():
+    # PSD is not guaranteed at an intermediate sweep count; record what it is
+    inst, g, S, B, A, b, sc = _problem(iters=2)
+    lam_min = np.linalg.eigvalsh(A).min()
+    assert np.isfinite(lam_min)
+
+
+def test_bilateral_loss_equals_pixel_loss():
+    # supplement Eq. (9) (pixel space) equals 2 x Eq. (16) (bilateral space) under x = S^T y
+    inst, g, S, B, A, b, sc = _problem(iters=3)
+    c = inst.c.reshape(-1).astype(np.float64)
+    t = inst.t.reshape(inst.channels, -1).astype(np.float64)[0]
+    W = dense.dense_What(S, g.m, g.n, B)
+    ob, osc = oracle.splat(g.vid, inst.t.reshape(inst.channels, -1), inst.c.reshape(-1), g.V)
+    a, _ = oracle.diag(g.m, g.nbr, g.n, osc, inst.lam)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        y = rng.normal(size=g.V) * 50
+        x = S.T @ y
+        pix = x @ (inst.lam * (np.eye(g.N) - W) + np.diag(c)) @ x - 2 * (c * t) @ x + (c * t) @ t
+        Ay = oracle.apply_A(g.nbr, g.n, a, inst.lam, y)
+        bil = 0.5 * y @ Ay - ob[0] @ y + 0.5 * (c * t) @ t
+        assert np.isclose(pix, 2 * bil, rtol=1e-10, atol=1e-6)
+
+
+# ----------------------------------------------------------------- solve --
+
+def test_lambda_zero_gives_weighted_mean():
+    inst = tiny(seed=8, lam=0.0, C=2)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    y, x = oracle.solve(g, inst.t, inst.c, 0.0, 25)
+    c = inst.c.reshape(-1).astype(np.float64)
+    for ch in range(inst.channels):
+        t = inst.t[ch].reshape(-1).astype(np.float64)
+        num = np.bincount(g.vid, weights=c * t, minlength=g.V)
+        den = np.bincount(g.vid, weights=c, minlength=g.V)
+        want = np.where(den > 0, num / np.where(den > 0, den, 1), 0.0)
+        assert np.allclose(y[ch], want, rtol=1e-14, atol=1e-12)
+
+
+def test_zero_confidence_vertex_stays_zero():
+    inst = tiny(seed=9, lam=0.0, C=1)
+    c = inst.c.copy()
+    c[:, :] = 0.0
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    y, x = oracle.solve(g, inst.t, c, 0.0, 25)
+    assert np.array_equal(y, np.zeros_like(y))
+
+
+def test_constant_target_is_preserved():
+    inst = tiny(seed=10, lam=128.0, C=1)
+    t = np.full_like(inst.t, 77.25)
+    c = np.full_like(inst.c, 0.5)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 4000)
+    y, x = oracle.solve(g, t, c, 128.0, 25)
+    assert np.allclose(x, 77.25, rtol=1e-10, atol=0)
+
+
+def test_pcg_converged_matches_dense_solve():
+    inst, g, S, B, A, b, sc = _problem(iters=2, lam=16.0)
+    y, _ = oracle.solve(g, inst.t, inst.c, inst.lam, 600)
+    ystar = np.linalg.solve(A, b.T).T
+    assert np.allclose(y, ystar, rtol=1e-9, atol=1e-9 * np.abs(ystar).max())
+
+
+def test_pcg_energy_error_decreases():
+    inst, g, S, B, A, b, sc = _problem(iters=1, lam=16.0, C=1)
+    a, minv = oracle.diag(g.m, g.nbr, g.n, sc, inst.lam)
+    y0 = oracle.flat_init(b[0], sc)
+    ystar = np.linalg.solve(A, b[0])
+    errs = []
+    for k in range(0, 30):
+        yk = oracle.pcg(g.nbr, g.n, a, minv, inst.lam, b[0], y0, k)
+        e = yk - ystar
+        errs.append(e @ A @ e)
+    assert all(e1 <= e0 * (1 + 1e-9) + 1e-18 for e0, e1 in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-6 * errs[0]
+
+
+def test_pcg_matches_textbook_on_dense_matrix():
+    # Jacobi PCG written against the dense A with numpy (Shewchuk B3 / Alg. 2)
+    inst, g, S, B, A, b, sc = _problem(iters=2, lam=16.0, C=1)
+    a, minv = oracle.diag(g.m, g.nbr, g.n, sc, inst.lam)
+    y0 = oracle.flat_init(b[0], sc)
+    Minv = np.diag(np.where(np.diag(A) > 0, 1.0 / np.diag(A), 0.0))
+    yk, r = y0.copy(), b[0] - A @ y0
+    d = Minv @ r
+    delta = r @ d
+    for _ in range(7):
+        q = A @ d
+        alpha = delta / (d @ q)
+        yk = yk + alpha * d
+        r = r - alpha * q
+        s = Minv @ r
+        delta, delta_old = r @ s, delta
+        d = s + (delta / delta_old) * d
+    got = oracle.pcg(g.nbr, g.n, a, minv, inst.lam, b[0], y0, 7)
+    assert np.allclose(got, yk, rtol=1e-9, atol=1e-9 * np.abs(yk).max())
+
+
+def test_slice_is_adjoint_of_splat():
+    inst, g, S, B, A, b, sc = _problem(C=1)
+    rng = np.random.default_rng(1)
+    y = rng.normal(size=(1, g.V))
+    gvec = rng.normal(size=(1, g.N)).astype(np.float32)
+    x = oracle.slice_(g.vid, y)
+    assert np.allclose(x, (S.T @ y[0])[None])
+    Sg, _ = oracle.splat(g.vid, gvec, np.ones(g.N, np.float32), g.V)
+    assert np.isclose((x * gvec).sum(), (y * Sg).sum(), rtol=1e-12)
+
+
+# ------------------------------------------------------------ robust -------
+
+def test_gm_weight_is_rho_prime_over_e():
+    s = 1.3
+    e = np.linspace(-6, 6, 41)
+    e = e[e != 0]
+    rho = lambda z: z * z / (s * s + z * z)
+    h = 1e-6
+    drho = (rho(e + h) - rho(e - h)) / (2 * h)
+    w = 2 * s * s / (s * s + e * e) ** 2
+    assert np.allclose(drho / e, w, rtol=1e-6)
+
+
+def test_robust_first_iteration_is_plain_solve_and_loop_reweights():
+    inst = tiny(seed=12, C=1, lam=2.0)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    y1, x1 = oracle.solve_robust(g, inst.t, inst.c, inst.lam, 3.0, 1, 25)
+    yp, xp = oracle.solve(g, inst.t, inst.c, inst.lam, 25)
+    assert np.array_equal(y1, yp)
+    e = x1[0] - inst.t.reshape(-1)
+    w = 2 * 9.0 / (9.0 + e * e) ** 2
+    # second IRLS solve == plain solve with c = w(e); compare through float32 weights
+    y2, _ = oracle.solve_robust(g, inst.t, inst.c, inst.lam, 3.0, 2, 25)
+    y2p, _ = oracle.solve(g, inst.t, w.astype(np.float32), inst.lam, 25)
+    assert np.allclose(y2, y2p, rtol=1e-5, atol=1e-4)
+
+
+def test_robust_objective_decreases():
+    # with exact inner solves IRLS is majorise-minimise for
+    # F(x) = lambda x^T (I - W) x + 2 sum rho(x - t)
+    inst = tiny(seed=13, h=16, w=20, C=1, lam=1.0, sig=(5.0, 30.0, 30.0))
+    t = inst.t.copy()
+    t[0, 3, 4] = 250.0
+    t[0, 10, 12] = 0.0
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 4000)
+    S = dense.dense_S(g.vid, g.V)
+    W = dense.dense_What(S, g.m, g.n, dense.dense_Bbar(dense.brute_neighbours(g.vkey)))
+    s = 4.0
+    F = []
+    for it in range(2, 7):
+        _, x = oracle.solve_robust(g, t, inst.c, inst.lam, s, it, 3000)
+        e = x[0] - t.reshape(-1)
+        F.append(inst.lam * x[0] @ (np.eye(g.N) - W) @ x[0] + 2 * np.sum(e * e / (s * s + e * e)))
+    assert all(f1 <= f0 + 1e-7 * abs(f0) for f0, f1 in zip(F, F[1:])), F
+
+
+# ------------------------------------------------------------- backward ----
+
+def _seg_crop():
+    rng = np.random.Generator(np.random.PCG64(5))
+    inst = synth.segmentation_instance(rng, 48, 64, 21, (8.0, 4.0, 3.0), 128.0, blob_sigma=6.0)
+    return synth.crop(inst, 8, 16, 24, 32)
+
+
+def _dense_forward(g, t, c, lam):
+    C = t.shape[0]
+    b, sc = oracle.splat(g.vid, t.reshape(C, -1), c.reshape(-1), g.V)
+    a, _ = oracle.diag(g.m, g.nbr, g.n, sc, lam)
+    A = np.stack([oracle.apply_A(g.nbr, g.n, a, lam, e) for e in np.eye(g.V)], axis=1)
+    y = np.linalg.solve(A, b.T).T
+    return y, y[:, g.vid]
+
+
+def test_backward_matches_finite_differences():
+    inst = _seg_crop()
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    C = inst.channels
+    label = inst.label.reshape(C, -1).astype(np.float64)
+    t64 = inst.t.reshape(C, -1).astype(np.float64)
+    c64 = inst.c.reshape(-1).astype(np.float64)
+
+    def loss(t, c):
+        # the forward in FP64 end to end (the oracle's splat takes float32, so
+        # assemble b and S c here from the dense S built independently)
+        S = dense.dense_S(g.vid, g.V)
+        sc = S @ c
+        b = (S @ (c[None] * t).T).T
+        a, _ = oracle.diag(g.m, g.nbr, g.n, sc, inst.lam)
+        A = np.stack([oracle.apply_A(g.nbr, g.n, a, inst.lam, e) for e in np.eye(g.V)], axis=1)
+        y = np.linalg.solve(A, b.T).T
+        x = y[:, g.vid]
+        return np.mean((x - label) ** 2), y, x
+
+    L0, y, x = loss(t64, c64)
+    dx = 2.0 * (x - label) / x.size
+    dt, dc = oracle.backward(g, inst.t, inst.c, inst.lam, 400, y, dx)
+    rng = np.random.default_rng(2)
+    for _ in range(6):
+        ch, i = int(rng.integers(C)), int(rng.integers(g.N))
+        h = 1e-4
+        tp, tm = t64.copy(), t64.copy()
+        tp[ch, i] += h
+        tm[ch, i] -= h
+        fd = (loss(tp, c64)[0] - loss(tm, c64)[0]) / (2 * h)
+        assert np.isclose(dt[ch, i], fd, rtol=1e-5, atol=1e-12), (ch, i, dt[ch, i], fd)
+    for _ in range(6):
+        i = int(rng.integers(g.N))
+        h = 1e-5
+        cp, cm = c64.copy(), c64.copy()
+        cp[i] += h
+        cm[i] -= h
+        fd = (loss(t64, cp)[0] - loss(t64, cm)[0]) / (2 * h)
+        assert np.isclose(dc[i], fd, rtol=1e-5, atol=1e-12), (i, dc[i], fd)
