@@ -1,0 +1,186 @@
+/*
+ * fbs.h -- C ABI of the GB300 Fast Bilateral Solver library (libfbs.so).
+ *
+ * The library runs the data-parallel hot path of the bilateral solver
+ * (Barron & Poole, "The Fast Bilateral Solver") on one sm_103a GPU:
+ *   quantised 5-D keys -> simplified bilateral grid (splat map S, +-1
+ *   neighbour tables) -> bistochastisation (D_n, D_m) -> Jacobi-PCG on
+ *   A y = b -> slice x = S^T y, plus the robust (IRLS) loop and the
+ *   backward pass.
+ *
+ * Conventions for every call:
+ *   - Array arguments are DEVICE pointers owned by the caller, unless a
+ *     parameter says "host".  The library never frees caller memory.
+ *   - A grid handle owns its own device memory until fbs_grid_destroy.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  Calls return once the work is enqueued,
+ *     except where a call says it synchronises.
+ *   - Argument errors return at once and enqueue nothing.  Errors found on
+ *     the device (key field out of range, non-finite input, a bounded wait
+ *     that ran out) are latched in the handle; fbs_grid_build reports its
+ *     own, and fbs_grid_sync reports any latched error of later calls.
+ *   - Images are planar float32: yuv is 3 x H x W (plane 0 luma l, plane 1
+ *     u, plane 2 v), targets are C x H x W, confidences H x W, all
+ *     row-major with pixel index row * W + col.
+ *   - Bilateral-space vectors of image k are C_k x V_k (channel-major);
+ *     V_k is reported by fbs_grid_info.
+ */
+#ifndef FBS_H_
+#define FBS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FBS_OK = 0,
+    FBS_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, sigma <= 0, ...) */
+    FBS_ERR_RANGE = 2,      /* a quantised key field is outside [0, 4095] (or NaN input)  */
+    FBS_ERR_OOM = 3,        /* device allocation failed                                    */
+    FBS_ERR_CUDA = 4,       /* a CUDA runtime call failed                                  */
+    FBS_ERR_TIMEOUT = 5,    /* a bounded device-side wait ran out                          */
+    FBS_ERR_NONFINITE = 6,  /* NaN or Inf in a target or confidence                        */
+    FBS_ERR_STATE = 7       /* call out of order (e.g. solve before bistochastize)         */
+} fbs_status;
+
+typedef struct fbs_grid fbs_grid;   /* opaque; library-owned device memory */
+
+/* One reference image (Sec. 2: "a reference RGB image", affinity of Eq. (2)
+ * measured in YUV with spatial, luma and chroma bandwidths). */
+typedef struct {
+    const float* yuv;     /* device, 3 x height x width float32, planar l, u, v */
+    int height;
+    int width;
+    float sigma_xy;       /* > 0 */
+    float sigma_l;        /* > 0 */
+    float sigma_uv;       /* > 0 */
+} fbs_image_desc;
+
+/* One problem on one image of the grid (Sec. 2: target t, confidence c,
+ * smoothness weight lambda; several targets share A, supplement Sec. 4). */
+typedef struct {
+    const float* t;       /* device, channels x H x W (target)                       */
+    const float* c;       /* device, H x W (confidence, >= 0)                        */
+    float* x;             /* device, channels x H x W output (sliced solution), or NULL */
+    float* y;             /* device, channels x V output (bilateral-space solution y),
+                             or NULL; the backward pass reads it as the saved y-hat   */
+    int channels;         /* >= 1 */
+    float lambda;         /* >= 0 */
+} fbs_problem_desc;
+
+/*
+ * fbs_grid_build -- simplified bilateral grid of one or more images
+ * (Sec. 2, Eq. (3)-(5); supplement Eq. (5): S S^T = D_m).
+ *
+ * Each pixel gets the integer key floor(p / sigma + 1/2) per coordinate
+ * p = (col, row, l, u, v) with sigma = (sigma_xy, sigma_xy, sigma_l,
+ * sigma_uv, sigma_uv); vertices are the distinct keys of each image in
+ * ascending order of the packed key (row, col, l, u, v), so vertex ids are
+ * canonical.  Builds the pixel -> vertex map, the counts m = S 1 and the
+ * +-1 neighbour table along each of the 5 dimensions.
+ *
+ * imgs: host array of n_images descriptors (the yuv buffers are device
+ * memory and only need to live until this call returns).  *out receives a
+ * new handle.  SYNCHRONISES `stream` once (to size the vertex arrays).
+ * Errors: FBS_ERR_ARG (null, n_images < 1, non-positive size or sigma, a
+ * grid cell of more than 16384 pixels, i.e. sigma_xy > 127), FBS_ERR_RANGE
+ * (a key field out of [0, 4095], including NaN / negative colours),
+ * FBS_ERR_OOM, FBS_ERR_CUDA.  On error *out is NULL.
+ */
+fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream,
+                          fbs_grid** out);
+
+/*
+ * fbs_bistochastize -- supplement Alg. 1: n <- sqrt(n o m / (Bbar n))
+ * repeated `iters` times (iters >= 1) from n = 1, in FP64, where
+ * Bbar = 10 I + (sum over the +-1 neighbours), the [1, 2, 1] blur summed over
+ * the 5 dimensions.  Stores D_n in the handle.  Must precede any solve.
+ */
+fbs_status fbs_bistochastize(fbs_grid* g, int iters, void* stream);
+
+/*
+ * fbs_solve -- the bilateral solver forward pass (Sec. 2, Eq. (6)-(8);
+ * Sec. 4 Jacobi preconditioner and flat initialisation; supplement Alg. 2).
+ * For each image k: b = S(c o t), A = lambda (D_m - D_n Bbar D_n) + diag(S c),
+ * y0 = b / S c, then `pcg_iters` PCG iterations per channel (all channels
+ * and all images advance together, one launch per CG phase), then
+ * x = S^T y.  probs: host array with one entry per image of the grid.
+ * FP32 vectors; dot products reduced with FP64 accuracy.
+ */
+fbs_status fbs_solve(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters, void* stream);
+
+/*
+ * fbs_solve_robust -- robust bilateral solver with the Geman-McClure loss
+ * (supplement Sec. 3, Alg. 3): c <- c_init (probs[k].c); repeat irls_iters
+ * times { x <- solve(t, c); e <- x - t; c <- 2 s^2 / (s^2 + e^2)^2 } with
+ * s = sigma_gm; each solve starts from the flat initialisation of the
+ * current weights.  channels must be 1.  probs[k].x / .y receive the last
+ * solve's x / y.
+ */
+fbs_status fbs_solve_robust(fbs_grid* g, const fbs_problem_desc* probs, float sigma_gm,
+                            int irls_iters, int pcg_iters, void* stream);
+
+/*
+ * fbs_solve_backward -- backward pass through the solver (Sec. 3):
+ *   dL/db = A^-1 (S dL/dx)            (PCG, same A, flat-initialised)
+ *   dL/dt = c o S^T dL/db
+ *   dL/dc = sum over channels [ S^T(-dL/db o y) + (S^T dL/db) o t ]
+ * probs[k].y must hold the forward solution y-hat (channels x V).
+ * dL_dx[k], dL_dt[k]: device, channels x H x W; dL_dc[k]: device, H x W.
+ * The host arrays dL_dx, dL_dt, dL_dc have one entry per image.
+ */
+fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
+                              const float* const* dL_dx, float* const* dL_dt,
+                              float* const* dL_dc, int pcg_iters, void* stream);
+
+/* Vertex count and offset (in the concatenated vertex order) of one image.
+ * Host outputs; no device work. */
+fbs_status fbs_grid_info(const fbs_grid* g, int image, int64_t* n_vertices,
+                         int64_t* vertex_offset);
+
+/*
+ * fbs_grid_export -- copy one image's grid to HOST buffers for inspection
+ * (parity checks).  Any output may be NULL.  Synchronises `stream`.
+ *   host_keys  uint64[V]   packed keys (row<<48 | col<<36 | l<<24 | u<<12 | v)
+ *   host_vid   uint32[N]   pixel -> vertex id (local to the image)
+ *   host_counts uint32[V]  m = S 1
+ *   host_nbr   int32[V*10] neighbour ids (local), order x-, x+, y-, y+, l-, l+,
+ *                          u-, u+, v-, v+; -1 if absent
+ *   host_n     double[V]   bistochastisation vector n (needs fbs_bistochastize)
+ */
+fbs_status fbs_grid_export(const fbs_grid* g, int image, void* stream, uint64_t* host_keys,
+                           uint32_t* host_vid, uint32_t* host_counts, int32_t* host_nbr,
+                           double* host_n);
+
+/* Wait for the handle's work on `stream` and return (then clear) any latched
+ * device-side error. */
+fbs_status fbs_grid_sync(fbs_grid* g, void* stream);
+
+/* Release the handle and its device memory (stream-ordered on `stream`). */
+fbs_status fbs_grid_destroy(fbs_grid* g, void* stream);
+
+/* Static description of a status code. */
+const char* fbs_status_string(fbs_status s);
+
+/*
+ * Device timing with CUDA events on the launching stream (no kernels are
+ * added).  fbs_profile_enable(level) clears the totals and records:
+ * level 0 nothing, level 1 every kernel family (one event pair around each
+ * launch), level 2 regions spanning several launches ("region:grid_build",
+ * "region:bistochastize", "region:solve_setup", "region:pcg_loop",
+ * "region:slice").  Nothing is recorded while a stream is being captured.
+ * fbs_profile_read fills, for family index i < *count, the name, number of
+ * recorded intervals and total milliseconds (host arrays of length *count on
+ * entry; on return *count is the number of families); it waits for the
+ * recorded events.
+ */
+fbs_status fbs_profile_enable(int on);
+fbs_status fbs_profile_read(int* count, const char** names, int64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBS_H_ */

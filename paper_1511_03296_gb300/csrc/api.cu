@@ -1,0 +1,797 @@
+// C ABI of libfbs (declared in include/fbs.h): grid handles, device memory,
+// argument checking, scheduling of the kernels on the caller's stream, and
+// per-kernel-family event timing.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fbs_internal.cuh"
+#include "solve.cuh"
+
+namespace fbs {
+// launchers defined in grid.cu
+cudaError_t launch_grid_count(const GTile*, int, const ImgDev*, int*, uint32_t*, int, cudaStream_t);
+cudaError_t launch_scan_tiles(const int*, int64_t*, int, cudaStream_t);
+cudaError_t launch_grid_fill(const GTile*, int, const ImgDev*, const int64_t*, uint32_t*, int, int,
+                             uint64_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+                             uint32_t*, cudaStream_t);
+cudaError_t launch_grid_neighbours(const GTile*, int, const ImgDev*, const int64_t*,
+                                   const uint64_t*, const uint32_t*, const uint32_t*, int32_t*,
+                                   int64_t, cudaStream_t);
+cudaError_t launch_bistoch(const double*, double*, float*, const uint32_t*, const int32_t*,
+                           int64_t, int, int, cudaStream_t);
+size_t grid_smem_count(int P2);
+size_t grid_smem_fill(int P2, int max_cells);
+
+// ----------------------------------------------------------- device info ---
+const DeviceInfo& device_info()
+{
+    static std::mutex mu;
+    static std::map<int, DeviceInfo> infos;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = infos.find(dev);
+    if (it == infos.end()) {
+        DeviceInfo d;
+        d.dev = dev;
+        cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        d.l2 = (size_t)l2;
+        it = infos.emplace(dev, d).first;
+    }
+    return it->second;
+}
+
+// -------------------------------------------------------------- profiler ---
+namespace {
+struct Family {
+    std::string name;
+    int level = 1;
+    int64_t launches = 0;
+    double ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    cudaEvent_t open = nullptr;
+};
+std::mutex g_prof_mu;
+std::vector<Family>& families()
+{
+    static std::vector<Family> f;
+    return f;
+}
+std::vector<cudaEvent_t>& event_pool()
+{
+    static std::vector<cudaEvent_t> p;
+    return p;
+}
+int g_prof_level = 0;
+
+cudaEvent_t take_event()
+{
+    auto& pool = event_pool();
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+bool capturing(cudaStream_t s)
+{
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &st);
+    return st != cudaStreamCaptureStatusNone;
+}
+}  // namespace
+
+int prof_family(const char* name, int level)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    auto& f = families();
+    for (size_t i = 0; i < f.size(); ++i)
+        if (f[i].name == name) return (int)i;
+    Family fam;
+    fam.name = name;
+    fam.level = level;
+    f.push_back(fam);
+    return (int)f.size() - 1;
+}
+
+void prof_begin(int fam, cudaStream_t s)
+{
+    if (!g_prof_level) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    Family& f = families()[fam];
+    if (f.level != g_prof_level || capturing(s)) return;
+    f.open = take_event();
+    cudaEventRecord(f.open, s);
+}
+
+void prof_end(int fam, cudaStream_t s)
+{
+    if (!g_prof_level) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    Family& f = families()[fam];
+    if (!f.open) return;
+    cudaEvent_t e = take_event();
+    cudaEventRecord(e, s);
+    f.pending.emplace_back(f.open, e);
+    f.open = nullptr;
+}
+
+// ---------------------------------------------------------- memory pool ---
+namespace {
+cudaMemPool_t pool_for_current_device()
+{
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = pools.find(dev);
+    if (it != pools.end()) return it->second;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    pools[dev] = pool;
+    return pool;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count, cudaStream_t s)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaMemPool_t pool = pool_for_current_device();
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync((void**)p, count * sizeof(T), pool, s);
+}
+
+template <typename T>
+void dfree(T*& p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+}
+
+// Small host -> device copies through kernel parameters: asynchronous with
+// respect to the host buffer and valid inside stream capture.
+struct Chunk {
+    unsigned char b[3968];
+};
+__global__ void upload_kernel(unsigned char* dst, Chunk c, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = c.b[i];
+}
+cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t s)
+{
+    static int fam = prof_family("upload");
+    const unsigned char* p = (const unsigned char*)src;
+    for (size_t off = 0; off < bytes; off += sizeof(Chunk)) {
+        Chunk c;
+        size_t n = std::min(bytes - off, sizeof(Chunk));
+        memcpy(c.b, p + off, n);
+        prof_begin(fam, s);
+        upload_kernel<<<1, 256, 0, s>>>((unsigned char*)dst + off, c, (int)n);
+        prof_end(fam, s);
+    }
+    return cudaGetLastError();
+}
+
+fbs_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return FBS_OK;
+    if (e == cudaErrorMemoryAllocation) return FBS_ERR_OOM;
+    return FBS_ERR_CUDA;
+}
+
+// floor(p / sigma + 1/2) in FP64 (exact for these operands; see the device
+// quantiser)
+int round_half_up(double p, double sigma) { return (int)floor(p / sigma + 0.5); }
+
+int64_t next_pow2(int64_t x)
+{
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+}  // namespace
+}  // namespace fbs
+
+using namespace fbs;
+
+// -------------------------------------------------------------- handle ----
+struct fbs_grid {
+    int dev = 0;
+    int n_images = 0;
+    std::vector<ImgDev> img;            // host copy (yuv pointer not kept)
+    std::vector<int64_t> voff;          // n_images + 1
+    std::vector<int> vt0, nvt_img;      // VTiles per image
+    int64_t Ntot = 0, Vtot = 0, ncells = 0;
+    int64_t max_pixels = 0;
+    // device arrays
+    uint64_t* vkey = nullptr;
+    uint32_t* vid = nullptr;
+    uint32_t* perm = nullptr;
+    uint32_t* pstart = nullptr;
+    uint32_t* m = nullptr;
+    int32_t* nbr = nullptr;
+    double* n64 = nullptr;
+    double* n64b = nullptr;
+    float* nf = nullptr;
+    uint32_t* cell_voff = nullptr;
+    uint32_t* cell_nv = nullptr;
+    uint32_t* err = nullptr;
+    VTile* vt = nullptr;
+    int nvt = 0;
+    int bistoch_iters = 0;
+    // solve workspace
+    size_t cap_vec = 0;                 // floats per vector
+    float* vec = nullptr;               // 5 x cap_vec: y, r, d0, d1, q
+    float* a = nullptr;
+    float2* nm = nullptr;
+    size_t cap_scal = 0, cap_part = 0;
+    Scal* scal = nullptr;
+    double* part = nullptr;
+    unsigned* cnt = nullptr;
+    InstDev* inst = nullptr;
+    std::vector<InstDev> inst_cached;
+};
+
+namespace {
+
+void free_grid_memory(fbs_grid* g, cudaStream_t s)
+{
+    dfree(g->vkey, s); dfree(g->vid, s); dfree(g->perm, s); dfree(g->pstart, s);
+    dfree(g->m, s); dfree(g->nbr, s); dfree(g->n64, s); dfree(g->n64b, s); dfree(g->nf, s);
+    dfree(g->cell_voff, s); dfree(g->cell_nv, s); dfree(g->err, s); dfree(g->vt, s);
+    dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s); dfree(g->part, s);
+    dfree(g->cnt, s); dfree(g->inst, s);
+}
+
+fbs_status latched(uint32_t bits)
+{
+    if (bits & kErrRange) return FBS_ERR_RANGE;
+    if (bits & kErrNonFinite) return FBS_ERR_NONFINITE;
+    if (bits & kErrTimeout) return FBS_ERR_TIMEOUT;
+    if (bits & kErrGeometry) return FBS_ERR_STATE;
+    return FBS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fbs_status_string(fbs_status s)
+{
+    switch (s) {
+        case FBS_OK: return "ok";
+        case FBS_ERR_ARG: return "invalid argument";
+        case FBS_ERR_RANGE: return "quantised key field out of range [0, 4095]";
+        case FBS_ERR_OOM: return "device out of memory";
+        case FBS_ERR_CUDA: return "CUDA runtime error";
+        case FBS_ERR_TIMEOUT: return "bounded device wait timed out";
+        case FBS_ERR_NONFINITE: return "non-finite target or confidence";
+        case FBS_ERR_STATE: return "call out of order or internal inconsistency";
+    }
+    return "unknown status";
+}
+
+fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream, fbs_grid** out)
+{
+    if (!out) return FBS_ERR_ARG;
+    *out = nullptr;
+    if (!imgs || n_images < 1) return FBS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // ---- host geometry: cells, cell-row / cell-column pixel ranges, tiles
+    std::vector<ImgDev> img(n_images);
+    std::vector<GTile> tiles;
+    int64_t pix = 0, cells = 0, sorted = 0;
+    int max_P = 0, max_cells = 1;
+    const int target = 2048;
+    for (int k = 0; k < n_images; ++k) {
+        const fbs_image_desc& d = imgs[k];
+        if (!d.yuv || d.height <= 0 || d.width <= 0) return FBS_ERR_ARG;
+        if (!(d.sigma_xy > 0.f) || !(d.sigma_l > 0.f) || !(d.sigma_uv > 0.f) ||
+            !isfinite(d.sigma_xy) || !isfinite(d.sigma_l) || !isfinite(d.sigma_uv))
+            return FBS_ERR_ARG;
+        const int kx_max = round_half_up(d.width - 1, d.sigma_xy);
+        const int ky_max = round_half_up(d.height - 1, d.sigma_xy);
+        if (kx_max > kFieldMax || ky_max > kFieldMax) return FBS_ERR_RANGE;
+        ImgDev& im = img[k];
+        im.yuv = d.yuv;
+        im.H = d.height;
+        im.W = d.width;
+        im.sxy = d.sigma_xy;
+        im.sl = d.sigma_l;
+        im.suv = d.sigma_uv;
+        im.ncx = kx_max + 1;
+        im.ncy = ky_max + 1;
+        im.pix_base = pix;
+        im.cell_base = cells;
+        // first pixel column / row of each cell (monotone rounding)
+        std::vector<int> xlo(im.ncx + 1, im.W), ylo(im.ncy + 1, im.H);
+        for (int x = im.W - 1; x >= 0; --x) xlo[round_half_up(x, d.sigma_xy)] = x;
+        for (int k2 = im.ncx - 1; k2 >= 0; --k2) xlo[k2] = std::min(xlo[k2], xlo[k2 + 1]);
+        for (int y = im.H - 1; y >= 0; --y) ylo[round_half_up(y, d.sigma_xy)] = y;
+        for (int k2 = im.ncy - 1; k2 >= 0; --k2) ylo[k2] = std::min(ylo[k2], ylo[k2 + 1]);
+        for (int ky = 0; ky < im.ncy; ++ky) {
+            const int rows = ylo[ky + 1] - ylo[ky];
+            int kx = 0;
+            while (kx < im.ncx) {
+                const int kx0 = kx;
+                int cols = 0;
+                while (kx < im.ncx) {
+                    const int c = xlo[kx + 1] - xlo[kx];
+                    if (kx > kx0 && ((int64_t)(cols + c) * rows > target || kx - kx0 >= 4096))
+                        break;
+                    cols += c;
+                    ++kx;
+                }
+                const int P = rows * cols;
+                if (P > kMaxTilePixels) return FBS_ERR_ARG;   // one cell too large
+                GTile t;
+                t.img = k;
+                t.ky = ky;
+                t.kx0 = kx0;
+                t.nkx = kx - kx0;
+                t.y0 = ylo[ky];
+                t.y1 = ylo[ky + 1];
+                t.x0 = xlo[kx0];
+                t.x1 = xlo[kx];
+                t.sort_off = sorted;
+                sorted += P;
+                max_P = std::max(max_P, P);
+                max_cells = std::max(max_cells, t.nkx);
+                tiles.push_back(t);
+            }
+        }
+        pix += (int64_t)im.H * im.W;
+        cells += (int64_t)im.ncx * im.ncy;
+    }
+    if (pix >= (int64_t)0xFFFFFFFFll || pix > INT32_MAX) return FBS_ERR_ARG;
+    const int ntiles = (int)tiles.size();
+    const int P2 = (int)std::max<int64_t>(1024, next_pow2(max_P));
+
+    static int f_region = prof_family("region:grid_build", 2);
+    prof_begin(f_region, s);
+    fbs_grid* g = new fbs_grid();
+    cudaGetDevice(&g->dev);
+    g->n_images = n_images;
+    g->img = img;
+    g->Ntot = pix;
+    g->ncells = cells;
+    for (auto& im : img) g->max_pixels = std::max<int64_t>(g->max_pixels, (int64_t)im.H * im.W);
+
+    ImgDev* d_img = nullptr;
+    GTile* d_tiles = nullptr;
+    int* d_tile_nv = nullptr;
+    int64_t* d_tile_voff = nullptr;
+    cudaError_t e = cudaSuccess;
+    fbs_status st = FBS_OK;
+    std::vector<int64_t> tile_voff(ntiles + 1);
+    uint32_t err_bits = 0;
+#define FBS_TRY(x)                       \
+    do {                                 \
+        e = (x);                         \
+        if (e != cudaSuccess) goto fail; \
+    } while (0)
+    FBS_TRY(dalloc(&d_img, img.size(), s));
+    FBS_TRY(dalloc(&d_tiles, tiles.size(), s));
+    FBS_TRY(dalloc(&d_tile_nv, (size_t)ntiles, s));
+    FBS_TRY(dalloc(&d_tile_voff, (size_t)ntiles + 1, s));
+    FBS_TRY(dalloc(&g->err, 1, s));
+    FBS_TRY(cudaMemsetAsync(g->err, 0, sizeof(uint32_t), s));
+    FBS_TRY(cudaMemcpyAsync(d_img, img.data(), img.size() * sizeof(ImgDev), cudaMemcpyHostToDevice, s));
+    FBS_TRY(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(GTile),
+                            cudaMemcpyHostToDevice, s));
+    FBS_TRY(launch_grid_count(d_tiles, ntiles, d_img, d_tile_nv, g->err, P2, s));
+    FBS_TRY(launch_scan_tiles(d_tile_nv, d_tile_voff, ntiles, s));
+    FBS_TRY(cudaMemcpyAsync(tile_voff.data(), d_tile_voff, (ntiles + 1) * sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, s));
+    FBS_TRY(cudaMemcpyAsync(&err_bits, g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    FBS_TRY(cudaStreamSynchronize(s));
+    if (err_bits) {
+        st = latched(err_bits);
+        goto fail_status;
+    }
+    {
+        g->Vtot = tile_voff[ntiles];
+        g->voff.assign(n_images + 1, g->Vtot);
+        int ti = 0;
+        for (int k = 0; k < n_images; ++k) {
+            while (ti < ntiles && tiles[ti].img < k) ++ti;
+            g->voff[k] = tile_voff[ti];
+        }
+        const int64_t V = g->Vtot;
+        FBS_TRY(dalloc(&g->vkey, V, s));
+        FBS_TRY(dalloc(&g->vid, g->Ntot, s));
+        FBS_TRY(dalloc(&g->perm, g->Ntot, s));
+        FBS_TRY(dalloc(&g->pstart, V, s));
+        FBS_TRY(dalloc(&g->m, V, s));
+        FBS_TRY(dalloc(&g->nbr, (size_t)V * 10, s));
+        FBS_TRY(dalloc(&g->n64, V, s));
+        FBS_TRY(dalloc(&g->n64b, V, s));
+        FBS_TRY(dalloc(&g->nf, V, s));
+        FBS_TRY(dalloc(&g->cell_voff, cells, s));
+        FBS_TRY(dalloc(&g->cell_nv, cells, s));
+        FBS_TRY(launch_grid_fill(d_tiles, ntiles, d_img, d_tile_voff, g->err, P2, max_cells,
+                                 g->vkey, g->vid, g->perm, g->pstart, g->m, g->cell_voff,
+                                 g->cell_nv, s));
+        FBS_TRY(launch_grid_neighbours(d_tiles, ntiles, d_img, d_tile_voff, g->vkey, g->cell_voff,
+                                       g->cell_nv, g->nbr, V, s));
+        // vertex tiles for the vertex kernels
+        std::vector<VTile> vt;
+        g->vt0.resize(n_images);
+        g->nvt_img.resize(n_images);
+        for (int k = 0; k < n_images; ++k) {
+            g->vt0[k] = (int)vt.size();
+            const int64_t a0 = g->voff[k], a1 = g->voff[k + 1];
+            int j = 0;
+            for (int64_t v = a0; v < a1; v += kVTile, ++j) {
+                VTile t;
+                t.inst = k;
+                t.v0 = (int)v;
+                t.v1 = (int)std::min<int64_t>(v + kVTile, a1);
+                t.t_in_inst = j;
+                vt.push_back(t);
+            }
+            g->nvt_img[k] = j;
+        }
+        g->nvt = (int)vt.size();
+        FBS_TRY(dalloc(&g->vt, vt.size(), s));
+        FBS_TRY(cudaMemcpyAsync(g->vt, vt.data(), vt.size() * sizeof(VTile),
+                                cudaMemcpyHostToDevice, s));
+    }
+    dfree(d_img, s);
+    dfree(d_tiles, s);
+    dfree(d_tile_nv, s);
+    dfree(d_tile_voff, s);
+    prof_end(f_region, s);
+    *out = g;
+    return FBS_OK;
+fail:
+    st = cuda_status(e);
+fail_status:
+    dfree(d_img, s);
+    dfree(d_tiles, s);
+    dfree(d_tile_nv, s);
+    dfree(d_tile_voff, s);
+    free_grid_memory(g, s);
+    delete g;
+    return st;
+#undef FBS_TRY
+}
+
+fbs_status fbs_bistochastize(fbs_grid* g, int iters, void* stream)
+{
+    if (!g || iters < 1) return FBS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    static int f_region = prof_family("region:bistochastize", 2);
+    prof_begin(f_region, s);
+    for (int it = 0; it < iters; ++it) {
+        const double* nold = g->n64;
+        double* nnew = g->n64b;
+        cudaError_t e = launch_bistoch(nold, nnew, g->nf, g->m, g->nbr, g->Vtot, it == 0,
+                                       it == iters - 1, s);
+        if (e != cudaSuccess) return cuda_status(e);
+        std::swap(g->n64, g->n64b);
+    }
+    prof_end(f_region, s);
+    g->bistoch_iters = iters;
+    return FBS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+fbs_status check_problems(const fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters)
+{
+    if (!g || !probs || pcg_iters < 0) return FBS_ERR_ARG;
+    for (int k = 0; k < g->n_images; ++k) {
+        const fbs_problem_desc& p = probs[k];
+        if (!p.t || !p.c || p.channels < 1 || !(p.lambda >= 0.f) || !isfinite(p.lambda))
+            return FBS_ERR_ARG;
+    }
+    if (g->bistoch_iters < 1) return FBS_ERR_STATE;
+    return FBS_OK;
+}
+
+// Sizes the workspace, uploads the image descriptors (if they changed) and
+// runs one solve plan.
+fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStream_t s)
+{
+    int64_t cv = 0, cpart = 0;
+    int pc = 0, cmax = 1;
+    for (int k = 0; k < g->n_images; ++k) {
+        InstDev& I = inst[k];
+        I.voff = g->voff[k];
+        I.V = (int)(g->voff[k + 1] - g->voff[k]);
+        I.vec_base = cv;
+        I.tile0 = g->vt0[k];
+        I.ntiles = g->nvt_img[k];
+        I.pc = pc;
+        I.part_base = cpart;
+        I.N = (int64_t)g->img[k].H * g->img[k].W;
+        I.pix_base = g->img[k].pix_base;
+        cv += (int64_t)I.C * I.V;
+        cpart += (int64_t)I.C * I.ntiles;
+        pc += I.C;
+        cmax = std::max(cmax, I.C);
+        plan.max_cv = std::max<int64_t>(plan.max_cv, (int64_t)I.C * I.V);
+    }
+    plan.max_pixels = g->max_pixels;
+    plan.chan_block = std::min(cmax, kChanBlock);
+    const bool cap = capturing(s);
+    cudaError_t e = cudaSuccess;
+    if ((size_t)cv > g->cap_vec || (size_t)pc > g->cap_scal || (size_t)cpart > g->cap_part ||
+        !g->a) {
+        if (cap) return FBS_ERR_STATE;   // size the workspace outside capture first
+        dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s);
+        dfree(g->part, s); dfree(g->cnt, s); dfree(g->inst, s);
+        g->inst_cached.clear();
+        g->cap_vec = (size_t)std::max<int64_t>(cv, 1);
+        g->cap_scal = (size_t)std::max(pc, 1);
+        g->cap_part = (size_t)std::max<int64_t>(cpart, 1);
+        if ((e = dalloc(&g->vec, 5 * g->cap_vec, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = dalloc(&g->a, g->Vtot, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = dalloc(&g->nm, g->Vtot, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = dalloc(&g->scal, g->cap_scal, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = dalloc(&g->part, g->cap_part, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = dalloc(&g->cnt, (size_t)3 * g->n_images, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = cudaMemsetAsync(g->cnt, 0, sizeof(unsigned) * 3 * g->n_images, s)) != cudaSuccess)
+            return cuda_status(e);
+        if ((e = dalloc(&g->inst, (size_t)g->n_images, s)) != cudaSuccess) return cuda_status(e);
+    }
+    if (g->inst_cached.size() != inst.size() ||
+        memcmp(g->inst_cached.data(), inst.data(), inst.size() * sizeof(InstDev)) != 0) {
+        if ((e = upload(g->inst, inst.data(), inst.size() * sizeof(InstDev), s)) != cudaSuccess)
+            return cuda_status(e);
+        g->inst_cached = inst;
+    }
+    SolveArgs A;
+    memset(&A, 0, sizeof(A));
+    A.vt = g->vt;
+    A.nvt = g->nvt;
+    A.inst = g->inst;
+    A.ninst = g->n_images;
+    A.nbr = g->nbr;
+    A.Vtot = g->Vtot;
+    A.n64 = g->n64;
+    A.m = g->m;
+    A.pstart = g->pstart;
+    A.perm = g->perm;
+    A.vid = g->vid;
+    A.a = g->a;
+    A.nm = g->nm;
+    A.y = g->vec;
+    A.r = g->vec + g->cap_vec;
+    A.d[0] = g->vec + 2 * g->cap_vec;
+    A.d[1] = g->vec + 3 * g->cap_vec;
+    A.q = g->vec + 4 * g->cap_vec;
+    A.scal = g->scal;
+    A.part = g->part;
+    A.cnt = g->cnt;
+    A.err = g->err;
+    e = launch_solve(A, plan, s);
+    return cuda_status(e);
+}
+
+std::vector<InstDev> base_instances(const fbs_grid* g, const fbs_problem_desc* probs)
+{
+    std::vector<InstDev> inst(g->n_images);
+    for (int k = 0; k < g->n_images; ++k) {
+        InstDev I;
+        memset(&I, 0, sizeof(I));
+        I.C = probs[k].channels;
+        I.lam = probs[k].lambda;
+        I.t = probs[k].t;
+        I.c = probs[k].c;
+        I.x = probs[k].x;
+        I.yout = probs[k].y;
+        inst[k] = I;
+    }
+    return inst;
+}
+
+}  // namespace
+
+extern "C" {
+
+fbs_status fbs_solve(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters, void* stream)
+{
+    fbs_status st = check_problems(g, probs, pcg_iters);
+    if (st) return st;
+    std::vector<InstDev> inst = base_instances(g, probs);
+    SolvePlan plan;
+    memset(&plan, 0, sizeof(plan));
+    plan.mode = kSplatConfidence;
+    plan.outer_iters = 1;
+    plan.pcg_iters = pcg_iters;
+    plan.sigma_gm = 1.0f;
+    plan.export_y = false;
+    for (int k = 0; k < g->n_images; ++k) plan.export_y |= probs[k].y != nullptr;
+    return run(g, inst, plan, (cudaStream_t)stream);
+}
+
+fbs_status fbs_solve_robust(fbs_grid* g, const fbs_problem_desc* probs, float sigma_gm,
+                            int irls_iters, int pcg_iters, void* stream)
+{
+    fbs_status st = check_problems(g, probs, pcg_iters);
+    if (st) return st;
+    if (!(sigma_gm > 0.f) || !isfinite(sigma_gm) || irls_iters < 1) return FBS_ERR_ARG;
+    for (int k = 0; k < g->n_images; ++k)
+        if (probs[k].channels != 1) return FBS_ERR_ARG;
+    std::vector<InstDev> inst = base_instances(g, probs);
+    SolvePlan plan;
+    memset(&plan, 0, sizeof(plan));
+    plan.mode = kSplatRobust;
+    plan.outer_iters = irls_iters;
+    plan.pcg_iters = pcg_iters;
+    plan.sigma_gm = sigma_gm;
+    for (int k = 0; k < g->n_images; ++k) plan.export_y |= probs[k].y != nullptr;
+    return run(g, inst, plan, (cudaStream_t)stream);
+}
+
+fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
+                              const float* const* dL_dx, float* const* dL_dt,
+                              float* const* dL_dc, int pcg_iters, void* stream)
+{
+    fbs_status st = check_problems(g, probs, pcg_iters);
+    if (st) return st;
+    if (!dL_dx || !dL_dt || !dL_dc) return FBS_ERR_ARG;
+    std::vector<InstDev> inst = base_instances(g, probs);
+    for (int k = 0; k < g->n_images; ++k) {
+        if (!probs[k].y || !dL_dx[k]) return FBS_ERR_ARG;
+        inst[k].x = nullptr;
+        inst[k].yout = nullptr;
+        inst[k].yhat = probs[k].y;
+        inst[k].dx = dL_dx[k];
+        inst[k].dt = dL_dt[k];
+        inst[k].dc = dL_dc[k];
+    }
+    SolvePlan plan;
+    memset(&plan, 0, sizeof(plan));
+    plan.mode = kSplatBackward;
+    plan.outer_iters = 1;
+    plan.pcg_iters = pcg_iters;
+    plan.sigma_gm = 1.0f;
+    return run(g, inst, plan, (cudaStream_t)stream);
+}
+
+fbs_status fbs_grid_info(const fbs_grid* g, int image, int64_t* n_vertices, int64_t* vertex_offset)
+{
+    if (!g || image < 0 || image >= g->n_images) return FBS_ERR_ARG;
+    if (n_vertices) *n_vertices = g->voff[image + 1] - g->voff[image];
+    if (vertex_offset) *vertex_offset = g->voff[image];
+    return FBS_OK;
+}
+
+fbs_status fbs_grid_export(const fbs_grid* g, int image, void* stream, uint64_t* host_keys,
+                           uint32_t* host_vid, uint32_t* host_counts, int32_t* host_nbr,
+                           double* host_n)
+{
+    if (!g || image < 0 || image >= g->n_images) return FBS_ERR_ARG;
+    if (host_n && g->bistoch_iters < 1) return FBS_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t v0 = g->voff[image], V = g->voff[image + 1] - v0;
+    const int64_t p0 = g->img[image].pix_base;
+    const int64_t N = (int64_t)g->img[image].H * g->img[image].W;
+    cudaError_t e = cudaSuccess;
+    if (host_keys && e == cudaSuccess)
+        e = cudaMemcpyAsync(host_keys, g->vkey + v0, V * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (host_vid && e == cudaSuccess)
+        e = cudaMemcpyAsync(host_vid, g->vid + p0, N * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (host_counts && e == cudaSuccess)
+        e = cudaMemcpyAsync(host_counts, g->m + v0, V * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    std::vector<int32_t> soa;
+    if (host_nbr && e == cudaSuccess) {
+        soa.resize((size_t)V * 10);
+        for (int k = 0; k < 10 && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(soa.data() + (size_t)k * V, g->nbr + (size_t)k * g->Vtot + v0,
+                                V * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    }
+    if (host_n && e == cudaSuccess)
+        e = cudaMemcpyAsync(host_n, g->n64 + v0, V * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (host_vid)
+        for (int64_t i = 0; i < N; ++i) host_vid[i] = (uint32_t)(host_vid[i] - v0);
+    if (host_nbr)
+        for (int64_t v = 0; v < V; ++v)
+            for (int k = 0; k < 10; ++k) {
+                const int32_t u = soa[(size_t)k * V + v];
+                host_nbr[v * 10 + k] = u >= 0 ? (int32_t)(u - v0) : -1;
+            }
+    return FBS_OK;
+}
+
+fbs_status fbs_grid_sync(fbs_grid* g, void* stream)
+{
+    if (!g) return FBS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t bits = 0;
+    cudaError_t e = cudaMemcpyAsync(&bits, g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (bits) {
+        cudaMemsetAsync(g->err, 0, sizeof(uint32_t), s);
+        cudaStreamSynchronize(s);
+    }
+    return latched(bits);
+}
+
+fbs_status fbs_grid_destroy(fbs_grid* g, void* stream)
+{
+    if (!g) return FBS_ERR_ARG;
+    free_grid_memory(g, (cudaStream_t)stream);
+    delete g;
+    return FBS_OK;
+}
+
+fbs_status fbs_profile_enable(int on)
+{
+    if (on < 0 || on > 2) return FBS_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_level = on;
+    for (auto& f : families()) {
+        for (auto& p : f.pending) {
+            event_pool().push_back(p.first);
+            event_pool().push_back(p.second);
+        }
+        f.pending.clear();
+        f.launches = 0;
+        f.ms = 0.0;
+        if (f.open) {
+            event_pool().push_back(f.open);
+            f.open = nullptr;
+        }
+    }
+    return FBS_OK;
+}
+
+fbs_status fbs_profile_read(int* count, const char** names, int64_t* launches, double* total_ms)
+{
+    if (!count) return FBS_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    auto& fams = families();
+    for (auto& f : fams) {
+        for (auto& p : f.pending) {
+            if (cudaEventSynchronize(p.second) != cudaSuccess) return FBS_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p.first, p.second);
+            f.ms += ms;
+            f.launches += 1;
+            event_pool().push_back(p.first);
+            event_pool().push_back(p.second);
+        }
+        f.pending.clear();
+    }
+    const int n = std::min<int>(*count, (int)fams.size());
+    for (int i = 0; i < n; ++i) {
+        if (names) names[i] = fams[i].name.c_str();
+        if (launches) launches[i] = fams[i].launches;
+        if (total_ms) total_ms[i] = fams[i].ms;
+    }
+    *count = (int)fams.size();
+    return FBS_OK;
+}
+
+}  // extern "C"

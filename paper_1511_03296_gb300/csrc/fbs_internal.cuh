@@ -1,0 +1,186 @@
+// Internal declarations of libfbs: device-side descriptors, helpers and the
+// launch functions shared between translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/fbs.h"
+
+namespace fbs {
+
+// ---------------------------------------------------------------- limits ---
+constexpr int kFieldMax = 4095;          // 12-bit key fields
+constexpr int kMaxTilePixels = 16384;    // pixels sorted by one CTA of the grid build
+constexpr int kGridThreads = 512;        // CTA size of the grid-build kernels
+constexpr int kVTile = 256;              // vertices per PCG tile (= CTA size)
+constexpr int kChanBlock = 4;            // channels processed per pass of a PCG tile
+
+// device error bits (latched in fbs_grid::err)
+enum : uint32_t {
+    kErrRange = 1u,       // key field outside [0, 4095] or NaN colour
+    kErrNonFinite = 2u,   // NaN / Inf in t or c
+    kErrGeometry = 4u,    // host / device disagree on a pixel's cell (internal)
+    kErrTimeout = 8u,     // bounded wait ran out
+};
+
+// bit position of dimension d = (x, y, l, u, v) in the packed key
+__host__ __device__ constexpr int key_shift(int d)
+{
+    return d == 0 ? 36 : d == 1 ? 48 : d == 2 ? 24 : d == 3 ? 12 : 0;
+}
+
+// --------------------------------------------------------- descriptors ---
+struct ImgDev {
+    const float* yuv;       // 3 x H x W
+    int H, W;
+    float sxy, sl, suv;
+    int ncx, ncy;           // number of cell columns / rows
+    int64_t pix_base;       // first pixel in the concatenated pixel order
+    int64_t cell_base;      // first cell in the concatenated cell order
+};
+
+// one CTA of the grid build: cells kx0 .. kx0+nkx-1 of cell row ky
+struct GTile {
+    int img, ky, kx0, nkx;
+    int y0, y1, x0, x1;     // pixel rectangle [y0, y1) x [x0, x1)
+    int64_t sort_off;       // offset of this tile's pixels in the sorted pixel order
+};
+
+// one CTA-sized run of vertices of one image, for the vertex kernels
+struct VTile {
+    int inst;
+    int v0, v1;             // global vertex range [v0, v1)
+    int t_in_inst;          // index of this tile among its image's tiles
+};
+
+// one problem (image) of a solve
+struct InstDev {
+    int64_t voff;           // first vertex (global)
+    int V;
+    int C;
+    int64_t vec_base;       // offset of this image's C x V block in the vector arrays
+    int tile0, ntiles;      // its VTiles
+    int pc;                 // first (image, channel) scalar slot
+    int64_t part_base;      // first tile-partial slot (C x ntiles doubles)
+    float lam;
+    int64_t N;
+    int64_t pix_base;
+    const float* t;         // C x N
+    const float* c;         // N
+    float* x;               // C x N (slice output) or nullptr
+    float* yout;            // C x V (caller's copy of y) or nullptr
+    const float* yhat;      // C x V (backward: forward solution)
+    const float* dx;        // C x N (backward: dL/dx)
+    float* dt;              // C x N (backward out)
+    float* dc;              // N     (backward out)
+};
+
+// CG scalars of one (image, channel)
+struct Scal {
+    double delta;      // r^T M^-1 r of the current residual
+    double alpha;
+    double beta;
+    double dq;         // d^T A d of the last apply (diagnostic)
+};
+
+// splat modes
+enum SplatMode : int {
+    kSplatConfidence = 0,   // weights c, b = S(c o t)
+    kSplatRobust = 1,       // weights w(y_v - t) (Geman-McClure), b = S(w o t)
+    kSplatBackward = 2,     // weights c for S c, b = S(dL/dx)
+};
+
+// ---------------------------------------------------- exact quantiser ---
+// k = floor(p / sigma + 1/2) exactly (as rational numbers), computed with
+// FP32 operations: an estimate, then one correction step decided by the
+// sign of 2p - (2k +- 1) sigma, which one fused multiply-add evaluates with
+// a single rounding (sign-exact).  Returns false when k is outside
+// [0, kFieldMax] or p is NaN.
+__device__ __forceinline__ bool quantise_exact(float p, float sigma, int& k)
+{
+    float q = __fdiv_rn(p, sigma);
+    float kf = floorf(__fadd_rn(q, 0.5f));
+    if (!(kf >= -1.0f && kf <= (float)(kFieldMax + 2))) return false;
+    float twop = __fmul_rn(2.0f, p);
+    if (__fmaf_rn(-(2.0f * kf + 1.0f), sigma, twop) >= 0.0f) kf += 1.0f;
+    else if (__fmaf_rn(-(2.0f * kf - 1.0f), sigma, twop) < 0.0f) kf -= 1.0f;
+    if (!(kf >= 0.0f && kf <= (float)kFieldMax)) return false;
+    k = (int)kf;
+    return true;
+}
+
+// ------------------------------------------- double-float accumulation ---
+// An unevaluated sum hi + lo of two floats (about 48 significant bits).
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    DF s = df_two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    float h = __fadd_rn(s.hi, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s.hi))};
+}
+
+// exact product a * b = hi + lo
+__device__ __forceinline__ DF df_mul_exact(float a, float b)
+{
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ DF df_shfl_down(DF v, int off)
+{
+    return {__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+}
+
+__device__ __forceinline__ DF df_warp_sum(DF v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = df_add(v, df_shfl_down(v, off));
+    return v;
+}
+
+// compensated (Neumaier) float sum for the splat
+struct KSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float t = __fadd_rn(s, x);
+        if (fabsf(s) >= fabsf(x)) c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
+        else c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+};
+
+// ----------------------------------------------------- launch helpers ---
+struct Profiler;
+
+struct DeviceInfo {
+    int dev = -1;
+    int sms = 0;
+    size_t l2 = 0;
+};
+const DeviceInfo& device_info();
+
+// profiling: returns an id to pass to prof_begin / prof_end.  level 1 =
+// one kernel family, level 2 = a region spanning several launches; only the
+// level chosen by fbs_profile_enable records.
+int prof_family(const char* name, int level = 1);
+void prof_begin(int fam, cudaStream_t s);
+void prof_end(int fam, cudaStream_t s);
+
+}  // namespace fbs

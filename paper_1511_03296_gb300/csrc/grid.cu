@@ -1,0 +1,391 @@
+// Grid construction on the GPU: quantised keys, canonical vertex ids, the
+// splat map S (pixel -> vertex, plus the pixels of each vertex in sorted
+// order), counts m = S 1, the +-1 neighbour tables, and bistochastisation.
+//
+// Design.  Vertices are ordered by packed key (row cell, column cell, l, u,
+// v).  All pixels of one spatial cell (ky, kx) -- the pixels whose rounded
+// (row / sigma_xy, col / sigma_xy) equal (ky, kx) -- form a small rectangle,
+// and their vertices are contiguous in the canonical order.  One CTA takes a
+// run of consecutive cells of one cell row (a "grid tile"), quantises its
+// pixels, sorts (cell, colour, pixel) items in shared memory and
+// de-duplicates them.  A scan over tiles gives every tile its first vertex
+// id.  No global hash table and no global sort are needed; every pixel is
+// read once per pass with coalesced row segments.
+#include "fbs_internal.cuh"
+
+namespace fbs {
+
+namespace {
+
+constexpr uint64_t kPad = ~0ull;
+constexpr int kPixBits = 14;                       // pixel index inside a tile
+constexpr uint64_t kPixMask = (1ull << kPixBits) - 1;
+constexpr int kColourShift = kPixBits;             // 36 colour bits above it
+constexpr int kCellShift = kPixBits + 36;          // cell index inside the tile
+
+// -------------------------------------------------------------- sorting ---
+// Bitonic sort of n (power of two) keys in shared memory, ascending.
+__device__ void bitonic_sort(uint64_t* s, int n)
+{
+    for (int k = 2; k <= n; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int p = threadIdx.x; p < (n >> 1); p += blockDim.x) {
+                int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
+                int l = i + j;
+                uint64_t a = s[i], b = s[l];
+                bool asc = (i & k) == 0;
+                if ((a > b) == asc) {
+                    s[i] = b;
+                    s[l] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Exclusive block scan of one int per thread; *total receives the block sum.
+__device__ int block_exclusive_scan(int v, int* warp_buf, int* total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_buf[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < nw ? warp_buf[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += y;
+        }
+        warp_buf[lane] = t;
+    }
+    __syncthreads();
+    int prefix = (w > 0 ? warp_buf[w - 1] : 0) + x - v;
+    *total = warp_buf[nw - 1];
+    __syncthreads();
+    return prefix;
+}
+
+__device__ int block_sum(int v, int* warp_buf)
+{
+    int total;
+    block_exclusive_scan(v, warp_buf, &total);
+    return total;
+}
+
+// Quantise the pixels of one tile into sortable items:
+//   cell index in tile << 50 | (l << 24 | u << 12 | v) << 14 | pixel index in tile.
+// Pads [P, P2) with kPad.
+__device__ void load_tile_items(const GTile& t, const ImgDev& im, uint64_t* items, int P, int P2,
+                                uint32_t* err)
+{
+    const int tw = t.x1 - t.x0;
+    const int64_t plane = (int64_t)im.H * im.W;
+    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+        uint64_t item = kPad;
+        if (i < P) {
+            int r = i / tw, cl = i - r * tw;
+            int y = t.y0 + r, x = t.x0 + cl;
+            int64_t pix = (int64_t)y * im.W + x;
+            float L = __ldg(im.yuv + pix), U = __ldg(im.yuv + plane + pix),
+                  Vv = __ldg(im.yuv + 2 * plane + pix);
+            int kx = 0, ky = 0, kl = 0, ku = 0, kv = 0;
+            bool okg = quantise_exact((float)x, im.sxy, kx) & quantise_exact((float)y, im.sxy, ky);
+            bool okc = quantise_exact(L, im.sl, kl) & quantise_exact(U, im.suv, ku) &
+                       quantise_exact(Vv, im.suv, kv);
+            if (!okc) {
+                atomicOr(err, kErrRange);
+                kl = ku = kv = 0;
+            }
+            if (!okg || ky != t.ky || kx < t.kx0 || kx >= t.kx0 + t.nkx) {
+                atomicOr(err, kErrGeometry);
+                kx = t.kx0;
+            }
+            uint64_t colour = ((uint64_t)kl << 24) | ((uint64_t)ku << 12) | (uint64_t)kv;
+            item = ((uint64_t)(kx - t.kx0) << kCellShift) | (colour << kColourShift) | (uint64_t)i;
+        }
+        items[i] = item;
+    }
+}
+
+__device__ __forceinline__ bool is_head(const uint64_t* items, int i)
+{
+    return i == 0 || (items[i] >> kColourShift) != (items[i - 1] >> kColourShift);
+}
+
+// ------------------------------------------------------------- kernels ---
+// Pass 1: number of distinct keys per tile.
+__global__ void __launch_bounds__(kGridThreads)
+grid_count_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ imgs,
+                  int* __restrict__ tile_nv, uint32_t* err, int P2)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* items = reinterpret_cast<uint64_t*>(smem_raw);
+    __shared__ int warp_buf[32];
+    const GTile t = tiles[blockIdx.x];
+    const ImgDev im = imgs[t.img];
+    const int P = (t.y1 - t.y0) * (t.x1 - t.x0);
+    load_tile_items(t, im, items, P, P2, err);
+    __syncthreads();
+    bitonic_sort(items, P2);
+    int cnt = 0;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) cnt += is_head(items, i) ? 1 : 0;
+    int total = block_sum(cnt, warp_buf);
+    if (threadIdx.x == 0) tile_nv[blockIdx.x] = total;
+}
+
+// Exclusive scan of the per-tile counts (one CTA; the tile count is small).
+__global__ void __launch_bounds__(1024) scan_tiles_kernel(const int* __restrict__ tile_nv,
+                                                          int64_t* __restrict__ tile_voff,
+                                                          int ntiles)
+{
+    __shared__ int warp_buf[32];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < ntiles; base += blockDim.x) {
+        int i = base + threadIdx.x;
+        int v = i < ntiles ? tile_nv[i] : 0;
+        int total;
+        int ex = block_exclusive_scan(v, warp_buf, &total);
+        if (i < ntiles) tile_voff[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) tile_voff[ntiles] = carry;
+}
+
+// Pass 2: recompute and sort the tile, then write the canonical vertex ids,
+// keys, counts, the pixel permutation and the per-cell vertex ranges.
+__global__ void __launch_bounds__(kGridThreads)
+grid_fill_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ imgs,
+                 const int64_t* __restrict__ tile_voff, uint32_t* err, int P2, int max_cells,
+                 uint64_t* __restrict__ vkey, uint32_t* __restrict__ vid,
+                 uint32_t* __restrict__ perm, uint32_t* __restrict__ pstart,
+                 uint32_t* __restrict__ m, uint32_t* __restrict__ cell_voff,
+                 uint32_t* __restrict__ cell_nv)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* items = reinterpret_cast<uint64_t*>(smem_raw);
+    int* headpos = reinterpret_cast<int*>(items + P2);
+    int* cellcnt = headpos + P2;
+    __shared__ int warp_buf[32];
+
+    const GTile t = tiles[blockIdx.x];
+    const ImgDev im = imgs[t.img];
+    const int tw = t.x1 - t.x0;
+    const int P = (t.y1 - t.y0) * tw;
+    const int64_t v0 = tile_voff[blockIdx.x];
+    const int nv = (int)(tile_voff[blockIdx.x + 1] - v0);
+
+    for (int c = threadIdx.x; c < t.nkx && c < max_cells; c += blockDim.x) cellcnt[c] = 0;
+    load_tile_items(t, im, items, P, P2, err);
+    __syncthreads();
+    bitonic_sort(items, P2);
+
+    // each thread owns a contiguous chunk of the sorted items
+    const int E = P2 / blockDim.x;
+    const int i0 = threadIdx.x * E;
+    int cnt = 0;
+    for (int i = i0; i < i0 + E && i < P; ++i) cnt += is_head(items, i) ? 1 : 0;
+    int total;
+    int run = block_exclusive_scan(cnt, warp_buf, &total);
+    for (int i = i0; i < i0 + E && i < P; ++i) {
+        const uint64_t it = items[i];
+        const bool head = is_head(items, i);
+        if (head) ++run;
+        const int rank = run - 1;
+        const int pl = (int)(it & kPixMask);
+        const int r = pl / tw;
+        const int64_t gpix = im.pix_base + (int64_t)(t.y0 + r) * im.W + (t.x0 + pl - r * tw);
+        const int64_t v = v0 + rank;
+        vid[gpix] = (uint32_t)v;
+        perm[t.sort_off + i] = (uint32_t)gpix;
+        if (head) {
+            const int cell = (int)(it >> kCellShift);
+            const uint64_t colour = (it >> kColourShift) & ((1ull << 36) - 1);
+            vkey[v] = ((uint64_t)t.ky << 48) | ((uint64_t)(t.kx0 + cell) << 36) | colour;
+            pstart[v] = (uint32_t)(t.sort_off + i);
+            headpos[rank] = i;
+            atomicAdd(&cellcnt[cell], 1);
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nv; r += blockDim.x)
+        m[v0 + r] = (uint32_t)((r + 1 < nv ? headpos[r + 1] : P) - headpos[r]);
+    // per-cell vertex ranges (cells of a tile are consecutive in key order)
+    const int64_t cell0 = im.cell_base + (int64_t)t.ky * im.ncx + t.kx0;
+    int carry = 0;
+    for (int base = 0; base < t.nkx; base += blockDim.x) {
+        int c = base + threadIdx.x;
+        int v = c < t.nkx ? cellcnt[c] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, warp_buf, &tot);
+        if (c < t.nkx) {
+            cell_voff[cell0 + c] = (uint32_t)(v0 + carry + ex);
+            cell_nv[cell0 + c] = (uint32_t)v;
+        }
+        carry += tot;
+    }
+}
+
+__device__ __forceinline__ int find_in_cell(const uint64_t* __restrict__ vkey, uint32_t lo,
+                                            uint32_t n, uint64_t key)
+{
+    uint32_t a = lo, b = lo + n;   // search [a, b)
+    while (a < b) {
+        uint32_t mid = a + ((b - a) >> 1);
+        uint64_t k = vkey[mid];
+        if (k < key) a = mid + 1; else b = mid;
+    }
+    return (a < lo + n && vkey[a] == key) ? (int)a : -1;
+}
+
+// +-1 neighbours along x, y, l, u, v of every vertex of a grid tile.
+__global__ void __launch_bounds__(256)
+grid_neighbours_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ imgs,
+                       const int64_t* __restrict__ tile_voff, const uint64_t* __restrict__ vkey,
+                       const uint32_t* __restrict__ cell_voff, const uint32_t* __restrict__ cell_nv,
+                       int32_t* __restrict__ nbr, int64_t Vtot)
+{
+    const GTile t = tiles[blockIdx.x];
+    const ImgDev im = imgs[t.img];
+    const int64_t v0 = tile_voff[blockIdx.x], v1 = tile_voff[blockIdx.x + 1];
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const uint64_t key = vkey[v];
+        const int kx = (int)((key >> 36) & kFieldMax), ky = (int)((key >> 48) & kFieldMax);
+        const int64_t cell = im.cell_base + (int64_t)ky * im.ncx + kx;
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            const int f = (int)((key >> key_shift(d)) & kFieldMax);
+            const uint64_t unit = 1ull << key_shift(d);
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                int found = -1;
+                const bool ok = s == 0 ? f > 0 : f < kFieldMax;
+                int64_t c = cell;
+                bool in_grid = true;
+                if (d == 0) {
+                    const int nx = kx + (s ? 1 : -1);
+                    in_grid = nx >= 0 && nx < im.ncx;
+                    c = cell + (s ? 1 : -1);
+                } else if (d == 1) {
+                    const int ny = ky + (s ? 1 : -1);
+                    in_grid = ny >= 0 && ny < im.ncy;
+                    c = cell + (s ? im.ncx : -im.ncx);
+                }
+                if (ok && in_grid) {
+                    const uint64_t target = s ? key + unit : key - unit;
+                    found = find_in_cell(vkey, cell_voff[c], cell_nv[c], target);
+                }
+                nbr[(int64_t)(2 * d + s) * Vtot + v] = found;
+            }
+        }
+    }
+}
+
+// One Jacobi sweep of supplement Alg. 1 in FP64, with the operations in a
+// fixed order: Bbar n = 10 n_v + n_u (k = 0..9), then sqrt(n_v m_v / Bbar n).
+__global__ void __launch_bounds__(256)
+bistoch_kernel(const double* __restrict__ nold, double* __restrict__ nnew,
+               float* __restrict__ nf, const uint32_t* __restrict__ m,
+               const int32_t* __restrict__ nbr, int64_t V, int first, int last)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const double nv = first ? 1.0 : nold[v];
+        double bn = __dmul_rn(10.0, nv);
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            const int32_t u = nbr[(int64_t)k * V + v];
+            if (u >= 0) bn = __dadd_rn(bn, first ? 1.0 : nold[u]);
+        }
+        const double r = __dsqrt_rn(__ddiv_rn(__dmul_rn(nv, (double)m[v]), bn));
+        nnew[v] = r;
+        if (last) nf[v] = (float)r;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------ host launchers ---
+size_t grid_smem_count(int P2) { return (size_t)P2 * sizeof(uint64_t); }
+size_t grid_smem_fill(int P2, int max_cells)
+{
+    return (size_t)P2 * (sizeof(uint64_t) + sizeof(int)) + (size_t)max_cells * sizeof(int);
+}
+
+cudaError_t launch_grid_count(const GTile* tiles, int ntiles, const ImgDev* imgs, int* tile_nv,
+                              uint32_t* err, int P2, cudaStream_t s)
+{
+    size_t smem = grid_smem_count(P2);
+    cudaError_t e = cudaFuncSetAttribute(grid_count_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    static int fam = prof_family("grid_count");
+    prof_begin(fam, s);
+    grid_count_kernel<<<ntiles, kGridThreads, smem, s>>>(tiles, imgs, tile_nv, err, P2);
+    prof_end(fam, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_tiles(const int* tile_nv, int64_t* tile_voff, int ntiles, cudaStream_t s)
+{
+    static int fam = prof_family("scan_tiles");
+    prof_begin(fam, s);
+    scan_tiles_kernel<<<1, 1024, 0, s>>>(tile_nv, tile_voff, ntiles);
+    prof_end(fam, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_fill(const GTile* tiles, int ntiles, const ImgDev* imgs,
+                             const int64_t* tile_voff, uint32_t* err, int P2, int max_cells,
+                             uint64_t* vkey, uint32_t* vid, uint32_t* perm, uint32_t* pstart,
+                             uint32_t* m, uint32_t* cell_voff, uint32_t* cell_nv, cudaStream_t s)
+{
+    size_t smem = grid_smem_fill(P2, max_cells);
+    cudaError_t e = cudaFuncSetAttribute(grid_fill_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    static int fam = prof_family("grid_fill");
+    prof_begin(fam, s);
+    grid_fill_kernel<<<ntiles, kGridThreads, smem, s>>>(tiles, imgs, tile_voff, err, P2, max_cells,
+                                                        vkey, vid, perm, pstart, m, cell_voff,
+                                                        cell_nv);
+    prof_end(fam, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_neighbours(const GTile* tiles, int ntiles, const ImgDev* imgs,
+                                   const int64_t* tile_voff, const uint64_t* vkey,
+                                   const uint32_t* cell_voff, const uint32_t* cell_nv,
+                                   int32_t* nbr, int64_t Vtot, cudaStream_t s)
+{
+    static int fam = prof_family("grid_neighbours");
+    prof_begin(fam, s);
+    grid_neighbours_kernel<<<ntiles, 256, 0, s>>>(tiles, imgs, tile_voff, vkey, cell_voff, cell_nv,
+                                                  nbr, Vtot);
+    prof_end(fam, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bistoch(const double* nold, double* nnew, float* nf, const uint32_t* m,
+                           const int32_t* nbr, int64_t V, int first, int last, cudaStream_t s)
+{
+    if (V == 0) return cudaSuccess;
+    static int fam = prof_family("bistochastize");
+    int blocks = (int)std::min<int64_t>((V + 255) / 256, (int64_t)device_info().sms * 8);
+    prof_begin(fam, s);
+    bistoch_kernel<<<blocks, 256, 0, s>>>(nold, nnew, nf, m, nbr, V, first, last);
+    prof_end(fam, s);
+    return cudaGetLastError();
+}
+
+}  // namespace fbs

@@ -1,0 +1,318 @@
+"""Python binding of libfbs (include/fbs.h): argument marshalling only.
+
+Every step of the solver runs in the CUDA kernels of libfbs.so; this module
+passes device pointers (torch CUDA tensors), sizes and the current CUDA
+stream through ctypes.  There is no CPU fallback: if the library is not
+built or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import List, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfbs.so")
+
+FBS_OK = 0
+STATUS_NAMES = {0: "FBS_OK", 1: "FBS_ERR_ARG", 2: "FBS_ERR_RANGE", 3: "FBS_ERR_OOM",
+                4: "FBS_ERR_CUDA", 5: "FBS_ERR_TIMEOUT", 6: "FBS_ERR_NONFINITE",
+                7: "FBS_ERR_STATE"}
+
+# every symbol include/fbs.h declares
+EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robust",
+            "fbs_solve_backward", "fbs_grid_info", "fbs_grid_export", "fbs_grid_sync",
+            "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read"]
+
+
+class FbsError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        name = STATUS_NAMES.get(self.status, str(status))
+        msg = _lib.fbs_status_string(self.status).decode() if _lib is not None else name
+        super().__init__(f"{where}: {name} ({msg})")
+
+
+class ImageDesc(ctypes.Structure):
+    _fields_ = [("yuv", ctypes.c_void_p), ("height", ctypes.c_int), ("width", ctypes.c_int),
+                ("sigma_xy", ctypes.c_float), ("sigma_l", ctypes.c_float),
+                ("sigma_uv", ctypes.c_float)]
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_void_p), ("c", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("y", ctypes.c_void_p), ("channels", ctypes.c_int), ("lambda_", ctypes.c_float)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: Optional[str] = None):
+    """Load libfbs.so (built by ``paper_1511_03296_gb300.build``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libfbs.so is not built ({p}); run "
+                               "`python -m paper_1511_03296_gb300.build` first")
+        L = ctypes.CDLL(p)
+        P, I, F, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_int64
+        L.fbs_grid_build.argtypes = [ctypes.POINTER(ImageDesc), I, P, ctypes.POINTER(P)]
+        L.fbs_bistochastize.argtypes = [P, I, P]
+        L.fbs_solve.argtypes = [P, ctypes.POINTER(ProblemDesc), I, P]
+        L.fbs_solve_robust.argtypes = [P, ctypes.POINTER(ProblemDesc), F, I, I, P]
+        L.fbs_solve_backward.argtypes = [P, ctypes.POINTER(ProblemDesc), ctypes.POINTER(P),
+                                         ctypes.POINTER(P), ctypes.POINTER(P), I, P]
+        L.fbs_grid_info.argtypes = [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+        L.fbs_grid_export.argtypes = [P, I, P, P, P, P, P, P]
+        L.fbs_grid_sync.argtypes = [P, P]
+        L.fbs_grid_destroy.argtypes = [P, P]
+        L.fbs_status_string.argtypes = [I]
+        L.fbs_status_string.restype = ctypes.c_char_p
+        L.fbs_profile_enable.argtypes = [I]
+        L.fbs_profile_read.argtypes = [ctypes.POINTER(I), ctypes.POINTER(ctypes.c_char_p),
+                                       ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double)]
+        for name in EXPORTED:
+            if name != "fbs_status_string":
+                getattr(L, name).restype = I
+        _lib = L
+        return L
+
+
+def _check(st, where):
+    if st != FBS_OK:
+        raise FbsError(st, where)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, name, dtype=None):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+class Grid:
+    """A bilateral grid handle (one or more reference images)."""
+
+    def __init__(self, handle, n_images, shapes):
+        self._h = handle
+        self.n_images = n_images
+        self.shapes = shapes           # [(H, W)]
+        self.vertex_counts = []
+        self.vertex_offsets = []
+        for k in range(n_images):
+            nv, off = ctypes.c_int64(), ctypes.c_int64()
+            _check(load().fbs_grid_info(self._h, k, ctypes.byref(nv), ctypes.byref(off)),
+                   "fbs_grid_info")
+            self.vertex_counts.append(nv.value)
+            self.vertex_offsets.append(off.value)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("grid destroyed")
+        return self._h
+
+    def destroy(self, stream=None):
+        if self._h is not None:
+            _check(load().fbs_grid_destroy(self._h, _stream_ptr(stream)), "fbs_grid_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h is not None and _lib is not None:
+                _lib.fbs_grid_destroy(self._h, None)
+        except Exception:
+            pass
+
+
+def grid_build(yuv: Sequence, sigma_xy, sigma_l, sigma_uv, stream=None) -> Grid:
+    """Build the grid of a list of planar 3 x H x W float32 CUDA images."""
+    import torch
+    n = len(yuv)
+    descs = (ImageDesc * n)()
+    sig = [sigma_xy, sigma_l, sigma_uv]
+    sig = [s if isinstance(s, (list, tuple)) else [s] * n for s in sig]
+    shapes = []
+    for k, im in enumerate(yuv):
+        if im.dim() != 3 or im.shape[0] != 3:
+            raise ValueError("yuv images must be 3 x H x W")
+        descs[k] = ImageDesc(_dev_ptr(im, f"yuv[{k}]", torch.float32), int(im.shape[1]),
+                             int(im.shape[2]), float(sig[0][k]), float(sig[1][k]),
+                             float(sig[2][k]))
+        shapes.append((int(im.shape[1]), int(im.shape[2])))
+    h = ctypes.c_void_p()
+    _check(load().fbs_grid_build(descs, n, _stream_ptr(stream), ctypes.byref(h)),
+           "fbs_grid_build")
+    return Grid(h, n, shapes)
+
+
+def bistochastize(grid: Grid, iters: int = 2, stream=None) -> None:
+    _check(load().fbs_bistochastize(grid.handle, int(iters), _stream_ptr(stream)),
+           "fbs_bistochastize")
+
+
+def _problems(grid, t, c, lam, x, y):
+    import torch
+    n = grid.n_images
+    if len(t) != n or len(c) != n:
+        raise ValueError("one target and one confidence per image")
+    lam = lam if isinstance(lam, (list, tuple)) else [lam] * n
+    x = x if x is not None else [None] * n
+    y = y if y is not None else [None] * n
+    probs = (ProblemDesc * n)()
+    for k in range(n):
+        H, W = grid.shapes[k]
+        if t[k].dim() != 3 or tuple(t[k].shape[1:]) != (H, W):
+            raise ValueError(f"t[{k}] must be C x {H} x {W}")
+        C = int(t[k].shape[0])
+        if tuple(c[k].shape) != (H, W):
+            raise ValueError(f"c[{k}] must be {H} x {W}")
+        if x[k] is not None and tuple(x[k].shape) != (C, H, W):
+            raise ValueError(f"x[{k}] must be {C} x {H} x {W}")
+        if y[k] is not None and tuple(y[k].shape) != (C, grid.vertex_counts[k]):
+            raise ValueError(f"y[{k}] must be {C} x {grid.vertex_counts[k]}")
+        probs[k] = ProblemDesc(_dev_ptr(t[k], f"t[{k}]", torch.float32),
+                               _dev_ptr(c[k], f"c[{k}]", torch.float32),
+                               _dev_ptr(x[k], f"x[{k}]", torch.float32),
+                               _dev_ptr(y[k], f"y[{k}]", torch.float32), C, float(lam[k]))
+    return probs
+
+
+def solve(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25, x: Optional[List] = None,
+          y: Optional[List] = None, stream=None) -> None:
+    """Forward solve; writes x (C x H x W) and/or y (C x V) per image."""
+    probs = _problems(grid, t, c, lam, x, y)
+    _check(load().fbs_solve(grid.handle, probs, int(pcg_iters), _stream_ptr(stream)), "fbs_solve")
+
+
+def solve_robust(grid: Grid, t: List, c: List, lam, sigma_gm: float, irls_iters: int = 10,
+                 pcg_iters: int = 25, x: Optional[List] = None, y: Optional[List] = None,
+                 stream=None) -> None:
+    probs = _problems(grid, t, c, lam, x, y)
+    _check(load().fbs_solve_robust(grid.handle, probs, float(sigma_gm), int(irls_iters),
+                                   int(pcg_iters), _stream_ptr(stream)), "fbs_solve_robust")
+
+
+def solve_backward(grid: Grid, t: List, c: List, lam, yhat: List, dL_dx: List, dL_dt: List,
+                   dL_dc: List, pcg_iters: int = 25, stream=None) -> None:
+    import torch
+    probs = _problems(grid, t, c, lam, None, yhat)
+    n = grid.n_images
+    P = ctypes.c_void_p
+    dx = (P * n)(*[_dev_ptr(g, "dL_dx", torch.float32) for g in dL_dx])
+    dt = (P * n)(*[_dev_ptr(g, "dL_dt", torch.float32) for g in dL_dt])
+    dc = (P * n)(*[_dev_ptr(g, "dL_dc", torch.float32) for g in dL_dc])
+    _check(load().fbs_solve_backward(grid.handle, probs, dx, dt, dc, int(pcg_iters),
+                                     _stream_ptr(stream)), "fbs_solve_backward")
+
+
+def grid_info(grid: Grid, image: int):
+    nv, off = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().fbs_grid_info(grid.handle, int(image), ctypes.byref(nv), ctypes.byref(off)),
+           "fbs_grid_info")
+    return nv.value, off.value
+
+
+def grid_export(grid: Grid, image: int, with_n: bool = True, stream=None):
+    """Host copies (numpy) of one image's keys, vid, counts, nbr and n."""
+    import numpy as np
+    V, _ = grid_info(grid, image)
+    H, W = grid.shapes[image]
+    keys = np.empty(V, np.uint64)
+    vid = np.empty(H * W, np.uint32)
+    m = np.empty(V, np.uint32)
+    nbr = np.empty((V, 10), np.int32)
+    n = np.empty(V, np.float64) if with_n else None
+    _check(load().fbs_grid_export(grid.handle, int(image), _stream_ptr(stream),
+                                  keys.ctypes.data, vid.ctypes.data, m.ctypes.data,
+                                  nbr.ctypes.data, n.ctypes.data if with_n else None),
+           "fbs_grid_export")
+    return keys, vid, m, nbr, n
+
+
+def grid_sync(grid: Grid, stream=None) -> None:
+    _check(load().fbs_grid_sync(grid.handle, _stream_ptr(stream)), "fbs_grid_sync")
+
+
+def grid_destroy(grid: Grid, stream=None) -> None:
+    grid.destroy(stream)
+
+
+def profile_enable(level: int = 1) -> None:
+    """0 = off, 1 = every kernel family, 2 = multi-launch regions."""
+    _check(load().fbs_profile_enable(int(level)), "fbs_profile_enable")
+
+
+def profile_read():
+    """{family: (launches, total_ms)} of the kernels launched since profile_enable."""
+    L = load()
+    cnt = ctypes.c_int(64)
+    names = (ctypes.c_char_p * 64)()
+    launches = (ctypes.c_int64 * 64)()
+    ms = (ctypes.c_double * 64)()
+    _check(L.fbs_profile_read(ctypes.byref(cnt), names, launches, ms), "fbs_profile_read")
+    return {names[i].decode(): (launches[i], ms[i]) for i in range(min(cnt.value, 64))}
+
+
+# ------------------------------------------------------------- autograd ---
+
+def _autograd_function():
+    import torch
+
+    class BilateralSolve(torch.autograd.Function):
+        """x = solve(t, c) on a prebuilt, bistochastised grid of ONE image.
+
+        forward saves only the bilateral-space solution y (C x V), as Sec. 3
+        notes; backward runs a second PCG with the same A (fbs_solve_backward)
+        to produce dL/dt and dL/dc."""
+
+        @staticmethod
+        def forward(ctx, t, c, grid, lam, pcg_iters):
+            t = t.contiguous()
+            c = c.contiguous()
+            C, H, W = t.shape
+            x = torch.empty_like(t)
+            y = torch.empty((C, grid.vertex_counts[0]), device=t.device, dtype=torch.float32)
+            solve(grid, [t], [c], lam, pcg_iters, x=[x], y=[y])
+            ctx.save_for_backward(t, c, y)
+            ctx.grid, ctx.lam, ctx.iters = grid, lam, pcg_iters
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            t, c, y = ctx.saved_tensors
+            gx = gx.contiguous()
+            dt = torch.empty_like(t)
+            dc = torch.empty_like(c)
+            solve_backward(ctx.grid, [t], [c], ctx.lam, [y], [gx], [dt], [dc], ctx.iters)
+            return dt, dc, None, None, None
+
+    return BilateralSolve
+
+
+_BS = None
+
+
+def bilateral_solve(t, c, grid: Grid, lam: float, pcg_iters: int = 25):
+    """Differentiable solve of one image (see BilateralSolve)."""
+    global _BS
+    if _BS is None:
+        _BS = _autograd_function()
+    return _BS.apply(t, c, grid, lam, pcg_iters)

@@ -182,16 +182,32 @@ def _smooth(field: np.ndarray, sigma: float) -> np.ndarray:
     return gaussian_filter(field, sigma=sigma, mode="reflect")
 
 
+def _smooth_stack(fields: np.ndarray, sigma: float) -> np.ndarray:
+    """Smooth each 2-D slice of a stack (no smoothing across the first axis)."""
+    from scipy.ndimage import gaussian_filter
+    return gaussian_filter(fields, sigma=(0.0, sigma, sigma), mode="reflect", truncate=3.0)
+
+
+def _smooth_field(rng, h, w, sigma, step=8):
+    """Gaussian-smoothed white noise, drawn on a grid `step` times coarser and
+    bilinearly upsampled (the field is smooth on that scale anyway)."""
+    from scipy.ndimage import zoom
+    hs, ws = max(2, -(-h // step) + 1), max(2, -(-w // step) + 1)
+    coarse = _smooth(rng.normal(size=(hs, ws)), sigma / step)
+    return zoom(coarse, (h / hs, w / ws), order=1)[:h, :w]
+
+
 def segmentation_instance(rng, h, w, n_classes, sigmas, lam, blob_sigma=24.0):
     """Label blobs = argmax over smoothed random fields; t = softmax of smoothed noisy logits."""
-    fields = np.stack([_smooth(rng.normal(size=(h, w)), blob_sigma) for _ in range(n_classes)])
+    step = 8 if blob_sigma >= 16 else 1
+    fields = np.stack([_smooth_field(rng, h, w, blob_sigma, step) for _ in range(n_classes)])
     labels = np.argmax(fields, axis=0)
     colours = rng.integers(0, 256, size=(n_classes, 3))
     rgb = colours[labels].astype(np.uint8)
     yuv = rgb_to_yuv_planar(add_noise_u8(rng, rgb, 4.0))
     onehot = (labels[None] == np.arange(n_classes)[:, None, None]).astype(np.float64)
     logits = 4.0 * onehot + rng.normal(size=onehot.shape)
-    logits = np.stack([_smooth(l, 2.0) for l in logits])
+    logits = _smooth_stack(logits, 2.0)
     logits -= logits.max(axis=0, keepdims=True)
     e = np.exp(logits)
     t = (e / e.sum(axis=0, keepdims=True)).astype(np.float32)

@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bit-exact: keys, vertex ids, counts, neighbour tables and the FP64
+bistochastisation vector n.  Within rel-L2 1e-5: y and x at equal iteration
+counts (FP32 vectors against the FP64 oracle)."""
+import numpy as np
+import pytest
+
+from paper_1511_03296_gb300 import synth
+from tests.gpu_util import (REL_L2_TOL, assert_grid_bit_exact, gpu_grid, gpu_solve, oracle_grid,
+                            rel_l2, to_dev)
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    from paper_1511_03296_gb300 import build, fbs
+    build.build()
+    fbs.load()
+    assert torch.cuda.is_available()
+
+
+def _inst(seed, h, w, sig, C=1, lam=128.0, npoly=4):
+    return synth.make_tiny(seed, h, w, npoly, C, sig, lam)
+
+
+GRID_CASES = [
+    ("64x48 plain", lambda: synth.plain_64x48().instances[0]),
+    ("1x1", lambda: _inst(1, 1, 1, (8.0, 4.0, 3.0))),
+    ("1x7", lambda: _inst(2, 1, 7, (2.0, 4.0, 3.0))),
+    ("37x53 odd sigma", lambda: _inst(3, 37, 53, (3.3, 5.0, 7.7))),
+    ("sigma_xy < 1", lambda: _inst(4, 13, 11, (0.7, 6.0, 9.0))),
+    ("fine colour", lambda: _inst(5, 61, 83, (5.0, 0.9, 1.3))),
+    ("large cells", lambda: _inst(6, 250, 301, (100.0, 8.0, 8.0))),
+    ("sigma_xy 127 (127x127 cells)", lambda: _inst(7, 256, 256, (127.0, 16.0, 16.0))),
+    ("ragged 257x385", lambda: _inst(8, 257, 385, (16.0, 8.0, 8.0), npoly=12)),
+]
+
+
+@pytest.mark.parametrize("name,make", GRID_CASES, ids=[c[0] for c in GRID_CASES])
+def test_grid_bit_exact(name, make):
+    inst = make()
+    g = gpu_grid([inst], bistoch_iters=2)
+    og = oracle_grid(inst, 2)
+    assert_grid_bit_exact(g, 0, og)
+
+
+@pytest.mark.parametrize("iters", [1, 3, 7])
+def test_bistochastisation_bit_exact(iters):
+    inst = _inst(9, 90, 120, (8.0, 4.0, 3.0), npoly=8)
+    g = gpu_grid([inst], bistoch_iters=iters)
+    og = oracle_grid(inst, iters)
+    assert_grid_bit_exact(g, 0, og)
+
+
+def _check_solve(insts, iters=25, tol=REL_L2_TOL):
+    g = gpu_grid(insts, 2)
+    xs, ys = gpu_solve(g, insts, iters)
+    errs = []
+    for k, inst in enumerate(insts):
+        og = oracle_grid(inst, 2)
+        oy, ox = oracle.solve(og, inst.t, inst.c, inst.lam, iters)
+        ey, ex = rel_l2(ys[k], oy), rel_l2(xs[k].reshape(inst.channels, -1), ox)
+        errs.append((ey, ex))
+        assert ey <= tol and ex <= tol, (k, ey, ex)
+    return errs
+
+
+def test_solve_plain_64x48():
+    _check_solve(synth.plain_64x48().instances)
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2, 5, 50])
+def test_solve_iteration_counts(iters):
+    _check_solve([_inst(10, 70, 90, (8.0, 4.0, 3.0), C=2, npoly=6)], iters)
+
+
+def test_solve_lambda_zero_is_weighted_mean():
+    inst = _inst(11, 40, 56, (8.0, 4.0, 3.0), C=2, lam=0.0)
+    g = gpu_grid([inst], 2)
+    xs, ys = gpu_solve(g, [inst], 25)
+    og = oracle_grid(inst, 2)
+    c = inst.c.reshape(-1).astype(np.float64)
+    for ch in range(2):
+        t = inst.t[ch].reshape(-1).astype(np.float64)
+        num = np.bincount(og.vid, weights=c * t, minlength=og.V)
+        den = np.bincount(og.vid, weights=c, minlength=og.V)
+        want = np.where(den > 0, num / np.where(den > 0, den, 1), 0.0)
+        assert np.allclose(ys[0][ch], want, rtol=1e-6, atol=1e-5)
+
+
+def test_solve_zero_confidence_channels_and_vertices():
+    # whole image at c = 0 except a band; a channel with t = 0 (b = 0)
+    inst = _inst(12, 48, 64, (8.0, 4.0, 3.0), C=3)
+    inst.c[:, 20:] = 0.0
+    inst.t[1] = 0.0
+    _check_solve([inst])
+
+
+def test_batched_uneven_images():
+    insts = [_inst(20, 37, 53, (3.3, 5.0, 7.7), C=1, lam=32.0),
+             _inst(21, 120, 160, (8.0, 4.0, 3.0), C=2, lam=128.0, npoly=8),
+             _inst(22, 9, 300, (16.0, 8.0, 8.0), C=3, lam=4.0),
+             _inst(23, 64, 48, (8.0, 4.0, 3.0), C=1, lam=0.0),
+             _inst(24, 200, 150, (16.0, 8.0, 8.0), C=2, lam=128.0, npoly=10)]
+    g = gpu_grid(insts, 2)
+    for k, inst in enumerate(insts):
+        assert_grid_bit_exact(g, k, oracle_grid(inst, 2))
+    _check_solve(insts)
+
+
+def test_full_1080p_parity():
+    # the benchmark's workload: 1920 x 1080, C = 3, sigma = (16, 8, 8), lambda = 128
+    wl = synth.plain_1080p()
+    inst = wl.instances[0]
+    g = gpu_grid([inst], 2)
+    og = oracle_grid(inst, 2)
+    assert_grid_bit_exact(g, 0, og)
+    errs = _check_solve([inst])
+    print("1080p rel-L2 (y, x):", errs)
+
+
+def test_deterministic():
+    inst = _inst(13, 100, 140, (8.0, 4.0, 3.0), C=2, npoly=8)
+    g = gpu_grid([inst], 2)
+    x1, y1 = gpu_solve(g, [inst], 25)
+    x2, y2 = gpu_solve(g, [inst], 25)
+    assert np.array_equal(x1[0], x2[0]) and np.array_equal(y1[0], y2[0])
+
+
+# ------------------------------------------------------------ robust -------
+
+def _robust_parity(inst, sigma_gm, irls, pcg, tol):
+    import torch
+    from paper_1511_03296_gb300 import fbs
+    g = gpu_grid([inst], 2)
+    t, c = to_dev(inst.t), to_dev(inst.c)
+    x = torch.empty_like(t)
+    y = torch.empty((1, g.vertex_counts[0]), device="cuda")
+    fbs.solve_robust(g, [t], [c], inst.lam, sigma_gm, irls, pcg, x=[x], y=[y])
+    fbs.grid_sync(g)
+    og = oracle_grid(inst, 2)
+    oy, ox = oracle.solve_robust(og, inst.t, inst.c, inst.lam, sigma_gm, irls, pcg)
+    ey, ex = rel_l2(y.cpu().numpy(), oy), rel_l2(x.cpu().numpy().reshape(1, -1), ox)
+    assert ey <= tol and ex <= tol, (ey, ex)
+    return ey, ex
+
+
+def test_robust_small():
+    rng = np.random.Generator(np.random.PCG64(31))
+    inst = synth.robust_instance(rng, 120, 160, 8, (8.0, 8.0, 8.0), 4.0)
+    _robust_parity(inst, 8.0, 4, 25, REL_L2_TOL)
+
+
+def test_robust_1400x1000():
+    inst = synth.robust_1400x1000().instances[0]
+    print("robust 1400x1000 rel-L2 (y, x):", _robust_parity(inst, 1.0, 10, 25, REL_L2_TOL))
+
+
+# ------------------------------------------------------------ backward -----
+
+def _backward_parity(inst, iters=25, tol=REL_L2_TOL):
+    import torch
+    from paper_1511_03296_gb300 import fbs
+    C = inst.channels
+    g = gpu_grid([inst], 2)
+    t, c = to_dev(inst.t), to_dev(inst.c)
+    x = torch.empty_like(t)
+    y = torch.empty((C, g.vertex_counts[0]), device="cuda")
+    fbs.solve(g, [t], [c], inst.lam, iters, x=[x], y=[y])
+    rng = np.random.default_rng(7)
+    dx = rng.normal(size=inst.t.shape).astype(np.float32)
+    dt = torch.empty_like(t)
+    dc = torch.empty_like(c)
+    fbs.solve_backward(g, [t], [c], inst.lam, [y], [to_dev(dx)], [dt], [dc], iters)
+    fbs.grid_sync(g)
+    og = oracle_grid(inst, 2)
+    oy, _ = oracle.solve(og, inst.t, inst.c, inst.lam, iters)
+    odt, odc = oracle.backward(og, inst.t, inst.c, inst.lam, iters, oy, dx.reshape(C, -1))
+    e_t = rel_l2(dt.cpu().numpy().reshape(C, -1), odt)
+    e_c = rel_l2(dc.cpu().numpy().reshape(-1), odc)
+    assert e_t <= tol and e_c <= tol, (e_t, e_c)
+    return e_t, e_c
+
+
+def test_backward_seg_crop_21ch():
+    rng = np.random.Generator(np.random.PCG64(5))
+    inst = synth.segmentation_instance(rng, 48, 64, 21, (8.0, 4.0, 3.0), 128.0, blob_sigma=6.0)
+    _backward_parity(synth.crop(inst, 8, 16, 24, 32))
+
+
+def test_backward_640x480_21ch():
+    rng = np.random.Generator(np.random.PCG64(5))
+    inst = synth.segmentation_instance(rng, 480, 640, 21, (8.0, 4.0, 3.0), 128.0)
+    print("backward 640x480 rel-L2 (dt, dc):", _backward_parity(inst))
+
+
+def test_autograd_function_matches_backward():
+    import torch
+    from paper_1511_03296_gb300 import fbs
+    inst = _inst(14, 40, 60, (8.0, 4.0, 3.0), C=3, lam=16.0)
+    g = gpu_grid([inst], 2)
+    t = to_dev(inst.t).requires_grad_(True)
+    c = to_dev(inst.c).requires_grad_(True)
+    x = fbs.bilateral_solve(t, c, g, inst.lam, 25)
+    label = to_dev(np.random.default_rng(0).random(inst.t.shape).astype(np.float32))
+    loss = ((x - label) ** 2).mean()
+    loss.backward()
+    og = oracle_grid(inst, 2)
+    oy, ox = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
+    dx = 2.0 * (ox - label.cpu().numpy().reshape(3, -1).astype(np.float64)) / ox.size
+    odt, odc = oracle.backward(og, inst.t, inst.c, inst.lam, 25, oy, dx)
+    assert rel_l2(t.grad.cpu().numpy().reshape(3, -1), odt) <= REL_L2_TOL * 10
+    assert rel_l2(c.grad.cpu().numpy().reshape(-1), odc) <= REL_L2_TOL * 10
+
+
+# ------------------------------------------------------------ errors -------
+
+def test_range_error_is_reported():
+    from paper_1511_03296_gb300 import fbs
+    inst = _inst(15, 20, 30, (8.0, 4.0, 3.0))
+    inst.yuv[1, 3, 4] = -50.0
+    with pytest.raises(fbs.FbsError, match="RANGE"):
+        gpu_grid([inst], 2)
+    inst.yuv[1, 3, 4] = np.nan
+    with pytest.raises(fbs.FbsError, match="RANGE"):
+        gpu_grid([inst], 2)
+
+
+def test_nonfinite_target_is_reported():
+    from paper_1511_03296_gb300 import fbs
+    inst = _inst(16, 20, 30, (8.0, 4.0, 3.0))
+    inst.t[0, 5, 5] = np.inf
+    g = gpu_grid([inst], 2)
+    with pytest.raises(fbs.FbsError, match="NONFINITE"):
+        gpu_solve(g, [inst], 5)
+
+
+def test_solve_before_bistochastize_is_a_state_error():
+    from paper_1511_03296_gb300 import fbs
+    inst = _inst(17, 20, 30, (8.0, 4.0, 3.0))
+    g = gpu_grid([inst], 0)
+    with pytest.raises(fbs.FbsError, match="STATE"):
+        gpu_solve(g, [inst], 5)
+
+
+def test_bad_arguments():
+    from paper_1511_03296_gb300 import fbs
+    inst = _inst(18, 20, 30, (8.0, 4.0, 3.0))
+    with pytest.raises(fbs.FbsError, match="ARG"):
+        fbs.grid_build([to_dev(inst.yuv)], 0.0, 4.0, 3.0)
+    big = to_dev(np.full((3, 300, 300), 100.0, np.float32))
+    with pytest.raises(fbs.FbsError, match="ARG"):
+        fbs.grid_build([big], 300.0, 4.0, 3.0)   # a 150 x 150 cell: above 16384 pixels
+    g = gpu_grid([inst], 2)
+    with pytest.raises(fbs.FbsError, match="ARG"):
+        fbs.bistochastize(g, 0)
+    t, c = to_dev(inst.t), to_dev(inst.c)
+    with pytest.raises(fbs.FbsError, match="ARG"):
+        fbs.solve(g, [t], [c], -1.0, 5)
+    with pytest.raises(fbs.FbsError, match="ARG"):
+        fbs.solve_robust(g, [to_dev(np.concatenate([inst.t, inst.t]))], [c], 1.0, 1.0, 2, 5)
