@@ -135,6 +135,24 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
                               const float* const* dL_dx, float* const* dL_dt,
                               float* const* dL_dc, int pcg_iters, void* stream);
 
+/*
+ * fbs_set_vector_precision -- how the CG state of later solves on this grid
+ * is held (the paper fixes no precision; every variant keeps the CG inner
+ * products FP64-accurate):
+ *   FBS_VECTORS_FP32         y, r, d, q in FP32; A d computed in FP32.
+ *   FBS_VECTORS_COMPENSATED  y, d in FP32; the residual r as a pair of FP32
+ *                            values (double-float) and q = A d recomputed in
+ *                            the update phase with error-free products, so
+ *                            r <- r - alpha A d carries no rounding of q.
+ *                            Same vector bytes per channel, one more
+ *                            neighbour-table pass per iteration.
+ *   FBS_VECTORS_AUTO         (default) compensated for fbs_solve_backward,
+ *                            FP32 for fbs_solve and fbs_solve_robust.
+ * Host-side setting; no device work.  Errors: FBS_ERR_ARG.
+ */
+enum { FBS_VECTORS_AUTO = 0, FBS_VECTORS_FP32 = 1, FBS_VECTORS_COMPENSATED = 2 };
+fbs_status fbs_set_vector_precision(fbs_grid* g, int precision);
+
 /* Vertex count and offset (in the concatenated vertex order) of one image.
  * Host outputs; no device work. */
 fbs_status fbs_grid_info(const fbs_grid* g, int image, int64_t* n_vertices,

@@ -71,6 +71,9 @@ std::vector<cudaEvent_t>& event_pool()
     return p;
 }
 int g_prof_level = 0;
+}  // namespace
+int prof_level() { return g_prof_level; }
+namespace {
 
 cudaEvent_t take_event()
 {
@@ -242,7 +245,8 @@ struct fbs_grid {
     int bistoch_iters = 0;
     // solve workspace
     size_t cap_vec = 0;                 // floats per vector
-    float* vec = nullptr;               // 5 x cap_vec: y, r, d0, d1, q
+    float* vec = nullptr;               // 6 x cap_vec: y, r, r_lo, d0, d1, q
+    int precision = FBS_VECTORS_AUTO;
     float* a = nullptr;
     float2* nm = nullptr;
     size_t cap_scal = 0, cap_part = 0;
@@ -251,12 +255,33 @@ struct fbs_grid {
     unsigned* cnt = nullptr;
     InstDev* inst = nullptr;
     std::vector<InstDev> inst_cached;
+    // CUDA graphs of the solve segments, keyed by the exact launch arguments
+    struct GraphEntry {
+        SolveArgs A;
+        SolvePlan P;
+        int seg, mode;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap_stream = nullptr;
 };
 
 namespace {
 
+void free_graphs(fbs_grid* g)
+{
+    for (auto& e : g->graphs)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    g->graphs.clear();
+}
+
 void free_grid_memory(fbs_grid* g, cudaStream_t s)
 {
+    free_graphs(g);
+    if (g->cap_stream) {
+        cudaStreamDestroy(g->cap_stream);
+        g->cap_stream = nullptr;
+    }
     dfree(g->vkey, s); dfree(g->vid, s); dfree(g->perm, s); dfree(g->pstart, s);
     dfree(g->m, s); dfree(g->nbr, s); dfree(g->n64, s); dfree(g->n64b, s); dfree(g->nf, s);
     dfree(g->cell_voff, s); dfree(g->cell_nv, s); dfree(g->err, s); dfree(g->vt, s);
@@ -514,6 +539,82 @@ fbs_status check_problems(const fbs_grid* g, const fbs_problem_desc* probs, int 
     return FBS_OK;
 }
 
+// One segment, replayed from a CUDA graph captured on first use (per exact
+// launch arguments), or launched directly while the caller's stream is being
+// captured or per-kernel timing is on.
+cudaError_t run_segment(fbs_grid* g, const SolveArgs& A, const SolvePlan& P, int seg, int mode,
+                        cudaStream_t s)
+{
+    if (capturing(s) || prof_level() == 1) return launch_segment(A, P, seg, mode, s);
+    fbs_grid::GraphEntry* seen = nullptr;
+    for (auto& e : g->graphs)
+        if (e.seg == seg && e.mode == mode && memcmp(&e.A, &A, sizeof(A)) == 0 &&
+            memcmp(&e.P, &P, sizeof(P)) == 0)
+            seen = &e;
+    if (seen && seen->exec) return cudaGraphLaunch(seen->exec, s);
+    if (!seen) {
+        // first sighting: launch directly and remember the arguments; a graph
+        // is captured only when the same launch comes back
+        if (g->graphs.size() >= 16) {
+            if (g->graphs.front().exec) cudaGraphExecDestroy(g->graphs.front().exec);
+            g->graphs.erase(g->graphs.begin());
+        }
+        fbs_grid::GraphEntry entry;
+        memcpy(&entry.A, &A, sizeof(A));
+        memcpy(&entry.P, &P, sizeof(P));
+        entry.seg = seg;
+        entry.mode = mode;
+        entry.exec = nullptr;
+        g->graphs.push_back(entry);
+        return launch_segment(A, P, seg, mode, s);
+    }
+    cudaError_t err = cudaSuccess;
+    if (!g->cap_stream) {
+        err = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+        if (err != cudaSuccess) return err;
+    }
+    err = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return err;
+    cudaError_t lerr = launch_segment(A, P, seg, mode, g->cap_stream);
+    cudaGraph_t graph = nullptr;
+    err = cudaStreamEndCapture(g->cap_stream, &graph);
+    if (lerr != cudaSuccess) err = lerr;
+    if (err != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return err;
+    }
+    cudaGraphExec_t exec = nullptr;
+    err = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) return err;
+    seen->exec = exec;
+    return cudaGraphLaunch(exec, s);
+}
+
+fbs_status run_segments(fbs_grid* g, const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
+{
+    static int f_setup = prof_family("region:solve_setup", 2);
+    static int f_loop = prof_family("region:pcg_loop", 2);
+    static int f_out = prof_family("region:slice", 2);
+    cudaError_t e = cudaSuccess;
+    for (int outer = 0; outer < P.outer_iters && e == cudaSuccess; ++outer) {
+        const int mode = P.mode == kSplatRobust && outer == 0 ? kSplatConfidence : P.mode;
+        prof_begin(f_setup, s);
+        e = run_segment(g, A, P, kSegSetup, mode, s);
+        prof_end(f_setup, s);
+        if (e != cudaSuccess) break;
+        prof_begin(f_loop, s);
+        e = run_segment(g, A, P, kSegLoop, mode, s);
+        prof_end(f_loop, s);
+    }
+    if (e == cudaSuccess) {
+        prof_begin(f_out, s);
+        e = run_segment(g, A, P, kSegOut, P.mode, s);
+        prof_end(f_out, s);
+    }
+    return cuda_status(e);
+}
+
 // Sizes the workspace, uploads the image descriptors (if they changed) and
 // runs one solve plan.
 fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStream_t s)
@@ -539,18 +640,25 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     }
     plan.max_pixels = g->max_pixels;
     plan.chan_block = std::min(cmax, kChanBlock);
+    // vector precision: FP32 state for forward and robust solves, the
+    // compensated variant for the backward solve (whose right-hand side is
+    // an arbitrary gradient) unless the caller chose otherwise
+    if (g->precision == FBS_VECTORS_FP32) plan.comp = 0;
+    else if (g->precision == FBS_VECTORS_COMPENSATED) plan.comp = 1;
+    else plan.comp = plan.mode == kSplatBackward ? 1 : 0;
     const bool cap = capturing(s);
     cudaError_t e = cudaSuccess;
     if ((size_t)cv > g->cap_vec || (size_t)pc > g->cap_scal || (size_t)cpart > g->cap_part ||
         !g->a) {
         if (cap) return FBS_ERR_STATE;   // size the workspace outside capture first
+        free_graphs(g);
         dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s);
         dfree(g->part, s); dfree(g->cnt, s); dfree(g->inst, s);
         g->inst_cached.clear();
         g->cap_vec = (size_t)std::max<int64_t>(cv, 1);
         g->cap_scal = (size_t)std::max(pc, 1);
         g->cap_part = (size_t)std::max<int64_t>(cpart, 1);
-        if ((e = dalloc(&g->vec, 5 * g->cap_vec, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = dalloc(&g->vec, 6 * g->cap_vec, s)) != cudaSuccess) return cuda_status(e);
         if ((e = dalloc(&g->a, g->Vtot, s)) != cudaSuccess) return cuda_status(e);
         if ((e = dalloc(&g->nm, g->Vtot, s)) != cudaSuccess) return cuda_status(e);
         if ((e = dalloc(&g->scal, g->cap_scal, s)) != cudaSuccess) return cuda_status(e);
@@ -583,15 +691,15 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.nm = g->nm;
     A.y = g->vec;
     A.r = g->vec + g->cap_vec;
-    A.d[0] = g->vec + 2 * g->cap_vec;
-    A.d[1] = g->vec + 3 * g->cap_vec;
-    A.q = g->vec + 4 * g->cap_vec;
+    A.rlo = g->vec + 2 * g->cap_vec;
+    A.d[0] = g->vec + 3 * g->cap_vec;
+    A.d[1] = g->vec + 4 * g->cap_vec;
+    A.q = g->vec + 5 * g->cap_vec;
     A.scal = g->scal;
     A.part = g->part;
     A.cnt = g->cnt;
     A.err = g->err;
-    e = launch_solve(A, plan, s);
-    return cuda_status(e);
+    return run_segments(g, A, plan, s);
 }
 
 std::vector<InstDev> base_instances(const fbs_grid* g, const fbs_problem_desc* probs)
@@ -674,6 +782,14 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
     plan.pcg_iters = pcg_iters;
     plan.sigma_gm = 1.0f;
     return run(g, inst, plan, (cudaStream_t)stream);
+}
+
+fbs_status fbs_set_vector_precision(fbs_grid* g, int precision)
+{
+    if (!g || precision < FBS_VECTORS_AUTO || precision > FBS_VECTORS_COMPENSATED)
+        return FBS_ERR_ARG;
+    g->precision = precision;
+    return FBS_OK;
 }
 
 fbs_status fbs_grid_info(const fbs_grid* g, int image, int64_t* n_vertices, int64_t* vertex_offset)

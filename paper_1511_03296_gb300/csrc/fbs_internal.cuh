@@ -153,18 +153,40 @@ __device__ __forceinline__ DF df_warp_sum(DF v)
     return v;
 }
 
-// compensated (Neumaier) float sum for the splat
-struct KSum {
-    float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add(float x)
-    {
-        float t = __fadd_rn(s, x);
-        if (fabsf(s) >= fabsf(x)) c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, t), x));
-        else c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), s));
-        s = t;
-    }
-    __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
-};
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+
+// (hi, lo) renormalised; requires |a| >= |b| or a == 0
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// a * b for a double-float a and a float b (relative error ~2^-44)
+__device__ __forceinline__ DF df_mul_f(DF a, float b)
+{
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return df_fast_two_sum(p, e);
+}
+
+// a * b for double-float a and b
+__device__ __forceinline__ DF df_mul(DF a, DF b)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+// split an FP64 scalar into a double-float pair
+__device__ __forceinline__ DF df_from_double(double x)
+{
+    float hi = (float)x;
+    return {hi, (float)(x - (double)hi)};
+}
 
 // ----------------------------------------------------- launch helpers ---
 struct Profiler;
@@ -182,5 +204,6 @@ const DeviceInfo& device_info();
 int prof_family(const char* name, int level = 1);
 void prof_begin(int fam, cudaStream_t s);
 void prof_end(int fam, cudaStream_t s);
+int prof_level();
 
 }  // namespace fbs

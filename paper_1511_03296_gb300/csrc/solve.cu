@@ -105,7 +105,7 @@ __device__ void finish_tile(const InstDev& I, int inst, double* __restrict__ par
 // {n, M^-1} into nm.
 template <int CB>
 __global__ void __launch_bounds__(kVTile)
-splat_kernel(SolveArgs A, int mode, float sigma_gm)
+splat_kernel(SolveArgs A, int mode, float sigma_gm, int comp)
 {
     const float s2 = sigma_gm * sigma_gm;
     for (int tile = blockIdx.x; tile < A.nvt; tile += gridDim.x) {
@@ -159,7 +159,13 @@ splat_kernel(SolveArgs A, int mode, float sigma_gm)
                 if (ch < I.C) {
                     const float b = acc[k].hi + acc[k].lo;
                     const int64_t idx = vec_index(I, ch, v);
-                    A.r[idx] = b;
+                    if (comp) {
+                        const DF bn = df_fast_two_sum(acc[k].hi, acc[k].lo);
+                        A.r[idx] = bn.hi;
+                        A.rlo[idx] = bn.lo;
+                    } else {
+                        A.r[idx] = b;
+                    }
                     A.y[idx] = scf > 0.0f ? b / scf : 0.0f;
                 }
             }
@@ -195,9 +201,57 @@ splat_kernel(SolveArgs A, int mode, float sigma_gm)
     }
 }
 
+// Laplacian-form apply at one vertex for one channel:
+//   (A z)_v = a'_v z_v + lambda n_v sum_u n_u (z_v - z_u).
+// COMP = false: FP32 arithmetic (result in .hi, .lo = 0).
+// COMP = true: every product is exact (two-product) and the sums are carried
+// as double-float pairs, so the result is accurate to ~2^-44 relative.
+template <bool COMP, typename NbrVal>
+__device__ __forceinline__ DF laplacian_apply(float av, float lam_n, const int32_t (&nb)[10],
+                                              const float2 (&nmu)[10], float zv, NbrVal zu)
+{
+    if (COMP) {
+        DF s = {0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < 10; ++j)
+            if (nb[j] >= 0) s = df_add(s, df_mul_exact(nmu[j].x, zv - zu(j)));
+        return df_add(df_mul_exact(av, zv), df_mul_f(s, lam_n));
+    } else {
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 10; ++j)
+            if (nb[j] >= 0) s = fmaf(nmu[j].x, zv - zu(j), s);
+        return DF{fmaf(av, zv, lam_n * s), 0.0f};
+    }
+}
+
+// topology of one vertex: neighbour ids, {n, M^-1} of the neighbours, a', {n, M^-1}
+struct VertexTopo {
+    int32_t nb[10];
+    float2 nmu[10];
+    float av;
+    float2 nmv;
+};
+
+__device__ __forceinline__ void load_topo(const SolveArgs& A, int64_t v, bool valid, VertexTopo& T)
+{
+    T.av = 0.0f;
+    T.nmv = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        T.nb[k] = valid ? A.nbr[(int64_t)k * A.Vtot + v] : -1;
+        T.nmu[k] = T.nb[k] >= 0 ? A.nm[T.nb[k]] : make_float2(0.0f, 0.0f);
+    }
+    if (valid) {
+        T.av = A.a[v];
+        T.nmv = A.nm[v];
+    }
+}
+
 // ------------------------------------------------------- initial residual ---
-// r = b - A y0 (b is in r), then r^T M^-1 r -> delta, beta = 0.
-template <int CB>
+// r = b - A y0 (b is in r, and in r_lo too when COMP), then r^T M^-1 r ->
+// delta, beta = 0.
+template <int CB, bool COMP>
 __global__ void __launch_bounds__(kVTile)
 residual_kernel(SolveArgs A)
 {
@@ -207,19 +261,9 @@ residual_kernel(SolveArgs A)
         const InstDev I = A.inst[vt.inst];
         const int64_t v = vt.v0 + threadIdx.x;
         const bool valid = v < vt.v1;
-        int32_t nb[10];
-        float2 nmu[10];
-        float av = 0.0f;
-        float2 nmv = make_float2(0.0f, 0.0f);
-        if (valid) {
-            av = A.a[v];
-            nmv = A.nm[v];
-#pragma unroll
-            for (int k = 0; k < 10; ++k) {
-                nb[k] = A.nbr[(int64_t)k * A.Vtot + v];
-                nmu[k] = nb[k] >= 0 ? A.nm[nb[k]] : make_float2(0.0f, 0.0f);
-            }
-        }
+        VertexTopo T;
+        load_topo(A, v, valid, T);
+        const float lam_n = I.lam * T.nmv.x;
         for (int cb = 0; cb < I.C; cb += CB) {
             DF acc[CB];
 #pragma unroll
@@ -228,15 +272,20 @@ residual_kernel(SolveArgs A)
                 const int ch = cb + k;
                 if (valid && ch < I.C) {
                     const int64_t base = I.vec_base + (int64_t)ch * I.V - I.voff;
-                    const float yv = A.y[base + v];
-                    float s = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < 10; ++j)
-                        if (nb[j] >= 0) s = fmaf(nmu[j].x, yv - A.y[base + nb[j]], s);
-                    const float Ay = fmaf(av, yv, I.lam * nmv.x * s);
-                    const float rv = A.r[base + v] - Ay;
-                    A.r[base + v] = rv;
-                    acc[k] = df_mul_exact(rv, nmv.y * rv);
+                    const float* y = A.y;
+                    const DF Ay = laplacian_apply<COMP>(T.av, lam_n, T.nb, T.nmu, y[base + v],
+                                                        [&](int j) { return y[base + T.nb[j]]; });
+                    float rhi;
+                    if (COMP) {
+                        const DF r = df_add(DF{A.r[base + v], A.rlo[base + v]}, df_neg(Ay));
+                        A.r[base + v] = r.hi;
+                        A.rlo[base + v] = r.lo;
+                        rhi = r.hi;
+                    } else {
+                        rhi = A.r[base + v] - Ay.hi;
+                        A.r[base + v] = rhi;
+                    }
+                    acc[k] = df_mul_exact(rhi, T.nmv.y * rhi);
                 }
             }
             store_tile_partials<CB>(acc, I, vt, cb, A.part, red);
@@ -248,7 +297,8 @@ residual_kernel(SolveArgs A)
 // ------------------------------------------------------- PCG phase 1 ---
 // d = M^-1 r + beta d_old (own vertex and, on the fly, its neighbours),
 // q = A d, partial d^T q; the last tile sets alpha = delta / d^T q.
-template <int CB>
+// COMP: q is not stored (phase 2 recomputes it exactly from d).
+template <int CB, bool COMP>
 __global__ void __launch_bounds__(kVTile)
 pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict__ dnew, int first)
 {
@@ -258,19 +308,9 @@ pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict_
         const InstDev I = A.inst[vt.inst];
         const int64_t v = vt.v0 + threadIdx.x;
         const bool valid = v < vt.v1;
-        int32_t nb[10];
-        float2 nmu[10];
-        float av = 0.0f;
-        float2 nmv = make_float2(0.0f, 0.0f);
-        if (valid) {
-            av = A.a[v];
-            nmv = A.nm[v];
-#pragma unroll
-            for (int k = 0; k < 10; ++k) {
-                nb[k] = A.nbr[(int64_t)k * A.Vtot + v];
-                nmu[k] = nb[k] >= 0 ? A.nm[nb[k]] : make_float2(0.0f, 0.0f);
-            }
-        }
+        VertexTopo T;
+        load_topo(A, v, valid, T);
+        const float lam_n = I.lam * T.nmv.x;
         for (int cb = 0; cb < I.C; cb += CB) {
             DF acc[CB];
 #pragma unroll
@@ -280,21 +320,22 @@ pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict_
                 if (valid && ch < I.C) {
                     const int64_t base = I.vec_base + (int64_t)ch * I.V - I.voff;
                     const float beta = first ? 0.0f : (float)A.scal[I.pc + ch].beta;
-                    float dv = nmv.y * A.r[base + v];
+                    const float* r = A.r;
+                    float dv = T.nmv.y * r[base + v];
                     if (!first) dv = fmaf(beta, dold[base + v], dv);
-                    float s = 0.0f;
-#pragma unroll
-                    for (int j = 0; j < 10; ++j) {
-                        if (nb[j] >= 0) {
-                            float du = nmu[j].y * A.r[base + nb[j]];
-                            if (!first) du = fmaf(beta, dold[base + nb[j]], du);
-                            s = fmaf(nmu[j].x, dv - du, s);
-                        }
-                    }
-                    const float qv = fmaf(av, dv, I.lam * nmv.x * s);
+                    const DF q = laplacian_apply<COMP>(T.av, lam_n, T.nb, T.nmu, dv, [&](int j) {
+                        const int64_t u = base + T.nb[j];
+                        float du = T.nmu[j].y * r[u];
+                        if (!first) du = fmaf(beta, dold[u], du);
+                        return du;
+                    });
                     dnew[base + v] = dv;
-                    A.q[base + v] = qv;
-                    acc[k] = df_mul_exact(dv, qv);
+                    if (COMP) {
+                        acc[k] = df_add(df_mul_exact(dv, q.hi), DF{dv * q.lo, 0.0f});
+                    } else {
+                        A.q[base + v] = q.hi;
+                        acc[k] = df_mul_exact(dv, q.hi);
+                    }
                 }
             }
             store_tile_partials<CB>(acc, I, vt, cb, A.part, red);
@@ -306,7 +347,10 @@ pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict_
 // ------------------------------------------------------- PCG phase 2 ---
 // y += alpha d; r -= alpha q; partial r^T M^-1 r; the last tile sets
 // beta = delta_new / delta_old.
-template <int CB>
+// COMP: q = A d is recomputed here with compensated arithmetic and the
+// residual is kept as a double-float pair (r, r_lo), so the recurrence
+// r <- r - alpha A d carries no rounding of q.
+template <int CB, bool COMP>
 __global__ void __launch_bounds__(kVTile)
 pcg_update_kernel(SolveArgs A, const float* __restrict__ d)
 {
@@ -316,7 +360,13 @@ pcg_update_kernel(SolveArgs A, const float* __restrict__ d)
         const InstDev I = A.inst[vt.inst];
         const int64_t v = vt.v0 + threadIdx.x;
         const bool valid = v < vt.v1;
-        const float minv = valid ? A.nm[v].y : 0.0f;
+        VertexTopo T;
+        if (COMP) {
+            load_topo(A, v, valid, T);
+        } else {
+            T.nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
+        }
+        const float lam_n = I.lam * T.nmv.x;
         for (int cb = 0; cb < I.C; cb += CB) {
             DF acc[CB];
 #pragma unroll
@@ -324,12 +374,25 @@ pcg_update_kernel(SolveArgs A, const float* __restrict__ d)
                 acc[k] = {0.0f, 0.0f};
                 const int ch = cb + k;
                 if (valid && ch < I.C) {
-                    const int64_t idx = vec_index(I, ch, v);
-                    const float alpha = (float)A.scal[I.pc + ch].alpha;
-                    A.y[idx] = fmaf(alpha, d[idx], A.y[idx]);
-                    const float rv = fmaf(-alpha, A.q[idx], A.r[idx]);
-                    A.r[idx] = rv;
-                    acc[k] = df_mul_exact(rv, minv * rv);
+                    const int64_t base = I.vec_base + (int64_t)ch * I.V - I.voff;
+                    const int64_t idx = base + v;
+                    const double alpha = A.scal[I.pc + ch].alpha;
+                    const float dv = d[idx];
+                    A.y[idx] = fmaf((float)alpha, dv, A.y[idx]);
+                    float rhi;
+                    if (COMP) {
+                        const DF q = laplacian_apply<true>(T.av, lam_n, T.nb, T.nmu, dv,
+                                                           [&](int j) { return d[base + T.nb[j]]; });
+                        const DF r = df_add(DF{A.r[idx], A.rlo[idx]},
+                                            df_neg(df_mul(df_from_double(alpha), q)));
+                        A.r[idx] = r.hi;
+                        A.rlo[idx] = r.lo;
+                        rhi = r.hi;
+                    } else {
+                        rhi = fmaf(-(float)alpha, A.q[idx], A.r[idx]);
+                        A.r[idx] = rhi;
+                    }
+                    acc[k] = df_mul_exact(rhi, T.nmv.y * rhi);
                 }
             }
             store_tile_partials<CB>(acc, I, vt, cb, A.part, red);
@@ -400,8 +463,9 @@ int persistent_blocks(int occ, int nvt)
     return nvt < cap ? nvt : cap;
 }
 
-template <int CB>
-cudaError_t launch_all(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
+template <int CB, bool COMP>
+cudaError_t launch_segment_t(const SolveArgs& A, const SolvePlan& P, int seg, int mode,
+                             cudaStream_t s)
 {
     static int f_splat = prof_family("splat");
     static int f_res = prof_family("residual");
@@ -409,72 +473,75 @@ cudaError_t launch_all(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
     static int f_update = prof_family("pcg_update");
     static int f_slice = prof_family("slice");
     static int f_bwd = prof_family("backward_slice");
-    static int f_setup = prof_family("region:solve_setup", 2);
-    static int f_loop = prof_family("region:pcg_loop", 2);
-    static int f_out = prof_family("region:slice", 2);
+    static int f_export = prof_family("export_y");
     static const int occ_s = occupancy((const void*)splat_kernel<CB>);
-    static const int occ_r = occupancy((const void*)residual_kernel<CB>);
-    static const int occ_p = occupancy((const void*)pcg_apply_kernel<CB>);
-    static const int occ_u = occupancy((const void*)pcg_update_kernel<CB>);
-    const int nb_s = persistent_blocks(occ_s, A.nvt);
-    const int nb_r = persistent_blocks(occ_r, A.nvt);
-    const int nb_p = persistent_blocks(occ_p, A.nvt);
-    const int nb_u = persistent_blocks(occ_u, A.nvt);
-    const dim3 pix_grid((unsigned)std::min<int64_t>((P.max_pixels + 255) / 256,
-                                                    (int64_t)device_info().sms * 8),
-                        (unsigned)A.ninst);
-    for (int outer = 0; outer < P.outer_iters; ++outer) {
-        const int mode = P.mode == kSplatRobust && outer == 0 ? kSplatConfidence : P.mode;
-        prof_begin(f_setup, s);
+    static const int occ_r = occupancy((const void*)residual_kernel<CB, COMP>);
+    static const int occ_p = occupancy((const void*)pcg_apply_kernel<CB, COMP>);
+    static const int occ_u = occupancy((const void*)pcg_update_kernel<CB, COMP>);
+    if (seg == kSegSetup) {
         prof_begin(f_splat, s);
-        splat_kernel<CB><<<nb_s, kVTile, 0, s>>>(A, mode, P.sigma_gm);
+        splat_kernel<CB><<<persistent_blocks(occ_s, A.nvt), kVTile, 0, s>>>(A, mode, P.sigma_gm,
+                                                                         COMP ? 1 : 0);
         prof_end(f_splat, s);
         prof_begin(f_res, s);
-        residual_kernel<CB><<<nb_r, kVTile, 0, s>>>(A);
+        residual_kernel<CB, COMP><<<persistent_blocks(occ_r, A.nvt), kVTile, 0, s>>>(A);
         prof_end(f_res, s);
-        prof_end(f_setup, s);
-        prof_begin(f_loop, s);
+    } else if (seg == kSegLoop) {
+        const int nb_p = persistent_blocks(occ_p, A.nvt);
+        const int nb_u = persistent_blocks(occ_u, A.nvt);
         for (int it = 0; it < P.pcg_iters; ++it) {
             const float* dold = A.d[(it + 1) & 1];
             float* dnew = A.d[it & 1];
             prof_begin(f_apply, s);
-            pcg_apply_kernel<CB><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it == 0);
+            pcg_apply_kernel<CB, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it == 0);
             prof_end(f_apply, s);
             prof_begin(f_update, s);
-            pcg_update_kernel<CB><<<nb_u, kVTile, 0, s>>>(A, dnew);
+            pcg_update_kernel<CB, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew);
             prof_end(f_update, s);
         }
-        prof_end(f_loop, s);
-    }
-    prof_begin(f_out, s);
-    if (P.mode == kSplatBackward) {
-        prof_begin(f_bwd, s);
-        backward_slice_kernel<<<pix_grid, 256, 0, s>>>(A);
-        prof_end(f_bwd, s);
     } else {
-        prof_begin(f_slice, s);
-        slice_kernel<<<pix_grid, 256, 0, s>>>(A);
-        prof_end(f_slice, s);
-        if (P.export_y) {
-            const dim3 yg((unsigned)std::min<int64_t>((P.max_cv + 255) / 256,
-                                                      (int64_t)device_info().sms * 4),
-                          (unsigned)A.ninst);
-            export_y_kernel<<<yg, 256, 0, s>>>(A);
+        const dim3 pix_grid((unsigned)std::min<int64_t>((P.max_pixels + 255) / 256,
+                                                        (int64_t)device_info().sms * 8),
+                            (unsigned)A.ninst);
+        if (P.mode == kSplatBackward) {
+            prof_begin(f_bwd, s);
+            backward_slice_kernel<<<pix_grid, 256, 0, s>>>(A);
+            prof_end(f_bwd, s);
+        } else {
+            prof_begin(f_slice, s);
+            slice_kernel<<<pix_grid, 256, 0, s>>>(A);
+            prof_end(f_slice, s);
+            if (P.export_y) {
+                const dim3 yg((unsigned)std::min<int64_t>((P.max_cv + 255) / 256,
+                                                          (int64_t)device_info().sms * 4),
+                              (unsigned)A.ninst);
+                prof_begin(f_export, s);
+                export_y_kernel<<<yg, 256, 0, s>>>(A);
+                prof_end(f_export, s);
+            }
         }
     }
-    prof_end(f_out, s);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_solve(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
+cudaError_t launch_segment(const SolveArgs& A, const SolvePlan& P, int seg, int mode,
+                           cudaStream_t s)
 {
+    if (P.comp) {
+        switch (P.chan_block) {
+            case 1: return launch_segment_t<1, true>(A, P, seg, mode, s);
+            case 2: return launch_segment_t<2, true>(A, P, seg, mode, s);
+            case 3: return launch_segment_t<3, true>(A, P, seg, mode, s);
+            default: return launch_segment_t<4, true>(A, P, seg, mode, s);
+        }
+    }
     switch (P.chan_block) {
-        case 1: return launch_all<1>(A, P, s);
-        case 2: return launch_all<2>(A, P, s);
-        case 3: return launch_all<3>(A, P, s);
-        default: return launch_all<4>(A, P, s);
+        case 1: return launch_segment_t<1, false>(A, P, seg, mode, s);
+        case 2: return launch_segment_t<2, false>(A, P, seg, mode, s);
+        case 3: return launch_segment_t<3, false>(A, P, seg, mode, s);
+        default: return launch_segment_t<4, false>(A, P, seg, mode, s);
     }
 }
 

@@ -24,6 +24,7 @@ struct SolveArgs {
     // vectors, all sum_k C_k V_k floats
     float* y;
     float* r;
+    float* rlo;                // low part of r (compensated variant)
     float* d[2];
     float* q;
     // reductions
@@ -42,8 +43,15 @@ struct SolvePlan {
     int64_t max_pixels;        // largest image
     int64_t max_cv;            // largest C x V block
     bool export_y;
+    int comp;                  // 1: compensated residual / recomputed q variant
 };
 
-cudaError_t launch_solve(const SolveArgs& A, const SolvePlan& P, cudaStream_t s);
+// A solve runs as segments: for each outer (IRLS) iteration a setup (splat,
+// diag(A), flat init, initial residual) and the PCG loop, then the output
+// (slice / y export, or the backward adjoints).  `mode` is the splat mode of
+// a setup segment.
+enum Segment : int { kSegSetup = 0, kSegLoop = 1, kSegOut = 2 };
+cudaError_t launch_segment(const SolveArgs& A, const SolvePlan& P, int seg, int mode,
+                           cudaStream_t s);
 
 }  // namespace fbs

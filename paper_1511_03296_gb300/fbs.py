@@ -23,7 +23,10 @@ STATUS_NAMES = {0: "FBS_OK", 1: "FBS_ERR_ARG", 2: "FBS_ERR_RANGE", 3: "FBS_ERR_O
 # every symbol include/fbs.h declares
 EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robust",
             "fbs_solve_backward", "fbs_grid_info", "fbs_grid_export", "fbs_grid_sync",
-            "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read"]
+            "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read",
+            "fbs_set_vector_precision"]
+
+VECTORS_AUTO, VECTORS_FP32, VECTORS_COMPENSATED = 0, 1, 2
 
 
 class FbsError(RuntimeError):
@@ -70,6 +73,7 @@ def load(path: Optional[str] = None):
         L.fbs_grid_info.argtypes = [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64)]
         L.fbs_grid_export.argtypes = [P, I, P, P, P, P, P, P]
         L.fbs_grid_sync.argtypes = [P, P]
+        L.fbs_set_vector_precision.argtypes = [P, I]
         L.fbs_grid_destroy.argtypes = [P, P]
         L.fbs_status_string.argtypes = [I]
         L.fbs_status_string.restype = ctypes.c_char_p
@@ -221,6 +225,12 @@ def solve_backward(grid: Grid, t: List, c: List, lam, yhat: List, dL_dx: List, d
     dc = (P * n)(*[_dev_ptr(g, "dL_dc", torch.float32) for g in dL_dc])
     _check(load().fbs_solve_backward(grid.handle, probs, dx, dt, dc, int(pcg_iters),
                                      _stream_ptr(stream)), "fbs_solve_backward")
+
+
+def set_vector_precision(grid: Grid, precision: int) -> None:
+    """VECTORS_AUTO (default), VECTORS_FP32 or VECTORS_COMPENSATED (see include/fbs.h)."""
+    _check(load().fbs_set_vector_precision(grid.handle, int(precision)),
+           "fbs_set_vector_precision")
 
 
 def grid_info(grid: Grid, image: int):
