@@ -66,7 +66,7 @@ typedef struct {
     float* x;             /* device, channels x H x W output (sliced solution), or NULL */
     float* y;             /* device, channels x V output (bilateral-space solution y),
                              or NULL; the backward pass reads it as the saved y-hat   */
-    int channels;         /* >= 1 */
+    int channels;         /* 1 .. 64 */
     float lambda;         /* >= 0 */
 } fbs_problem_desc;
 
@@ -136,9 +136,11 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
                               float* const* dL_dc, int pcg_iters, void* stream);
 
 /*
- * fbs_set_vector_precision -- how the CG state of later solves on this grid
- * is held (the paper fixes no precision; every variant keeps the CG inner
- * products FP64-accurate):
+ * fbs_set_option -- per-grid settings for later solves (host-side; no
+ * device work).  Errors: FBS_ERR_ARG for an unknown option or value.
+ *
+ * FBS_OPT_VECTOR_PRECISION: how the CG state is held (the paper fixes no
+ * precision; every variant keeps the CG inner products FP64-accurate):
  *   FBS_VECTORS_FP32         y, r, d, q in FP32; A d computed in FP32.
  *   FBS_VECTORS_COMPENSATED  y, d in FP32; the residual r as a pair of FP32
  *                            values (double-float) and q = A d recomputed in
@@ -148,10 +150,24 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *                            neighbour-table pass per iteration.
  *   FBS_VECTORS_AUTO         (default) compensated for fbs_solve_backward,
  *                            FP32 for fbs_solve and fbs_solve_robust.
- * Host-side setting; no device work.  Errors: FBS_ERR_ARG.
+ * FBS_OPT_PCG_LAUNCH: how the PCG iterations are launched:
+ *   FBS_PCG_PERSISTENT       (default) all iterations in one cooperative
+ *                            launch whose blocks meet at grid barriers (each
+ *                            wait bounded; on time-out the solve stops and
+ *                            FBS_ERR_TIMEOUT is latched).  Falls back to
+ *                            FBS_PCG_PER_PHASE when the cooperative launch is
+ *                            refused or the stream is being captured.
+ *   FBS_PCG_PER_PHASE        two launches per iteration (replayed from a CUDA
+ *                            graph when the same solve repeats).
+ * FBS_OPT_INJECT_BARRIER_TIMEOUT: value 1 makes the next persistent PCG
+ *   loop start with its barrier counter preset so that no barrier can
+ *   complete; every block waits out its bounded spin, latches
+ *   FBS_ERR_TIMEOUT and returns (a test of the failure path; one-shot).
  */
+enum { FBS_OPT_VECTOR_PRECISION = 1, FBS_OPT_PCG_LAUNCH = 2, FBS_OPT_INJECT_BARRIER_TIMEOUT = 3 };
 enum { FBS_VECTORS_AUTO = 0, FBS_VECTORS_FP32 = 1, FBS_VECTORS_COMPENSATED = 2 };
-fbs_status fbs_set_vector_precision(fbs_grid* g, int precision);
+enum { FBS_PCG_PERSISTENT = 0, FBS_PCG_PER_PHASE = 1 };
+fbs_status fbs_set_option(fbs_grid* g, int option, int value);
 
 /* Vertex count and offset (in the concatenated vertex order) of one image.
  * Host outputs; no device work. */

@@ -247,12 +247,14 @@ struct fbs_grid {
     size_t cap_vec = 0;                 // floats per vector
     float* vec = nullptr;               // 6 x cap_vec: y, r, r_lo, d0, d1, q
     int precision = FBS_VECTORS_AUTO;
+    int persistent = 1;
+    int inject_timeout = 0;
     float* a = nullptr;
     float2* nm = nullptr;
     size_t cap_scal = 0, cap_part = 0;
     Scal* scal = nullptr;
-    double* part = nullptr;
-    unsigned* cnt = nullptr;
+    float2* part = nullptr;             // 3 x cap_part: rs slot 0, rs slot 1, dq
+    unsigned* barrier = nullptr;        // grid-barrier words of the persistent PCG loop
     InstDev* inst = nullptr;
     std::vector<InstDev> inst_cached;
     // CUDA graphs of the solve segments, keyed by the exact launch arguments
@@ -286,7 +288,7 @@ void free_grid_memory(fbs_grid* g, cudaStream_t s)
     dfree(g->m, s); dfree(g->nbr, s); dfree(g->n64, s); dfree(g->n64b, s); dfree(g->nf, s);
     dfree(g->cell_voff, s); dfree(g->cell_nv, s); dfree(g->err, s); dfree(g->vt, s);
     dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s); dfree(g->part, s);
-    dfree(g->cnt, s); dfree(g->inst, s);
+    dfree(g->inst, s); dfree(g->barrier, s);
 }
 
 fbs_status latched(uint32_t bits)
@@ -532,7 +534,8 @@ fbs_status check_problems(const fbs_grid* g, const fbs_problem_desc* probs, int 
     if (!g || !probs || pcg_iters < 0) return FBS_ERR_ARG;
     for (int k = 0; k < g->n_images; ++k) {
         const fbs_problem_desc& p = probs[k];
-        if (!p.t || !p.c || p.channels < 1 || !(p.lambda >= 0.f) || !isfinite(p.lambda))
+        if (!p.t || !p.c || p.channels < 1 || p.channels > kMaxChannels || !(p.lambda >= 0.f) ||
+            !isfinite(p.lambda))
             return FBS_ERR_ARG;
     }
     if (g->bistoch_iters < 1) return FBS_ERR_STATE;
@@ -545,7 +548,8 @@ fbs_status check_problems(const fbs_grid* g, const fbs_problem_desc* probs, int 
 cudaError_t run_segment(fbs_grid* g, const SolveArgs& A, const SolvePlan& P, int seg, int mode,
                         cudaStream_t s)
 {
-    if (capturing(s) || prof_level() == 1) return launch_segment(A, P, seg, mode, s);
+    if (capturing(s) || prof_level() == 1 || (seg == kSegLoop && P.persistent))
+        return launch_segment(A, P, seg, mode, s);
     fbs_grid::GraphEntry* seen = nullptr;
     for (auto& e : g->graphs)
         if (e.seg == seg && e.mode == mode && memcmp(&e.A, &A, sizeof(A)) == 0 &&
@@ -640,12 +644,18 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     }
     plan.max_pixels = g->max_pixels;
     plan.chan_block = std::min(cmax, kChanBlock);
+    plan.cmax = cmax;
     // vector precision: FP32 state for forward and robust solves, the
     // compensated variant for the backward solve (whose right-hand side is
     // an arbitrary gradient) unless the caller chose otherwise
     if (g->precision == FBS_VECTORS_FP32) plan.comp = 0;
     else if (g->precision == FBS_VECTORS_COMPENSATED) plan.comp = 1;
     else plan.comp = plan.mode == kSplatBackward ? 1 : 0;
+    // the whole PCG loop as one cooperative launch, except inside a caller's
+    // stream capture (per-phase launches are captured instead)
+    plan.persistent = g->persistent && !capturing(s) ? 1 : 0;
+    plan.inject_timeout = plan.persistent ? g->inject_timeout : 0;
+    if (plan.persistent) g->inject_timeout = 0;
     const bool cap = capturing(s);
     cudaError_t e = cudaSuccess;
     if ((size_t)cv > g->cap_vec || (size_t)pc > g->cap_scal || (size_t)cpart > g->cap_part ||
@@ -653,7 +663,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
         if (cap) return FBS_ERR_STATE;   // size the workspace outside capture first
         free_graphs(g);
         dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s);
-        dfree(g->part, s); dfree(g->cnt, s); dfree(g->inst, s);
+        dfree(g->part, s); dfree(g->inst, s);
         g->inst_cached.clear();
         g->cap_vec = (size_t)std::max<int64_t>(cv, 1);
         g->cap_scal = (size_t)std::max(pc, 1);
@@ -662,9 +672,8 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
         if ((e = dalloc(&g->a, g->Vtot, s)) != cudaSuccess) return cuda_status(e);
         if ((e = dalloc(&g->nm, g->Vtot, s)) != cudaSuccess) return cuda_status(e);
         if ((e = dalloc(&g->scal, g->cap_scal, s)) != cudaSuccess) return cuda_status(e);
-        if ((e = dalloc(&g->part, g->cap_part, s)) != cudaSuccess) return cuda_status(e);
-        if ((e = dalloc(&g->cnt, (size_t)3 * g->n_images, s)) != cudaSuccess) return cuda_status(e);
-        if ((e = cudaMemsetAsync(g->cnt, 0, sizeof(unsigned) * 3 * g->n_images, s)) != cudaSuccess)
+        if ((e = dalloc(&g->part, 3 * g->cap_part, s)) != cudaSuccess) return cuda_status(e);
+        if (!g->barrier && (e = dalloc(&g->barrier, kBarrierWords, s)) != cudaSuccess)
             return cuda_status(e);
         if ((e = dalloc(&g->inst, (size_t)g->n_images, s)) != cudaSuccess) return cuda_status(e);
     }
@@ -696,8 +705,10 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.d[1] = g->vec + 4 * g->cap_vec;
     A.q = g->vec + 5 * g->cap_vec;
     A.scal = g->scal;
-    A.part = g->part;
-    A.cnt = g->cnt;
+    plan.barrier = g->barrier;
+    A.part_rs[0] = g->part;
+    A.part_rs[1] = g->part + g->cap_part;
+    A.part_dq = g->part + 2 * g->cap_part;
     A.err = g->err;
     return run_segments(g, A, plan, s);
 }
@@ -784,12 +795,25 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
     return run(g, inst, plan, (cudaStream_t)stream);
 }
 
-fbs_status fbs_set_vector_precision(fbs_grid* g, int precision)
+fbs_status fbs_set_option(fbs_grid* g, int option, int value)
 {
-    if (!g || precision < FBS_VECTORS_AUTO || precision > FBS_VECTORS_COMPENSATED)
-        return FBS_ERR_ARG;
-    g->precision = precision;
-    return FBS_OK;
+    if (!g) return FBS_ERR_ARG;
+    if (option == FBS_OPT_VECTOR_PRECISION) {
+        if (value < FBS_VECTORS_AUTO || value > FBS_VECTORS_COMPENSATED) return FBS_ERR_ARG;
+        g->precision = value;
+        return FBS_OK;
+    }
+    if (option == FBS_OPT_INJECT_BARRIER_TIMEOUT) {
+        if (value != 0 && value != 1) return FBS_ERR_ARG;
+        g->inject_timeout = value;
+        return FBS_OK;
+    }
+    if (option == FBS_OPT_PCG_LAUNCH) {
+        if (value != FBS_PCG_PERSISTENT && value != FBS_PCG_PER_PHASE) return FBS_ERR_ARG;
+        g->persistent = value == FBS_PCG_PERSISTENT ? 1 : 0;
+        return FBS_OK;
+    }
+    return FBS_ERR_ARG;
 }
 
 fbs_status fbs_grid_info(const fbs_grid* g, int image, int64_t* n_vertices, int64_t* vertex_offset)

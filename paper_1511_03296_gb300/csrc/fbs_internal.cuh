@@ -17,6 +17,10 @@ constexpr int kMaxTilePixels = 16384;    // pixels sorted by one CTA of the grid
 constexpr int kGridThreads = 512;        // CTA size of the grid-build kernels
 constexpr int kVTile = 256;              // vertices per PCG tile (= CTA size)
 constexpr int kChanBlock = 4;            // channels processed per pass of a PCG tile
+constexpr int kMaxChannels = 64;         // channels per image
+constexpr unsigned kBarrierGroups = 32;            // first-level counters of the grid barrier
+constexpr unsigned kBarrierWords = 32 * (kBarrierGroups + 1);
+constexpr unsigned kBarrierSpinLimit = 1u << 20;   // polls of >= 64 ns: >= 67 ms before a time-out
 
 // device error bits (latched in fbs_grid::err)
 enum : uint32_t {
@@ -78,12 +82,10 @@ struct InstDev {
     float* dc;              // N     (backward out)
 };
 
-// CG scalars of one (image, channel)
+// CG scalar carried between phases of one (image, channel): delta =
+// r^T M^-1 r of iteration `it` in slot it % 2
 struct Scal {
-    double delta;      // r^T M^-1 r of the current residual
-    double alpha;
-    double beta;
-    double dq;         // d^T A d of the last apply (diagnostic)
+    double delta[2];
 };
 
 // splat modes

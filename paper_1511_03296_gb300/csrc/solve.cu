@@ -4,12 +4,14 @@
 //
 // Every vertex kernel walks a table of CTA-sized vertex tiles; each tile
 // belongs to one image ("instance"), so one launch advances every (image,
-// channel) problem of a batch.  The two CG inner products of an iteration
-// are reduced per tile (exact FP32 products summed as double-float pairs in
-// registers, then FP64 across warps), stored as FP64 tile partials, and the
-// last tile of an image to finish (counted with an atomic) sums that image's
-// partials in a fixed order and updates its CG scalars -- so results are
-// bitwise reproducible run to run and no host round trip is needed.
+// channel) problem of a batch.  Each block takes a contiguous chunk of tiles.
+//
+// CG inner products: every tile writes, per channel, the sum of its exact
+// FP32 products as a double-float pair ("tile partial").  The next phase's
+// blocks each reduce the partials of the instances they touch, in a fixed
+// order, and form the CG scalar they need (alpha or beta) in FP64 -- every
+// block obtains the same value, so there is no grid-wide serial step, no
+// atomic and no fence, and results are bitwise reproducible.
 #include "fbs_internal.cuh"
 #include "solve.cuh"
 
@@ -24,78 +26,63 @@ __device__ __forceinline__ int64_t vec_index(const InstDev& I, int ch, int64_t v
 
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
 
-// Block-reduce CB double-float partials per channel and store each as the
-// FP64 partial of this tile.
+// contiguous chunk of tiles for this block
+__device__ __forceinline__ void block_chunk(int nvt, int& t0, int& t1)
+{
+    const int chunk = (nvt + gridDim.x - 1) / gridDim.x;
+    t0 = blockIdx.x * chunk;
+    t1 = min(t0 + chunk, nvt);
+}
+
+// Block-reduce the CB double-float partials per channel of this tile and
+// store them (one float2 per (tile, channel)).
 template <int CB>
 __device__ void store_tile_partials(DF (&acc)[CB], const InstDev& I, const VTile& vt, int cb,
-                                    double* __restrict__ part, double (*red)[kVTile / 32])
+                                    float2* __restrict__ part, DF (*red)[kVTile / 32])
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < CB; ++k) {
         DF s = df_warp_sum(acc[k]);
-        if (lane == 0) red[k][w] = df_to_double(s);
+        if (lane == 0) red[k][w] = s;
     }
     __syncthreads();
     if (threadIdx.x < CB) {
         const int k = threadIdx.x, ch = cb + k;
         if (ch < I.C) {
-            double t = 0.0;
-            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += red[k][j];
-            part[I.part_base + (int64_t)ch * I.ntiles + vt.t_in_inst] = t;
+            DF t = red[k][0];
+            for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = df_add(t, red[k][j]);
+            part[I.part_base + (int64_t)ch * I.ntiles + vt.t_in_inst] = make_float2(t.hi, t.lo);
         }
     }
     __syncthreads();
 }
 
-enum FinishKind { kFinishDelta0 = 0, kFinishAlpha = 1, kFinishBeta = 2 };
-
-// Called by every block after it wrote all partials of a tile: the last
-// tile of the image sums the image's partials (fixed order) and updates the
-// CG scalars of its channels.
-__device__ void finish_tile(const InstDev& I, int inst, double* __restrict__ part,
-                            unsigned* __restrict__ cnt, Scal* __restrict__ scal, int kind)
+// Sum, per channel, the tile partials of one instance (fixed order: lane j
+// takes tiles j, j+32, ... in groups of 8 loads issued together; then the
+// warp tree) into out[ch] (FP64).  Warps take channels round-robin.  Must
+// be called by the whole block.  Partials written earlier in the same kernel
+// by other blocks are read through L2 (ld.cg).
+__device__ void reduce_instance_partials(const float2* __restrict__ part, const InstDev& I,
+                                         double* out)
 {
-    __shared__ int s_last;
-    __shared__ double s_red[kVTile / 32];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(&cnt[inst], 1u);
-        s_last = prev == (unsigned)(I.ntiles - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int ch = 0; ch < I.C; ++ch) {
-        const double* p = part + I.part_base + (int64_t)ch * I.ntiles;
-        double t = 0.0;
-        for (int j = threadIdx.x; j < I.ntiles; j += blockDim.x) t += __ldcg(p + j);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int ch = w; ch < I.C; ch += nw) {
+        const float2* p = part + I.part_base + (int64_t)ch * I.ntiles;
+        DF t = {0.0f, 0.0f};
+        for (int j0 = lane; j0 < I.ntiles; j0 += 32 * 8) {
+            float2 v[8];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-        if (lane == 0) s_red[w] = t;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double total = 0.0;
-            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) total += s_red[j];
-            Scal& S = scal[I.pc + ch];
-            if (kind == kFinishDelta0) {
-                S.delta = total;
-                S.beta = 0.0;
-                S.alpha = 0.0;
-            } else if (kind == kFinishAlpha) {
-                S.dq = total;
-                S.alpha = (total > 0.0 && S.delta != 0.0) ? S.delta / total : 0.0;
-            } else {
-                const double old = S.delta;
-                S.delta = total;
-                S.beta = old != 0.0 ? total / old : 0.0;
+            for (int k = 0; k < 8; ++k) {
+                const int j = j0 + 32 * k;
+                v[k] = j < I.ntiles ? __ldcg(p + j) : make_float2(0.0f, 0.0f);
             }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t = df_add(t, DF{v[k].x, v[k].y});
         }
-        __syncthreads();
+        t = df_warp_sum(t);
+        if (lane == 0) out[ch] = df_to_double(t);
     }
-    if (threadIdx.x == 0) cnt[inst] = 0u;
 }
 
 // ---------------------------------------------------------------- splat ---
@@ -108,7 +95,9 @@ __global__ void __launch_bounds__(kVTile)
 splat_kernel(SolveArgs A, int mode, float sigma_gm, int comp)
 {
     const float s2 = sigma_gm * sigma_gm;
-    for (int tile = blockIdx.x; tile < A.nvt; tile += gridDim.x) {
+    int t0, t1;
+    block_chunk(A.nvt, t0, t1);
+    for (int tile = t0; tile < t1; ++tile) {
         const VTile vt = A.vt[tile];
         const InstDev I = A.inst[vt.inst];
         const int64_t v = vt.v0 + threadIdx.x;
@@ -225,6 +214,25 @@ __device__ __forceinline__ DF laplacian_apply(float av, float lam_n, const int32
     }
 }
 
+// Branch-free form over register arrays: nu[j] = n of neighbour j (0 when
+// absent, which makes its term an exact zero), zu[j] its (finite) value.
+template <bool COMP>
+__device__ __forceinline__ DF laplacian_apply_v(float av, float lam_n, float zv,
+                                                const float (&nu)[10], const float (&zu)[10])
+{
+    if (COMP) {
+        DF s = {0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < 10; ++j) s = df_add(s, df_mul_exact(nu[j], zv - zu[j]));
+        return df_add(df_mul_exact(av, zv), df_mul_f(s, lam_n));
+    } else {
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 10; ++j) s = fmaf(nu[j], zv - zu[j], s);
+        return DF{fmaf(av, zv, lam_n * s), 0.0f};
+    }
+}
+
 // topology of one vertex: neighbour ids, {n, M^-1} of the neighbours, a', {n, M^-1}
 struct VertexTopo {
     int32_t nb[10];
@@ -249,14 +257,16 @@ __device__ __forceinline__ void load_topo(const SolveArgs& A, int64_t v, bool va
 }
 
 // ------------------------------------------------------- initial residual ---
-// r = b - A y0 (b is in r, and in r_lo too when COMP), then r^T M^-1 r ->
-// delta, beta = 0.
+// r = b - A y0 (b is in r, and in r_lo too when COMP); tile partials of
+// r^T M^-1 r (delta_0) into rs slot 0.
 template <int CB, bool COMP>
 __global__ void __launch_bounds__(kVTile)
 residual_kernel(SolveArgs A)
 {
-    __shared__ double red[CB][kVTile / 32];
-    for (int tile = blockIdx.x; tile < A.nvt; tile += gridDim.x) {
+    __shared__ DF red[CB][kVTile / 32];
+    int t0, t1;
+    block_chunk(A.nvt, t0, t1);
+    for (int tile = t0; tile < t1; ++tile) {
         const VTile vt = A.vt[tile];
         const InstDev I = A.inst[vt.inst];
         const int64_t v = vt.v0 + threadIdx.x;
@@ -288,24 +298,64 @@ residual_kernel(SolveArgs A)
                     acc[k] = df_mul_exact(rhi, T.nmv.y * rhi);
                 }
             }
-            store_tile_partials<CB>(acc, I, vt, cb, A.part, red);
+            store_tile_partials<CB>(acc, I, vt, cb, A.part_rs[0], red);
         }
-        finish_tile(I, vt.inst, A.part, A.cnt + 0 * A.ninst, A.scal, kFinishDelta0);
     }
 }
 
-// ------------------------------------------------------- PCG phase 1 ---
-// d = M^-1 r + beta d_old (own vertex and, on the fly, its neighbours),
-// q = A d, partial d^T q; the last tile sets alpha = delta / d^T q.
-// COMP: q is not stored (phase 2 recomputes it exactly from d).
-template <int CB, bool COMP>
-__global__ void __launch_bounds__(kVTile)
-pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict__ dnew, int first)
+// Loads of CG vectors: plain in the per-phase kernels; through L2 (ld.cg)
+// in the persistent loop, where other blocks rewrite them between grid
+// barriers and an SM's L1 could otherwise hold a stale line.
+template <bool CO>
+__device__ __forceinline__ float ldv(const float* p)
 {
-    __shared__ double red[CB][kVTile / 32];
-    for (int tile = blockIdx.x; tile < A.nvt; tile += gridDim.x) {
+    return CO ? __ldcg(p) : *p;
+}
+
+// shared scratch of the two PCG phases
+template <int CB>
+struct PhaseSmem {
+    DF red[CB][kVTile / 32];
+    double sd[kMaxChannels];     // reduced inner products
+    float sf[kMaxChannels];      // beta (phase 1)
+    double sa[kMaxChannels];     // alpha (phase 2)
+};
+
+// ------------------------------------------------------- PCG phase 1 ---
+// Iteration `it`: delta_it = reduce(rs partials of slot it % 2);
+// beta = delta_it / delta_{it-1} (0 at it = 0); d = M^-1 r + beta d_old (own
+// vertex and, on the fly, its neighbours); q = A d; tile partials of d^T q.
+// delta_it is also stored (slot it % 2) for phase 2 and the next phase 1.
+// COMP: q is not stored (phase 2 recomputes it exactly from d).
+template <int CB, bool COMP, bool CO>
+__device__ void phase_apply(const SolveArgs& A, const float* __restrict__ dold,
+                            float* __restrict__ dnew, int it, int t0, int t1, PhaseSmem<CB>& S)
+{
+    const int slot = it & 1;
+    const bool first = it == 0;
+    int cur = -1;
+    for (int tile = t0; tile < t1; ++tile) {
         const VTile vt = A.vt[tile];
         const InstDev I = A.inst[vt.inst];
+        if (vt.inst != cur) {
+            __syncthreads();
+            reduce_instance_partials(A.part_rs[slot], I, S.sd);
+            __syncthreads();
+            if (threadIdx.x < I.C) {
+                const int ch = threadIdx.x;
+                const double dnow = S.sd[ch];
+                double beta = 0.0;
+                if (!first) {
+                    const double dprev = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1])
+                                            : A.scal[I.pc + ch].delta[slot ^ 1];
+                    beta = dprev != 0.0 ? dnow / dprev : 0.0;
+                }
+                S.sf[ch] = (float)beta;
+                A.scal[I.pc + ch].delta[slot] = dnow;   // same value from every block
+            }
+            __syncthreads();
+            cur = vt.inst;
+        }
         const int64_t v = vt.v0 + threadIdx.x;
         const bool valid = v < vt.v1;
         VertexTopo T;
@@ -319,14 +369,14 @@ pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict_
                 const int ch = cb + k;
                 if (valid && ch < I.C) {
                     const int64_t base = I.vec_base + (int64_t)ch * I.V - I.voff;
-                    const float beta = first ? 0.0f : (float)A.scal[I.pc + ch].beta;
+                    const float beta = S.sf[ch];
                     const float* r = A.r;
-                    float dv = T.nmv.y * r[base + v];
-                    if (!first) dv = fmaf(beta, dold[base + v], dv);
+                    float dv = T.nmv.y * ldv<CO>(r + base + v);
+                    if (!first) dv = fmaf(beta, ldv<CO>(dold + base + v), dv);
                     const DF q = laplacian_apply<COMP>(T.av, lam_n, T.nb, T.nmu, dv, [&](int j) {
                         const int64_t u = base + T.nb[j];
-                        float du = T.nmu[j].y * r[u];
-                        if (!first) du = fmaf(beta, dold[u], du);
+                        float du = T.nmu[j].y * ldv<CO>(r + u);
+                        if (!first) du = fmaf(beta, ldv<CO>(dold + u), du);
                         return du;
                     });
                     dnew[base + v] = dv;
@@ -338,26 +388,41 @@ pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict_
                     }
                 }
             }
-            store_tile_partials<CB>(acc, I, vt, cb, A.part, red);
+            store_tile_partials<CB>(acc, I, vt, cb, A.part_dq, S.red);
         }
-        finish_tile(I, vt.inst, A.part, A.cnt + 1 * A.ninst, A.scal, kFinishAlpha);
     }
 }
 
 // ------------------------------------------------------- PCG phase 2 ---
-// y += alpha d; r -= alpha q; partial r^T M^-1 r; the last tile sets
-// beta = delta_new / delta_old.
+// alpha = delta_it / reduce(d^T q partials) (0 if d^T q <= 0 or delta = 0);
+// y += alpha d; r -= alpha q; tile partials of r^T M^-1 r into rs slot
+// (it + 1) % 2.
 // COMP: q = A d is recomputed here with compensated arithmetic and the
 // residual is kept as a double-float pair (r, r_lo), so the recurrence
 // r <- r - alpha A d carries no rounding of q.
-template <int CB, bool COMP>
-__global__ void __launch_bounds__(kVTile)
-pcg_update_kernel(SolveArgs A, const float* __restrict__ d)
+template <int CB, bool COMP, bool CO>
+__device__ void phase_update(const SolveArgs& A, const float* __restrict__ d, int it, int t0,
+                             int t1, PhaseSmem<CB>& S)
 {
-    __shared__ double red[CB][kVTile / 32];
-    for (int tile = blockIdx.x; tile < A.nvt; tile += gridDim.x) {
+    const int slot = it & 1;
+    int cur = -1;
+    for (int tile = t0; tile < t1; ++tile) {
         const VTile vt = A.vt[tile];
         const InstDev I = A.inst[vt.inst];
+        if (vt.inst != cur) {
+            __syncthreads();
+            reduce_instance_partials(A.part_dq, I, S.sd);
+            __syncthreads();
+            if (threadIdx.x < I.C) {
+                const int ch = threadIdx.x;
+                const double delta = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot])
+                                        : A.scal[I.pc + ch].delta[slot];
+                const double dq = S.sd[ch];
+                S.sa[ch] = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
+            }
+            __syncthreads();
+            cur = vt.inst;
+        }
         const int64_t v = vt.v0 + threadIdx.x;
         const bool valid = v < vt.v1;
         VertexTopo T;
@@ -376,29 +441,321 @@ pcg_update_kernel(SolveArgs A, const float* __restrict__ d)
                 if (valid && ch < I.C) {
                     const int64_t base = I.vec_base + (int64_t)ch * I.V - I.voff;
                     const int64_t idx = base + v;
-                    const double alpha = A.scal[I.pc + ch].alpha;
-                    const float dv = d[idx];
-                    A.y[idx] = fmaf((float)alpha, dv, A.y[idx]);
+                    const double alpha = S.sa[ch];
+                    const float dv = ldv<CO>(d + idx);
+                    A.y[idx] = fmaf((float)alpha, dv, ldv<CO>(A.y + idx));
                     float rhi;
                     if (COMP) {
                         const DF q = laplacian_apply<true>(T.av, lam_n, T.nb, T.nmu, dv,
-                                                           [&](int j) { return d[base + T.nb[j]]; });
-                        const DF r = df_add(DF{A.r[idx], A.rlo[idx]},
+                                                           [&](int j) { return ldv<CO>(d + base + T.nb[j]); });
+                        const DF r = df_add(DF{ldv<CO>(A.r + idx), ldv<CO>(A.rlo + idx)},
                                             df_neg(df_mul(df_from_double(alpha), q)));
                         A.r[idx] = r.hi;
                         A.rlo[idx] = r.lo;
                         rhi = r.hi;
                     } else {
-                        rhi = fmaf(-(float)alpha, A.q[idx], A.r[idx]);
+                        rhi = fmaf(-(float)alpha, ldv<CO>(A.q + idx), ldv<CO>(A.r + idx));
                         A.r[idx] = rhi;
                     }
                     acc[k] = df_mul_exact(rhi, T.nmv.y * rhi);
                 }
             }
-            store_tile_partials<CB>(acc, I, vt, cb, A.part, red);
+            store_tile_partials<CB>(acc, I, vt, cb, A.part_rs[slot ^ 1], S.red);
         }
-        finish_tile(I, vt.inst, A.part, A.cnt + 2 * A.ninst, A.scal, kFinishBeta);
     }
+}
+
+template <int CB, bool COMP>
+__global__ void __launch_bounds__(kVTile)
+pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict__ dnew, int it)
+{
+    __shared__ PhaseSmem<CB> S;
+    int t0, t1;
+    block_chunk(A.nvt, t0, t1);
+    phase_apply<CB, COMP, false>(A, dold, dnew, it, t0, t1, S);
+}
+
+template <int CB, bool COMP>
+__global__ void __launch_bounds__(kVTile)
+pcg_update_kernel(SolveArgs A, const float* __restrict__ d, int it)
+{
+    __shared__ PhaseSmem<CB> S;
+    int t0, t1;
+    block_chunk(A.nvt, t0, t1);
+    phase_update<CB, COMP, false>(A, d, it, t0, t1, S);
+}
+
+// ------------------------------------------------- persistent PCG loop ---
+// Grid barrier for a cooperative launch.  Thread 0 of each block arrives on
+// its group's counter (groups of consecutive blocks, each counter on its own
+// 128-byte line); the last arrival of a group arrives on the top counter;
+// the last group to arrive resets the top counter and advances the
+// generation word that every block polls.  Layout of `bar` (words): [0] top
+// counter, [1] generation, [32 g] counter of group g.  Every wait is
+// bounded: on time-out the block records kErrTimeout and false is returned.
+__device__ bool grid_barrier(unsigned* bar, uint32_t* err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned* top = bar;
+        unsigned* gen = bar + 1;
+        const unsigned gsize = (gridDim.x + kBarrierGroups - 1) / kBarrierGroups;
+        const unsigned ngroups = (gridDim.x + gsize - 1) / gsize;
+        const unsigned grp = blockIdx.x / gsize;
+        const unsigned members = min(gsize, gridDim.x - grp * gsize);
+        unsigned* gcount = bar + 32 * (grp + 1);
+        const unsigned g = *(volatile unsigned*)gen;
+        __threadfence();
+        bool released = false;
+        if (atomicAdd(gcount, 1u) == members - 1) {
+            *(volatile unsigned*)gcount = 0u;
+            if (atomicAdd(top, 1u) == ngroups - 1) {
+                *(volatile unsigned*)top = 0u;
+                __threadfence();
+                atomicAdd(gen, 1u);
+                released = true;
+            }
+        }
+        if (!released) {
+            unsigned spins = 0;
+            while (*(volatile unsigned*)gen == g) {
+                if (++spins > kBarrierSpinLimit) {
+                    atomicOr(err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// All `iters` PCG iterations in one cooperative launch: phase 1, barrier,
+// phase 2, barrier.  Every block keeps the same chunk of tiles throughout.
+template <int CB, bool COMP>
+__global__ void __launch_bounds__(kVTile)
+pcg_loop_kernel(SolveArgs A, int iters, unsigned* bar)
+{
+    __shared__ PhaseSmem<CB> S;
+    int t0, t1;
+    block_chunk(A.nvt, t0, t1);
+    for (int it = 0; it < iters; ++it) {
+        const float* dold = A.d[(it + 1) & 1];
+        float* dnew = A.d[it & 1];
+        phase_apply<CB, COMP, true>(A, dold, dnew, it, t0, t1, S);
+        if (!grid_barrier(bar, A.err)) return;
+        phase_update<CB, COMP, true>(A, dnew, it, t0, t1, S);
+        if (!grid_barrier(bar, A.err)) return;
+    }
+}
+
+// ------------------------------------------ resident persistent PCG loop ---
+// The same iterations when every tile has its own co-resident block and an
+// image has at most CB channels: each block keeps its tile's neighbour ids
+// and neighbours' {n, M^-1} in shared memory for the whole loop, and each
+// thread keeps its vertex's r, y, d (and q) in registers, writing d and r for
+// the neighbours and y once at the end.  Neighbour gathers use a safe index
+// (the vertex itself when a neighbour is absent) so they issue together.
+
+// All threads sum the tile partials of one instance for all its channels
+// (thread t takes tiles t, t + blockDim, ...), then a block tree; out[ch].
+template <int CB>
+__device__ void reduce_partials_all(const float2* __restrict__ part, const InstDev& I,
+                                    double* out, DF (*red)[kVTile / 32])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    DF acc[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) acc[k] = {0.0f, 0.0f};
+    for (int j0 = threadIdx.x; j0 < I.ntiles; j0 += 2 * blockDim.x) {
+        float2 v[CB][2];
+#pragma unroll
+        for (int k = 0; k < CB; ++k)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = j0 + h * blockDim.x;
+                v[k][h] = (k < I.C && j < I.ntiles)
+                              ? __ldcg(part + I.part_base + (int64_t)k * I.ntiles + j)
+                              : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+        for (int k = 0; k < CB; ++k)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) acc[k] = df_add(acc[k], DF{v[k][h].x, v[k][h].y});
+    }
+#pragma unroll
+    for (int k = 0; k < CB; ++k) {
+        const DF t = df_warp_sum(acc[k]);
+        if (lane == 0) red[k][w] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < CB && threadIdx.x < I.C) {
+        const int k = threadIdx.x;
+        DF t = red[k][0];
+        for (int j = 1; j < nw; ++j) t = df_add(t, red[k][j]);
+        out[k] = df_to_double(t);
+    }
+    __syncthreads();
+}
+
+template <int CB>
+__device__ __forceinline__ void store_partials_resident(DF (&acc)[CB], const InstDev& I,
+                                                        const VTile& vt, float2* __restrict__ part,
+                                                        DF (*red)[kVTile / 32])
+{
+    store_tile_partials<CB>(acc, I, vt, 0, part, red);
+}
+
+template <int CB, bool COMP>
+__global__ void __launch_bounds__(kVTile, 3)
+pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
+{
+    __shared__ int32_t s_nb[10][kVTile];
+    __shared__ float2 s_nmu[10][kVTile];
+    __shared__ PhaseSmem<CB> S;
+    const VTile vt = A.vt[blockIdx.x];
+    const InstDev I = A.inst[vt.inst];
+    const int64_t v = vt.v0 + threadIdx.x;
+    const bool valid = v < vt.v1;
+    const int tx = threadIdx.x;
+    // topology, once
+    float av = 0.0f;
+    float2 nmv = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        const int32_t u = valid ? A.nbr[(int64_t)k * A.Vtot + v] : -1;
+        s_nb[k][tx] = u;
+        s_nmu[k][tx] = u >= 0 ? A.nm[u] : make_float2(0.0f, 0.0f);
+    }
+    if (valid) {
+        av = A.a[v];
+        nmv = A.nm[v];
+    }
+    const float lam_n = I.lam * nmv.x;
+    // own state in registers
+    float r[CB], rlo[CB], y[CB], d[CB], q[CB];
+    int64_t base[CB];
+#pragma unroll
+    for (int k = 0; k < CB; ++k) {
+        base[k] = I.vec_base + (int64_t)min(k, I.C - 1) * I.V - I.voff;
+        const bool on = valid && k < I.C;
+        r[k] = on ? A.r[base[k] + v] : 0.0f;
+        rlo[k] = on && COMP ? A.rlo[base[k] + v] : 0.0f;
+        y[k] = on ? A.y[base[k] + v] : 0.0f;
+        d[k] = 0.0f;
+        q[k] = 0.0f;
+    }
+    const int64_t vs = valid ? v : vt.v0;   // safe gather index for absent neighbours
+    for (int it = 0; it < iters; ++it) {
+        const int slot = it & 1;
+        const float* dold = A.d[(it + 1) & 1];
+        float* dnew = A.d[it & 1];
+        // ---- phase 1
+        reduce_partials_all<CB>(A.part_rs[slot], I, S.sd, S.red);
+        if (threadIdx.x < I.C && threadIdx.x < CB) {
+            const int ch = threadIdx.x;
+            double beta = 0.0;
+            if (it > 0) {
+                const double dprev = __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1]);
+                beta = dprev != 0.0 ? S.sd[ch] / dprev : 0.0;
+            }
+            S.sf[ch] = (float)beta;
+            A.scal[I.pc + ch].delta[slot] = S.sd[ch];
+        }
+        __syncthreads();
+        {
+            DF acc[CB];
+            float ru[CB][10], du[CB][10], nu[10], mu[10];
+#pragma unroll
+            for (int j = 0; j < 10; ++j) {
+                const int32_t u0 = s_nb[j][tx];
+                const int64_t u = u0 >= 0 ? u0 : vs;
+                const float2 nm = s_nmu[j][tx];
+                nu[j] = nm.x;
+                mu[j] = nm.y;
+#pragma unroll
+                for (int k = 0; k < CB; ++k) {
+                    ru[k][j] = __ldcg(A.r + base[k] + u);
+                    du[k][j] = it > 0 ? __ldcg(dold + base[k] + u) : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                acc[k] = {0.0f, 0.0f};
+                if (valid && k < I.C) {
+                    const float beta = S.sf[k];
+                    const float dv = fmaf(beta, d[k], nmv.y * r[k]);
+                    float dz[10];
+#pragma unroll
+                    for (int j = 0; j < 10; ++j) dz[j] = fmaf(beta, du[k][j], mu[j] * ru[k][j]);
+                    const DF qq = laplacian_apply_v<COMP>(av, lam_n, dv, nu, dz);
+                    d[k] = dv;
+                    q[k] = qq.hi;
+                    dnew[base[k] + v] = dv;
+                    acc[k] = COMP ? df_add(df_mul_exact(dv, qq.hi), DF{dv * qq.lo, 0.0f})
+                                  : df_mul_exact(dv, qq.hi);
+                }
+            }
+            store_partials_resident<CB>(acc, I, vt, A.part_dq, S.red);
+        }
+        if (!grid_barrier(bar, A.err)) return;
+        // ---- phase 2
+        reduce_partials_all<CB>(A.part_dq, I, S.sd, S.red);
+        if (threadIdx.x < I.C && threadIdx.x < CB) {
+            const int ch = threadIdx.x;
+            const double delta = __ldcg(&A.scal[I.pc + ch].delta[slot]);
+            const double dq = S.sd[ch];
+            S.sa[ch] = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
+        }
+        __syncthreads();
+        {
+            DF acc[CB];
+            float dn[CB][10], nu[10];
+            if (COMP) {
+#pragma unroll
+                for (int j = 0; j < 10; ++j) {
+                    const int32_t u0 = s_nb[j][tx];
+                    const int64_t u = u0 >= 0 ? u0 : vs;
+                    nu[j] = s_nmu[j][tx].x;
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) dn[k][j] = __ldcg(dnew + base[k] + u);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < CB; ++k) {
+                acc[k] = {0.0f, 0.0f};
+                if (valid && k < I.C) {
+                    const double alpha = S.sa[k];
+                    y[k] = fmaf((float)alpha, d[k], y[k]);
+                    if (COMP) {
+                        const DF qq = laplacian_apply_v<true>(av, lam_n, d[k], nu, dn[k]);
+                        const DF rr = df_add(DF{r[k], rlo[k]},
+                                             df_neg(df_mul(df_from_double(alpha), qq)));
+                        r[k] = rr.hi;
+                        rlo[k] = rr.lo;
+                    } else {
+                        r[k] = fmaf(-(float)alpha, q[k], r[k]);
+                    }
+                    A.r[base[k] + v] = r[k];
+                    acc[k] = df_mul_exact(r[k], nmv.y * r[k]);
+                }
+            }
+            store_partials_resident<CB>(acc, I, vt, A.part_rs[slot ^ 1], S.red);
+        }
+        if (!grid_barrier(bar, A.err)) return;
+    }
+#pragma unroll
+    for (int k = 0; k < CB; ++k)
+        if (valid && k < I.C) {
+            A.y[base[k] + v] = y[k];
+            if (COMP) A.rlo[base[k] + v] = rlo[k];
+        }
 }
 
 // ---------------------------------------------------------------- slice ---
@@ -487,16 +844,47 @@ cudaError_t launch_segment_t(const SolveArgs& A, const SolvePlan& P, int seg, in
         residual_kernel<CB, COMP><<<persistent_blocks(occ_r, A.nvt), kVTile, 0, s>>>(A);
         prof_end(f_res, s);
     } else if (seg == kSegLoop) {
+        if (P.persistent && P.pcg_iters > 0) {
+            static const int occ_l = occupancy((const void*)pcg_loop_kernel<CB, COMP>);
+            static const int occ_res = occupancy((const void*)pcg_resident_kernel<CB, COMP>);
+            static int f_loop = prof_family("pcg_loop");
+            static int f_res_loop = prof_family("pcg_resident");
+            const bool resident = P.cmax <= CB && A.nvt <= device_info().sms * occ_res;
+            // barrier words zero (or, for the failure-path test, a top counter
+            // that the last arrival can never match)
+            cudaError_t e = cudaMemsetAsync(P.barrier, 0, kBarrierWords * sizeof(unsigned), s);
+            if (e == cudaSuccess && P.inject_timeout)   // top counter = 0x40000000 (little-endian)
+                e = cudaMemsetAsync(reinterpret_cast<unsigned char*>(P.barrier) + 3, 0x40, 1, s);
+            if (e != cudaSuccess) return e;
+            SolveArgs a = A;
+            int iters = P.pcg_iters;
+            unsigned* bar = P.barrier;
+            void* args[] = {&a, &iters, &bar};
+            if (resident) {
+                prof_begin(f_res_loop, s);
+                e = cudaLaunchCooperativeKernel((const void*)pcg_resident_kernel<CB, COMP>,
+                                                dim3(A.nvt), dim3(kVTile), args, 0, s);
+                prof_end(f_res_loop, s);
+            } else {
+                const int nb_l = persistent_blocks(occ_l, A.nvt);
+                prof_begin(f_loop, s);
+                e = cudaLaunchCooperativeKernel((const void*)pcg_loop_kernel<CB, COMP>, dim3(nb_l),
+                                                dim3(kVTile), args, 0, s);
+                prof_end(f_loop, s);
+            }
+            if (e == cudaSuccess) return cudaGetLastError();
+            cudaGetLastError();   // clear, and fall back to per-phase launches
+        }
         const int nb_p = persistent_blocks(occ_p, A.nvt);
         const int nb_u = persistent_blocks(occ_u, A.nvt);
         for (int it = 0; it < P.pcg_iters; ++it) {
             const float* dold = A.d[(it + 1) & 1];
             float* dnew = A.d[it & 1];
             prof_begin(f_apply, s);
-            pcg_apply_kernel<CB, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it == 0);
+            pcg_apply_kernel<CB, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
             prof_end(f_apply, s);
             prof_begin(f_update, s);
-            pcg_update_kernel<CB, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew);
+            pcg_update_kernel<CB, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
             prof_end(f_update, s);
         }
     } else {

@@ -29,8 +29,8 @@ struct SolveArgs {
     float* q;
     // reductions
     Scal* scal;                // sum_k C_k
-    double* part;              // sum_k C_k * ntiles_k
-    unsigned* cnt;             // 3 x ninst arrival counters (zero between launches)
+    float2* part_rs[2];        // sum_k C_k * ntiles_k double-float tile partials of r^T M^-1 r
+    float2* part_dq;           // ... of d^T A d
     uint32_t* err;
 };
 
@@ -40,10 +40,14 @@ struct SolvePlan {
     int pcg_iters;
     float sigma_gm;
     int chan_block;            // channels per tile pass (1..4)
+    int cmax;                  // most channels of any image
     int64_t max_pixels;        // largest image
     int64_t max_cv;            // largest C x V block
     bool export_y;
     int comp;                  // 1: compensated residual / recomputed q variant
+    int persistent;            // 1: the whole PCG loop in one cooperative launch
+    unsigned* barrier;         // kBarrierWords words of grid-barrier state (persistent loop)
+    int inject_timeout;        // preset the barrier counter so no wait completes (test)
 };
 
 // A solve runs as segments: for each outer (IRLS) iteration a setup (splat,

@@ -24,9 +24,11 @@ STATUS_NAMES = {0: "FBS_OK", 1: "FBS_ERR_ARG", 2: "FBS_ERR_RANGE", 3: "FBS_ERR_O
 EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robust",
             "fbs_solve_backward", "fbs_grid_info", "fbs_grid_export", "fbs_grid_sync",
             "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read",
-            "fbs_set_vector_precision"]
+            "fbs_set_option"]
 
+OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT = 1, 2, 3
 VECTORS_AUTO, VECTORS_FP32, VECTORS_COMPENSATED = 0, 1, 2
+PCG_PERSISTENT, PCG_PER_PHASE = 0, 1
 
 
 class FbsError(RuntimeError):
@@ -73,7 +75,7 @@ def load(path: Optional[str] = None):
         L.fbs_grid_info.argtypes = [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64)]
         L.fbs_grid_export.argtypes = [P, I, P, P, P, P, P, P]
         L.fbs_grid_sync.argtypes = [P, P]
-        L.fbs_set_vector_precision.argtypes = [P, I]
+        L.fbs_set_option.argtypes = [P, I, I]
         L.fbs_grid_destroy.argtypes = [P, P]
         L.fbs_status_string.argtypes = [I]
         L.fbs_status_string.restype = ctypes.c_char_p
@@ -227,10 +229,14 @@ def solve_backward(grid: Grid, t: List, c: List, lam, yhat: List, dL_dx: List, d
                                      _stream_ptr(stream)), "fbs_solve_backward")
 
 
+def set_option(grid: Grid, option: int, value: int) -> None:
+    """OPT_VECTOR_PRECISION: VECTORS_AUTO / VECTORS_FP32 / VECTORS_COMPENSATED;
+    OPT_PCG_LAUNCH: PCG_PERSISTENT / PCG_PER_PHASE (see include/fbs.h)."""
+    _check(load().fbs_set_option(grid.handle, int(option), int(value)), "fbs_set_option")
+
+
 def set_vector_precision(grid: Grid, precision: int) -> None:
-    """VECTORS_AUTO (default), VECTORS_FP32 or VECTORS_COMPENSATED (see include/fbs.h)."""
-    _check(load().fbs_set_vector_precision(grid.handle, int(precision)),
-           "fbs_set_vector_precision")
+    set_option(grid, OPT_VECTOR_PRECISION, precision)
 
 
 def grid_info(grid: Grid, image: int):

@@ -19,11 +19,15 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+PCG_LAUNCH = {"mode": 0}    # fbs.PCG_PERSISTENT; tests may switch to PCG_PER_PHASE
+
+
 def gpu_grid(insts, bistoch_iters=2):
     from paper_1511_03296_gb300 import fbs
     yuv = [to_dev(i.yuv) for i in insts]
     g = fbs.grid_build(yuv, [i.sigma_xy for i in insts], [i.sigma_l for i in insts],
                        [i.sigma_uv for i in insts])
+    fbs.set_option(g, fbs.OPT_PCG_LAUNCH, PCG_LAUNCH["mode"])
     if bistoch_iters:
         fbs.bistochastize(g, bistoch_iters)
     return g

@@ -7,8 +7,8 @@ import numpy as np
 import pytest
 
 from paper_1511_03296_gb300 import synth
-from tests.gpu_util import (REL_L2_TOL, assert_grid_bit_exact, gpu_grid, gpu_solve, oracle_grid,
-                            rel_l2, to_dev)
+from tests.gpu_util import (PCG_LAUNCH, REL_L2_TOL, assert_grid_bit_exact, gpu_grid, gpu_solve,
+                            oracle_grid, rel_l2, to_dev)
 
 import oracle
 
@@ -70,12 +70,19 @@ def _check_solve(insts, iters=25, tol=REL_L2_TOL):
     return errs
 
 
-def test_solve_plain_64x48():
+@pytest.fixture(params=["persistent", "per_phase"])
+def pcg_launch(request):
+    PCG_LAUNCH["mode"] = 0 if request.param == "persistent" else 1
+    yield request.param
+    PCG_LAUNCH["mode"] = 0
+
+
+def test_solve_plain_64x48(pcg_launch):
     _check_solve(synth.plain_64x48().instances)
 
 
 @pytest.mark.parametrize("iters", [0, 1, 2, 5, 50])
-def test_solve_iteration_counts(iters):
+def test_solve_iteration_counts(iters, pcg_launch):
     _check_solve([_inst(10, 70, 90, (8.0, 4.0, 3.0), C=2, npoly=6)], iters)
 
 
@@ -101,7 +108,7 @@ def test_solve_zero_confidence_channels_and_vertices():
     _check_solve([inst])
 
 
-def test_batched_uneven_images():
+def test_batched_uneven_images(pcg_launch):
     insts = [_inst(20, 37, 53, (3.3, 5.0, 7.7), C=1, lam=32.0),
              _inst(21, 120, 160, (8.0, 4.0, 3.0), C=2, lam=128.0, npoly=8),
              _inst(22, 9, 300, (16.0, 8.0, 8.0), C=3, lam=4.0),
@@ -113,7 +120,7 @@ def test_batched_uneven_images():
     _check_solve(insts)
 
 
-def test_full_1080p_parity():
+def test_full_1080p_parity(pcg_launch):
     # the benchmark's workload: 1920 x 1080, C = 3, sigma = (16, 8, 8), lambda = 128
     wl = synth.plain_1080p()
     inst = wl.instances[0]
@@ -124,7 +131,7 @@ def test_full_1080p_parity():
     print("1080p rel-L2 (y, x):", errs)
 
 
-def test_graph_replay_picks_up_new_inputs():
+def test_graph_replay_picks_up_new_inputs(pcg_launch):
     # the second and later solves with the same buffers replay a CUDA graph;
     # new target contents and a new lambda must still be honoured
     import torch
@@ -144,7 +151,7 @@ def test_graph_replay_picks_up_new_inputs():
         assert rel_l2(x.cpu().numpy().reshape(2, -1), ox) <= REL_L2_TOL, k
 
 
-def test_deterministic():
+def test_deterministic(pcg_launch):
     inst = _inst(13, 100, 140, (8.0, 4.0, 3.0), C=2, npoly=8)
     g = gpu_grid([inst], 2)
     x1, y1 = gpu_solve(g, [inst], 25)
@@ -170,7 +177,7 @@ def _robust_parity(inst, sigma_gm, irls, pcg, tol):
     return ey, ex
 
 
-def test_robust_small():
+def test_robust_small(pcg_launch):
     rng = np.random.Generator(np.random.PCG64(31))
     inst = synth.robust_instance(rng, 120, 160, 8, (8.0, 8.0, 8.0), 4.0)
     _robust_parity(inst, 8.0, 4, 25, REL_L2_TOL)
@@ -221,7 +228,7 @@ def _backward_parity(inst, iters=25, tol=REL_L2_TOL):
     return e_t, e_c
 
 
-def test_backward_seg_crop_21ch():
+def test_backward_seg_crop_21ch(pcg_launch):
     rng = np.random.Generator(np.random.PCG64(5))
     inst = synth.segmentation_instance(rng, 48, 64, 21, (8.0, 4.0, 3.0), 128.0, blob_sigma=6.0)
     _backward_parity(synth.crop(inst, 8, 16, 24, 32))
@@ -318,6 +325,21 @@ def test_solve_before_bistochastize_is_a_state_error():
     g = gpu_grid([inst], 0)
     with pytest.raises(fbs.FbsError, match="STATE"):
         gpu_solve(g, [inst], 5)
+
+
+def test_barrier_timeout_is_reported_and_recoverable():
+    # every grid barrier of the persistent PCG loop is made unreachable: the
+    # bounded waits run out, the kernel returns and the host reads the status
+    from paper_1511_03296_gb300 import fbs
+    inst = _inst(26, 60, 80, (8.0, 4.0, 3.0), C=1, npoly=5)
+    g = gpu_grid([inst], 2)
+    fbs.set_option(g, fbs.OPT_INJECT_BARRIER_TIMEOUT, 1)
+    with pytest.raises(fbs.FbsError, match="TIMEOUT"):
+        gpu_solve(g, [inst], 25)
+    xs, ys = gpu_solve(g, [inst], 25)     # the next solve is clean
+    og = oracle_grid(inst, 2)
+    oy, _ = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
+    assert rel_l2(ys[0], oy) <= REL_L2_TOL
 
 
 def test_bad_arguments():
