@@ -169,6 +169,31 @@ enum { FBS_VECTORS_AUTO = 0, FBS_VECTORS_FP32 = 1, FBS_VECTORS_COMPENSATED = 2 }
 enum { FBS_PCG_PERSISTENT = 0, FBS_PCG_PER_PHASE = 1 };
 fbs_status fbs_set_option(fbs_grid* g, int option, int value);
 
+/*
+ * fbs_solve_static -- fbs_solve for callers that cannot allocate device
+ * memory (a fixed memory budget handed over up front, a real-time loop that
+ * must never enter an allocator, an embedding runtime whose own allocator
+ * owns the device).  There is no counterpart in the paper: it is the same
+ * forward solve, but every piece of scratch (CG vectors, diag(A), inner
+ * product partials, grid-barrier words, image descriptors) comes from one
+ * 64 MiB array compiled into the library, and the call allocates nothing.
+ * The grid (built earlier by fbs_grid_build) and all inputs and outputs
+ * are the caller's, with the same meaning as for fbs_solve; the CG state is
+ * FP32 unless FBS_OPT_VECTOR_PRECISION selects the compensated variant, and
+ * no CUDA graph is used.
+ *
+ * Limits and sharing: the array holds 6 float vectors of sum_k C_k V_k
+ * entries plus per-vertex and per-tile terms; a problem that does not fit
+ * returns FBS_ERR_ARG.  Every GPU that loads the library holds the array
+ * until the process exits.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) -- make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents: calls whose work overlaps on the GPU race, so
+ * serialise them (one stream, or events).
+ */
+fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters,
+                            void* stream);
+
 /* Vertex count and offset (in the concatenated vertex order) of one image.
  * Host outputs; no device work. */
 fbs_status fbs_grid_info(const fbs_grid* g, int image, int64_t* n_vertices,

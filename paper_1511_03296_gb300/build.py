@@ -18,8 +18,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfbs.so")
-SOURCES = ["api.cu", "grid.cu", "solve.cu"]
-HEADERS = ["fbs_internal.cuh", "solve.cuh", os.path.join("..", "..", "include", "fbs.h")]
+SOURCES = ["api.cu", "grid.cu", "solve.cu", "solve_static.cu"]
+HEADERS = ["fbs_internal.cuh", "solve.cuh", "grid_view.cuh",
+           os.path.join("..", "..", "include", "fbs.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -935,3 +935,34 @@ fbs_status fbs_profile_read(int* count, const char** names, int64_t* launches, d
 }
 
 }  // extern "C"
+
+#include "grid_view.cuh"
+
+namespace fbs {
+
+bool grid_view(const fbs_grid* g, GridView* out)
+{
+    if (!g || !out) return false;
+    out->n_images = g->n_images;
+    out->Vtot = g->Vtot;
+    out->max_pixels = g->max_pixels;
+    out->nvt = g->nvt;
+    out->bistoch_iters = g->bistoch_iters;
+    out->precision = g->precision;
+    out->persistent = g->persistent;
+    out->img = g->img.data();
+    out->voff = g->voff.data();
+    out->vt0 = g->vt0.data();
+    out->nvt_img = g->nvt_img.data();
+    out->vt = g->vt;
+    out->nbr = g->nbr;
+    out->n64 = g->n64;
+    out->m = g->m;
+    out->pstart = g->pstart;
+    out->perm = g->perm;
+    out->vid = g->vid;
+    out->err = g->err;
+    return true;
+}
+
+}  // namespace fbs

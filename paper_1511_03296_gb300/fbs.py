@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "FBS_OK", 1: "FBS_ERR_ARG", 2: "FBS_ERR_RANGE", 3: "FBS_ERR_O
 EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robust",
             "fbs_solve_backward", "fbs_grid_info", "fbs_grid_export", "fbs_grid_sync",
             "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read",
-            "fbs_set_option"]
+            "fbs_set_option", "fbs_solve_static"]
 
 OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT = 1, 2, 3
 VECTORS_AUTO, VECTORS_FP32, VECTORS_COMPENSATED = 0, 1, 2
@@ -76,6 +76,7 @@ def load(path: Optional[str] = None):
         L.fbs_grid_export.argtypes = [P, I, P, P, P, P, P, P]
         L.fbs_grid_sync.argtypes = [P, P]
         L.fbs_set_option.argtypes = [P, I, I]
+        L.fbs_solve_static.argtypes = [P, ctypes.POINTER(ProblemDesc), I, P]
         L.fbs_grid_destroy.argtypes = [P, P]
         L.fbs_status_string.argtypes = [I]
         L.fbs_status_string.restype = ctypes.c_char_p
@@ -206,6 +207,16 @@ def solve(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25, x: Optional[Li
     """Forward solve; writes x (C x H x W) and/or y (C x V) per image."""
     probs = _problems(grid, t, c, lam, x, y)
     _check(load().fbs_solve(grid.handle, probs, int(pcg_iters), _stream_ptr(stream)), "fbs_solve")
+
+
+def solve_static(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25,
+                 x: Optional[List] = None, y: Optional[List] = None, stream=None) -> None:
+    """fbs_solve without any device allocation: the solver's scratch lives in
+    a fixed 64 MiB array inside the library (for callers that cannot
+    allocate; calls must not overlap on the GPU -- see include/fbs.h)."""
+    probs = _problems(grid, t, c, lam, x, y)
+    _check(load().fbs_solve_static(grid.handle, probs, int(pcg_iters), _stream_ptr(stream)),
+           "fbs_solve_static")
 
 
 def solve_robust(grid: Grid, t: List, c: List, lam, sigma_gm: float, irls_iters: int = 10,
