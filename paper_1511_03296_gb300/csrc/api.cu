@@ -15,18 +15,18 @@
 
 namespace fbs {
 // launchers defined in grid.cu
-cudaError_t launch_grid_count(const GTile*, int, const ImgDev*, int*, uint32_t*, int, cudaStream_t);
-cudaError_t launch_scan_tiles(const int*, int64_t*, int, cudaStream_t);
-cudaError_t launch_grid_fill(const GTile*, int, const ImgDev*, const int64_t*, uint32_t*, int, int,
-                             uint64_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+cudaError_t launch_grid_sort(const GTile*, int, const ImgDev*, int*, uint32_t*, int, int,
+                             uint32_t*, uint32_t*, uint64_t*, uint32_t*, uint32_t*, uint32_t*,
                              uint32_t*, cudaStream_t);
+cudaError_t launch_scan_tiles(const int*, int64_t*, int, cudaStream_t);
+cudaError_t launch_grid_finalize(const GTile*, int, const ImgDev*, const int64_t*, uint32_t*,
+                                 const uint64_t*, const uint32_t*, const uint32_t*, uint64_t*,
+                                 uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
 cudaError_t launch_grid_neighbours(const GTile*, int, const ImgDev*, const int64_t*,
                                    const uint64_t*, const uint32_t*, const uint32_t*, int32_t*,
                                    int64_t, cudaStream_t);
 cudaError_t launch_bistoch(const double*, double*, float*, const uint32_t*, const int32_t*,
                            int64_t, int, int, cudaStream_t);
-size_t grid_smem_count(int P2);
-size_t grid_smem_fill(int P2, int max_cells);
 
 // ----------------------------------------------------------- device info ---
 const DeviceInfo& device_info()
@@ -242,6 +242,10 @@ struct fbs_grid {
     uint32_t* err = nullptr;
     VTile* vt = nullptr;
     int nvt = 0;
+    GTile* gt = nullptr;                // grid tiles, kept for the splat
+    int64_t* gt_voff = nullptr;
+    int ngt = 0;
+    int gt_p2 = 0;
     int bistoch_iters = 0;
     // solve workspace
     size_t cap_vec = 0;                 // floats per vector
@@ -287,6 +291,7 @@ void free_grid_memory(fbs_grid* g, cudaStream_t s)
     dfree(g->vkey, s); dfree(g->vid, s); dfree(g->perm, s); dfree(g->pstart, s);
     dfree(g->m, s); dfree(g->nbr, s); dfree(g->n64, s); dfree(g->n64b, s); dfree(g->nf, s);
     dfree(g->cell_voff, s); dfree(g->cell_nv, s); dfree(g->err, s); dfree(g->vt, s);
+    dfree(g->gt, s); dfree(g->gt_voff, s);
     dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s); dfree(g->part, s);
     dfree(g->inst, s); dfree(g->barrier, s);
 }
@@ -410,6 +415,9 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
     GTile* d_tiles = nullptr;
     int* d_tile_nv = nullptr;
     int64_t* d_tile_voff = nullptr;
+    uint64_t* d_tkey = nullptr;
+    uint32_t* d_tm = nullptr;
+    uint32_t* d_tps = nullptr;
     cudaError_t e = cudaSuccess;
     fbs_status st = FBS_OK;
     std::vector<int64_t> tile_voff(ntiles + 1);
@@ -423,12 +431,20 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
     FBS_TRY(dalloc(&d_tiles, tiles.size(), s));
     FBS_TRY(dalloc(&d_tile_nv, (size_t)ntiles, s));
     FBS_TRY(dalloc(&d_tile_voff, (size_t)ntiles + 1, s));
+    FBS_TRY(dalloc(&d_tkey, (size_t)pix, s));
+    FBS_TRY(dalloc(&d_tm, (size_t)pix, s));
+    FBS_TRY(dalloc(&d_tps, (size_t)pix, s));
     FBS_TRY(dalloc(&g->err, 1, s));
+    FBS_TRY(dalloc(&g->vid, g->Ntot, s));
+    FBS_TRY(dalloc(&g->perm, g->Ntot, s));
+    FBS_TRY(dalloc(&g->cell_voff, cells, s));
+    FBS_TRY(dalloc(&g->cell_nv, cells, s));
     FBS_TRY(cudaMemsetAsync(g->err, 0, sizeof(uint32_t), s));
     FBS_TRY(cudaMemcpyAsync(d_img, img.data(), img.size() * sizeof(ImgDev), cudaMemcpyHostToDevice, s));
     FBS_TRY(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(GTile),
                             cudaMemcpyHostToDevice, s));
-    FBS_TRY(launch_grid_count(d_tiles, ntiles, d_img, d_tile_nv, g->err, P2, s));
+    FBS_TRY(launch_grid_sort(d_tiles, ntiles, d_img, d_tile_nv, g->err, P2, max_cells, g->vid,
+                             g->perm, d_tkey, d_tm, d_tps, g->cell_voff, g->cell_nv, s));
     FBS_TRY(launch_scan_tiles(d_tile_nv, d_tile_voff, ntiles, s));
     FBS_TRY(cudaMemcpyAsync(tile_voff.data(), d_tile_voff, (ntiles + 1) * sizeof(int64_t),
                             cudaMemcpyDeviceToHost, s));
@@ -448,19 +464,14 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
         }
         const int64_t V = g->Vtot;
         FBS_TRY(dalloc(&g->vkey, V, s));
-        FBS_TRY(dalloc(&g->vid, g->Ntot, s));
-        FBS_TRY(dalloc(&g->perm, g->Ntot, s));
         FBS_TRY(dalloc(&g->pstart, V, s));
         FBS_TRY(dalloc(&g->m, V, s));
         FBS_TRY(dalloc(&g->nbr, (size_t)V * 10, s));
         FBS_TRY(dalloc(&g->n64, V, s));
         FBS_TRY(dalloc(&g->n64b, V, s));
         FBS_TRY(dalloc(&g->nf, V, s));
-        FBS_TRY(dalloc(&g->cell_voff, cells, s));
-        FBS_TRY(dalloc(&g->cell_nv, cells, s));
-        FBS_TRY(launch_grid_fill(d_tiles, ntiles, d_img, d_tile_voff, g->err, P2, max_cells,
-                                 g->vkey, g->vid, g->perm, g->pstart, g->m, g->cell_voff,
-                                 g->cell_nv, s));
+        FBS_TRY(launch_grid_finalize(d_tiles, ntiles, d_img, d_tile_voff, g->vid, d_tkey, d_tm,
+                                     d_tps, g->vkey, g->m, g->pstart, g->cell_voff, s));
         FBS_TRY(launch_grid_neighbours(d_tiles, ntiles, d_img, d_tile_voff, g->vkey, g->cell_voff,
                                        g->cell_nv, g->nbr, V, s));
         // vertex tiles for the vertex kernels
@@ -487,9 +498,14 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
                                 cudaMemcpyHostToDevice, s));
     }
     dfree(d_img, s);
-    dfree(d_tiles, s);
     dfree(d_tile_nv, s);
-    dfree(d_tile_voff, s);
+    dfree(d_tkey, s);
+    dfree(d_tm, s);
+    dfree(d_tps, s);
+    g->gt = d_tiles;          // kept for the splat
+    g->gt_voff = d_tile_voff;
+    g->ngt = ntiles;
+    g->gt_p2 = P2;
     prof_end(f_region, s);
     *out = g;
     return FBS_OK;
@@ -500,6 +516,9 @@ fail_status:
     dfree(d_tiles, s);
     dfree(d_tile_nv, s);
     dfree(d_tile_voff, s);
+    dfree(d_tkey, s);
+    dfree(d_tm, s);
+    dfree(d_tps, s);
     free_grid_memory(g, s);
     delete g;
     return st;

@@ -120,24 +120,82 @@ __device__ __forceinline__ bool is_head(const uint64_t* items, int i)
 }
 
 // ------------------------------------------------------------- kernels ---
-// Pass 1: number of distinct keys per tile.
+// Pass 1: sort and de-duplicate each tile once.  Writes everything that does
+// not depend on the tile's first vertex id:
+//   perm[sort_off + i]   = global pixel of sorted item i
+//   vid[pixel]           = tile-local vertex rank of the pixel
+//   tkey/tm/tps[sort_off + r] = key, count and first sorted slot of local vertex r
+//   cell_voff[cell]      = tile-local first vertex of the cell, cell_nv = its count
+//   tile_nv[tile]        = number of distinct keys in the tile
 __global__ void __launch_bounds__(kGridThreads)
-grid_count_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ imgs,
-                  int* __restrict__ tile_nv, uint32_t* err, int P2)
+grid_sort_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ imgs,
+                 int* __restrict__ tile_nv, uint32_t* err, int P2, int max_cells,
+                 uint32_t* __restrict__ vid, uint32_t* __restrict__ perm,
+                 uint64_t* __restrict__ tkey, uint32_t* __restrict__ tm,
+                 uint32_t* __restrict__ tps, uint32_t* __restrict__ cell_voff,
+                 uint32_t* __restrict__ cell_nv)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* items = reinterpret_cast<uint64_t*>(smem_raw);
+    int* headpos = reinterpret_cast<int*>(items + P2);
+    int* cellcnt = headpos + P2;
     __shared__ int warp_buf[32];
+
     const GTile t = tiles[blockIdx.x];
     const ImgDev im = imgs[t.img];
-    const int P = (t.y1 - t.y0) * (t.x1 - t.x0);
+    const int tw = t.x1 - t.x0;
+    const int P = (t.y1 - t.y0) * tw;
+
+    for (int c = threadIdx.x; c < t.nkx && c < max_cells; c += blockDim.x) cellcnt[c] = 0;
     load_tile_items(t, im, items, P, P2, err);
     __syncthreads();
     bitonic_sort(items, P2);
+
+    // each thread owns a contiguous chunk of the sorted items
+    const int E = P2 / blockDim.x;
+    const int i0 = threadIdx.x * E;
     int cnt = 0;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) cnt += is_head(items, i) ? 1 : 0;
-    int total = block_sum(cnt, warp_buf);
-    if (threadIdx.x == 0) tile_nv[blockIdx.x] = total;
+    for (int i = i0; i < i0 + E && i < P; ++i) cnt += is_head(items, i) ? 1 : 0;
+    int nv;
+    int run = block_exclusive_scan(cnt, warp_buf, &nv);
+    for (int i = i0; i < i0 + E && i < P; ++i) {
+        const uint64_t it = items[i];
+        const bool head = is_head(items, i);
+        if (head) ++run;
+        const int rank = run - 1;
+        const int pl = (int)(it & kPixMask);
+        const int r = pl / tw;
+        const int64_t gpix = im.pix_base + (int64_t)(t.y0 + r) * im.W + (t.x0 + pl - r * tw);
+        vid[gpix] = (uint32_t)rank;
+        perm[t.sort_off + i] = (uint32_t)gpix;
+        if (head) {
+            const int cell = (int)(it >> kCellShift);
+            const uint64_t colour = (it >> kColourShift) & ((1ull << 36) - 1);
+            tkey[t.sort_off + rank] =
+                ((uint64_t)t.ky << 48) | ((uint64_t)(t.kx0 + cell) << 36) | colour;
+            tps[t.sort_off + rank] = (uint32_t)(t.sort_off + i);
+            headpos[rank] = i;
+            atomicAdd(&cellcnt[cell], 1);
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nv; r += blockDim.x)
+        tm[t.sort_off + r] = (uint32_t)((r + 1 < nv ? headpos[r + 1] : P) - headpos[r]);
+    if (threadIdx.x == 0) tile_nv[blockIdx.x] = nv;
+    // per-cell vertex ranges, tile-local (cells of a tile are consecutive in key order)
+    const int64_t cell0 = im.cell_base + (int64_t)t.ky * im.ncx + t.kx0;
+    int carry = 0;
+    for (int base = 0; base < t.nkx; base += blockDim.x) {
+        int c = base + threadIdx.x;
+        int v = c < t.nkx ? cellcnt[c] : 0;
+        int tot;
+        int ex = block_exclusive_scan(v, warp_buf, &tot);
+        if (c < t.nkx) {
+            cell_voff[cell0 + c] = (uint32_t)(carry + ex);
+            cell_nv[cell0 + c] = (uint32_t)v;
+        }
+        carry += tot;
+    }
 }
 
 // Exclusive scan of the per-tile counts (one CTA; the tile count is small).
@@ -162,78 +220,34 @@ __global__ void __launch_bounds__(1024) scan_tiles_kernel(const int* __restrict_
     if (threadIdx.x == 0) tile_voff[ntiles] = carry;
 }
 
-// Pass 2: recompute and sort the tile, then write the canonical vertex ids,
-// keys, counts, the pixel permutation and the per-cell vertex ranges.
-__global__ void __launch_bounds__(kGridThreads)
-grid_fill_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ imgs,
-                 const int64_t* __restrict__ tile_voff, uint32_t* err, int P2, int max_cells,
-                 uint64_t* __restrict__ vkey, uint32_t* __restrict__ vid,
-                 uint32_t* __restrict__ perm, uint32_t* __restrict__ pstart,
-                 uint32_t* __restrict__ m, uint32_t* __restrict__ cell_voff,
-                 uint32_t* __restrict__ cell_nv)
+// Pass 2: add each tile's first vertex id and move its vertex records to
+// their canonical places.
+__global__ void __launch_bounds__(256)
+grid_finalize_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ imgs,
+                     const int64_t* __restrict__ tile_voff, uint32_t* __restrict__ vid,
+                     const uint64_t* __restrict__ tkey, const uint32_t* __restrict__ tm,
+                     const uint32_t* __restrict__ tps, uint64_t* __restrict__ vkey,
+                     uint32_t* __restrict__ m, uint32_t* __restrict__ pstart,
+                     uint32_t* __restrict__ cell_voff)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t* items = reinterpret_cast<uint64_t*>(smem_raw);
-    int* headpos = reinterpret_cast<int*>(items + P2);
-    int* cellcnt = headpos + P2;
-    __shared__ int warp_buf[32];
-
     const GTile t = tiles[blockIdx.x];
     const ImgDev im = imgs[t.img];
-    const int tw = t.x1 - t.x0;
-    const int P = (t.y1 - t.y0) * tw;
     const int64_t v0 = tile_voff[blockIdx.x];
     const int nv = (int)(tile_voff[blockIdx.x + 1] - v0);
-
-    for (int c = threadIdx.x; c < t.nkx && c < max_cells; c += blockDim.x) cellcnt[c] = 0;
-    load_tile_items(t, im, items, P, P2, err);
-    __syncthreads();
-    bitonic_sort(items, P2);
-
-    // each thread owns a contiguous chunk of the sorted items
-    const int E = P2 / blockDim.x;
-    const int i0 = threadIdx.x * E;
-    int cnt = 0;
-    for (int i = i0; i < i0 + E && i < P; ++i) cnt += is_head(items, i) ? 1 : 0;
-    int total;
-    int run = block_exclusive_scan(cnt, warp_buf, &total);
-    for (int i = i0; i < i0 + E && i < P; ++i) {
-        const uint64_t it = items[i];
-        const bool head = is_head(items, i);
-        if (head) ++run;
-        const int rank = run - 1;
-        const int pl = (int)(it & kPixMask);
-        const int r = pl / tw;
-        const int64_t gpix = im.pix_base + (int64_t)(t.y0 + r) * im.W + (t.x0 + pl - r * tw);
-        const int64_t v = v0 + rank;
-        vid[gpix] = (uint32_t)v;
-        perm[t.sort_off + i] = (uint32_t)gpix;
-        if (head) {
-            const int cell = (int)(it >> kCellShift);
-            const uint64_t colour = (it >> kColourShift) & ((1ull << 36) - 1);
-            vkey[v] = ((uint64_t)t.ky << 48) | ((uint64_t)(t.kx0 + cell) << 36) | colour;
-            pstart[v] = (uint32_t)(t.sort_off + i);
-            headpos[rank] = i;
-            atomicAdd(&cellcnt[cell], 1);
-        }
+    const int tw = t.x1 - t.x0;
+    const int P = (t.y1 - t.y0) * tw;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int r = i / tw;
+        const int64_t gpix = im.pix_base + (int64_t)(t.y0 + r) * im.W + (t.x0 + i - r * tw);
+        vid[gpix] += (uint32_t)v0;
     }
-    __syncthreads();
-    for (int r = threadIdx.x; r < nv; r += blockDim.x)
-        m[v0 + r] = (uint32_t)((r + 1 < nv ? headpos[r + 1] : P) - headpos[r]);
-    // per-cell vertex ranges (cells of a tile are consecutive in key order)
+    for (int r = threadIdx.x; r < nv; r += blockDim.x) {
+        vkey[v0 + r] = tkey[t.sort_off + r];
+        m[v0 + r] = tm[t.sort_off + r];
+        pstart[v0 + r] = tps[t.sort_off + r];
+    }
     const int64_t cell0 = im.cell_base + (int64_t)t.ky * im.ncx + t.kx0;
-    int carry = 0;
-    for (int base = 0; base < t.nkx; base += blockDim.x) {
-        int c = base + threadIdx.x;
-        int v = c < t.nkx ? cellcnt[c] : 0;
-        int tot;
-        int ex = block_exclusive_scan(v, warp_buf, &tot);
-        if (c < t.nkx) {
-            cell_voff[cell0 + c] = (uint32_t)(v0 + carry + ex);
-            cell_nv[cell0 + c] = (uint32_t)v;
-        }
-        carry += tot;
-    }
+    for (int c = threadIdx.x; c < t.nkx; c += blockDim.x) cell_voff[cell0 + c] += (uint32_t)v0;
 }
 
 __device__ __forceinline__ int find_in_cell(const uint64_t* __restrict__ vkey, uint32_t lo,
@@ -316,22 +330,25 @@ bistoch_kernel(const double* __restrict__ nold, double* __restrict__ nnew,
 }  // namespace
 
 // ------------------------------------------------------ host launchers ---
-size_t grid_smem_count(int P2) { return (size_t)P2 * sizeof(uint64_t); }
-size_t grid_smem_fill(int P2, int max_cells)
+size_t grid_smem_sort(int P2, int max_cells)
 {
     return (size_t)P2 * (sizeof(uint64_t) + sizeof(int)) + (size_t)max_cells * sizeof(int);
 }
 
-cudaError_t launch_grid_count(const GTile* tiles, int ntiles, const ImgDev* imgs, int* tile_nv,
-                              uint32_t* err, int P2, cudaStream_t s)
+cudaError_t launch_grid_sort(const GTile* tiles, int ntiles, const ImgDev* imgs, int* tile_nv,
+                             uint32_t* err, int P2, int max_cells, uint32_t* vid, uint32_t* perm,
+                             uint64_t* tkey, uint32_t* tm, uint32_t* tps, uint32_t* cell_voff,
+                             uint32_t* cell_nv, cudaStream_t s)
 {
-    size_t smem = grid_smem_count(P2);
-    cudaError_t e = cudaFuncSetAttribute(grid_count_kernel,
+    size_t smem = grid_smem_sort(P2, max_cells);
+    cudaError_t e = cudaFuncSetAttribute(grid_sort_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    static int fam = prof_family("grid_count");
+    static int fam = prof_family("grid_sort");
     prof_begin(fam, s);
-    grid_count_kernel<<<ntiles, kGridThreads, smem, s>>>(tiles, imgs, tile_nv, err, P2);
+    grid_sort_kernel<<<ntiles, kGridThreads, smem, s>>>(tiles, imgs, tile_nv, err, P2, max_cells,
+                                                        vid, perm, tkey, tm, tps, cell_voff,
+                                                        cell_nv);
     prof_end(fam, s);
     return cudaGetLastError();
 }
@@ -345,20 +362,16 @@ cudaError_t launch_scan_tiles(const int* tile_nv, int64_t* tile_voff, int ntiles
     return cudaGetLastError();
 }
 
-cudaError_t launch_grid_fill(const GTile* tiles, int ntiles, const ImgDev* imgs,
-                             const int64_t* tile_voff, uint32_t* err, int P2, int max_cells,
-                             uint64_t* vkey, uint32_t* vid, uint32_t* perm, uint32_t* pstart,
-                             uint32_t* m, uint32_t* cell_voff, uint32_t* cell_nv, cudaStream_t s)
+cudaError_t launch_grid_finalize(const GTile* tiles, int ntiles, const ImgDev* imgs,
+                                 const int64_t* tile_voff, uint32_t* vid, const uint64_t* tkey,
+                                 const uint32_t* tm, const uint32_t* tps, uint64_t* vkey,
+                                 uint32_t* m, uint32_t* pstart, uint32_t* cell_voff,
+                                 cudaStream_t s)
 {
-    size_t smem = grid_smem_fill(P2, max_cells);
-    cudaError_t e = cudaFuncSetAttribute(grid_fill_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    static int fam = prof_family("grid_fill");
+    static int fam = prof_family("grid_finalize");
     prof_begin(fam, s);
-    grid_fill_kernel<<<ntiles, kGridThreads, smem, s>>>(tiles, imgs, tile_voff, err, P2, max_cells,
-                                                        vkey, vid, perm, pstart, m, cell_voff,
-                                                        cell_nv);
+    grid_finalize_kernel<<<ntiles, 256, 0, s>>>(tiles, imgs, tile_voff, vid, tkey, tm, tps, vkey,
+                                                m, pstart, cell_voff);
     prof_end(fam, s);
     return cudaGetLastError();
 }

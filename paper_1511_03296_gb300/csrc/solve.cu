@@ -86,6 +86,45 @@ __device__ void reduce_instance_partials(const float2* __restrict__ part, const 
 }
 
 // ---------------------------------------------------------------- splat ---
+// A is applied in Laplacian form,
+//   (A z)_v = a'_v z_v + lambda n_v sum_u n_u (z_v - z_u),
+//   a'_v    = lambda (m_v - n_v (Bbar n)_v) + (S c)_v,
+// which equals a_v z_v - lambda n_v sum_u n_u z_u with
+// a_v = diag(A)_v = lambda (m_v - 10 n_v^2) + (S c)_v.  a' is formed in FP64
+// here; the off-diagonal part has zero row sums whatever the rounding of n,
+// so FP32 vectors keep the data term intact.  A vertex without neighbours
+// has smoothness part 0 (its row of lambda (D_m - D_n Bbar D_n) vanishes once
+// n^2 = m / 10).  M^-1 = 1 / diag(A), 0 where diag(A) <= 0.
+__device__ __forceinline__ void vertex_epilogue_terms(const SolveArgs& A, const InstDev& I,
+                                                      int64_t v, uint32_t cnt, DF sc, bool has_nbr,
+                                                      double sum_n)
+{
+    const double nv = A.n64[v];
+    const double scd = (double)sc.hi + (double)sc.lo;
+    const double lam = (double)I.lam;
+    const double rem = has_nbr ? lam * ((double)cnt - nv * (10.0 * nv + sum_n)) : 0.0;
+    const double diag = has_nbr ? lam * ((double)cnt - 10.0 * nv * nv) + scd : scd;
+    A.a[v] = (float)(rem + scd);
+    A.nm[v] = make_float2((float)nv, diag > 0.0 ? (float)(1.0 / diag) : 0.0f);
+}
+
+__device__ __forceinline__ void vertex_epilogue(const SolveArgs& A, const InstDev& I, int64_t v,
+                                                uint32_t cnt, DF sc)
+{
+    bool has_nbr = false;
+    double sum_n = 0.0;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        const int32_t u = A.nbr[(int64_t)k * A.Vtot + v];
+        if (u >= 0) {
+            has_nbr = true;
+            sum_n += A.n64[u];
+        }
+    }
+    vertex_epilogue_terms(A, I, v, cnt, sc, has_nbr, sum_n);
+}
+
+
 // One thread per vertex sums its pixels (in the sorted pixel order, so the
 // result is deterministic) with exact products accumulated as double-float
 // pairs.  Writes b into r, y0 = b / S c into y, diag(A) into a, and
@@ -111,32 +150,47 @@ splat_kernel(SolveArgs A, int mode, float sigma_gm, int comp)
             DF acc[CB];
 #pragma unroll
             for (int k = 0; k < CB; ++k) acc[k] = {0.0f, 0.0f};
-            for (uint32_t j = 0; j < cnt; ++j) {
-                const int64_t i = (int64_t)A.perm[p0 + j] - I.pix_base;
-                float w;
-                if (mode == kSplatRobust) {
-                    const float e = yv - I.t[i];
-                    const float den = s2 + e * e;
-                    w = (2.0f * s2) / (den * den);
-                } else {
-                    w = I.c[i];
-                }
-                if (cb == 0) {
-                    sc = df_add(sc, DF{w, 0.0f});
-                    bad |= !isfinite(w);
+            // software-pipelined: the pixel indices of 8 items, then their
+            // values, then the accumulation in item order (same order, so the
+            // sums are those of a plain sequential loop)
+            for (uint32_t j0 = 0; j0 < cnt; j0 += 8) {
+                int64_t ii[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    ii[u] = j0 + u < cnt ? (int64_t)A.perm[p0 + j0 + u] - I.pix_base : -1;
+                float wv[8], val[CB][8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int64_t i = ii[u] >= 0 ? ii[u] : 0;
+                    if (mode == kSplatRobust) {
+                        const float e = yv - I.t[i];
+                        const float den = s2 + e * e;
+                        wv[u] = (2.0f * s2) / (den * den);
+                    } else {
+                        wv[u] = I.c[i];
+                    }
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) {
+                        const int ch = min(cb + k, I.C - 1);
+                        val[k][u] = mode == kSplatBackward ? I.dx[(int64_t)ch * I.N + i]
+                                                           : I.t[(int64_t)ch * I.N + i];
+                    }
                 }
 #pragma unroll
-                for (int k = 0; k < CB; ++k) {
-                    const int ch = cb + k;
-                    if (ch < I.C) {
-                        if (mode == kSplatBackward) {
-                            const float g = I.dx[(int64_t)ch * I.N + i];
-                            acc[k] = df_add(acc[k], DF{g, 0.0f});
-                            bad |= !isfinite(g);
-                        } else {
-                            const float tv = I.t[(int64_t)ch * I.N + i];
-                            acc[k] = df_add(acc[k], df_mul_exact(w, tv));
-                            bad |= !isfinite(tv);
+                for (int u = 0; u < 8; ++u) {
+                    if (ii[u] < 0) break;
+                    const float w = wv[u];
+                    if (cb == 0) {
+                        sc = df_add(sc, DF{w, 0.0f});
+                        bad |= !isfinite(w);
+                    }
+#pragma unroll
+                    for (int k = 0; k < CB; ++k) {
+                        if (cb + k < I.C) {
+                            const float x = val[k][u];
+                            acc[k] = df_add(acc[k], mode == kSplatBackward ? DF{x, 0.0f}
+                                                                           : df_mul_exact(w, x));
+                            bad |= !isfinite(x);
                         }
                     }
                 }
@@ -160,33 +214,7 @@ splat_kernel(SolveArgs A, int mode, float sigma_gm, int comp)
             }
         }
         if (bad) atomicOr(A.err, kErrNonFinite);
-        // A is applied in Laplacian form,
-        //   (A z)_v = a'_v z_v + lambda n_v sum_u n_u (z_v - z_u),
-        //   a'_v    = lambda (m_v - n_v (Bbar n)_v) + (S c)_v,
-        // which equals a_v z_v - lambda n_v sum_u n_u z_u with
-        // a_v = diag(A)_v = lambda (m_v - 10 n_v^2) + (S c)_v.  a' is formed
-        // in FP64 here; the off-diagonal part has zero row sums whatever the
-        // rounding of n, so FP32 vectors keep the data term intact.  A vertex
-        // without neighbours has smoothness part 0 (its row of
-        // lambda (D_m - D_n Bbar D_n) vanishes once n^2 = m / 10).
-        // M^-1 = 1 / diag(A), 0 where diag(A) <= 0.
-        bool has_nbr = false;
-        double sum_n = 0.0;
-#pragma unroll
-        for (int k = 0; k < 10; ++k) {
-            const int32_t u = A.nbr[(int64_t)k * A.Vtot + v];
-            if (u >= 0) {
-                has_nbr = true;
-                sum_n += A.n64[u];
-            }
-        }
-        const double nv = A.n64[v];
-        const double scd = (double)sc.hi + (double)sc.lo;
-        const double lam = (double)I.lam;
-        const double rem = has_nbr ? lam * ((double)cnt - nv * (10.0 * nv + sum_n)) : 0.0;
-        const double diag = has_nbr ? lam * ((double)cnt - 10.0 * nv * nv) + scd : scd;
-        A.a[v] = (float)(rem + scd);
-        A.nm[v] = make_float2((float)nv, diag > 0.0 ? (float)(1.0 / diag) : 0.0f);
+        vertex_epilogue(A, I, v, cnt, sc);
     }
 }
 
@@ -656,19 +684,8 @@ pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
         const int slot = it & 1;
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
-        // ---- phase 1
-        reduce_partials_all<CB>(A.part_rs[slot], I, S.sd, S.red);
-        if (threadIdx.x < I.C && threadIdx.x < CB) {
-            const int ch = threadIdx.x;
-            double beta = 0.0;
-            if (it > 0) {
-                const double dprev = __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1]);
-                beta = dprev != 0.0 ? S.sd[ch] / dprev : 0.0;
-            }
-            S.sf[ch] = (float)beta;
-            A.scal[I.pc + ch].delta[slot] = S.sd[ch];
-        }
-        __syncthreads();
+        // ---- phase 1: gathers first (they do not depend on beta), then the
+        // reduction of the previous phase's partials overlaps their latency
         {
             DF acc[CB];
             float ru[CB][10], du[CB][10], nu[10], mu[10];
@@ -685,6 +702,18 @@ pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
                     du[k][j] = it > 0 ? __ldcg(dold + base[k] + u) : 0.0f;
                 }
             }
+            reduce_partials_all<CB>(A.part_rs[slot], I, S.sd, S.red);
+            if (threadIdx.x < I.C && threadIdx.x < CB) {
+                const int ch = threadIdx.x;
+                double beta = 0.0;
+                if (it > 0) {
+                    const double dprev = __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1]);
+                    beta = dprev != 0.0 ? S.sd[ch] / dprev : 0.0;
+                }
+                S.sf[ch] = (float)beta;
+                A.scal[I.pc + ch].delta[slot] = S.sd[ch];
+            }
+            __syncthreads();
 #pragma unroll
             for (int k = 0; k < CB; ++k) {
                 acc[k] = {0.0f, 0.0f};
