@@ -25,6 +25,8 @@ import tempfile
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -45,6 +47,12 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=10.0,
                    help="host time spent timing the oracle for cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the batched and forward+backward workloads")
+    p.add_argument("--only", choices=["batched", "fwd_bwd"], default=None,
+                   help="run one extra workload alone (for profiling) and print its line")
+    p.add_argument("--images", type=int, default=None,
+                   help="image count of the --only workload (default: its full size)")
     return p.parse_args()
 
 
@@ -225,8 +233,159 @@ def measured_peaks():
         return None
 
 
+def time_steps(step, steps, warmup, flush, stream):
+    """Device time (ms) of each of `steps` calls of step(), after `warmup`
+    untimed calls; L2 is flushed before every call, outside the events."""
+    import torch
+    for _ in range(warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+
+
+def pcg_roofline(regions, solves_per_step, steps, bytes_per_iter, peak):
+    """Achieved GB/s of the PCG iteration from the region events of the
+    timed steps (all PCG iterations of a step share the same byte count)."""
+    n, ms = regions.get("region:pcg_loop", (0, 0.0))
+    if not n:
+        return None
+    iter_ms = ms / n / PCG_ITERS
+    achieved = bytes_per_iter / (iter_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "bytes_per_iter": bytes_per_iter, "iter_us": iter_ms * 1e3}
+
+
+def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, sequential=True):
+    """64 images of uneven size in one grid and one batched solve, against the
+    same images solved one at a time."""
+    import torch
+    from paper_1511_03296_gb300 import fbs, synth
+    wl = synth.batched_64(seed=4 + dist.rank, n_images=n_images)
+    insts = wl.instances
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    yuv = [dev(i.yuv) for i in insts]
+    t = [dev(i.t) for i in insts]
+    c = [dev(i.c) for i in insts]
+    x = [torch.empty_like(tt) for tt in t]
+    sig = ([i.sigma_xy for i in insts], [i.sigma_l for i in insts], [i.sigma_uv for i in insts])
+    lam = [i.lam for i in insts]
+    info = {}
+
+    def batched():
+        g = fbs.grid_build(yuv, *sig)
+        fbs.bistochastize(g, BISTOCH_ITERS)
+        fbs.solve(g, t, c, lam, PCG_ITERS, x=x)
+        info["V"] = g.vertex_counts
+        g.destroy()
+
+    def one_at_a_time():
+        for k in range(len(insts)):
+            g = fbs.grid_build([yuv[k]], sig[0][k], sig[1][k], sig[2][k])
+            fbs.bistochastize(g, BISTOCH_ITERS)
+            fbs.solve(g, [t[k]], [c[k]], lam[k], PCG_ITERS, x=[x[k]])
+            g.destroy()
+
+    fbs.profile_enable(2)
+    ms_b = time_steps(batched, steps, warmup, flush, stream)
+    regions = fbs.profile_read()
+    fbs.profile_enable(0)
+    ms_s = time_steps(one_at_a_time, max(2, steps // 4), 1, flush, stream) if sequential else [0.0]
+    npix = wl.n_pixels
+    mb = dist.max(sum(ms_b) / len(ms_b))
+    ms1 = dist.max(sum(ms_s) / len(ms_s)) or float("nan")
+    bytes_iter = sum(V * (48 + 40 * i.channels) for V, i in zip(info["V"], insts))
+    return {"workload": "64 images, sizes U{320..1920} x U{240..1080}, half depth (C=1), half "
+                        "chroma (C=2, c=1 on 2% of pixels), sigma_xy in {8,16}, lambda in {32,128}",
+            "pixels": npix, "vertices": int(sum(info["V"])),
+            "batched_mpix_s": dist.world * npix / (mb / 1e3) / 1e6, "batched_ms": mb,
+            "one_at_a_time_mpix_s": dist.world * npix / (ms1 / 1e3) / 1e6,
+            "one_at_a_time_ms": ms1,
+            "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
+                            for k, v in regions.items() if v[0]},
+            "pcg_roofline": pcg_roofline(regions, 1, steps, bytes_iter, peak)}
+
+
+def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
+    """16 images 640x480, 21-channel softmax targets: forward solve, MSE loss
+    gradient against a label map, backward solve (dL/dt, dL/dc)."""
+    import torch
+    from paper_1511_03296_gb300 import fbs, synth
+    wl = synth.segmentation_16(seed=5 + dist.rank, n_images=n_images)
+    insts = wl.instances
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    yuv = [dev(i.yuv) for i in insts]
+    t = [dev(i.t) for i in insts]
+    c = [dev(i.c) for i in insts]
+    lab = [dev(i.label) for i in insts]
+    x = [torch.empty_like(tt) for tt in t]
+    dx = [torch.empty_like(tt) for tt in t]
+    dt = [torch.empty_like(tt) for tt in t]
+    dc = [torch.empty_like(cc) for cc in c]
+    sig = ([i.sigma_xy for i in insts], [i.sigma_l for i in insts], [i.sigma_uv for i in insts])
+    lam = [i.lam for i in insts]
+    numel = sum(tt.numel() for tt in t)
+    info = {}
+
+    def step():
+        g = fbs.grid_build(yuv, *sig)
+        fbs.bistochastize(g, BISTOCH_ITERS)
+        y = [torch.empty((i.channels, g.vertex_counts[k]), device="cuda")
+             for k, i in enumerate(insts)]
+        fbs.solve(g, t, c, lam, PCG_ITERS, x=x, y=y)
+        for k in range(len(insts)):               # the loss: mean((x - label)^2)
+            torch.sub(x[k], lab[k], out=dx[k]).mul_(2.0 / numel)
+        fbs.solve_backward(g, t, c, lam, y, dx, dt, dc, PCG_ITERS)
+        info["V"] = g.vertex_counts
+        g.destroy()
+
+    fbs.profile_enable(2)
+    ms = time_steps(step, steps, warmup, flush, stream)
+    regions = fbs.profile_read()
+    fbs.profile_enable(0)
+    m = dist.max(sum(ms) / len(ms))
+    npix = wl.n_pixels
+    bytes_iter = sum(V * (48 + 40 * i.channels) for V, i in zip(info["V"], insts))
+    return {"workload": "16 images 640x480, C=21 softmax targets, c~U[0,1], sigma=(8,4,3), "
+                        "lambda=128, forward + backward (2 x 25 PCG iterations)",
+            "pixels": npix, "vertices": int(sum(info["V"])),
+            "fwd_bwd_mpix_s": dist.world * npix / (m / 1e3) / 1e6, "ms_per_step": m,
+            "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
+                            for k, v in regions.items() if v[0]},
+            "pcg_roofline": pcg_roofline(regions, 2, steps, bytes_iter, peak)}
+
+
+def run_only(args, dist):
+    """One extra workload alone (a profiling aid): prints its own JSON line."""
+    import torch
+    from paper_1511_03296_gb300 import build as fbs_build
+    from paper_1511_03296_gb300 import fbs
+    torch.cuda.set_device(dist.local_rank if torch.cuda.device_count() > 1 else 0)
+    fbs_build.build()
+    fbs.load()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    if args.only == "batched":
+        out = run_extra_batched(dist, flush, stream, peak, args.steps, args.warmup,
+                                n_images=args.images or 64, sequential=False)
+    else:
+        out = run_extra_fwd_bwd(dist, flush, stream, peak, args.steps, args.warmup,
+                                n_images=args.images or 16)
+    if dist.rank == 0:
+        print(json.dumps({"only": args.only, **out}), flush=True)
+
+
 def run_ours(args, dist):
-    import numpy as np
     import torch
 
     from paper_1511_03296_gb300 import build as fbs_build
@@ -300,34 +459,25 @@ def run_ours(args, dist):
     h_x = torch.empty(inst.t.shape, dtype=torch.float32).pin_memory()
     e_yuv, e_t, e_c, e_x = (torch.empty_like(d_yuv), torch.empty_like(d_t),
                             torch.empty_like(d_c), torch.empty_like(d_x))
-    e2e_steps = max(3, min(args.steps, 20))
-    es = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
-    ee = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps)]
-    for i in range(e2e_steps + 2):
-        flush.zero_()
-        j = i - 2
-        if j >= 0:
-            es[j].record(stream)
+
+    def e2e_step():
         e_yuv.copy_(h_yuv, non_blocking=True)
         e_t.copy_(h_t, non_blocking=True)
         e_c.copy_(h_c, non_blocking=True)
         step(e_yuv, e_t, e_c, e_x)
         h_x.copy_(e_x, non_blocking=True)
-        if j >= 0:
-            ee[j].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = dist.max(sum(s.elapsed_time(e) for s, e in zip(es, ee)) / e2e_steps)
+
+    e2e = time_steps(e2e_step, max(3, min(args.steps, 20)), 2, flush, stream)
+    e2e_ms = dist.max(sum(e2e) / len(e2e))
     assert np.allclose(h_x.numpy(), d_x.cpu().numpy())
     h2d = inst.yuv.nbytes + inst.t.nbytes + inst.c.nbytes
     d2h = inst.t.nbytes
 
-    # ---- roofline: the PCG iteration (apply + update), timed as a region
-    loop_n, loop_ms = regions.get("region:pcg_loop", (0, 0.0))
-    iter_ms = loop_ms / max(1, loop_n) / PCG_ITERS
-    bytes_iter = algorithmic_bytes_per_pcg_iteration(V, inst.channels)
+    # ---- roofline: the PCG iteration (both phases), timed as a region
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    achieved = bytes_iter / (iter_ms / 1e3) / 1e9 if iter_ms > 0 else None
+    bytes_iter = algorithmic_bytes_per_pcg_iteration(V, inst.channels)
+    roof = pcg_roofline(regions, 1, args.steps, bytes_iter, peak)
     region_share = {k: round(t / max(1e-9, sum(tt for _, tt in regions.values())), 4)
                     for k, (n, t) in regions.items() if n}
 
@@ -345,15 +495,17 @@ def run_ours(args, dist):
         "e2e": {"value": dist.world * inst.n_pixels / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
-        "roofline": {"kernel": "pcg iteration (pcg_apply + pcg_update)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None,
-                     "peak_source": "measured" if peaks else "fallback",
-                     "bytes_per_launch": bytes_iter, "iter_us": iter_ms * 1e3,
-                     "note": "working set L2-resident at this size (see design notes)"},
+        "roofline": dict(roof or {}, kernel="pcg iteration (both CG phases, persistent loop)",
+                         traffic=None, peak_source="measured" if peaks else "fallback",
+                         note="working set L2-resident at this size; see batched / fwd_bwd "
+                              "for the HBM-bound sizes"),
         "phase_share": region_share,
         "kernel_share": shares,
     }
+    if not args.no_extra:
+        xs = max(3, min(args.steps // 10, 20))
+        line["batched"] = run_extra_batched(dist, flush, stream, peak, xs, 2)
+        line["fwd_bwd"] = run_extra_fwd_bwd(dist, flush, stream, peak, xs, 2)
     if dist.rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(synth.plain_1080p().instances[0], args.cpu_seconds)
     if dist.rank == 0:
@@ -366,6 +518,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.only:
+            run_only(args, dist)
         else:
             run_ours(args, dist)
     finally:

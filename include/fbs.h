@@ -151,12 +151,17 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *   FBS_VECTORS_AUTO         (default) compensated for fbs_solve_backward,
  *                            FP32 for fbs_solve and fbs_solve_robust.
  * FBS_OPT_PCG_LAUNCH: how the PCG iterations are launched:
- *   FBS_PCG_PERSISTENT       (default) all iterations in one cooperative
- *                            launch whose blocks meet at grid barriers (each
- *                            wait bounded; on time-out the solve stops and
- *                            FBS_ERR_TIMEOUT is latched).  Falls back to
- *                            FBS_PCG_PER_PHASE when the cooperative launch is
- *                            refused or the stream is being captured.
+ *   FBS_PCG_AUTO             (default) FBS_PCG_PERSISTENT when every vertex tile
+ *                            gets its own co-resident block and no image has
+ *                            more than 4 channels (the topology then stays in
+ *                            shared memory for the whole loop), else
+ *                            FBS_PCG_PER_PHASE.
+ *   FBS_PCG_PERSISTENT       all iterations in one cooperative launch whose
+ *                            blocks meet at grid barriers (each wait bounded;
+ *                            on time-out the solve stops and FBS_ERR_TIMEOUT
+ *                            is latched).  Falls back to FBS_PCG_PER_PHASE when
+ *                            the cooperative launch is refused or the stream
+ *                            is being captured.
  *   FBS_PCG_PER_PHASE        two launches per iteration (replayed from a CUDA
  *                            graph when the same solve repeats).
  * FBS_OPT_INJECT_BARRIER_TIMEOUT: value 1 makes the next persistent PCG
@@ -166,7 +171,7 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  */
 enum { FBS_OPT_VECTOR_PRECISION = 1, FBS_OPT_PCG_LAUNCH = 2, FBS_OPT_INJECT_BARRIER_TIMEOUT = 3 };
 enum { FBS_VECTORS_AUTO = 0, FBS_VECTORS_FP32 = 1, FBS_VECTORS_COMPENSATED = 2 };
-enum { FBS_PCG_PERSISTENT = 0, FBS_PCG_PER_PHASE = 1 };
+enum { FBS_PCG_AUTO = 0, FBS_PCG_PERSISTENT = 1, FBS_PCG_PER_PHASE = 2 };
 fbs_status fbs_set_option(fbs_grid* g, int option, int value);
 
 /*

@@ -252,6 +252,7 @@ struct fbs_grid {
     float* vec = nullptr;               // 6 x cap_vec: y, r, r_lo, d0, d1, q
     int precision = FBS_VECTORS_AUTO;
     int persistent = 1;
+    int force_persistent = 0;
     int inject_timeout = 0;
     float* a = nullptr;
     float2* nm = nullptr;
@@ -648,6 +649,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
         InstDev& I = inst[k];
         I.voff = g->voff[k];
         I.V = (int)(g->voff[k + 1] - g->voff[k]);
+        I.Cp = padded_channels(I.C);
         I.vec_base = cv;
         I.tile0 = g->vt0[k];
         I.ntiles = g->nvt_img[k];
@@ -655,7 +657,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
         I.part_base = cpart;
         I.N = (int64_t)g->img[k].H * g->img[k].W;
         I.pix_base = g->img[k].pix_base;
-        cv += (int64_t)I.C * I.V;
+        cv += ((int64_t)I.Cp * I.V + 3) / 4 * 4;     // 16-byte aligned image blocks
         cpart += (int64_t)I.C * I.ntiles;
         pc += I.C;
         cmax = std::max(cmax, I.C);
@@ -673,6 +675,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     // the whole PCG loop as one cooperative launch, except inside a caller's
     // stream capture (per-phase launches are captured instead)
     plan.persistent = g->persistent && !capturing(s) ? 1 : 0;
+    plan.force_persistent = g->force_persistent;
     plan.inject_timeout = plan.persistent ? g->inject_timeout : 0;
     if (plan.persistent) g->inject_timeout = 0;
     const bool cap = capturing(s);
@@ -684,7 +687,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
         dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s);
         dfree(g->part, s); dfree(g->inst, s);
         g->inst_cached.clear();
-        g->cap_vec = (size_t)std::max<int64_t>(cv, 1);
+        g->cap_vec = (size_t)std::max<int64_t>(cv, 4);
         g->cap_scal = (size_t)std::max(pc, 1);
         g->cap_part = (size_t)std::max<int64_t>(cpart, 1);
         if ((e = dalloc(&g->vec, 6 * g->cap_vec, s)) != cudaSuccess) return cuda_status(e);
@@ -729,6 +732,8 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.part_rs[1] = g->part + g->cap_part;
     A.part_dq = g->part + 2 * g->cap_part;
     A.err = g->err;
+    // AUTO: persistent only where the resident form fits; per-phase (graph) otherwise
+    if (plan.persistent && !plan.force_persistent && !resident_fits(A, plan)) plan.persistent = 0;
     return run_segments(g, A, plan, s);
 }
 
@@ -828,8 +833,10 @@ fbs_status fbs_set_option(fbs_grid* g, int option, int value)
         return FBS_OK;
     }
     if (option == FBS_OPT_PCG_LAUNCH) {
-        if (value != FBS_PCG_PERSISTENT && value != FBS_PCG_PER_PHASE) return FBS_ERR_ARG;
-        g->persistent = value == FBS_PCG_PERSISTENT ? 1 : 0;
+        if (value != FBS_PCG_AUTO && value != FBS_PCG_PERSISTENT && value != FBS_PCG_PER_PHASE)
+            return FBS_ERR_ARG;
+        g->persistent = value == FBS_PCG_PER_PHASE ? 0 : 1;
+        g->force_persistent = value == FBS_PCG_PERSISTENT ? 1 : 0;
         return FBS_OK;
     }
     return FBS_ERR_ARG;

@@ -65,7 +65,8 @@ struct InstDev {
     int64_t voff;           // first vertex (global)
     int V;
     int C;
-    int64_t vec_base;       // offset of this image's C x V block in the vector arrays
+    int Cp;                 // channels padded: 1, 2 or a multiple of 4 (vector row length)
+    int64_t vec_base;       // offset (multiple of 4) of this image's V x Cp block
     int tile0, ntiles;      // its VTiles
     int pc;                 // first (image, channel) scalar slot
     int64_t part_base;      // first tile-partial slot (C x ntiles doubles)
@@ -81,6 +82,9 @@ struct InstDev {
     float* dt;              // C x N (backward out)
     float* dc;              // N     (backward out)
 };
+
+// padded channel count of a vector row
+__host__ __device__ inline int padded_channels(int C) { return C <= 2 ? C : (C + 3) / 4 * 4; }
 
 // CG scalar carried between phases of one (image, channel): delta =
 // r^T M^-1 r of iteration `it` in slot it % 2

@@ -6,12 +6,19 @@
 // belongs to one image ("instance"), so one launch advances every (image,
 // channel) problem of a batch.  Each block takes a contiguous chunk of tiles.
 //
-// CG inner products: every tile writes, per channel, the sum of its exact
-// FP32 products as a double-float pair ("tile partial").  The next phase's
-// blocks each reduce the partials of the instances they touch, in a fixed
-// order, and form the CG scalar they need (alpha or beta) in FP64 -- every
-// block obtains the same value, so there is no grid-wide serial step, no
-// atomic and no fence, and results are bitwise reproducible.
+// Vector layout: the CG vectors of an image are vertex-major with each
+// vertex's channels padded to Cp (1, 2, or a multiple of 4), so a vertex's
+// channels -- its own and, above all, a neighbour's in a gather -- move as
+// one aligned float, float2 or float4 per pass of W = min(Cp, 4) channels.
+// Padding entries are kept at zero.
+//
+// CG inner products: every tile (or, when an image's channels fit one pass,
+// every block's run of tiles of that image) writes per channel the sum of its
+// exact FP32 products as a double-float pair.  The next phase's blocks each
+// reduce the partials of the images they touch, in a fixed order, and form
+// the CG scalar they need (alpha or beta) in FP64 -- every block obtains the
+// same value, so there is no grid-wide serial step, no atomic and no fence,
+// and results are bitwise reproducible.
 #include "fbs_internal.cuh"
 #include "solve.cuh"
 
@@ -19,9 +26,16 @@ namespace fbs {
 
 namespace {
 
+// element (ch, v) of image I
 __device__ __forceinline__ int64_t vec_index(const InstDev& I, int ch, int64_t v)
 {
-    return I.vec_base + (int64_t)ch * I.V + (v - I.voff);
+    return I.vec_base + (v - I.voff) * I.Cp + ch;
+}
+
+// element (cb, v) is at pass_base(I, cb) + v * I.Cp
+__device__ __forceinline__ int64_t pass_base(const InstDev& I, int cb)
+{
+    return I.vec_base - I.voff * I.Cp + cb;
 }
 
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
@@ -34,35 +48,77 @@ __device__ __forceinline__ void block_chunk(int nvt, int& t0, int& t1)
     t1 = min(t0 + chunk, nvt);
 }
 
-// Block-reduce the CB double-float partials per channel of this tile and
-// store them (one float2 per (tile, channel)).
-template <int CB>
-__device__ void store_tile_partials(DF (&acc)[CB], const InstDev& I, const VTile& vt, int cb,
-                                    float2* __restrict__ part, DF (*red)[kVTile / 32])
+// ---------------------------------------------------- vector load/store ---
+// W consecutive floats at p (W-aligned); CO: through L2 (ld.cg), for data
+// that other blocks rewrite within the same launch.
+template <int W, bool CO>
+__device__ __forceinline__ void ldw(const float* p, float (&o)[W])
+{
+    if (W == 4) {
+        const float4 v = CO ? __ldcg(reinterpret_cast<const float4*>(p))
+                            : *reinterpret_cast<const float4*>(p);
+        o[0] = v.x;
+        o[1 % W] = v.y;
+        o[2 % W] = v.z;
+        o[3 % W] = v.w;
+    } else if (W == 2) {
+        const float2 v = CO ? __ldcg(reinterpret_cast<const float2*>(p))
+                            : *reinterpret_cast<const float2*>(p);
+        o[0] = v.x;
+        o[1 % W] = v.y;
+    } else {
+        o[0] = CO ? __ldcg(p) : *p;
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void stw(float* p, const float (&v)[W])
+{
+    if (W == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1 % W], v[2 % W], v[3 % W]);
+    } else if (W == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1 % W]);
+    } else {
+        *p = v[0];
+    }
+}
+
+// -------------------------------------------------------- inner products ---
+struct PhaseSmem {
+    DF red[4][kVTile / 32];
+    double sd[kMaxChannels];     // reduced inner products
+    float sf[kMaxChannels];      // beta (phase 1)
+    double sa[kMaxChannels];     // alpha (phase 2)
+};
+
+// Block-reduce W double-float partials (channels cb .. cb+W-1) and store each
+// in partial slot `slot` of its channel.
+template <int W>
+__device__ void store_partials(DF (&acc)[W], int C, int ntiles, int64_t part_base, int cb,
+                               int slot, float2* __restrict__ part, DF (*red)[kVTile / 32])
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < CB; ++k) {
+    for (int k = 0; k < W; ++k) {
         DF s = df_warp_sum(acc[k]);
         if (lane == 0) red[k][w] = s;
+        acc[k] = {0.0f, 0.0f};
     }
     __syncthreads();
-    if (threadIdx.x < CB) {
+    if ((int)threadIdx.x < W && cb + (int)threadIdx.x < C) {
         const int k = threadIdx.x, ch = cb + k;
-        if (ch < I.C) {
-            DF t = red[k][0];
-            for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = df_add(t, red[k][j]);
-            part[I.part_base + (int64_t)ch * I.ntiles + vt.t_in_inst] = make_float2(t.hi, t.lo);
-        }
+        DF t = red[k][0];
+        for (int j = 1; j < (int)(blockDim.x >> 5); ++j) t = df_add(t, red[k][j]);
+        part[part_base + (int64_t)ch * ntiles + slot] = make_float2(t.hi, t.lo);
     }
     __syncthreads();
 }
 
-// Sum, per channel, the tile partials of one instance (fixed order: lane j
-// takes tiles j, j+32, ... in groups of 8 loads issued together; then the
-// warp tree) into out[ch] (FP64).  Warps take channels round-robin.  Must
-// be called by the whole block.  Partials written earlier in the same kernel
-// by other blocks are read through L2 (ld.cg).
+// Sum, per channel, the partials of one instance (fixed order: lane j takes
+// slots j, j+32, ... in groups of 8 loads issued together; then the warp
+// tree) into out[ch] (FP64).  Warps take channels round-robin.  Whole block.
+// Partials written earlier in the same launch by other blocks are read
+// through L2 (ld.cg).
 __device__ void reduce_instance_partials(const float2* __restrict__ part, const InstDev& I,
                                          double* out)
 {
@@ -95,19 +151,6 @@ __device__ void reduce_instance_partials(const float2* __restrict__ part, const 
 // so FP32 vectors keep the data term intact.  A vertex without neighbours
 // has smoothness part 0 (its row of lambda (D_m - D_n Bbar D_n) vanishes once
 // n^2 = m / 10).  M^-1 = 1 / diag(A), 0 where diag(A) <= 0.
-__device__ __forceinline__ void vertex_epilogue_terms(const SolveArgs& A, const InstDev& I,
-                                                      int64_t v, uint32_t cnt, DF sc, bool has_nbr,
-                                                      double sum_n)
-{
-    const double nv = A.n64[v];
-    const double scd = (double)sc.hi + (double)sc.lo;
-    const double lam = (double)I.lam;
-    const double rem = has_nbr ? lam * ((double)cnt - nv * (10.0 * nv + sum_n)) : 0.0;
-    const double diag = has_nbr ? lam * ((double)cnt - 10.0 * nv * nv) + scd : scd;
-    A.a[v] = (float)(rem + scd);
-    A.nm[v] = make_float2((float)nv, diag > 0.0 ? (float)(1.0 / diag) : 0.0f);
-}
-
 __device__ __forceinline__ void vertex_epilogue(const SolveArgs& A, const InstDev& I, int64_t v,
                                                 uint32_t cnt, DF sc)
 {
@@ -121,14 +164,20 @@ __device__ __forceinline__ void vertex_epilogue(const SolveArgs& A, const InstDe
             sum_n += A.n64[u];
         }
     }
-    vertex_epilogue_terms(A, I, v, cnt, sc, has_nbr, sum_n);
+    const double nv = A.n64[v];
+    const double scd = (double)sc.hi + (double)sc.lo;
+    const double lam = (double)I.lam;
+    const double rem = has_nbr ? lam * ((double)cnt - nv * (10.0 * nv + sum_n)) : 0.0;
+    const double diag = has_nbr ? lam * ((double)cnt - 10.0 * nv * nv) + scd : scd;
+    A.a[v] = (float)(rem + scd);
+    A.nm[v] = make_float2((float)nv, diag > 0.0 ? (float)(1.0 / diag) : 0.0f);
 }
-
 
 // One thread per vertex sums its pixels (in the sorted pixel order, so the
 // result is deterministic) with exact products accumulated as double-float
-// pairs.  Writes b into r, y0 = b / S c into y, diag(A) into a, and
-// {n, M^-1} into nm.
+// pairs.  Writes b into r (as a double-float pair r, r_lo when comp), y0 =
+// b / S c into y (zero in the padding channels), the diagonal remainder a'
+// into a, and {n, M^-1} into nm.
 template <int CB>
 __global__ void __launch_bounds__(kVTile)
 splat_kernel(SolveArgs A, int mode, float sigma_gm, int comp)
@@ -213,304 +262,377 @@ splat_kernel(SolveArgs A, int mode, float sigma_gm, int comp)
                 }
             }
         }
+        for (int ch = I.C; ch < I.Cp; ++ch) {   // padding channels stay zero
+            const int64_t idx = vec_index(I, ch, v);
+            A.r[idx] = 0.0f;
+            A.rlo[idx] = 0.0f;
+            A.y[idx] = 0.0f;
+            A.d[0][idx] = 0.0f;
+            A.d[1][idx] = 0.0f;
+            A.q[idx] = 0.0f;
+        }
         if (bad) atomicOr(A.err, kErrNonFinite);
         vertex_epilogue(A, I, v, cnt, sc);
     }
 }
 
-// Laplacian-form apply at one vertex for one channel:
-//   (A z)_v = a'_v z_v + lambda n_v sum_u n_u (z_v - z_u).
-// COMP = false: FP32 arithmetic (result in .hi, .lo = 0).
-// COMP = true: every product is exact (two-product) and the sums are carried
-// as double-float pairs, so the result is accurate to ~2^-44 relative.
-template <bool COMP, typename NbrVal>
-__device__ __forceinline__ DF laplacian_apply(float av, float lam_n, const int32_t (&nb)[10],
-                                              const float2 (&nmu)[10], float zv, NbrVal zu)
+// ------------------------------------------------- Laplacian-form apply ---
+// Accumulates, for W channels, sum_u n_u (z_v - z_u) over the neighbours;
+// with COMP every product is exact and the sums are double-float pairs.
+template <int W, bool COMP>
+__device__ __forceinline__ void lap_acc(DF (&s)[W], float nu, const float (&zv)[W],
+                                        const float (&zu)[W])
 {
-    if (COMP) {
-        DF s = {0.0f, 0.0f};
 #pragma unroll
-        for (int j = 0; j < 10; ++j)
-            if (nb[j] >= 0) s = df_add(s, df_mul_exact(nmu[j].x, zv - zu(j)));
-        return df_add(df_mul_exact(av, zv), df_mul_f(s, lam_n));
-    } else {
-        float s = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 10; ++j)
-            if (nb[j] >= 0) s = fmaf(nmu[j].x, zv - zu(j), s);
-        return DF{fmaf(av, zv, lam_n * s), 0.0f};
+    for (int k = 0; k < W; ++k) {
+        if (COMP) s[k] = df_add(s[k], df_mul_exact(nu, zv[k] - zu[k]));
+        else s[k].hi = fmaf(nu, zv[k] - zu[k], s[k].hi);
     }
 }
 
-// Branch-free form over register arrays: nu[j] = n of neighbour j (0 when
-// absent, which makes its term an exact zero), zu[j] its (finite) value.
+// (A z)_v = a'_v z_v + lambda n_v s
 template <bool COMP>
-__device__ __forceinline__ DF laplacian_apply_v(float av, float lam_n, float zv,
-                                                const float (&nu)[10], const float (&zu)[10])
+__device__ __forceinline__ DF lap_finish(float av, float lam_n, float zv, DF s)
 {
-    if (COMP) {
-        DF s = {0.0f, 0.0f};
-#pragma unroll
-        for (int j = 0; j < 10; ++j) s = df_add(s, df_mul_exact(nu[j], zv - zu[j]));
-        return df_add(df_mul_exact(av, zv), df_mul_f(s, lam_n));
-    } else {
-        float s = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 10; ++j) s = fmaf(nu[j], zv - zu[j], s);
-        return DF{fmaf(av, zv, lam_n * s), 0.0f};
-    }
-}
-
-// topology of one vertex: neighbour ids, {n, M^-1} of the neighbours, a', {n, M^-1}
-struct VertexTopo {
-    int32_t nb[10];
-    float2 nmu[10];
-    float av;
-    float2 nmv;
-};
-
-__device__ __forceinline__ void load_topo(const SolveArgs& A, int64_t v, bool valid, VertexTopo& T)
-{
-    T.av = 0.0f;
-    T.nmv = make_float2(0.0f, 0.0f);
-#pragma unroll
-    for (int k = 0; k < 10; ++k) {
-        T.nb[k] = valid ? A.nbr[(int64_t)k * A.Vtot + v] : -1;
-        T.nmu[k] = T.nb[k] >= 0 ? A.nm[T.nb[k]] : make_float2(0.0f, 0.0f);
-    }
-    if (valid) {
-        T.av = A.a[v];
-        T.nmv = A.nm[v];
-    }
+    return COMP ? df_add(df_mul_exact(av, zv), df_mul_f(s, lam_n))
+                : DF{fmaf(av, zv, lam_n * s.hi), 0.0f};
 }
 
 // ------------------------------------------------------- initial residual ---
 // r = b - A y0 (b is in r, and in r_lo too when COMP); tile partials of
 // r^T M^-1 r (delta_0) into rs slot 0.
-template <int CB, bool COMP>
+template <int W, bool COMP>
+__device__ __forceinline__ void residual_tile(const SolveArgs& A, const InstDev& I,
+                                              const VTile& vt, PhaseSmem& S)
+{
+    const int64_t v = vt.v0 + threadIdx.x;
+    const bool valid = v < vt.v1;
+    const int64_t vs = valid ? v : vt.v0;
+    const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
+    const float av = valid ? A.a[v] : 0.0f;
+    const float lam_n = I.lam * nmv.x;
+    int32_t nb[10];
+#pragma unroll
+    for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+    for (int cb = 0; cb < I.C; cb += W) {
+        const int64_t base = pass_base(I, cb);
+        float yv[W];
+        ldw<W, false>(A.y + base + vs * I.Cp, yv);
+        DF s[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            const int64_t u = nb[j] >= 0 ? nb[j] : vs;
+            const float nu = nb[j] >= 0 ? A.nm[u].x : 0.0f;
+            float yu[W];
+            ldw<W, false>(A.y + base + u * I.Cp, yu);
+            lap_acc<W, COMP>(s, nu, yv, yu);
+        }
+        float rv[W];
+        ldw<W, false>(A.r + base + vs * I.Cp, rv);
+        float rl[W];
+        if (COMP) ldw<W, false>(A.rlo + base + vs * I.Cp, rl);
+        DF acc[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const DF Ay = lap_finish<COMP>(av, lam_n, yv[k], s[k]);
+            if (COMP) {
+                const DF r = df_add(DF{rv[k], rl[k]}, df_neg(Ay));
+                rv[k] = r.hi;
+                rl[k] = r.lo;
+            } else {
+                rv[k] = rv[k] - Ay.hi;
+            }
+            acc[k] = valid && cb + k < I.C ? df_mul_exact(rv[k], nmv.y * rv[k]) : DF{0.0f, 0.0f};
+        }
+        if (valid) {
+            stw<W>(A.r + base + v * I.Cp, rv);
+            if (COMP) stw<W>(A.rlo + base + v * I.Cp, rl);
+        }
+        store_partials<W>(acc, I.C, I.ntiles, I.part_base, cb, vt.t_in_inst, A.part_rs[0], S.red);
+    }
+}
+
+template <bool COMP>
 __global__ void __launch_bounds__(kVTile)
 residual_kernel(SolveArgs A)
 {
-    __shared__ DF red[CB][kVTile / 32];
+    __shared__ PhaseSmem S;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
     for (int tile = t0; tile < t1; ++tile) {
         const VTile vt = A.vt[tile];
         const InstDev I = A.inst[vt.inst];
-        const int64_t v = vt.v0 + threadIdx.x;
-        const bool valid = v < vt.v1;
-        VertexTopo T;
-        load_topo(A, v, valid, T);
-        const float lam_n = I.lam * T.nmv.x;
-        for (int cb = 0; cb < I.C; cb += CB) {
-            DF acc[CB];
+        if (I.Cp == 1) residual_tile<1, COMP>(A, I, vt, S);
+        else if (I.Cp == 2) residual_tile<2, COMP>(A, I, vt, S);
+        else residual_tile<4, COMP>(A, I, vt, S);
+    }
+}
+
+// -------------------------------------------------- PCG phase bodies ---
+// Phase 1 of iteration `it` on one tile: d = M^-1 r + beta d_old (own vertex
+// and, on the fly, its neighbours), q = A d, products d q.  COMP: q is not
+// stored (phase 2 recomputes it exactly from d).
+template <int W, bool COMP, bool CO>
+__device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
+                                           const float* __restrict__ dold,
+                                           float* __restrict__ dnew, bool first, PhaseSmem& S,
+                                           DF (&run)[4], bool single)
+{
+    const int64_t v = vt.v0 + threadIdx.x;
+    const bool valid = v < vt.v1;
+    const int64_t vs = valid ? v : vt.v0;
+    const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
+    const float av = valid ? A.a[v] : 0.0f;
+    const float lam_n = I.lam * nmv.x;
+    int32_t nb[10];
 #pragma unroll
-            for (int k = 0; k < CB; ++k) {
-                acc[k] = {0.0f, 0.0f};
-                const int ch = cb + k;
-                if (valid && ch < I.C) {
-                    const int64_t base = I.vec_base + (int64_t)ch * I.V - I.voff;
-                    const float* y = A.y;
-                    const DF Ay = laplacian_apply<COMP>(T.av, lam_n, T.nb, T.nmu, y[base + v],
-                                                        [&](int j) { return y[base + T.nb[j]]; });
-                    float rhi;
-                    if (COMP) {
-                        const DF r = df_add(DF{A.r[base + v], A.rlo[base + v]}, df_neg(Ay));
-                        A.r[base + v] = r.hi;
-                        A.rlo[base + v] = r.lo;
-                        rhi = r.hi;
-                    } else {
-                        rhi = A.r[base + v] - Ay.hi;
-                        A.r[base + v] = rhi;
-                    }
-                    acc[k] = df_mul_exact(rhi, T.nmv.y * rhi);
-                }
+    for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+    for (int cb = 0; cb < I.C; cb += W) {
+        const int64_t base = pass_base(I, cb);
+        float beta[W], rv[W], dv[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) beta[k] = S.sf[min(cb + k, kMaxChannels - 1)];
+        ldw<W, CO>(A.r + base + vs * I.Cp, rv);
+        if (first) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) dv[k] = nmv.y * rv[k];
+        } else {
+            float ov[W];
+            ldw<W, CO>(dold + base + vs * I.Cp, ov);
+#pragma unroll
+            for (int k = 0; k < W; ++k) dv[k] = fmaf(beta[k], ov[k], nmv.y * rv[k]);
+        }
+        DF s[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            const int64_t u = nb[j] >= 0 ? nb[j] : vs;
+            const float2 nmu = nb[j] >= 0 ? A.nm[u] : make_float2(0.0f, 0.0f);
+            float ru[W], du[W];
+            ldw<W, CO>(A.r + base + u * I.Cp, ru);
+            if (first) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) du[k] = nmu.y * ru[k];
+            } else {
+                float ou[W];
+                ldw<W, CO>(dold + base + u * I.Cp, ou);
+#pragma unroll
+                for (int k = 0; k < W; ++k) du[k] = fmaf(beta[k], ou[k], nmu.y * ru[k]);
             }
-            store_tile_partials<CB>(acc, I, vt, cb, A.part_rs[0], red);
+            lap_acc<W, COMP>(s, nmu.x, dv, du);
+        }
+        DF acc[W];
+        float qh[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const DF q = lap_finish<COMP>(av, lam_n, dv[k], s[k]);
+            qh[k] = q.hi;
+            const bool on = valid && cb + k < I.C;
+            acc[k] = !on ? DF{0.0f, 0.0f}
+                         : COMP ? df_add(df_mul_exact(dv[k], q.hi), DF{dv[k] * q.lo, 0.0f})
+                                : df_mul_exact(dv[k], q.hi);
+        }
+        if (valid) {
+            stw<W>(dnew + base + v * I.Cp, dv);
+            if (!COMP) stw<W>(A.q + base + v * I.Cp, qh);
+        }
+        if (single) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) run[k] = df_add(run[k], acc[k]);
+        } else {
+            store_partials<W>(acc, I.C, I.ntiles, I.part_base, cb, vt.t_in_inst, A.part_dq,
+                              S.red);
         }
     }
 }
 
-// Loads of CG vectors: plain in the per-phase kernels; through L2 (ld.cg)
-// in the persistent loop, where other blocks rewrite them between grid
-// barriers and an SM's L1 could otherwise hold a stale line.
-template <bool CO>
-__device__ __forceinline__ float ldv(const float* p)
-{
-    return CO ? __ldcg(p) : *p;
-}
-
-// shared scratch of the two PCG phases
-template <int CB>
-struct PhaseSmem {
-    DF red[CB][kVTile / 32];
-    double sd[kMaxChannels];     // reduced inner products
-    float sf[kMaxChannels];      // beta (phase 1)
-    double sa[kMaxChannels];     // alpha (phase 2)
-};
-
-// ------------------------------------------------------- PCG phase 1 ---
-// Iteration `it`: delta_it = reduce(rs partials of slot it % 2);
-// beta = delta_it / delta_{it-1} (0 at it = 0); d = M^-1 r + beta d_old (own
-// vertex and, on the fly, its neighbours); q = A d; tile partials of d^T q.
-// delta_it is also stored (slot it % 2) for phase 2 and the next phase 1.
-// COMP: q is not stored (phase 2 recomputes it exactly from d).
-template <int CB, bool COMP, bool CO>
-__device__ void phase_apply(const SolveArgs& A, const float* __restrict__ dold,
-                            float* __restrict__ dnew, int it, int t0, int t1, PhaseSmem<CB>& S)
-{
-    const int slot = it & 1;
-    const bool first = it == 0;
-    int cur = -1;
-    for (int tile = t0; tile < t1; ++tile) {
-        const VTile vt = A.vt[tile];
-        const InstDev I = A.inst[vt.inst];
-        if (vt.inst != cur) {
-            __syncthreads();
-            reduce_instance_partials(A.part_rs[slot], I, S.sd);
-            __syncthreads();
-            if (threadIdx.x < I.C) {
-                const int ch = threadIdx.x;
-                const double dnow = S.sd[ch];
-                double beta = 0.0;
-                if (!first) {
-                    const double dprev = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1])
-                                            : A.scal[I.pc + ch].delta[slot ^ 1];
-                    beta = dprev != 0.0 ? dnow / dprev : 0.0;
-                }
-                S.sf[ch] = (float)beta;
-                A.scal[I.pc + ch].delta[slot] = dnow;   // same value from every block
-            }
-            __syncthreads();
-            cur = vt.inst;
-        }
-        const int64_t v = vt.v0 + threadIdx.x;
-        const bool valid = v < vt.v1;
-        VertexTopo T;
-        load_topo(A, v, valid, T);
-        const float lam_n = I.lam * T.nmv.x;
-        for (int cb = 0; cb < I.C; cb += CB) {
-            DF acc[CB];
-#pragma unroll
-            for (int k = 0; k < CB; ++k) {
-                acc[k] = {0.0f, 0.0f};
-                const int ch = cb + k;
-                if (valid && ch < I.C) {
-                    const int64_t base = I.vec_base + (int64_t)ch * I.V - I.voff;
-                    const float beta = S.sf[ch];
-                    const float* r = A.r;
-                    float dv = T.nmv.y * ldv<CO>(r + base + v);
-                    if (!first) dv = fmaf(beta, ldv<CO>(dold + base + v), dv);
-                    const DF q = laplacian_apply<COMP>(T.av, lam_n, T.nb, T.nmu, dv, [&](int j) {
-                        const int64_t u = base + T.nb[j];
-                        float du = T.nmu[j].y * ldv<CO>(r + u);
-                        if (!first) du = fmaf(beta, ldv<CO>(dold + u), du);
-                        return du;
-                    });
-                    dnew[base + v] = dv;
-                    if (COMP) {
-                        acc[k] = df_add(df_mul_exact(dv, q.hi), DF{dv * q.lo, 0.0f});
-                    } else {
-                        A.q[base + v] = q.hi;
-                        acc[k] = df_mul_exact(dv, q.hi);
-                    }
-                }
-            }
-            store_tile_partials<CB>(acc, I, vt, cb, A.part_dq, S.red);
-        }
-    }
-}
-
-// ------------------------------------------------------- PCG phase 2 ---
-// alpha = delta_it / reduce(d^T q partials) (0 if d^T q <= 0 or delta = 0);
-// y += alpha d; r -= alpha q; tile partials of r^T M^-1 r into rs slot
-// (it + 1) % 2.
+// Phase 2 on one tile: y += alpha d; r -= alpha q; products r M^-1 r.
 // COMP: q = A d is recomputed here with compensated arithmetic and the
 // residual is kept as a double-float pair (r, r_lo), so the recurrence
 // r <- r - alpha A d carries no rounding of q.
-template <int CB, bool COMP, bool CO>
-__device__ void phase_update(const SolveArgs& A, const float* __restrict__ d, int it, int t0,
-                             int t1, PhaseSmem<CB>& S)
+template <int W, bool COMP, bool CO>
+__device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
+                                            const float* __restrict__ d, float2* __restrict__ out,
+                                            PhaseSmem& S, DF (&run)[4], bool single)
 {
-    const int slot = it & 1;
-    int cur = -1;
-    for (int tile = t0; tile < t1; ++tile) {
-        const VTile vt = A.vt[tile];
-        const InstDev I = A.inst[vt.inst];
-        if (vt.inst != cur) {
-            __syncthreads();
-            reduce_instance_partials(A.part_dq, I, S.sd);
-            __syncthreads();
-            if (threadIdx.x < I.C) {
-                const int ch = threadIdx.x;
-                const double delta = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot])
-                                        : A.scal[I.pc + ch].delta[slot];
-                const double dq = S.sd[ch];
-                S.sa[ch] = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
-            }
-            __syncthreads();
-            cur = vt.inst;
-        }
-        const int64_t v = vt.v0 + threadIdx.x;
-        const bool valid = v < vt.v1;
-        VertexTopo T;
-        if (COMP) {
-            load_topo(A, v, valid, T);
-        } else {
-            T.nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
-        }
-        const float lam_n = I.lam * T.nmv.x;
-        for (int cb = 0; cb < I.C; cb += CB) {
-            DF acc[CB];
+    const int64_t v = vt.v0 + threadIdx.x;
+    const bool valid = v < vt.v1;
+    const int64_t vs = valid ? v : vt.v0;
+    const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
+    const float av = COMP && valid ? A.a[v] : 0.0f;
+    const float lam_n = I.lam * nmv.x;
+    int32_t nb[10];
+    if (COMP) {
 #pragma unroll
-            for (int k = 0; k < CB; ++k) {
-                acc[k] = {0.0f, 0.0f};
-                const int ch = cb + k;
-                if (valid && ch < I.C) {
-                    const int64_t base = I.vec_base + (int64_t)ch * I.V - I.voff;
-                    const int64_t idx = base + v;
-                    const double alpha = S.sa[ch];
-                    const float dv = ldv<CO>(d + idx);
-                    A.y[idx] = fmaf((float)alpha, dv, ldv<CO>(A.y + idx));
-                    float rhi;
-                    if (COMP) {
-                        const DF q = laplacian_apply<true>(T.av, lam_n, T.nb, T.nmu, dv,
-                                                           [&](int j) { return ldv<CO>(d + base + T.nb[j]); });
-                        const DF r = df_add(DF{ldv<CO>(A.r + idx), ldv<CO>(A.rlo + idx)},
-                                            df_neg(df_mul(df_from_double(alpha), q)));
-                        A.r[idx] = r.hi;
-                        A.rlo[idx] = r.lo;
-                        rhi = r.hi;
-                    } else {
-                        rhi = fmaf(-(float)alpha, ldv<CO>(A.q + idx), ldv<CO>(A.r + idx));
-                        A.r[idx] = rhi;
-                    }
-                    acc[k] = df_mul_exact(rhi, T.nmv.y * rhi);
-                }
+        for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+    }
+    for (int cb = 0; cb < I.C; cb += W) {
+        const int64_t base = pass_base(I, cb);
+        float dv[W], yv[W], rv[W], rl[W], qv[W];
+        ldw<W, CO>(d + base + vs * I.Cp, dv);
+        ldw<W, CO>(A.y + base + vs * I.Cp, yv);
+        ldw<W, CO>(A.r + base + vs * I.Cp, rv);
+        DF s[W];
+        if (COMP) {
+            ldw<W, CO>(A.rlo + base + vs * I.Cp, rl);
+#pragma unroll
+            for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < 10; ++j) {
+                const int64_t u = nb[j] >= 0 ? nb[j] : vs;
+                const float nu = nb[j] >= 0 ? A.nm[u].x : 0.0f;
+                float du[W];
+                ldw<W, CO>(d + base + u * I.Cp, du);
+                lap_acc<W, true>(s, nu, dv, du);
             }
-            store_tile_partials<CB>(acc, I, vt, cb, A.part_rs[slot ^ 1], S.red);
+        } else {
+            ldw<W, CO>(A.q + base + vs * I.Cp, qv);
+        }
+        DF acc[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const double alpha = S.sa[min(cb + k, kMaxChannels - 1)];
+            yv[k] = fmaf((float)alpha, dv[k], yv[k]);
+            if (COMP) {
+                const DF q = lap_finish<true>(av, lam_n, dv[k], s[k]);
+                const DF r = df_add(DF{rv[k], rl[k]}, df_neg(df_mul(df_from_double(alpha), q)));
+                rv[k] = r.hi;
+                rl[k] = r.lo;
+            } else {
+                rv[k] = fmaf(-(float)alpha, qv[k], rv[k]);
+            }
+            const bool on = valid && cb + k < I.C;
+            acc[k] = on ? df_mul_exact(rv[k], nmv.y * rv[k]) : DF{0.0f, 0.0f};
+        }
+        if (valid) {
+            stw<W>(A.y + base + v * I.Cp, yv);
+            stw<W>(A.r + base + v * I.Cp, rv);
+            if (COMP) stw<W>(A.rlo + base + v * I.Cp, rl);
+        }
+        if (single) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) run[k] = df_add(run[k], acc[k]);
+        } else {
+            store_partials<W>(acc, I.C, I.ntiles, I.part_base, cb, vt.t_in_inst, out, S.red);
         }
     }
 }
 
-template <int CB, bool COMP>
+// Store the block's run partial (channels of one pass) in the slot of the
+// first tile of the run; the other slots of the run were written as exact
+// zeros as their tiles were visited, so the reducers' sums are unchanged.
+__device__ __forceinline__ void flush_run(DF (&run)[4], int W, int C, int ntiles,
+                                          int64_t part_base, int slot, float2* part,
+                                          PhaseSmem& S)
+{
+    if (W == 1) {
+        DF r1[1] = {run[0]};
+        store_partials<1>(r1, C, ntiles, part_base, 0, slot, part, S.red);
+    } else if (W == 2) {
+        DF r2[2] = {run[0], run[1]};
+        store_partials<2>(r2, C, ntiles, part_base, 0, slot, part, S.red);
+    } else {
+        store_partials<4>(run, C, ntiles, part_base, 0, slot, part, S.red);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) run[k] = {0.0f, 0.0f};
+}
+
+// Loop over a block's chunk of tiles for one phase.  At each new image the
+// block reduces the previous phase's partials of that image and forms the CG
+// scalars (phase 1: delta_it and beta; phase 2: alpha), then dispatches each
+// tile on the image's pass width.  When an image's channels fit one pass the
+// products are accumulated over the run of its tiles in this chunk.
+template <int PHASE, bool COMP, bool CO>
+__device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
+                          float* __restrict__ ddst, int it, int t0, int t1, PhaseSmem& S)
+{
+    const int slot = it & 1;
+    const bool first = it == 0;
+    float2* const out = PHASE == 1 ? A.part_dq : A.part_rs[slot ^ 1];
+    const float2* const in = PHASE == 1 ? A.part_rs[slot] : A.part_dq;
+    int cur = -1, run_tile = 0, run_C = 0, run_W = 1, run_ntiles = 0;
+    int64_t run_base = 0;
+    bool single = false;
+    DF run[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) run[k] = {0.0f, 0.0f};
+    for (int tile = t0; tile < t1; ++tile) {
+        const VTile vt = A.vt[tile];
+        const InstDev I = A.inst[vt.inst];
+        if (vt.inst != cur) {
+            if (cur >= 0 && single)
+                flush_run(run, run_W, run_C, run_ntiles, run_base, run_tile, out, S);
+            __syncthreads();
+            reduce_instance_partials(in, I, S.sd);
+            __syncthreads();
+            for (int ch = threadIdx.x; ch < I.Cp; ch += blockDim.x) {
+                if (ch >= I.C) {            // padding channels: scalars 0 keep them at 0
+                    S.sf[ch] = 0.0f;
+                    S.sa[ch] = 0.0;
+                } else if (PHASE == 1) {
+                    const double dnow = S.sd[ch];
+                    double beta = 0.0;
+                    if (!first) {
+                        const double dprev = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1])
+                                                : A.scal[I.pc + ch].delta[slot ^ 1];
+                        beta = dprev != 0.0 ? dnow / dprev : 0.0;
+                    }
+                    S.sf[ch] = (float)beta;
+                    A.scal[I.pc + ch].delta[slot] = dnow;   // same value from every block
+                } else {
+                    const double delta = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot])
+                                            : A.scal[I.pc + ch].delta[slot];
+                    const double dq = S.sd[ch];
+                    S.sa[ch] = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
+                }
+            }
+            __syncthreads();
+            cur = vt.inst;
+            run_tile = vt.t_in_inst;
+            run_C = I.C;
+            run_W = I.Cp < 4 ? I.Cp : 4;
+            run_ntiles = I.ntiles;
+            run_base = I.part_base;
+            single = I.Cp <= 4;
+        } else if (single && (int)threadIdx.x < I.C) {
+            out[I.part_base + (int64_t)threadIdx.x * I.ntiles + vt.t_in_inst] =
+                make_float2(0.0f, 0.0f);
+        }
+        if (PHASE == 1) {
+            if (I.Cp == 1) apply_tile<1, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
+            else if (I.Cp == 2) apply_tile<2, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
+            else apply_tile<4, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
+        } else {
+            if (I.Cp == 1) update_tile<1, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
+            else if (I.Cp == 2) update_tile<2, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
+            else update_tile<4, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
+        }
+    }
+    if (cur >= 0 && single) flush_run(run, run_W, run_C, run_ntiles, run_base, run_tile, out, S);
+}
+
+template <bool COMP>
 __global__ void __launch_bounds__(kVTile)
 pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict__ dnew, int it)
 {
-    __shared__ PhaseSmem<CB> S;
+    __shared__ PhaseSmem S;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
-    phase_apply<CB, COMP, false>(A, dold, dnew, it, t0, t1, S);
+    phase_run<1, COMP, false>(A, dold, dnew, it, t0, t1, S);
 }
 
-template <int CB, bool COMP>
+template <bool COMP>
 __global__ void __launch_bounds__(kVTile)
 pcg_update_kernel(SolveArgs A, const float* __restrict__ d, int it)
 {
-    __shared__ PhaseSmem<CB> S;
+    __shared__ PhaseSmem S;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
-    phase_update<CB, COMP, false>(A, d, it, t0, t1, S);
+    phase_run<2, COMP, false>(A, d, nullptr, it, t0, t1, S);
 }
 
 // ------------------------------------------------- persistent PCG loop ---
@@ -566,45 +688,46 @@ __device__ bool grid_barrier(unsigned* bar, uint32_t* err)
 
 // All `iters` PCG iterations in one cooperative launch: phase 1, barrier,
 // phase 2, barrier.  Every block keeps the same chunk of tiles throughout.
-template <int CB, bool COMP>
+template <bool COMP>
 __global__ void __launch_bounds__(kVTile)
 pcg_loop_kernel(SolveArgs A, int iters, unsigned* bar)
 {
-    __shared__ PhaseSmem<CB> S;
+    __shared__ PhaseSmem S;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
     for (int it = 0; it < iters; ++it) {
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
-        phase_apply<CB, COMP, true>(A, dold, dnew, it, t0, t1, S);
+        phase_run<1, COMP, true>(A, dold, dnew, it, t0, t1, S);
         if (!grid_barrier(bar, A.err)) return;
-        phase_update<CB, COMP, true>(A, dnew, it, t0, t1, S);
+        phase_run<2, COMP, true>(A, dnew, nullptr, it, t0, t1, S);
         if (!grid_barrier(bar, A.err)) return;
     }
 }
 
 // ------------------------------------------ resident persistent PCG loop ---
-// The same iterations when every tile has its own co-resident block and an
-// image has at most CB channels: each block keeps its tile's neighbour ids
-// and neighbours' {n, M^-1} in shared memory for the whole loop, and each
-// thread keeps its vertex's r, y, d (and q) in registers, writing d and r for
-// the neighbours and y once at the end.  Neighbour gathers use a safe index
-// (the vertex itself when a neighbour is absent) so they issue together.
+// The same iterations when every tile has its own co-resident block and each
+// image's channels fit one pass (Cp <= 4): each block keeps its tile's
+// neighbour ids and neighbours' {n, M^-1} in shared memory for the whole
+// loop, and each thread keeps its vertex's r, y, d (and q) in registers,
+// writing d and r for the neighbours and y once at the end.  Neighbour
+// gathers use a safe index (the vertex itself when a neighbour is absent) so
+// they issue together with the reduction of the previous phase's partials.
 
-// All threads sum the tile partials of one instance for all its channels
-// (thread t takes tiles t, t + blockDim, ...), then a block tree; out[ch].
-template <int CB>
+// All threads sum the partials of one instance for all its (<= W) channels
+// (thread t takes slots t, t + blockDim, ...), then a block tree; out[ch].
+template <int W>
 __device__ void reduce_partials_all(const float2* __restrict__ part, const InstDev& I,
                                     double* out, DF (*red)[kVTile / 32])
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    DF acc[CB];
+    DF acc[W];
 #pragma unroll
-    for (int k = 0; k < CB; ++k) acc[k] = {0.0f, 0.0f};
+    for (int k = 0; k < W; ++k) acc[k] = {0.0f, 0.0f};
     for (int j0 = threadIdx.x; j0 < I.ntiles; j0 += 2 * blockDim.x) {
-        float2 v[CB][2];
+        float2 v[W][2];
 #pragma unroll
-        for (int k = 0; k < CB; ++k)
+        for (int k = 0; k < W; ++k)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int j = j0 + h * blockDim.x;
@@ -613,17 +736,17 @@ __device__ void reduce_partials_all(const float2* __restrict__ part, const InstD
                               : make_float2(0.0f, 0.0f);
             }
 #pragma unroll
-        for (int k = 0; k < CB; ++k)
+        for (int k = 0; k < W; ++k)
 #pragma unroll
             for (int h = 0; h < 2; ++h) acc[k] = df_add(acc[k], DF{v[k][h].x, v[k][h].y});
     }
 #pragma unroll
-    for (int k = 0; k < CB; ++k) {
+    for (int k = 0; k < W; ++k) {
         const DF t = df_warp_sum(acc[k]);
         if (lane == 0) red[k][w] = t;
     }
     __syncthreads();
-    if (threadIdx.x < CB && threadIdx.x < I.C) {
+    if ((int)threadIdx.x < W && (int)threadIdx.x < I.C) {
         const int k = threadIdx.x;
         DF t = red[k][0];
         for (int j = 1; j < nw; ++j) t = df_add(t, red[k][j]);
@@ -632,26 +755,14 @@ __device__ void reduce_partials_all(const float2* __restrict__ part, const InstD
     __syncthreads();
 }
 
-template <int CB>
-__device__ __forceinline__ void store_partials_resident(DF (&acc)[CB], const InstDev& I,
-                                                        const VTile& vt, float2* __restrict__ part,
-                                                        DF (*red)[kVTile / 32])
+template <int W, bool COMP>
+__device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile& vt, int iters,
+                              unsigned* bar, int32_t (*s_nb)[kVTile], float2 (*s_nmu)[kVTile],
+                              PhaseSmem& S)
 {
-    store_tile_partials<CB>(acc, I, vt, 0, part, red);
-}
-
-template <int CB, bool COMP>
-__global__ void __launch_bounds__(kVTile, 3)
-pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
-{
-    __shared__ int32_t s_nb[10][kVTile];
-    __shared__ float2 s_nmu[10][kVTile];
-    __shared__ PhaseSmem<CB> S;
-    const VTile vt = A.vt[blockIdx.x];
-    const InstDev I = A.inst[vt.inst];
-    const int64_t v = vt.v0 + threadIdx.x;
-    const bool valid = v < vt.v1;
     const int tx = threadIdx.x;
+    const int64_t v = vt.v0 + tx;
+    const bool valid = v < vt.v1;
     // topology, once
     float av = 0.0f;
     float2 nmv = make_float2(0.0f, 0.0f);
@@ -666,20 +777,19 @@ pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
         nmv = A.nm[v];
     }
     const float lam_n = I.lam * nmv.x;
+    const int64_t vs = valid ? v : vt.v0;   // safe gather index for absent neighbours
+    const int64_t base = pass_base(I, 0);
     // own state in registers
-    float r[CB], rlo[CB], y[CB], d[CB], q[CB];
-    int64_t base[CB];
+    float r[W], rlo[W], y[W], d[W], q[W];
+    ldw<W, false>(A.r + base + vs * I.Cp, r);
+    ldw<W, false>(A.y + base + vs * I.Cp, y);
+    if (COMP) ldw<W, false>(A.rlo + base + vs * I.Cp, rlo);
 #pragma unroll
-    for (int k = 0; k < CB; ++k) {
-        base[k] = I.vec_base + (int64_t)min(k, I.C - 1) * I.V - I.voff;
-        const bool on = valid && k < I.C;
-        r[k] = on ? A.r[base[k] + v] : 0.0f;
-        rlo[k] = on && COMP ? A.rlo[base[k] + v] : 0.0f;
-        y[k] = on ? A.y[base[k] + v] : 0.0f;
+    for (int k = 0; k < W; ++k) {
         d[k] = 0.0f;
         q[k] = 0.0f;
+        if (!COMP) rlo[k] = 0.0f;
     }
-    const int64_t vs = valid ? v : vt.v0;   // safe gather index for absent neighbours
     for (int it = 0; it < iters; ++it) {
         const int slot = it & 1;
         const float* dold = A.d[(it + 1) & 1];
@@ -687,105 +797,139 @@ pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
         // ---- phase 1: gathers first (they do not depend on beta), then the
         // reduction of the previous phase's partials overlaps their latency
         {
-            DF acc[CB];
-            float ru[CB][10], du[CB][10], nu[10], mu[10];
+            float ru[10][W], du[10][W];
 #pragma unroll
             for (int j = 0; j < 10; ++j) {
                 const int32_t u0 = s_nb[j][tx];
                 const int64_t u = u0 >= 0 ? u0 : vs;
-                const float2 nm = s_nmu[j][tx];
-                nu[j] = nm.x;
-                mu[j] = nm.y;
+                ldw<W, true>(A.r + base + u * I.Cp, ru[j]);
+                if (it > 0) {
+                    ldw<W, true>(dold + base + u * I.Cp, du[j]);
+                } else {
 #pragma unroll
-                for (int k = 0; k < CB; ++k) {
-                    ru[k][j] = __ldcg(A.r + base[k] + u);
-                    du[k][j] = it > 0 ? __ldcg(dold + base[k] + u) : 0.0f;
+                    for (int k = 0; k < W; ++k) du[j][k] = 0.0f;
                 }
             }
-            reduce_partials_all<CB>(A.part_rs[slot], I, S.sd, S.red);
-            if (threadIdx.x < I.C && threadIdx.x < CB) {
-                const int ch = threadIdx.x;
+            reduce_partials_all<W>(A.part_rs[slot], I, S.sd, S.red);
+            if (tx < W) {
                 double beta = 0.0;
-                if (it > 0) {
-                    const double dprev = __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1]);
-                    beta = dprev != 0.0 ? S.sd[ch] / dprev : 0.0;
+                if (tx < I.C) {
+                    if (it > 0) {
+                        const double dprev = __ldcg(&A.scal[I.pc + tx].delta[slot ^ 1]);
+                        beta = dprev != 0.0 ? S.sd[tx] / dprev : 0.0;
+                    }
+                    A.scal[I.pc + tx].delta[slot] = S.sd[tx];
                 }
-                S.sf[ch] = (float)beta;
-                A.scal[I.pc + ch].delta[slot] = S.sd[ch];
+                S.sf[tx] = (float)beta;
             }
             __syncthreads();
+            float beta[W], dv[W];
 #pragma unroll
-            for (int k = 0; k < CB; ++k) {
-                acc[k] = {0.0f, 0.0f};
-                if (valid && k < I.C) {
-                    const float beta = S.sf[k];
-                    const float dv = fmaf(beta, d[k], nmv.y * r[k]);
-                    float dz[10];
-#pragma unroll
-                    for (int j = 0; j < 10; ++j) dz[j] = fmaf(beta, du[k][j], mu[j] * ru[k][j]);
-                    const DF qq = laplacian_apply_v<COMP>(av, lam_n, dv, nu, dz);
-                    d[k] = dv;
-                    q[k] = qq.hi;
-                    dnew[base[k] + v] = dv;
-                    acc[k] = COMP ? df_add(df_mul_exact(dv, qq.hi), DF{dv * qq.lo, 0.0f})
-                                  : df_mul_exact(dv, qq.hi);
-                }
+            for (int k = 0; k < W; ++k) {
+                beta[k] = S.sf[k];
+                dv[k] = fmaf(beta[k], d[k], nmv.y * r[k]);
             }
-            store_partials_resident<CB>(acc, I, vt, A.part_dq, S.red);
+            DF s[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < 10; ++j) {
+                const float2 nm = s_nmu[j][tx];
+                float dz[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) dz[k] = fmaf(beta[k], du[j][k], nm.y * ru[j][k]);
+                lap_acc<W, COMP>(s, nm.x, dv, dz);
+            }
+            DF acc[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const DF qq = lap_finish<COMP>(av, lam_n, dv[k], s[k]);
+                d[k] = dv[k];
+                q[k] = qq.hi;
+                const bool on = valid && k < I.C;
+                acc[k] = !on ? DF{0.0f, 0.0f}
+                             : COMP ? df_add(df_mul_exact(dv[k], qq.hi), DF{dv[k] * qq.lo, 0.0f})
+                                    : df_mul_exact(dv[k], qq.hi);
+            }
+            if (valid) stw<W>(dnew + base + v * I.Cp, dv);
+            store_partials<W>(acc, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst, A.part_dq, S.red);
         }
         if (!grid_barrier(bar, A.err)) return;
         // ---- phase 2
-        reduce_partials_all<CB>(A.part_dq, I, S.sd, S.red);
-        if (threadIdx.x < I.C && threadIdx.x < CB) {
-            const int ch = threadIdx.x;
-            const double delta = __ldcg(&A.scal[I.pc + ch].delta[slot]);
-            const double dq = S.sd[ch];
-            S.sa[ch] = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
-        }
-        __syncthreads();
         {
-            DF acc[CB];
-            float dn[CB][10], nu[10];
+            float dn[10][W];
             if (COMP) {
 #pragma unroll
                 for (int j = 0; j < 10; ++j) {
                     const int32_t u0 = s_nb[j][tx];
                     const int64_t u = u0 >= 0 ? u0 : vs;
-                    nu[j] = s_nmu[j][tx].x;
-#pragma unroll
-                    for (int k = 0; k < CB; ++k) dn[k][j] = __ldcg(dnew + base[k] + u);
+                    ldw<W, true>(dnew + base + u * I.Cp, dn[j]);
                 }
             }
-#pragma unroll
-            for (int k = 0; k < CB; ++k) {
-                acc[k] = {0.0f, 0.0f};
-                if (valid && k < I.C) {
-                    const double alpha = S.sa[k];
-                    y[k] = fmaf((float)alpha, d[k], y[k]);
-                    if (COMP) {
-                        const DF qq = laplacian_apply_v<true>(av, lam_n, d[k], nu, dn[k]);
-                        const DF rr = df_add(DF{r[k], rlo[k]},
-                                             df_neg(df_mul(df_from_double(alpha), qq)));
-                        r[k] = rr.hi;
-                        rlo[k] = rr.lo;
-                    } else {
-                        r[k] = fmaf(-(float)alpha, q[k], r[k]);
-                    }
-                    A.r[base[k] + v] = r[k];
-                    acc[k] = df_mul_exact(r[k], nmv.y * r[k]);
+            reduce_partials_all<W>(A.part_dq, I, S.sd, S.red);
+            if (tx < W) {
+                double alpha = 0.0;
+                if (tx < I.C) {
+                    const double delta = __ldcg(&A.scal[I.pc + tx].delta[slot]);
+                    const double dq = S.sd[tx];
+                    alpha = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
                 }
+                S.sa[tx] = alpha;
             }
-            store_partials_resident<CB>(acc, I, vt, A.part_rs[slot ^ 1], S.red);
+            __syncthreads();
+            DF s[W];
+            if (COMP) {
+#pragma unroll
+                for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
+#pragma unroll
+                for (int j = 0; j < 10; ++j) lap_acc<W, true>(s, s_nmu[j][tx].x, d, dn[j]);
+            }
+            DF acc[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const double alpha = S.sa[k];
+                y[k] = fmaf((float)alpha, d[k], y[k]);
+                if (COMP) {
+                    const DF qq = lap_finish<true>(av, lam_n, d[k], s[k]);
+                    const DF rr = df_add(DF{r[k], rlo[k]},
+                                         df_neg(df_mul(df_from_double(alpha), qq)));
+                    r[k] = rr.hi;
+                    rlo[k] = rr.lo;
+                } else {
+                    r[k] = fmaf(-(float)alpha, q[k], r[k]);
+                }
+                const bool on = valid && k < I.C;
+                acc[k] = on ? df_mul_exact(r[k], nmv.y * r[k]) : DF{0.0f, 0.0f};
+            }
+            if (valid) stw<W>(A.r + base + v * I.Cp, r);
+            store_partials<W>(acc, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst,
+                              A.part_rs[slot ^ 1], S.red);
         }
         if (!grid_barrier(bar, A.err)) return;
     }
-#pragma unroll
-    for (int k = 0; k < CB; ++k)
-        if (valid && k < I.C) {
-            A.y[base[k] + v] = y[k];
-            if (COMP) A.rlo[base[k] + v] = rlo[k];
-        }
+    if (valid) {
+        stw<W>(A.y + base + v * I.Cp, y);
+        if (COMP) stw<W>(A.rlo + base + v * I.Cp, rlo);
+    }
 }
+
+// WMAX: the widest pass of the batch (the largest Cp), so that a batch of
+// single-channel images gets the register budget of the W = 1 body alone.
+template <int WMAX, bool COMP>
+__global__ void __launch_bounds__(kVTile, WMAX == 4 ? 2 : 3)
+pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
+{
+    __shared__ int32_t s_nb[10][kVTile];
+    __shared__ float2 s_nmu[10][kVTile];
+    __shared__ PhaseSmem S;
+    const VTile vt = A.vt[blockIdx.x];
+    const InstDev I = A.inst[vt.inst];
+    if (WMAX == 1 || I.Cp == 1) resident_loop<1, COMP>(A, I, vt, iters, bar, s_nb, s_nmu, S);
+    else if (WMAX == 2 || I.Cp == 2) resident_loop<2, COMP>(A, I, vt, iters, bar, s_nb, s_nmu, S);
+    else resident_loop<4, COMP>(A, I, vt, iters, bar, s_nb, s_nmu, S);
+}
+
+int resident_width(int cmax) { return cmax <= 1 ? 1 : cmax <= 2 ? 2 : 4; }
 
 // ---------------------------------------------------------------- slice ---
 // x = S^T y for every pixel of image blockIdx.y.
@@ -823,7 +967,7 @@ backward_slice_kernel(SolveArgs A)
     }
 }
 
-// copy y (C x V of each image) to the caller's buffers
+// copy y to the caller's buffers (their layout: C x V per image)
 __global__ void __launch_bounds__(256)
 export_y_kernel(SolveArgs A)
 {
@@ -832,8 +976,10 @@ export_y_kernel(SolveArgs A)
     if (dst == nullptr) return;
     const int64_t n = (int64_t)I.C * I.V;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        dst[i] = A.y[I.vec_base + i];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ch = i / I.V, j = i - ch * I.V;
+        dst[i] = A.y[I.vec_base + j * I.Cp + ch];
+    }
 }
 
 int occupancy(const void* fn)
@@ -849,36 +995,24 @@ int persistent_blocks(int occ, int nvt)
     return nvt < cap ? nvt : cap;
 }
 
-template <int CB, bool COMP>
-cudaError_t launch_segment_t(const SolveArgs& A, const SolvePlan& P, int seg, int mode,
-                             cudaStream_t s)
+template <bool COMP>
+cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
 {
-    static int f_splat = prof_family("splat");
-    static int f_res = prof_family("residual");
     static int f_apply = prof_family("pcg_apply");
     static int f_update = prof_family("pcg_update");
-    static int f_slice = prof_family("slice");
-    static int f_bwd = prof_family("backward_slice");
-    static int f_export = prof_family("export_y");
-    static const int occ_s = occupancy((const void*)splat_kernel<CB>);
-    static const int occ_r = occupancy((const void*)residual_kernel<CB, COMP>);
-    static const int occ_p = occupancy((const void*)pcg_apply_kernel<CB, COMP>);
-    static const int occ_u = occupancy((const void*)pcg_update_kernel<CB, COMP>);
-    if (seg == kSegSetup) {
-        prof_begin(f_splat, s);
-        splat_kernel<CB><<<persistent_blocks(occ_s, A.nvt), kVTile, 0, s>>>(A, mode, P.sigma_gm,
-                                                                         COMP ? 1 : 0);
-        prof_end(f_splat, s);
-        prof_begin(f_res, s);
-        residual_kernel<CB, COMP><<<persistent_blocks(occ_r, A.nvt), kVTile, 0, s>>>(A);
-        prof_end(f_res, s);
-    } else if (seg == kSegLoop) {
-        if (P.persistent && P.pcg_iters > 0) {
-            static const int occ_l = occupancy((const void*)pcg_loop_kernel<CB, COMP>);
-            static const int occ_res = occupancy((const void*)pcg_resident_kernel<CB, COMP>);
-            static int f_loop = prof_family("pcg_loop");
-            static int f_res_loop = prof_family("pcg_resident");
-            const bool resident = P.cmax <= CB && A.nvt <= device_info().sms * occ_res;
+    static int f_loop = prof_family("pcg_loop");
+    static int f_res_loop = prof_family("pcg_resident");
+    static const int occ_p = occupancy((const void*)pcg_apply_kernel<COMP>);
+    static const int occ_u = occupancy((const void*)pcg_update_kernel<COMP>);
+    static const int occ_l = occupancy((const void*)pcg_loop_kernel<COMP>);
+    static const int occ_res[3] = {occupancy((const void*)pcg_resident_kernel<1, COMP>),
+                                   occupancy((const void*)pcg_resident_kernel<2, COMP>),
+                                   occupancy((const void*)pcg_resident_kernel<4, COMP>)};
+    if (P.persistent && P.pcg_iters > 0) {
+        const int wres = resident_width(P.cmax);
+        const int wi = wres == 1 ? 0 : wres == 2 ? 1 : 2;
+        const bool resident = P.cmax <= 4 && A.nvt <= device_info().sms * occ_res[wi];
+        if (resident || P.force_persistent) {
             // barrier words zero (or, for the failure-path test, a top counter
             // that the last arrival can never match)
             cudaError_t e = cudaMemsetAsync(P.barrier, 0, kBarrierWords * sizeof(unsigned), s);
@@ -891,75 +1025,112 @@ cudaError_t launch_segment_t(const SolveArgs& A, const SolvePlan& P, int seg, in
             void* args[] = {&a, &iters, &bar};
             if (resident) {
                 prof_begin(f_res_loop, s);
-                e = cudaLaunchCooperativeKernel((const void*)pcg_resident_kernel<CB, COMP>,
-                                                dim3(A.nvt), dim3(kVTile), args, 0, s);
+                const void* fn = wres == 1   ? (const void*)pcg_resident_kernel<1, COMP>
+                                 : wres == 2 ? (const void*)pcg_resident_kernel<2, COMP>
+                                             : (const void*)pcg_resident_kernel<4, COMP>;
+                e = cudaLaunchCooperativeKernel(fn, dim3(A.nvt), dim3(kVTile), args, 0, s);
                 prof_end(f_res_loop, s);
             } else {
-                const int nb_l = persistent_blocks(occ_l, A.nvt);
                 prof_begin(f_loop, s);
-                e = cudaLaunchCooperativeKernel((const void*)pcg_loop_kernel<CB, COMP>, dim3(nb_l),
+                e = cudaLaunchCooperativeKernel((const void*)pcg_loop_kernel<COMP>,
+                                                dim3(persistent_blocks(occ_l, A.nvt)),
                                                 dim3(kVTile), args, 0, s);
                 prof_end(f_loop, s);
             }
             if (e == cudaSuccess) return cudaGetLastError();
             cudaGetLastError();   // clear, and fall back to per-phase launches
         }
-        const int nb_p = persistent_blocks(occ_p, A.nvt);
-        const int nb_u = persistent_blocks(occ_u, A.nvt);
-        for (int it = 0; it < P.pcg_iters; ++it) {
-            const float* dold = A.d[(it + 1) & 1];
-            float* dnew = A.d[it & 1];
-            prof_begin(f_apply, s);
-            pcg_apply_kernel<CB, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
-            prof_end(f_apply, s);
-            prof_begin(f_update, s);
-            pcg_update_kernel<CB, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
-            prof_end(f_update, s);
-        }
-    } else {
-        const dim3 pix_grid((unsigned)std::min<int64_t>((P.max_pixels + 255) / 256,
-                                                        (int64_t)device_info().sms * 8),
-                            (unsigned)A.ninst);
-        if (P.mode == kSplatBackward) {
-            prof_begin(f_bwd, s);
-            backward_slice_kernel<<<pix_grid, 256, 0, s>>>(A);
-            prof_end(f_bwd, s);
-        } else {
-            prof_begin(f_slice, s);
-            slice_kernel<<<pix_grid, 256, 0, s>>>(A);
-            prof_end(f_slice, s);
-            if (P.export_y) {
-                const dim3 yg((unsigned)std::min<int64_t>((P.max_cv + 255) / 256,
-                                                          (int64_t)device_info().sms * 4),
-                              (unsigned)A.ninst);
-                prof_begin(f_export, s);
-                export_y_kernel<<<yg, 256, 0, s>>>(A);
-                prof_end(f_export, s);
-            }
-        }
     }
+    const int nb_p = persistent_blocks(occ_p, A.nvt);
+    const int nb_u = persistent_blocks(occ_u, A.nvt);
+    for (int it = 0; it < P.pcg_iters; ++it) {
+        const float* dold = A.d[(it + 1) & 1];
+        float* dnew = A.d[it & 1];
+        prof_begin(f_apply, s);
+        pcg_apply_kernel<COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+        prof_end(f_apply, s);
+        prof_begin(f_update, s);
+        pcg_update_kernel<COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
+        prof_end(f_update, s);
+    }
+    return cudaGetLastError();
+}
+
+template <int CB>
+cudaError_t launch_splat(const SolveArgs& A, const SolvePlan& P, int mode, cudaStream_t s)
+{
+    static const int occ_s = occupancy((const void*)splat_kernel<CB>);
+    splat_kernel<CB><<<persistent_blocks(occ_s, A.nvt), kVTile, 0, s>>>(A, mode, P.sigma_gm,
+                                                                     P.comp);
     return cudaGetLastError();
 }
 
 }  // namespace
 
+bool resident_fits(const SolveArgs& A, const SolvePlan& P)
+{
+    static const int occ[2][3] = {{occupancy((const void*)pcg_resident_kernel<1, false>),
+                                   occupancy((const void*)pcg_resident_kernel<2, false>),
+                                   occupancy((const void*)pcg_resident_kernel<4, false>)},
+                                  {occupancy((const void*)pcg_resident_kernel<1, true>),
+                                   occupancy((const void*)pcg_resident_kernel<2, true>),
+                                   occupancy((const void*)pcg_resident_kernel<4, true>)}};
+    if (P.cmax > 4) return false;
+    const int w = resident_width(P.cmax);
+    return A.nvt <= device_info().sms * occ[P.comp ? 1 : 0][w == 1 ? 0 : w == 2 ? 1 : 2];
+}
+
 cudaError_t launch_segment(const SolveArgs& A, const SolvePlan& P, int seg, int mode,
                            cudaStream_t s)
 {
-    if (P.comp) {
+    static int f_splat = prof_family("splat");
+    static int f_res = prof_family("residual");
+    static int f_slice = prof_family("slice");
+    static int f_bwd = prof_family("backward_slice");
+    static int f_export = prof_family("export_y");
+    static const int occ_rf = occupancy((const void*)residual_kernel<false>);
+    static const int occ_rt = occupancy((const void*)residual_kernel<true>);
+    cudaError_t e = cudaSuccess;
+    if (seg == kSegSetup) {
+        prof_begin(f_splat, s);
         switch (P.chan_block) {
-            case 1: return launch_segment_t<1, true>(A, P, seg, mode, s);
-            case 2: return launch_segment_t<2, true>(A, P, seg, mode, s);
-            case 3: return launch_segment_t<3, true>(A, P, seg, mode, s);
-            default: return launch_segment_t<4, true>(A, P, seg, mode, s);
+            case 1: e = launch_splat<1>(A, P, mode, s); break;
+            case 2: e = launch_splat<2>(A, P, mode, s); break;
+            case 3: e = launch_splat<3>(A, P, mode, s); break;
+            default: e = launch_splat<4>(A, P, mode, s); break;
+        }
+        prof_end(f_splat, s);
+        if (e != cudaSuccess) return e;
+        prof_begin(f_res, s);
+        if (P.comp)
+            residual_kernel<true><<<persistent_blocks(occ_rt, A.nvt), kVTile, 0, s>>>(A);
+        else
+            residual_kernel<false><<<persistent_blocks(occ_rf, A.nvt), kVTile, 0, s>>>(A);
+        prof_end(f_res, s);
+        return cudaGetLastError();
+    }
+    if (seg == kSegLoop) return P.comp ? launch_loop<true>(A, P, s) : launch_loop<false>(A, P, s);
+    const dim3 pix_grid((unsigned)std::min<int64_t>((P.max_pixels + 255) / 256,
+                                                    (int64_t)device_info().sms * 8),
+                        (unsigned)A.ninst);
+    if (P.mode == kSplatBackward) {
+        prof_begin(f_bwd, s);
+        backward_slice_kernel<<<pix_grid, 256, 0, s>>>(A);
+        prof_end(f_bwd, s);
+    } else {
+        prof_begin(f_slice, s);
+        slice_kernel<<<pix_grid, 256, 0, s>>>(A);
+        prof_end(f_slice, s);
+        if (P.export_y) {
+            const dim3 yg((unsigned)std::min<int64_t>((P.max_cv + 255) / 256,
+                                                      (int64_t)device_info().sms * 4),
+                          (unsigned)A.ninst);
+            prof_begin(f_export, s);
+            export_y_kernel<<<yg, 256, 0, s>>>(A);
+            prof_end(f_export, s);
         }
     }
-    switch (P.chan_block) {
-        case 1: return launch_segment_t<1, false>(A, P, seg, mode, s);
-        case 2: return launch_segment_t<2, false>(A, P, seg, mode, s);
-        case 3: return launch_segment_t<3, false>(A, P, seg, mode, s);
-        default: return launch_segment_t<4, false>(A, P, seg, mode, s);
-    }
+    return cudaGetLastError();
 }
 
 }  // namespace fbs

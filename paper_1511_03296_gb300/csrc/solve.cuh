@@ -45,7 +45,9 @@ struct SolvePlan {
     int64_t max_cv;            // largest C x V block
     bool export_y;
     int comp;                  // 1: compensated residual / recomputed q variant
-    int persistent;            // 1: the whole PCG loop in one cooperative launch
+    int persistent;            // 1: the whole PCG loop in one cooperative launch when the
+                               //    resident form fits (or always, with force_persistent)
+    int force_persistent;
     unsigned* barrier;         // kBarrierWords words of grid-barrier state (persistent loop)
     int inject_timeout;        // preset the barrier counter so no wait completes (test)
 };
@@ -57,5 +59,9 @@ struct SolvePlan {
 enum Segment : int { kSegSetup = 0, kSegLoop = 1, kSegOut = 2 };
 cudaError_t launch_segment(const SolveArgs& A, const SolvePlan& P, int seg, int mode,
                            cudaStream_t s);
+
+// true when every vertex tile can have its own co-resident block of the
+// resident persistent PCG loop and no image has more channels than a pass
+bool resident_fits(const SolveArgs& A, const SolvePlan& P);
 
 }  // namespace fbs

@@ -123,6 +123,7 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
         I.yout = probs[k].y;
         I.voff = G.voff[k];
         I.V = (int)(G.voff[k + 1] - G.voff[k]);
+        I.Cp = padded_channels(I.C);
         I.vec_base = cv;
         I.tile0 = G.vt0[k];
         I.ntiles = G.nvt_img[k];
@@ -130,7 +131,7 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
         I.part_base = cpart;
         I.N = (int64_t)G.img[k].H * G.img[k].W;
         I.pix_base = G.img[k].pix_base;
-        cv += (int64_t)I.C * I.V;
+        cv += ((int64_t)I.Cp * I.V + 3) / 4 * 4;     // 16-byte aligned image blocks
         cpart += (int64_t)I.C * I.ntiles;
         pc += I.C;
         cmax = cmax > I.C ? cmax : I.C;
@@ -203,6 +204,7 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
     cudaStreamIsCapturing(s, &cs);
     P.persistent = G.persistent && cs == cudaStreamCaptureStatusNone ? 1 : 0;
     P.barrier = reinterpret_cast<unsigned*>(base + L.barrier);
+    if (P.persistent && !resident_fits(A, P)) P.persistent = 0;
 
     e = launch_segment(A, P, kSegSetup, kSplatConfidence, s);
     if (e == cudaSuccess) e = launch_segment(A, P, kSegLoop, kSplatConfidence, s);

@@ -28,7 +28,7 @@ EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robus
 
 OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT = 1, 2, 3
 VECTORS_AUTO, VECTORS_FP32, VECTORS_COMPENSATED = 0, 1, 2
-PCG_PERSISTENT, PCG_PER_PHASE = 0, 1
+PCG_AUTO, PCG_PERSISTENT, PCG_PER_PHASE = 0, 1, 2
 
 
 class FbsError(RuntimeError):

@@ -19,7 +19,7 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-PCG_LAUNCH = {"mode": 0}    # fbs.PCG_PERSISTENT; tests may switch to PCG_PER_PHASE
+PCG_LAUNCH = {"mode": 0}    # fbs.PCG_AUTO; tests may switch to PCG_PERSISTENT / PCG_PER_PHASE
 
 
 def gpu_grid(insts, bistoch_iters=2):
