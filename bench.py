@@ -91,6 +91,16 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def rank_seed(base: int, rank: int) -> int:
+    """Each rank draws its own independent problems (weak scaling)."""
+    return base + rank
+
+
+def whole_job_mpix(world: int, pixels_per_rank: int, ms_max: float) -> float:
+    """Whole-job Mpix/s: every rank's pixels over the slowest rank's step time."""
+    return world * pixels_per_rank / (ms_max / 1e3) / 1e6
+
+
 # ---------------------------------------------------------------- clocks ---
 
 class ClockSampler:
@@ -269,7 +279,7 @@ def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, seq
     same images solved one at a time."""
     import torch
     from paper_1511_03296_gb300 import fbs, synth
-    wl = synth.batched_64(seed=4 + dist.rank, n_images=n_images)
+    wl = synth.batched_64(seed=rank_seed(4, dist.rank), n_images=n_images)
     insts = wl.instances
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     yuv = [dev(i.yuv) for i in insts]
@@ -306,8 +316,8 @@ def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, seq
     return {"workload": "64 images, sizes U{320..1920} x U{240..1080}, half depth (C=1), half "
                         "chroma (C=2, c=1 on 2% of pixels), sigma_xy in {8,16}, lambda in {32,128}",
             "pixels": npix, "vertices": int(sum(info["V"])),
-            "batched_mpix_s": dist.world * npix / (mb / 1e3) / 1e6, "batched_ms": mb,
-            "one_at_a_time_mpix_s": dist.world * npix / (ms1 / 1e3) / 1e6,
+            "batched_mpix_s": whole_job_mpix(dist.world, npix, mb), "batched_ms": mb,
+            "one_at_a_time_mpix_s": whole_job_mpix(dist.world, npix, ms1),
             "one_at_a_time_ms": ms1,
             "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
                             for k, v in regions.items() if v[0]},
@@ -319,7 +329,7 @@ def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
     gradient against a label map, backward solve (dL/dt, dL/dc)."""
     import torch
     from paper_1511_03296_gb300 import fbs, synth
-    wl = synth.segmentation_16(seed=5 + dist.rank, n_images=n_images)
+    wl = synth.segmentation_16(seed=rank_seed(5, dist.rank), n_images=n_images)
     insts = wl.instances
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     yuv = [dev(i.yuv) for i in insts]
@@ -357,7 +367,7 @@ def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
     return {"workload": "16 images 640x480, C=21 softmax targets, c~U[0,1], sigma=(8,4,3), "
                         "lambda=128, forward + backward (2 x 25 PCG iterations)",
             "pixels": npix, "vertices": int(sum(info["V"])),
-            "fwd_bwd_mpix_s": dist.world * npix / (m / 1e3) / 1e6, "ms_per_step": m,
+            "fwd_bwd_mpix_s": whole_job_mpix(dist.world, npix, m), "ms_per_step": m,
             "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
                             for k, v in regions.items() if v[0]},
             "pcg_roofline": pcg_roofline(regions, 2, steps, bytes_iter, peak)}
@@ -395,7 +405,7 @@ def run_ours(args, dist):
     torch.cuda.set_device(dev)
     fbs_build.build()
     fbs.load()
-    inst = synth.plain_1080p(seed=2 + dist.rank).instances[0]
+    inst = synth.plain_1080p(seed=rank_seed(2, dist.rank)).instances[0]
     stream = torch.cuda.current_stream()
     d_yuv = torch.from_numpy(inst.yuv).cuda()
     d_t = torch.from_numpy(inst.t).cuda()
@@ -436,7 +446,7 @@ def run_ours(args, dist):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_local = sum(step_ms) / len(step_ms)
     ms = dist.max(ms_local)
-    value = dist.world * inst.n_pixels / (ms / 1e3) / 1e6
+    value = whole_job_mpix(dist.world, inst.n_pixels, ms)
     V = V_holder["V"]
 
     # ---- per-kernel launch list of a few steps (separate pass)
@@ -492,10 +502,10 @@ def run_ours(args, dist):
                    "precision": "FP32 vectors, FP64-accurate CG dot products, FP64 "
                                 "bistochastisation"},
         "clocks": clk.summary(),
-        "e2e": {"value": dist.world * inst.n_pixels / (e2e_ms / 1e3) / 1e6, "unit": "Mpix/s",
+        "e2e": {"value": whole_job_mpix(dist.world, inst.n_pixels, e2e_ms), "unit": "Mpix/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
-        "roofline": dict(roof or {}, kernel="pcg iteration (both CG phases, persistent loop)",
+        "roofline": dict(roof or {}, kernel="pcg iteration (both CG phases)",
                          traffic=None, peak_source="measured" if peaks else "fallback",
                          note="working set L2-resident at this size; see batched / fwd_bwd "
                               "for the HBM-bound sizes"),
@@ -504,8 +514,8 @@ def run_ours(args, dist):
     }
     if not args.no_extra:
         xs = max(3, min(args.steps // 10, 20))
-        line["batched"] = run_extra_batched(dist, flush, stream, peak, xs, 2)
-        line["fwd_bwd"] = run_extra_fwd_bwd(dist, flush, stream, peak, xs, 2)
+        line["batched"] = run_extra_batched(dist, flush, stream, peak, xs, 3)
+        line["fwd_bwd"] = run_extra_fwd_bwd(dist, flush, stream, peak, xs, 3)
     if dist.rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(synth.plain_1080p().instances[0], args.cpu_seconds)
     if dist.rank == 0:

@@ -72,13 +72,6 @@ __device__ int block_exclusive_scan(int v, int* warp_buf, int* total)
     return prefix;
 }
 
-__device__ int block_sum(int v, int* warp_buf)
-{
-    int total;
-    block_exclusive_scan(v, warp_buf, &total);
-    return total;
-}
-
 // Quantise the pixels of one tile into sortable items:
 //   cell index in tile << 50 | (l << 24 | u << 12 | v) << 14 | pixel index in tile.
 // Pads [P, P2) with kPad.

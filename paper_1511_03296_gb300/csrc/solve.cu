@@ -546,7 +546,7 @@ __device__ __forceinline__ void flush_run(DF (&run)[4], int W, int C, int ntiles
 // scalars (phase 1: delta_it and beta; phase 2: alpha), then dispatches each
 // tile on the image's pass width.  When an image's channels fit one pass the
 // products are accumulated over the run of its tiles in this chunk.
-template <int PHASE, bool COMP, bool CO>
+template <int PHASE, bool COMP, bool CO, int WMAX>
 __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
                           float* __restrict__ ddst, int it, int t0, int t1, PhaseSmem& S)
 {
@@ -603,36 +603,51 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
                 make_float2(0.0f, 0.0f);
         }
         if (PHASE == 1) {
-            if (I.Cp == 1) apply_tile<1, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
-            else if (I.Cp == 2) apply_tile<2, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
-            else apply_tile<4, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
+            if (WMAX == 1 || I.Cp == 1)
+                apply_tile<1, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
+            else if (WMAX == 2 || I.Cp == 2)
+                apply_tile<2, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
+            else
+                apply_tile<4, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
         } else {
-            if (I.Cp == 1) update_tile<1, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
-            else if (I.Cp == 2) update_tile<2, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
-            else update_tile<4, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
+            if (WMAX == 1 || I.Cp == 1)
+                update_tile<1, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
+            else if (WMAX == 2 || I.Cp == 2)
+                update_tile<2, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
+            else
+                update_tile<4, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
         }
     }
     if (cur >= 0 && single) flush_run(run, run_W, run_C, run_ntiles, run_base, run_tile, out, S);
 }
 
-template <bool COMP>
-__global__ void __launch_bounds__(kVTile)
+// Phase kernels are instantiated per widest pass of the batch (WMAX = the
+// largest Cp, capped at 4): a batch of one- and two-channel images gets the
+// register budget of the narrow bodies and with it more resident warps.
+// Resident blocks per SM asked of the compiler, per WMAX (measured best: the
+// gathers are latency-bound, and more resident warps beat deeper per-thread
+// load batches once those drop below ~64 registers for W <= 2).
+template <int WMAX>
+constexpr int phase_min_blocks() { return WMAX <= 2 ? 4 : 2; }
+
+template <int WMAX, bool COMP>
+__global__ void __launch_bounds__(kVTile, phase_min_blocks<WMAX>())
 pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict__ dnew, int it)
 {
     __shared__ PhaseSmem S;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
-    phase_run<1, COMP, false>(A, dold, dnew, it, t0, t1, S);
+    phase_run<1, COMP, false, WMAX>(A, dold, dnew, it, t0, t1, S);
 }
 
-template <bool COMP>
-__global__ void __launch_bounds__(kVTile)
+template <int WMAX, bool COMP>
+__global__ void __launch_bounds__(kVTile, phase_min_blocks<WMAX>())
 pcg_update_kernel(SolveArgs A, const float* __restrict__ d, int it)
 {
     __shared__ PhaseSmem S;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
-    phase_run<2, COMP, false>(A, d, nullptr, it, t0, t1, S);
+    phase_run<2, COMP, false, WMAX>(A, d, nullptr, it, t0, t1, S);
 }
 
 // ------------------------------------------------- persistent PCG loop ---
@@ -688,8 +703,8 @@ __device__ bool grid_barrier(unsigned* bar, uint32_t* err)
 
 // All `iters` PCG iterations in one cooperative launch: phase 1, barrier,
 // phase 2, barrier.  Every block keeps the same chunk of tiles throughout.
-template <bool COMP>
-__global__ void __launch_bounds__(kVTile)
+template <int WMAX, bool COMP>
+__global__ void __launch_bounds__(kVTile, phase_min_blocks<WMAX>())
 pcg_loop_kernel(SolveArgs A, int iters, unsigned* bar)
 {
     __shared__ PhaseSmem S;
@@ -698,9 +713,9 @@ pcg_loop_kernel(SolveArgs A, int iters, unsigned* bar)
     for (int it = 0; it < iters; ++it) {
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
-        phase_run<1, COMP, true>(A, dold, dnew, it, t0, t1, S);
+        phase_run<1, COMP, true, WMAX>(A, dold, dnew, it, t0, t1, S);
         if (!grid_barrier(bar, A.err)) return;
-        phase_run<2, COMP, true>(A, dnew, nullptr, it, t0, t1, S);
+        phase_run<2, COMP, true, WMAX>(A, dnew, nullptr, it, t0, t1, S);
         if (!grid_barrier(bar, A.err)) return;
     }
 }
@@ -929,7 +944,8 @@ pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
     else resident_loop<4, COMP>(A, I, vt, iters, bar, s_nb, s_nmu, S);
 }
 
-int resident_width(int cmax) { return cmax <= 1 ? 1 : cmax <= 2 ? 2 : 4; }
+// index of the widest pass: 0 (W = 1), 1 (W = 2), 2 (W = 4)
+int width_index(int cmax) { return cmax <= 1 ? 0 : cmax <= 2 ? 1 : 2; }
 
 // ---------------------------------------------------------------- slice ---
 // x = S^T y for every pixel of image blockIdx.y.
@@ -1002,15 +1018,23 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
     static int f_update = prof_family("pcg_update");
     static int f_loop = prof_family("pcg_loop");
     static int f_res_loop = prof_family("pcg_resident");
-    static const int occ_p = occupancy((const void*)pcg_apply_kernel<COMP>);
-    static const int occ_u = occupancy((const void*)pcg_update_kernel<COMP>);
-    static const int occ_l = occupancy((const void*)pcg_loop_kernel<COMP>);
+    static const void* const fn_p[3] = {(const void*)pcg_apply_kernel<1, COMP>,
+                                        (const void*)pcg_apply_kernel<2, COMP>,
+                                        (const void*)pcg_apply_kernel<4, COMP>};
+    static const void* const fn_u[3] = {(const void*)pcg_update_kernel<1, COMP>,
+                                        (const void*)pcg_update_kernel<2, COMP>,
+                                        (const void*)pcg_update_kernel<4, COMP>};
+    static const void* const fn_l[3] = {(const void*)pcg_loop_kernel<1, COMP>,
+                                        (const void*)pcg_loop_kernel<2, COMP>,
+                                        (const void*)pcg_loop_kernel<4, COMP>};
+    static const int occ_p[3] = {occupancy(fn_p[0]), occupancy(fn_p[1]), occupancy(fn_p[2])};
+    static const int occ_u[3] = {occupancy(fn_u[0]), occupancy(fn_u[1]), occupancy(fn_u[2])};
+    static const int occ_l[3] = {occupancy(fn_l[0]), occupancy(fn_l[1]), occupancy(fn_l[2])};
+    const int wi = width_index(P.cmax);
     static const int occ_res[3] = {occupancy((const void*)pcg_resident_kernel<1, COMP>),
                                    occupancy((const void*)pcg_resident_kernel<2, COMP>),
                                    occupancy((const void*)pcg_resident_kernel<4, COMP>)};
     if (P.persistent && P.pcg_iters > 0) {
-        const int wres = resident_width(P.cmax);
-        const int wi = wres == 1 ? 0 : wres == 2 ? 1 : 2;
         const bool resident = P.cmax <= 4 && A.nvt <= device_info().sms * occ_res[wi];
         if (resident || P.force_persistent) {
             // barrier words zero (or, for the failure-path test, a top counter
@@ -1025,15 +1049,15 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
             void* args[] = {&a, &iters, &bar};
             if (resident) {
                 prof_begin(f_res_loop, s);
-                const void* fn = wres == 1   ? (const void*)pcg_resident_kernel<1, COMP>
-                                 : wres == 2 ? (const void*)pcg_resident_kernel<2, COMP>
-                                             : (const void*)pcg_resident_kernel<4, COMP>;
+                const void* fn = wi == 0   ? (const void*)pcg_resident_kernel<1, COMP>
+                                 : wi == 1 ? (const void*)pcg_resident_kernel<2, COMP>
+                                           : (const void*)pcg_resident_kernel<4, COMP>;
                 e = cudaLaunchCooperativeKernel(fn, dim3(A.nvt), dim3(kVTile), args, 0, s);
                 prof_end(f_res_loop, s);
             } else {
                 prof_begin(f_loop, s);
-                e = cudaLaunchCooperativeKernel((const void*)pcg_loop_kernel<COMP>,
-                                                dim3(persistent_blocks(occ_l, A.nvt)),
+                e = cudaLaunchCooperativeKernel(fn_l[wi],
+                                                dim3(persistent_blocks(occ_l[wi], A.nvt)),
                                                 dim3(kVTile), args, 0, s);
                 prof_end(f_loop, s);
             }
@@ -1041,16 +1065,20 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
             cudaGetLastError();   // clear, and fall back to per-phase launches
         }
     }
-    const int nb_p = persistent_blocks(occ_p, A.nvt);
-    const int nb_u = persistent_blocks(occ_u, A.nvt);
+    const int nb_p = persistent_blocks(occ_p[wi], A.nvt);
+    const int nb_u = persistent_blocks(occ_u[wi], A.nvt);
     for (int it = 0; it < P.pcg_iters; ++it) {
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
         prof_begin(f_apply, s);
-        pcg_apply_kernel<COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+        if (wi == 0) pcg_apply_kernel<1, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+        else if (wi == 1) pcg_apply_kernel<2, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+        else pcg_apply_kernel<4, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
         prof_end(f_apply, s);
         prof_begin(f_update, s);
-        pcg_update_kernel<COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
+        if (wi == 0) pcg_update_kernel<1, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
+        else if (wi == 1) pcg_update_kernel<2, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
+        else pcg_update_kernel<4, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
         prof_end(f_update, s);
     }
     return cudaGetLastError();
@@ -1076,8 +1104,7 @@ bool resident_fits(const SolveArgs& A, const SolvePlan& P)
                                    occupancy((const void*)pcg_resident_kernel<2, true>),
                                    occupancy((const void*)pcg_resident_kernel<4, true>)}};
     if (P.cmax > 4) return false;
-    const int w = resident_width(P.cmax);
-    return A.nvt <= device_info().sms * occ[P.comp ? 1 : 0][w == 1 ? 0 : w == 2 ? 1 : 2];
+    return A.nvt <= device_info().sms * occ[P.comp ? 1 : 0][width_index(P.cmax)];
 }
 
 cudaError_t launch_segment(const SolveArgs& A, const SolvePlan& P, int seg, int mode,
