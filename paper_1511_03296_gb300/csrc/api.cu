@@ -732,8 +732,9 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.part_rs[1] = g->part + g->cap_part;
     A.part_dq = g->part + 2 * g->cap_part;
     A.err = g->err;
-    // AUTO: persistent only where the resident form fits; per-phase (graph) otherwise
-    if (plan.persistent && !plan.force_persistent && !resident_fits(A, plan)) plan.persistent = 0;
+    // AUTO: the resident loop for small batches; per-phase (graph) otherwise
+    if (plan.persistent && !plan.force_persistent && !resident_preferred(A, plan))
+        plan.persistent = 0;
     return run_segments(g, A, plan, s);
 }
 

@@ -20,6 +20,8 @@ constexpr int kChanBlock = 4;            // channels processed per pass of a PCG
 constexpr int kMaxChannels = 64;         // channels per image
 constexpr unsigned kBarrierGroups = 32;            // first-level counters of the grid barrier
 constexpr unsigned kBarrierWords = 32 * (kBarrierGroups + 1);
+constexpr unsigned kWorkCounterWord = 2;   // in the barrier block, unused by the barrier:
+                                           // the splat's work counter
 constexpr unsigned kBarrierSpinLimit = 1u << 20;   // polls of >= 64 ns: >= 67 ms before a time-out
 
 // device error bits (latched in fbs_grid::err)

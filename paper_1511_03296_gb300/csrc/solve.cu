@@ -173,106 +173,225 @@ __device__ __forceinline__ void vertex_epilogue(const SolveArgs& A, const InstDe
     A.nm[v] = make_float2((float)nv, diag > 0.0 ? (float)(1.0 / diag) : 0.0f);
 }
 
-// One thread per vertex sums its pixels (in the sorted pixel order, so the
-// result is deterministic) with exact products accumulated as double-float
-// pairs.  Writes b into r (as a double-float pair r, r_lo when comp), y0 =
-// b / S c into y (zero in the padding channels), the diagonal remainder a'
-// into a, and {n, M^-1} into nm.
-template <int CB>
-__global__ void __launch_bounds__(kVTile)
-splat_kernel(SolveArgs A, int mode, float sigma_gm, int comp)
+// Splat weight and value of one pixel (index i within its image) for channel
+// ch: robust weights are Geman-McClure of the residual against the vertex's
+// current solution yv.
+__device__ __forceinline__ float splat_weight(const InstDev& I, int mode, int64_t i, float yv,
+                                              float s2)
 {
-    const float s2 = sigma_gm * sigma_gm;
-    int t0, t1;
-    block_chunk(A.nvt, t0, t1);
-    for (int tile = t0; tile < t1; ++tile) {
-        const VTile vt = A.vt[tile];
-        const InstDev I = A.inst[vt.inst];
-        const int64_t v = vt.v0 + threadIdx.x;
-        if (v >= vt.v1) continue;
-        const uint32_t p0 = A.pstart[v], cnt = A.m[v];
-        float yv = 0.0f;
-        if (mode == kSplatRobust) yv = A.y[vec_index(I, 0, v)];
-        DF sc = {0.0f, 0.0f};
-        bool bad = false;
-        for (int cb = 0; cb < I.C; cb += CB) {
-            DF acc[CB];
+    if (mode == kSplatRobust) {
+        const float e = yv - I.t[i];
+        const float den = s2 + e * e;
+        return (2.0f * s2) / (den * den);
+    }
+    return I.c[i];
+}
+
+__device__ __forceinline__ float splat_value(const InstDev& I, int mode, int ch, int64_t i)
+{
+    return mode == kSplatBackward ? I.dx[(int64_t)ch * I.N + i] : I.t[(int64_t)ch * I.N + i];
+}
+
+__device__ __forceinline__ DF df_shfl_idx(DF v, int src)
+{
+    return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+// Write b (into r, or the double-float pair r, r_lo when comp) and the flat
+// initialisation y0 = b / S c for channels cb .. cb+CB-1 of vertex v.
+template <int CB>
+__device__ __forceinline__ void splat_store(const SolveArgs& A, const InstDev& I, int64_t v,
+                                            int cb, const DF (&acc)[CB], DF sc, int comp)
+{
+    const float scf = sc.hi + sc.lo;
 #pragma unroll
-            for (int k = 0; k < CB; ++k) acc[k] = {0.0f, 0.0f};
-            // software-pipelined: the pixel indices of 8 items, then their
-            // values, then the accumulation in item order (same order, so the
-            // sums are those of a plain sequential loop)
-            for (uint32_t j0 = 0; j0 < cnt; j0 += 8) {
-                int64_t ii[8];
+    for (int k = 0; k < CB; ++k) {
+        const int ch = cb + k;
+        if (ch < I.C) {
+            const float b = acc[k].hi + acc[k].lo;
+            const int64_t idx = vec_index(I, ch, v);
+            if (comp) {
+                const DF bn = df_fast_two_sum(acc[k].hi, acc[k].lo);
+                A.r[idx] = bn.hi;
+                A.rlo[idx] = bn.lo;
+            } else {
+                A.r[idx] = b;
+            }
+            A.y[idx] = scf > 0.0f ? b / scf : 0.0f;
+        }
+    }
+}
+
+// Padding channels zero, non-finite flag, diagonal and preconditioner.
+__device__ __forceinline__ void splat_finish(const SolveArgs& A, const InstDev& I, int64_t v,
+                                             uint32_t cnt, DF sc)
+{
+    for (int ch = I.C; ch < I.Cp; ++ch) {
+        const int64_t idx = vec_index(I, ch, v);
+        A.r[idx] = 0.0f;
+        A.rlo[idx] = 0.0f;
+        A.y[idx] = 0.0f;
+        A.d[0][idx] = 0.0f;
+        A.d[1][idx] = 0.0f;
+        A.q[idx] = 0.0f;
+    }
+    vertex_epilogue(A, I, v, cnt, sc);
+}
+
+// Pixels of a vertex with more than this many are summed by the whole warp.
+constexpr uint32_t kSplatWarpMin = 24;
+
+// One warp unit (32 consecutive vertices of one tile): a vertex with at most
+// kSplatWarpMin pixels is summed by its own thread, walking its pixels in the
+// sorted order; a larger vertex is summed by the whole warp (lane j takes
+// pixels j, j + 32, ..., then a fixed-order warp reduction).
+template <int CB>
+__device__ __forceinline__ void splat_unit(const SolveArgs& A, const InstDev& I, int64_t v,
+                                           bool valid, int mode, float s2, int comp)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t p0 = valid ? A.pstart[v] : 0u, cnt = valid ? A.m[v] : 0u;
+    const bool big = cnt > kSplatWarpMin;
+    const uint32_t own = big ? 0u : cnt;
+    float yv = 0.0f;
+    if (mode == kSplatRobust && valid) yv = A.y[vec_index(I, 0, v)];
+    DF sc = {0.0f, 0.0f};
+    bool bad = false;
+    for (int cb = 0; cb < I.C; cb += CB) {
+        DF acc[CB];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    ii[u] = j0 + u < cnt ? (int64_t)A.perm[p0 + j0 + u] - I.pix_base : -1;
-                float wv[8], val[CB][8];
+        for (int k = 0; k < CB; ++k) acc[k] = {0.0f, 0.0f};
+        for (uint32_t j0 = 0; j0 < own; j0 += 8) {
+            int64_t ii[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int64_t i = ii[u] >= 0 ? ii[u] : 0;
-                    if (mode == kSplatRobust) {
-                        const float e = yv - I.t[i];
-                        const float den = s2 + e * e;
-                        wv[u] = (2.0f * s2) / (den * den);
-                    } else {
-                        wv[u] = I.c[i];
-                    }
+            for (int u = 0; u < 8; ++u)
+                ii[u] = j0 + u < own ? (int64_t)A.perm[p0 + j0 + u] - I.pix_base : -1;
+            float wv[8], val[CB][8];
 #pragma unroll
-                    for (int k = 0; k < CB; ++k) {
-                        const int ch = min(cb + k, I.C - 1);
-                        val[k][u] = mode == kSplatBackward ? I.dx[(int64_t)ch * I.N + i]
-                                                           : I.t[(int64_t)ch * I.N + i];
-                    }
+            for (int u = 0; u < 8; ++u) {
+                const int64_t i = ii[u] >= 0 ? ii[u] : 0;
+                wv[u] = splat_weight(I, mode, i, yv, s2);
+#pragma unroll
+                for (int k = 0; k < CB; ++k)
+                    val[k][u] = splat_value(I, mode, min(cb + k, I.C - 1), i);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (ii[u] < 0) break;
+                const float w = wv[u];
+                if (cb == 0) {
+                    sc = df_add(sc, DF{w, 0.0f});
+                    bad |= !isfinite(w);
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    if (ii[u] < 0) break;
+                for (int k = 0; k < CB; ++k) {
+                    if (cb + k < I.C) {
+                        const float x = val[k][u];
+                        acc[k] = df_add(acc[k], mode == kSplatBackward ? DF{x, 0.0f}
+                                                                       : df_mul_exact(w, x));
+                        bad |= !isfinite(x);
+                    }
+                }
+            }
+        }
+        unsigned bigmask = __ballot_sync(FULL, big);
+        while (bigmask) {
+            const int owner = __ffs(bigmask) - 1;
+            bigmask &= bigmask - 1;
+            const uint32_t q0 = __shfl_sync(FULL, p0, owner);
+            const uint32_t qn = __shfl_sync(FULL, cnt, owner);
+            const float qy = __shfl_sync(FULL, yv, owner);
+            DF wacc[CB], wsc = {0.0f, 0.0f};
+#pragma unroll
+            for (int k = 0; k < CB; ++k) wacc[k] = {0.0f, 0.0f};
+            bool wbad = false;
+            for (uint32_t j0 = 0; j0 < qn; j0 += 4 * 32) {
+                int64_t ii[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t j = j0 + 32 * u + lane;
+                    ii[u] = j < qn ? (int64_t)A.perm[q0 + j] - I.pix_base : -1;
+                }
+                float wv[4], val[CB][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t i = ii[u] >= 0 ? ii[u] : 0;
+                    wv[u] = splat_weight(I, mode, i, qy, s2);
+#pragma unroll
+                    for (int k = 0; k < CB; ++k)
+                        val[k][u] = splat_value(I, mode, min(cb + k, I.C - 1), i);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (ii[u] < 0) continue;
                     const float w = wv[u];
                     if (cb == 0) {
-                        sc = df_add(sc, DF{w, 0.0f});
-                        bad |= !isfinite(w);
+                        wsc = df_add(wsc, DF{w, 0.0f});
+                        wbad |= !isfinite(w);
                     }
 #pragma unroll
                     for (int k = 0; k < CB; ++k) {
                         if (cb + k < I.C) {
                             const float x = val[k][u];
-                            acc[k] = df_add(acc[k], mode == kSplatBackward ? DF{x, 0.0f}
-                                                                           : df_mul_exact(w, x));
-                            bad |= !isfinite(x);
+                            wacc[k] = df_add(wacc[k], mode == kSplatBackward ? DF{x, 0.0f}
+                                                                             : df_mul_exact(w, x));
+                            wbad |= !isfinite(x);
                         }
                     }
                 }
             }
-            const float scf = sc.hi + sc.lo;
 #pragma unroll
             for (int k = 0; k < CB; ++k) {
-                const int ch = cb + k;
-                if (ch < I.C) {
-                    const float b = acc[k].hi + acc[k].lo;
-                    const int64_t idx = vec_index(I, ch, v);
-                    if (comp) {
-                        const DF bn = df_fast_two_sum(acc[k].hi, acc[k].lo);
-                        A.r[idx] = bn.hi;
-                        A.rlo[idx] = bn.lo;
-                    } else {
-                        A.r[idx] = b;
-                    }
-                    A.y[idx] = scf > 0.0f ? b / scf : 0.0f;
-                }
+                const DF t = df_warp_sum(wacc[k]);
+                const DF g = df_shfl_idx(t, 0);
+                if (lane == owner) acc[k] = g;
             }
+            if (cb == 0) {
+                const DF t = df_warp_sum(wsc);
+                const DF g = df_shfl_idx(t, 0);
+                if (lane == owner) sc = g;
+            }
+            if (__any_sync(FULL, wbad) && lane == owner) bad = true;
         }
-        for (int ch = I.C; ch < I.Cp; ++ch) {   // padding channels stay zero
-            const int64_t idx = vec_index(I, ch, v);
-            A.r[idx] = 0.0f;
-            A.rlo[idx] = 0.0f;
-            A.y[idx] = 0.0f;
-            A.d[0][idx] = 0.0f;
-            A.d[1][idx] = 0.0f;
-            A.q[idx] = 0.0f;
+        if (valid) splat_store<CB>(A, I, v, cb, acc, sc, comp);
+    }
+    if (bad) atomicOr(A.err, kErrNonFinite);
+    if (valid) splat_finish(A, I, v, cnt, sc);
+}
+
+// b = S(c o t) (or its robust / backward form), S c, the flat initialisation
+// y0 = b / S c (zero in the padding channels), the diagonal remainder a' and
+// {n, M^-1}.  Work is split in warp units of 32 consecutive vertices of one
+// tile, which warps claim from a counter (*work, zero at launch): the pixel
+// counts of vertices differ by orders of magnitude between images (a grey
+// colourisation reference puts whole cells in one vertex), so a static split
+// leaves most blocks idle behind a few.  Products are exact and accumulated
+// as double-float pairs in a fixed order, so results do not depend on which
+// warp takes which unit.
+template <int CB>
+__global__ void __launch_bounds__(kVTile)
+splat_kernel(SolveArgs A, int mode, float sigma_gm, int comp, unsigned* work)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int kUnits = kVTile / 32;
+    const float s2 = sigma_gm * sigma_gm;
+    const int lane = threadIdx.x & 31;
+    const int nunits = A.nvt * kUnits;
+    int unit = 0;
+    if (lane == 0) unit = (int)atomicAdd(work, 1u);
+    unit = __shfl_sync(FULL, unit, 0);
+    while (unit < nunits) {
+        int next = 0;
+        if (lane == 0) next = (int)atomicAdd(work, 1u);   // overlaps this unit
+        const int tile = unit / kUnits;
+        const VTile vt = A.vt[tile];
+        const int64_t v = vt.v0 + (unit - tile * kUnits) * 32 + lane;
+        if (vt.v0 + (unit - tile * kUnits) * 32 < vt.v1) {       // warp-uniform
+            const InstDev I = A.inst[vt.inst];
+            splat_unit<CB>(A, I, v, v < vt.v1, mode, s2, comp);
         }
-        if (bad) atomicOr(A.err, kErrNonFinite);
-        vertex_epilogue(A, I, v, cnt, sc);
+        unit = __shfl_sync(FULL, next, 0);
     }
 }
 
@@ -739,12 +858,13 @@ __device__ void reduce_partials_all(const float2* __restrict__ part, const InstD
     DF acc[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) acc[k] = {0.0f, 0.0f};
-    for (int j0 = threadIdx.x; j0 < I.ntiles; j0 += 2 * blockDim.x) {
-        float2 v[W][2];
+    constexpr int H = W == 4 ? 1 : 2;    // slots in flight per thread and channel
+    for (int j0 = threadIdx.x; j0 < I.ntiles; j0 += H * blockDim.x) {
+        float2 v[W][H];
 #pragma unroll
         for (int k = 0; k < W; ++k)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < H; ++h) {
                 const int j = j0 + h * blockDim.x;
                 v[k][h] = (k < I.C && j < I.ntiles)
                               ? __ldcg(part + I.part_base + (int64_t)k * I.ntiles + j)
@@ -753,7 +873,7 @@ __device__ void reduce_partials_all(const float2* __restrict__ part, const InstD
 #pragma unroll
         for (int k = 0; k < W; ++k)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) acc[k] = df_add(acc[k], DF{v[k][h].x, v[k][h].y});
+            for (int h = 0; h < H; ++h) acc[k] = df_add(acc[k], DF{v[k][h].x, v[k][h].y});
     }
 #pragma unroll
     for (int k = 0; k < W; ++k) {
@@ -770,7 +890,7 @@ __device__ void reduce_partials_all(const float2* __restrict__ part, const InstD
     __syncthreads();
 }
 
-template <int W, bool COMP>
+template <int W, bool COMP, int NG = (W == 4 ? 5 : 10)>
 __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile& vt, int iters,
                               unsigned* bar, int32_t (*s_nb)[kVTile], float2 (*s_nmu)[kVTile],
                               PhaseSmem& S)
@@ -810,50 +930,58 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
         // ---- phase 1: gathers first (they do not depend on beta), then the
-        // reduction of the previous phase's partials overlaps their latency
+        // reduction of the previous phase's partials overlaps their latency.
+        // Neighbours are gathered in groups of NG (all ten when W <= 2; two
+        // groups of five for W = 4, to stay within the register budget of
+        // three resident blocks per SM).
         {
-            float ru[10][W], du[10][W];
-#pragma unroll
-            for (int j = 0; j < 10; ++j) {
-                const int32_t u0 = s_nb[j][tx];
-                const int64_t u = u0 >= 0 ? u0 : vs;
-                ldw<W, true>(A.r + base + u * I.Cp, ru[j]);
-                if (it > 0) {
-                    ldw<W, true>(dold + base + u * I.Cp, du[j]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < W; ++k) du[j][k] = 0.0f;
-                }
-            }
-            reduce_partials_all<W>(A.part_rs[slot], I, S.sd, S.red);
-            if (tx < W) {
-                double beta = 0.0;
-                if (tx < I.C) {
-                    if (it > 0) {
-                        const double dprev = __ldcg(&A.scal[I.pc + tx].delta[slot ^ 1]);
-                        beta = dprev != 0.0 ? S.sd[tx] / dprev : 0.0;
-                    }
-                    A.scal[I.pc + tx].delta[slot] = S.sd[tx];
-                }
-                S.sf[tx] = (float)beta;
-            }
-            __syncthreads();
-            float beta[W], dv[W];
-#pragma unroll
-            for (int k = 0; k < W; ++k) {
-                beta[k] = S.sf[k];
-                dv[k] = fmaf(beta[k], d[k], nmv.y * r[k]);
-            }
+            float dv[W], beta[W];
             DF s[W];
 #pragma unroll
             for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
 #pragma unroll
-            for (int j = 0; j < 10; ++j) {
-                const float2 nm = s_nmu[j][tx];
-                float dz[W];
+            for (int g0 = 0; g0 < 10; g0 += NG) {
+                float ru[NG][W], du[NG][W];
 #pragma unroll
-                for (int k = 0; k < W; ++k) dz[k] = fmaf(beta[k], du[j][k], nm.y * ru[j][k]);
-                lap_acc<W, COMP>(s, nm.x, dv, dz);
+                for (int j = 0; j < NG; ++j) {
+                    const int32_t u0 = s_nb[g0 + j][tx];
+                    const int64_t u = u0 >= 0 ? u0 : vs;
+                    ldw<W, true>(A.r + base + u * I.Cp, ru[j]);
+                    if (it > 0) {
+                        ldw<W, true>(dold + base + u * I.Cp, du[j]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < W; ++k) du[j][k] = 0.0f;
+                    }
+                }
+                if (g0 == 0) {
+                    reduce_partials_all<W>(A.part_rs[slot], I, S.sd, S.red);
+                    if (tx < W) {
+                        double beta = 0.0;
+                        if (tx < I.C) {
+                            if (it > 0) {
+                                const double dprev = __ldcg(&A.scal[I.pc + tx].delta[slot ^ 1]);
+                                beta = dprev != 0.0 ? S.sd[tx] / dprev : 0.0;
+                            }
+                            A.scal[I.pc + tx].delta[slot] = S.sd[tx];
+                        }
+                        S.sf[tx] = (float)beta;
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        beta[k] = S.sf[k];
+                        dv[k] = fmaf(beta[k], d[k], nmv.y * r[k]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NG; ++j) {
+                    const float2 nm = s_nmu[g0 + j][tx];
+                    float dz[W];
+#pragma unroll
+                    for (int k = 0; k < W; ++k) dz[k] = fmaf(beta[k], du[j][k], nm.y * ru[j][k]);
+                    lap_acc<W, COMP>(s, nm.x, dv, dz);
+                }
             }
             DF acc[W];
 #pragma unroll
@@ -872,32 +1000,38 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
         if (!grid_barrier(bar, A.err)) return;
         // ---- phase 2
         {
-            float dn[10][W];
-            if (COMP) {
-#pragma unroll
-                for (int j = 0; j < 10; ++j) {
-                    const int32_t u0 = s_nb[j][tx];
-                    const int64_t u = u0 >= 0 ? u0 : vs;
-                    ldw<W, true>(dnew + base + u * I.Cp, dn[j]);
-                }
-            }
-            reduce_partials_all<W>(A.part_dq, I, S.sd, S.red);
-            if (tx < W) {
-                double alpha = 0.0;
-                if (tx < I.C) {
-                    const double delta = __ldcg(&A.scal[I.pc + tx].delta[slot]);
-                    const double dq = S.sd[tx];
-                    alpha = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
-                }
-                S.sa[tx] = alpha;
-            }
-            __syncthreads();
             DF s[W];
-            if (COMP) {
 #pragma unroll
-                for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
+            for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
 #pragma unroll
-                for (int j = 0; j < 10; ++j) lap_acc<W, true>(s, s_nmu[j][tx].x, d, dn[j]);
+            for (int g0 = 0; g0 < 10; g0 += NG) {
+                float dn[NG][W];
+                if (COMP) {
+#pragma unroll
+                    for (int j = 0; j < NG; ++j) {
+                        const int32_t u0 = s_nb[g0 + j][tx];
+                        const int64_t u = u0 >= 0 ? u0 : vs;
+                        ldw<W, true>(dnew + base + u * I.Cp, dn[j]);
+                    }
+                }
+                if (g0 == 0) {
+                    reduce_partials_all<W>(A.part_dq, I, S.sd, S.red);
+                    if (tx < W) {
+                        double alpha = 0.0;
+                        if (tx < I.C) {
+                            const double delta = __ldcg(&A.scal[I.pc + tx].delta[slot]);
+                            const double dq = S.sd[tx];
+                            alpha = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
+                        }
+                        S.sa[tx] = alpha;
+                    }
+                    __syncthreads();
+                }
+                if (COMP) {
+#pragma unroll
+                    for (int j = 0; j < NG; ++j) lap_acc<W, true>(s, s_nmu[g0 + j][tx].x, d, dn[j]);
+                }
+                if (!COMP) break;   // no gathers in the FP32 update
             }
             DF acc[W];
 #pragma unroll
@@ -931,7 +1065,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
 // WMAX: the widest pass of the batch (the largest Cp), so that a batch of
 // single-channel images gets the register budget of the W = 1 body alone.
 template <int WMAX, bool COMP>
-__global__ void __launch_bounds__(kVTile, WMAX == 4 ? 2 : 3)
+__global__ void __launch_bounds__(kVTile, 3)
 pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
 {
     __shared__ int32_t s_nb[10][kVTile];
@@ -1088,8 +1222,11 @@ template <int CB>
 cudaError_t launch_splat(const SolveArgs& A, const SolvePlan& P, int mode, cudaStream_t s)
 {
     static const int occ_s = occupancy((const void*)splat_kernel<CB>);
+    unsigned* work = P.barrier + kWorkCounterWord;
+    cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
     splat_kernel<CB><<<persistent_blocks(occ_s, A.nvt), kVTile, 0, s>>>(A, mode, P.sigma_gm,
-                                                                     P.comp);
+                                                                     P.comp, work);
     return cudaGetLastError();
 }
 
@@ -1105,6 +1242,11 @@ bool resident_fits(const SolveArgs& A, const SolvePlan& P)
                                    occupancy((const void*)pcg_resident_kernel<4, true>)}};
     if (P.cmax > 4) return false;
     return A.nvt <= device_info().sms * occ[P.comp ? 1 : 0][width_index(P.cmax)];
+}
+
+bool resident_preferred(const SolveArgs& A, const SolvePlan& P)
+{
+    return resident_fits(A, P) && A.nvt <= device_info().sms;
 }
 
 cudaError_t launch_segment(const SolveArgs& A, const SolvePlan& P, int seg, int mode,

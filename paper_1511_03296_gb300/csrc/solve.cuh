@@ -64,4 +64,9 @@ cudaError_t launch_segment(const SolveArgs& A, const SolvePlan& P, int seg, int 
 // resident persistent PCG loop and no image has more channels than a pass
 bool resident_fits(const SolveArgs& A, const SolvePlan& P);
 
+// the automatic launch policy's choice of the resident loop: it fits and the
+// batch has at most one vertex tile per SM (measured: with more tiles the two
+// grid barriers per iteration cost more than graph-replayed phase launches)
+bool resident_preferred(const SolveArgs& A, const SolvePlan& P);
+
 }  // namespace fbs

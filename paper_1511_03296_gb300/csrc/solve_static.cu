@@ -204,7 +204,7 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
     cudaStreamIsCapturing(s, &cs);
     P.persistent = G.persistent && cs == cudaStreamCaptureStatusNone ? 1 : 0;
     P.barrier = reinterpret_cast<unsigned*>(base + L.barrier);
-    if (P.persistent && !resident_fits(A, P)) P.persistent = 0;
+    if (P.persistent && !resident_preferred(A, P)) P.persistent = 0;
 
     e = launch_segment(A, P, kSegSetup, kSplatConfidence, s);
     if (e == cudaSuccess) e = launch_segment(A, P, kSegLoop, kSplatConfidence, s);
