@@ -145,15 +145,18 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *   FBS_VECTORS_COMPENSATED  y, d in FP32; the residual r as a pair of FP32
  *                            values (double-float) and q = A d recomputed in
  *                            the update phase with error-free products, so
- *                            r <- r - alpha A d carries no rounding of q.
- *                            Same vector bytes per channel, one more
- *                            neighbour-table pass per iteration.
+ *                            r <- r - alpha A d carries no rounding of q
+ *                            (the FP32 A d of the first phase only enters
+ *                            d^T q, i.e. the step length).  Same vector bytes
+ *                            per channel, one more neighbour-table pass per
+ *                            iteration.
  *   FBS_VECTORS_AUTO         (default) compensated for fbs_solve_backward,
  *                            FP32 for fbs_solve and fbs_solve_robust.
  * FBS_OPT_PCG_LAUNCH: how the PCG iterations are launched:
- *   FBS_PCG_AUTO             (default) FBS_PCG_PERSISTENT when every vertex tile
- *                            gets its own co-resident block and no image has
- *                            more than 4 channels (the topology then stays in
+ *   FBS_PCG_AUTO             (default) FBS_PCG_PERSISTENT when the batch has
+ *                            at most one vertex tile per SM and no image has
+ *                            more than 4 channels (every tile then gets its
+ *                            own co-resident block and its topology stays in
  *                            shared memory for the whole loop), else
  *                            FBS_PCG_PER_PHASE.
  *   FBS_PCG_PERSISTENT       all iterations in one cooperative launch whose

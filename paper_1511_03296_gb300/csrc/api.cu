@@ -657,7 +657,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
         I.part_base = cpart;
         I.N = (int64_t)g->img[k].H * g->img[k].W;
         I.pix_base = g->img[k].pix_base;
-        cv += ((int64_t)I.Cp * I.V + 3) / 4 * 4;     // 16-byte aligned image blocks
+        cv += ((int64_t)I.Cp * I.V + 31) / 32 * 32;  // 128-byte aligned image blocks
         cpart += (int64_t)I.C * I.ntiles;
         pc += I.C;
         cmax = std::max(cmax, I.C);
@@ -687,7 +687,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
         dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s);
         dfree(g->part, s); dfree(g->inst, s);
         g->inst_cached.clear();
-        g->cap_vec = (size_t)std::max<int64_t>(cv, 4);
+        g->cap_vec = (size_t)std::max<int64_t>(cv, 32);
         g->cap_scal = (size_t)std::max(pc, 1);
         g->cap_part = (size_t)std::max<int64_t>(cpart, 1);
         if ((e = dalloc(&g->vec, 6 * g->cap_vec, s)) != cudaSuccess) return cuda_status(e);

@@ -91,6 +91,12 @@ struct PhaseSmem {
     double sa[kMaxChannels];     // alpha (phase 2)
 };
 
+// scratch of the per-channel reduction of wide images (Cp > 4)
+struct WideSmem {
+    DF lane[kVTile][4];          // each thread's four channel sums
+    DF group[kVTile];            // [group][channel] partial sums
+};
+
 // Block-reduce W double-float partials (channels cb .. cb+W-1) and store each
 // in partial slot `slot` of its channel.
 template <int W>
@@ -491,8 +497,9 @@ residual_kernel(SolveArgs A)
 
 // -------------------------------------------------- PCG phase bodies ---
 // Phase 1 of iteration `it` on one tile: d = M^-1 r + beta d_old (own vertex
-// and, on the fly, its neighbours), q = A d, products d q.  COMP: q is not
-// stored (phase 2 recomputes it exactly from d).
+// and, on the fly, its neighbours), q = A d, products d q.  q is formed in
+// FP32 in both precisions: here it only enters d^T q (the step length).
+// COMP: q is not stored (phase 2 recomputes it exactly from d).
 template <int W, bool COMP, bool CO>
 __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
                                            const float* __restrict__ dold,
@@ -541,18 +548,17 @@ __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I,
 #pragma unroll
                 for (int k = 0; k < W; ++k) du[k] = fmaf(beta[k], ou[k], nmu.y * ru[k]);
             }
-            lap_acc<W, COMP>(s, nmu.x, dv, du);
+            lap_acc<W, false>(s, nmu.x, dv, du);
         }
         DF acc[W];
         float qh[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            const DF q = lap_finish<COMP>(av, lam_n, dv[k], s[k]);
+            const DF q = lap_finish<false>(av, lam_n, dv[k], s[k]);
             qh[k] = q.hi;
             const bool on = valid && cb + k < I.C;
             acc[k] = !on ? DF{0.0f, 0.0f}
-                         : COMP ? df_add(df_mul_exact(dv[k], q.hi), DF{dv[k] * q.lo, 0.0f})
-                                : df_mul_exact(dv[k], q.hi);
+                         : df_mul_exact(dv[k], q.hi);
         }
         if (valid) {
             stw<W>(dnew + base + v * I.Cp, dv);
@@ -640,6 +646,185 @@ __device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I
     }
 }
 
+// ------------------------------------------------ wide images (Cp > 4) ---
+// The Cp / 4 consecutive threads of a vertex each take one float4 of its
+// channel row (thread p: channels 4p .. 4p+3), so a neighbour's whole row is
+// one coalesced request and the topology loads are shared (same address)
+// by the vertex's threads.  A tile is walked in chunks of kVTile / P
+// vertices.  A thread's channels stay fixed, so its products accumulate in
+// run[] over the block's whole run of the image's tiles.
+__device__ __forceinline__ void wide_lane(const InstDev& I, int& P, int& nvc, int& lv, int& p)
+{
+    P = I.Cp >> 2;
+    nvc = kVTile / P;
+    lv = threadIdx.x / P;
+    p = threadIdx.x - lv * P;
+}
+
+template <bool COMP, bool CO>
+__device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I, const VTile& vt,
+                                           const float* __restrict__ dold,
+                                           float* __restrict__ dnew, bool first, PhaseSmem& S,
+                                           DF (&run)[4])
+{
+    int P, nvc, lv, p;
+    wide_lane(I, P, nvc, lv, p);
+    const int cb = 4 * p;
+    const int64_t base = pass_base(I, cb);
+    float beta[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) beta[k] = S.sf[min(cb + k, kMaxChannels - 1)];
+    const int nverts = (int)(vt.v1 - vt.v0);
+    for (int c0 = 0; c0 < nverts; c0 += nvc) {
+        const int64_t v = vt.v0 + c0 + lv;
+        const bool valid = lv < nvc && c0 + lv < nverts;
+        const int64_t vs = valid ? v : vt.v0;
+        const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
+        const float av = valid ? A.a[v] : 0.0f;
+        const float lam_n = I.lam * nmv.x;
+        int32_t nb[10];
+#pragma unroll
+        for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+        float rv[4], dv[4];
+        ldw<4, CO>(A.r + base + vs * I.Cp, rv);
+        if (first) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dv[k] = nmv.y * rv[k];
+        } else {
+            float ov[4];
+            ldw<4, CO>(dold + base + vs * I.Cp, ov);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dv[k] = fmaf(beta[k], ov[k], nmv.y * rv[k]);
+        }
+        DF sacc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sacc[k] = {0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            const int64_t u = nb[j] >= 0 ? nb[j] : vs;
+            const float2 nmu = nb[j] >= 0 ? A.nm[u] : make_float2(0.0f, 0.0f);
+            float ru[4], du[4];
+            ldw<4, CO>(A.r + base + u * I.Cp, ru);
+            if (first) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) du[k] = nmu.y * ru[k];
+            } else {
+                float ou[4];
+                ldw<4, CO>(dold + base + u * I.Cp, ou);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) du[k] = fmaf(beta[k], ou[k], nmu.y * ru[k]);
+            }
+            lap_acc<4, false>(sacc, nmu.x, dv, du);
+        }
+        float qh[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const DF q = lap_finish<false>(av, lam_n, dv[k], sacc[k]);
+            qh[k] = q.hi;
+            if (valid && cb + k < I.C)
+                run[k] = df_add(run[k], df_mul_exact(dv[k], q.hi));
+        }
+        if (valid) {
+            stw<4>(dnew + base + v * I.Cp, dv);
+            if (!COMP) stw<4>(A.q + base + v * I.Cp, qh);
+        }
+    }
+}
+
+template <bool COMP, bool CO>
+__device__ __forceinline__ void update_wide(const SolveArgs& A, const InstDev& I, const VTile& vt,
+                                            const float* __restrict__ d, PhaseSmem& S,
+                                            DF (&run)[4])
+{
+    int P, nvc, lv, p;
+    wide_lane(I, P, nvc, lv, p);
+    const int cb = 4 * p;
+    const int64_t base = pass_base(I, cb);
+    double alpha[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) alpha[k] = S.sa[min(cb + k, kMaxChannels - 1)];
+    const int nverts = (int)(vt.v1 - vt.v0);
+    for (int c0 = 0; c0 < nverts; c0 += nvc) {
+        const int64_t v = vt.v0 + c0 + lv;
+        const bool valid = lv < nvc && c0 + lv < nverts;
+        const int64_t vs = valid ? v : vt.v0;
+        const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
+        float dv[4], yv[4], rv[4], rl[4], qv[4];
+        ldw<4, CO>(d + base + vs * I.Cp, dv);
+        ldw<4, CO>(A.y + base + vs * I.Cp, yv);
+        ldw<4, CO>(A.r + base + vs * I.Cp, rv);
+        DF sacc[4];
+        float av = 0.0f, lam_n = 0.0f;
+        if (COMP) {
+            av = valid ? A.a[v] : 0.0f;
+            lam_n = I.lam * nmv.x;
+            ldw<4, CO>(A.rlo + base + vs * I.Cp, rl);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sacc[k] = {0.0f, 0.0f};
+#pragma unroll
+            for (int j = 0; j < 10; ++j) {
+                const int32_t u0 = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+                const int64_t u = u0 >= 0 ? u0 : vs;
+                const float nu = u0 >= 0 ? A.nm[u].x : 0.0f;
+                float du[4];
+                ldw<4, CO>(d + base + u * I.Cp, du);
+                lap_acc<4, true>(sacc, nu, dv, du);
+            }
+        } else {
+            ldw<4, CO>(A.q + base + vs * I.Cp, qv);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            yv[k] = fmaf((float)alpha[k], dv[k], yv[k]);
+            if (COMP) {
+                const DF q = lap_finish<true>(av, lam_n, dv[k], sacc[k]);
+                const DF r = df_add(DF{rv[k], rl[k]}, df_neg(df_mul(df_from_double(alpha[k]), q)));
+                rv[k] = r.hi;
+                rl[k] = r.lo;
+            } else {
+                rv[k] = fmaf(-(float)alpha[k], qv[k], rv[k]);
+            }
+            if (valid && cb + k < I.C) run[k] = df_add(run[k], df_mul_exact(rv[k], nmv.y * rv[k]));
+        }
+        if (valid) {
+            stw<4>(A.y + base + v * I.Cp, yv);
+            stw<4>(A.r + base + v * I.Cp, rv);
+            if (COMP) stw<4>(A.rlo + base + v * I.Cp, rl);
+        }
+    }
+}
+
+// Per-channel sums of the block's run over a wide image, into the run's
+// slot: thread sums first go to shared memory; G = kVTile / Cp threads per
+// channel each add every G-th vertex lane in order, then one thread per
+// channel adds the G group sums in order.
+__device__ void flush_wide(DF (&run)[4], int Cp, int C, int ntiles, int64_t part_base, int slot,
+                           float2* part, WideSmem& Wd)
+{
+    const int P = Cp >> 2, nvc = kVTile / P, lv = threadIdx.x / P;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        Wd.lane[t][k] = lv < nvc ? run[k] : DF{0.0f, 0.0f};
+        run[k] = {0.0f, 0.0f};
+    }
+    __syncthreads();
+    const int G = kVTile / Cp;
+    if (t < G * Cp) {
+        const int ch = t % Cp, g = t / Cp;
+        DF acc = {0.0f, 0.0f};
+        for (int l = g; l < nvc; l += G) acc = df_add(acc, Wd.lane[l * P + (ch >> 2)][ch & 3]);
+        Wd.group[g * Cp + ch] = acc;
+    }
+    __syncthreads();
+    if (t < C) {
+        DF acc = Wd.group[t];
+        for (int g = 1; g < G; ++g) acc = df_add(acc, Wd.group[g * Cp + t]);
+        part[part_base + (int64_t)t * ntiles + slot] = make_float2(acc.hi, acc.lo);
+    }
+    __syncthreads();
+}
+
 // Store the block's run partial (channels of one pass) in the slot of the
 // first tile of the run; the other slots of the run were written as exact
 // zeros as their tiles were visited, so the reducers' sums are unchanged.
@@ -667,13 +852,14 @@ __device__ __forceinline__ void flush_run(DF (&run)[4], int W, int C, int ntiles
 // products are accumulated over the run of its tiles in this chunk.
 template <int PHASE, bool COMP, bool CO, int WMAX>
 __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
-                          float* __restrict__ ddst, int it, int t0, int t1, PhaseSmem& S)
+                          float* __restrict__ ddst, int it, int t0, int t1, PhaseSmem& S,
+                          WideSmem& Wd)
 {
     const int slot = it & 1;
     const bool first = it == 0;
     float2* const out = PHASE == 1 ? A.part_dq : A.part_rs[slot ^ 1];
     const float2* const in = PHASE == 1 ? A.part_rs[slot] : A.part_dq;
-    int cur = -1, run_tile = 0, run_C = 0, run_W = 1, run_ntiles = 0;
+    int cur = -1, run_tile = 0, run_C = 0, run_Cp = 1, run_W = 1, run_ntiles = 0;
     int64_t run_base = 0;
     bool single = false;
     DF run[4];
@@ -683,8 +869,12 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
         const VTile vt = A.vt[tile];
         const InstDev I = A.inst[vt.inst];
         if (vt.inst != cur) {
-            if (cur >= 0 && single)
-                flush_run(run, run_W, run_C, run_ntiles, run_base, run_tile, out, S);
+            if (cur >= 0 && single) {
+                if (WMAX == 4 && run_Cp > 4)
+                    flush_wide(run, run_Cp, run_C, run_ntiles, run_base, run_tile, out, Wd);
+                else
+                    flush_run(run, run_W, run_C, run_ntiles, run_base, run_tile, out, S);
+            }
             __syncthreads();
             reduce_instance_partials(in, I, S.sd);
             __syncthreads();
@@ -713,15 +903,19 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
             cur = vt.inst;
             run_tile = vt.t_in_inst;
             run_C = I.C;
+            run_Cp = I.Cp;
             run_W = I.Cp < 4 ? I.Cp : 4;
             run_ntiles = I.ntiles;
             run_base = I.part_base;
-            single = I.Cp <= 4;
+            single = true;
         } else if (single && (int)threadIdx.x < I.C) {
             out[I.part_base + (int64_t)threadIdx.x * I.ntiles + vt.t_in_inst] =
                 make_float2(0.0f, 0.0f);
         }
-        if (PHASE == 1) {
+        if (WMAX == 4 && I.Cp > 4) {
+            if (PHASE == 1) apply_wide<COMP, CO>(A, I, vt, dsrc, ddst, first, S, run);
+            else update_wide<COMP, CO>(A, I, vt, dsrc, S, run);
+        } else if (PHASE == 1) {
             if (WMAX == 1 || I.Cp == 1)
                 apply_tile<1, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
             else if (WMAX == 2 || I.Cp == 2)
@@ -737,7 +931,12 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
                 update_tile<4, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
         }
     }
-    if (cur >= 0 && single) flush_run(run, run_W, run_C, run_ntiles, run_base, run_tile, out, S);
+    if (cur >= 0 && single) {
+        if (WMAX == 4 && run_Cp > 4)
+            flush_wide(run, run_Cp, run_C, run_ntiles, run_base, run_tile, out, Wd);
+        else
+            flush_run(run, run_W, run_C, run_ntiles, run_base, run_tile, out, S);
+    }
 }
 
 // Phase kernels are instantiated per widest pass of the batch (WMAX = the
@@ -754,9 +953,10 @@ __global__ void __launch_bounds__(kVTile, phase_min_blocks<WMAX>())
 pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict__ dnew, int it)
 {
     __shared__ PhaseSmem S;
+    __shared__ WideSmem Wd;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
-    phase_run<1, COMP, false, WMAX>(A, dold, dnew, it, t0, t1, S);
+    phase_run<1, COMP, false, WMAX>(A, dold, dnew, it, t0, t1, S, Wd);
 }
 
 template <int WMAX, bool COMP>
@@ -764,9 +964,10 @@ __global__ void __launch_bounds__(kVTile, phase_min_blocks<WMAX>())
 pcg_update_kernel(SolveArgs A, const float* __restrict__ d, int it)
 {
     __shared__ PhaseSmem S;
+    __shared__ WideSmem Wd;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
-    phase_run<2, COMP, false, WMAX>(A, d, nullptr, it, t0, t1, S);
+    phase_run<2, COMP, false, WMAX>(A, d, nullptr, it, t0, t1, S, Wd);
 }
 
 // ------------------------------------------------- persistent PCG loop ---
@@ -827,14 +1028,15 @@ __global__ void __launch_bounds__(kVTile, phase_min_blocks<WMAX>())
 pcg_loop_kernel(SolveArgs A, int iters, unsigned* bar)
 {
     __shared__ PhaseSmem S;
+    __shared__ WideSmem Wd;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
     for (int it = 0; it < iters; ++it) {
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
-        phase_run<1, COMP, true, WMAX>(A, dold, dnew, it, t0, t1, S);
+        phase_run<1, COMP, true, WMAX>(A, dold, dnew, it, t0, t1, S, Wd);
         if (!grid_barrier(bar, A.err)) return;
-        phase_run<2, COMP, true, WMAX>(A, dnew, nullptr, it, t0, t1, S);
+        phase_run<2, COMP, true, WMAX>(A, dnew, nullptr, it, t0, t1, S, Wd);
         if (!grid_barrier(bar, A.err)) return;
     }
 }
@@ -980,19 +1182,18 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
                     float dz[W];
 #pragma unroll
                     for (int k = 0; k < W; ++k) dz[k] = fmaf(beta[k], du[j][k], nm.y * ru[j][k]);
-                    lap_acc<W, COMP>(s, nm.x, dv, dz);
+                    lap_acc<W, false>(s, nm.x, dv, dz);
                 }
             }
             DF acc[W];
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                const DF qq = lap_finish<COMP>(av, lam_n, dv[k], s[k]);
+                const DF qq = lap_finish<false>(av, lam_n, dv[k], s[k]);
                 d[k] = dv[k];
                 q[k] = qq.hi;
                 const bool on = valid && k < I.C;
                 acc[k] = !on ? DF{0.0f, 0.0f}
-                             : COMP ? df_add(df_mul_exact(dv[k], qq.hi), DF{dv[k] * qq.lo, 0.0f})
-                                    : df_mul_exact(dv[k], qq.hi);
+                             : df_mul_exact(dv[k], qq.hi);
             }
             if (valid) stw<W>(dnew + base + v * I.Cp, dv);
             store_partials<W>(acc, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst, A.part_dq, S.red);

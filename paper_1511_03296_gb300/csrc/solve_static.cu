@@ -131,7 +131,7 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
         I.part_base = cpart;
         I.N = (int64_t)G.img[k].H * G.img[k].W;
         I.pix_base = G.img[k].pix_base;
-        cv += ((int64_t)I.Cp * I.V + 3) / 4 * 4;     // 16-byte aligned image blocks
+        cv += ((int64_t)I.Cp * I.V + 31) / 32 * 32;  // 128-byte aligned image blocks
         cpart += (int64_t)I.C * I.ntiles;
         pc += I.C;
         cmax = cmax > I.C ? cmax : I.C;
