@@ -147,6 +147,90 @@ __device__ void reduce_instance_partials(const float2* __restrict__ part, const 
     }
 }
 
+// All threads sum the partials of one instance for all its (<= W) channels
+// (thread t takes slots t, t + blockDim, ..., H of them per channel in
+// flight), then a block tree; out[ch].  Whole block; ends with a barrier.
+template <int W, int H = (W == 4 ? 1 : 2)>
+__device__ void reduce_partials_all(const float2* __restrict__ part, const InstDev& I,
+                                    double* out, DF (*red)[kVTile / 32])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    DF acc[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) acc[k] = {0.0f, 0.0f};
+    for (int j0 = threadIdx.x; j0 < I.ntiles; j0 += H * blockDim.x) {
+        float2 v[W][H];
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const int j = j0 + h * blockDim.x;
+                v[k][h] = (k < I.C && j < I.ntiles)
+                              ? __ldcg(part + I.part_base + (int64_t)k * I.ntiles + j)
+                              : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+        for (int k = 0; k < W; ++k)
+#pragma unroll
+            for (int h = 0; h < H; ++h) acc[k] = df_add(acc[k], DF{v[k][h].x, v[k][h].y});
+    }
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const DF t = df_warp_sum(acc[k]);
+        if (lane == 0) red[k][w] = t;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < W && (int)threadIdx.x < I.C) {
+        const int k = threadIdx.x;
+        DF t = red[k][0];
+        for (int j = 1; j < nw; ++j) t = df_add(t, red[k][j]);
+        out[k] = df_to_double(t);
+    }
+    __syncthreads();
+}
+
+// The CG scalars a block needs for image I at the start of a phase, from the
+// previous phase's partials (every block forms the same values): phase 1
+// delta_it = r^T M^-1 r and beta = delta_it / delta_(it-1) (delta_it is also
+// stored); phase 2 alpha = delta_it / d^T q.  Padding channels get 0.
+// Whole block; ends with a barrier.
+template <int PHASE, bool CO, int WMAX>
+__device__ void phase_scalars(const SolveArgs& A, const InstDev& I, const float2* in, int it,
+                              PhaseSmem& S)
+{
+    const int slot = it & 1;
+    __syncthreads();
+    if (WMAX == 1 || I.Cp == 1) reduce_partials_all<1, 8>(in, I, S.sd, S.red);
+    else if (WMAX == 2 || I.Cp == 2) reduce_partials_all<2, 4>(in, I, S.sd, S.red);
+    else if (I.Cp == 4) reduce_partials_all<4, 2>(in, I, S.sd, S.red);
+    else {
+        reduce_instance_partials(in, I, S.sd);
+        __syncthreads();
+    }
+    for (int ch = threadIdx.x; ch < I.Cp; ch += blockDim.x) {
+        if (ch >= I.C) {            // padding channels: scalars 0 keep them at 0
+            S.sf[ch] = 0.0f;
+            S.sa[ch] = 0.0;
+        } else if (PHASE == 1) {
+            const double dnow = S.sd[ch];
+            double beta = 0.0;
+            if (it > 0) {
+                const double dprev = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1])
+                                        : A.scal[I.pc + ch].delta[slot ^ 1];
+                beta = dprev != 0.0 ? dnow / dprev : 0.0;
+            }
+            S.sf[ch] = (float)beta;
+            A.scal[I.pc + ch].delta[slot] = dnow;   // same value from every block
+        } else {
+            const double delta = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot])
+                                    : A.scal[I.pc + ch].delta[slot];
+            const double dq = S.sd[ch];
+            S.sa[ch] = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
+        }
+    }
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- splat ---
 // A is applied in Laplacian form,
 //   (A z)_v = a'_v z_v + lambda n_v sum_u n_u (z_v - z_u),
@@ -496,153 +580,129 @@ residual_kernel(SolveArgs A)
 }
 
 // -------------------------------------------------- PCG phase bodies ---
-// Phase 1 of iteration `it` on one tile: d = M^-1 r + beta d_old (own vertex
-// and, on the fly, its neighbours), q = A d, products d q.  q is formed in
-// FP32 in both precisions: here it only enters d^T q (the step length).
-// COMP: q is not stored (phase 2 recomputes it exactly from d).
+// Phase 1 of iteration `it` on one tile of an image with Cp = W <= 4 (one
+// pass; the row stride is the compile-time W, and vertex ids are 32-bit):
+// d = M^-1 r + beta d_old (own vertex and, on the fly, its neighbours),
+// q = A d, products d q into run[].  q is formed in FP32 in both precisions:
+// here it only enters d^T q (the step length).  COMP: q is not stored
+// (phase 2 recomputes it exactly from d).  With fetch (the tile starts the
+// block's run over an image) the CG scalars are formed first, after the
+// tile's neighbour ids and own values have been requested.
 template <int W, bool COMP, bool CO>
 __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
                                            const float* __restrict__ dold,
                                            float* __restrict__ dnew, bool first, PhaseSmem& S,
-                                           DF (&run)[4], bool single)
+                                           DF (&run)[4], bool fetch, const float2* in, int it)
 {
-    const int64_t v = vt.v0 + threadIdx.x;
-    const bool valid = v < vt.v1;
-    const int64_t vs = valid ? v : vt.v0;
+    const int v = (int)vt.v0 + (int)threadIdx.x;
+    const bool valid = v < (int)vt.v1;
+    const int vs = valid ? v : (int)vt.v0;
+    const int64_t off = I.vec_base - I.voff * W;        // element (ch, u) at off + u W + ch
+    const float* __restrict__ rb = A.r + off;
+    const float* __restrict__ ob = dold + off;
     const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
     const float av = valid ? A.a[v] : 0.0f;
-    const float lam_n = I.lam * nmv.x;
-    int32_t nb[10];
+    int nb[10];
 #pragma unroll
     for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
-    for (int cb = 0; cb < I.C; cb += W) {
-        const int64_t base = pass_base(I, cb);
-        float beta[W], rv[W], dv[W];
+    float rv[W], ov[W];
+    ldw<W, CO>(rb + vs * W, rv);
+    if (!first) ldw<W, CO>(ob + vs * W, ov);
+    if (fetch) phase_scalars<1, CO, W>(A, I, in, it, S);
+    float beta[W], dv[W];
 #pragma unroll
-        for (int k = 0; k < W; ++k) beta[k] = S.sf[min(cb + k, kMaxChannels - 1)];
-        ldw<W, CO>(A.r + base + vs * I.Cp, rv);
-        if (first) {
+    for (int k = 0; k < W; ++k) {
+        beta[k] = S.sf[k];
+        dv[k] = first ? nmv.y * rv[k] : fmaf(beta[k], ov[k], nmv.y * rv[k]);
+    }
+    float sacc[W];
 #pragma unroll
-            for (int k = 0; k < W; ++k) dv[k] = nmv.y * rv[k];
-        } else {
-            float ov[W];
-            ldw<W, CO>(dold + base + vs * I.Cp, ov);
+    for (int k = 0; k < W; ++k) sacc[k] = 0.0f;
 #pragma unroll
-            for (int k = 0; k < W; ++k) dv[k] = fmaf(beta[k], ov[k], nmv.y * rv[k]);
-        }
-        DF s[W];
-#pragma unroll
-        for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
-#pragma unroll
-        for (int j = 0; j < 10; ++j) {
-            const int64_t u = nb[j] >= 0 ? nb[j] : vs;
-            const float2 nmu = nb[j] >= 0 ? A.nm[u] : make_float2(0.0f, 0.0f);
-            float ru[W], du[W];
-            ldw<W, CO>(A.r + base + u * I.Cp, ru);
-            if (first) {
-#pragma unroll
-                for (int k = 0; k < W; ++k) du[k] = nmu.y * ru[k];
-            } else {
-                float ou[W];
-                ldw<W, CO>(dold + base + u * I.Cp, ou);
-#pragma unroll
-                for (int k = 0; k < W; ++k) du[k] = fmaf(beta[k], ou[k], nmu.y * ru[k]);
-            }
-            lap_acc<W, false>(s, nmu.x, dv, du);
-        }
-        DF acc[W];
-        float qh[W];
+    for (int j = 0; j < 10; ++j) {
+        const bool has = nb[j] >= 0;
+        const int u = has ? nb[j] : vs;
+        const float2 nm = has ? A.nm[u] : make_float2(0.0f, 0.0f);
+        float ru[W], ou[W];
+        ldw<W, CO>(rb + u * W, ru);
+        if (!first) ldw<W, CO>(ob + u * W, ou);
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            const DF q = lap_finish<false>(av, lam_n, dv[k], s[k]);
-            qh[k] = q.hi;
-            const bool on = valid && cb + k < I.C;
-            acc[k] = !on ? DF{0.0f, 0.0f}
-                         : df_mul_exact(dv[k], q.hi);
+            const float du = first ? nm.y * ru[k] : fmaf(beta[k], ou[k], nm.y * ru[k]);
+            sacc[k] = fmaf(nm.x, dv[k] - du, sacc[k]);
         }
-        if (valid) {
-            stw<W>(dnew + base + v * I.Cp, dv);
-            if (!COMP) stw<W>(A.q + base + v * I.Cp, qh);
-        }
-        if (single) {
+    }
+    const float lam_n = I.lam * nmv.x;
+    float qh[W];
 #pragma unroll
-            for (int k = 0; k < W; ++k) run[k] = df_add(run[k], acc[k]);
-        } else {
-            store_partials<W>(acc, I.C, I.ntiles, I.part_base, cb, vt.t_in_inst, A.part_dq,
-                              S.red);
-        }
+    for (int k = 0; k < W; ++k) {
+        qh[k] = fmaf(av, dv[k], lam_n * sacc[k]);
+        if (valid && k < I.C) run[k] = df_add(run[k], df_mul_exact(dv[k], qh[k]));
+    }
+    if (valid) {
+        stw<W>(dnew + off + v * W, dv);
+        if (!COMP) stw<W>(A.q + off + v * W, qh);
     }
 }
 
-// Phase 2 on one tile: y += alpha d; r -= alpha q; products r M^-1 r.
-// COMP: q = A d is recomputed here with compensated arithmetic and the
-// residual is kept as a double-float pair (r, r_lo), so the recurrence
-// r <- r - alpha A d carries no rounding of q.
+// Phase 2 on one tile of an image with Cp = W <= 4: y += alpha d;
+// r -= alpha q; products r M^-1 r into run[].  COMP: q = A d is recomputed
+// here with compensated arithmetic and the residual is kept as a
+// double-float pair (r, r_lo), so the recurrence r <- r - alpha A d carries
+// no rounding of q.  With fetch, the CG scalars are formed after the tile's
+// own loads have been requested.
 template <int W, bool COMP, bool CO>
 __device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
-                                            const float* __restrict__ d, float2* __restrict__ out,
-                                            PhaseSmem& S, DF (&run)[4], bool single)
+                                            const float* __restrict__ d, PhaseSmem& S,
+                                            DF (&run)[4], bool fetch, const float2* in, int it)
 {
-    const int64_t v = vt.v0 + threadIdx.x;
-    const bool valid = v < vt.v1;
-    const int64_t vs = valid ? v : vt.v0;
+    const int v = (int)vt.v0 + (int)threadIdx.x;
+    const bool valid = v < (int)vt.v1;
+    const int vs = valid ? v : (int)vt.v0;
+    const int64_t off = I.vec_base - I.voff * W;
     const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
-    const float av = COMP && valid ? A.a[v] : 0.0f;
-    const float lam_n = I.lam * nmv.x;
-    int32_t nb[10];
+    float dv[W], yv[W], rv[W], rl[W], qv[W];
+    ldw<W, CO>(d + off + vs * W, dv);
+    ldw<W, CO>(A.y + off + vs * W, yv);
+    ldw<W, CO>(A.r + off + vs * W, rv);
+    if (COMP) ldw<W, CO>(A.rlo + off + vs * W, rl);
+    else ldw<W, CO>(A.q + off + vs * W, qv);
+    if (fetch) phase_scalars<2, CO, W>(A, I, in, it, S);
+    DF sacc[W];
+    float av = 0.0f;
     if (COMP) {
+        av = valid ? A.a[v] : 0.0f;
 #pragma unroll
-        for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+        for (int k = 0; k < W; ++k) sacc[k] = {0.0f, 0.0f};
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            const int u0 = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+            const int u = u0 >= 0 ? u0 : vs;
+            const float nu = u0 >= 0 ? A.nm[u].x : 0.0f;
+            float du[W];
+            ldw<W, CO>(d + off + u * W, du);
+            lap_acc<W, true>(sacc, nu, dv, du);
+        }
     }
-    for (int cb = 0; cb < I.C; cb += W) {
-        const int64_t base = pass_base(I, cb);
-        float dv[W], yv[W], rv[W], rl[W], qv[W];
-        ldw<W, CO>(d + base + vs * I.Cp, dv);
-        ldw<W, CO>(A.y + base + vs * I.Cp, yv);
-        ldw<W, CO>(A.r + base + vs * I.Cp, rv);
-        DF s[W];
+    const float lam_n = I.lam * nmv.x;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const double alpha = S.sa[k];
+        yv[k] = fmaf((float)alpha, dv[k], yv[k]);
         if (COMP) {
-            ldw<W, CO>(A.rlo + base + vs * I.Cp, rl);
-#pragma unroll
-            for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
-#pragma unroll
-            for (int j = 0; j < 10; ++j) {
-                const int64_t u = nb[j] >= 0 ? nb[j] : vs;
-                const float nu = nb[j] >= 0 ? A.nm[u].x : 0.0f;
-                float du[W];
-                ldw<W, CO>(d + base + u * I.Cp, du);
-                lap_acc<W, true>(s, nu, dv, du);
-            }
+            const DF q = lap_finish<true>(av, lam_n, dv[k], sacc[k]);
+            const DF r = df_add(DF{rv[k], rl[k]}, df_neg(df_mul(df_from_double(alpha), q)));
+            rv[k] = r.hi;
+            rl[k] = r.lo;
         } else {
-            ldw<W, CO>(A.q + base + vs * I.Cp, qv);
+            rv[k] = fmaf(-(float)alpha, qv[k], rv[k]);
         }
-        DF acc[W];
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-            const double alpha = S.sa[min(cb + k, kMaxChannels - 1)];
-            yv[k] = fmaf((float)alpha, dv[k], yv[k]);
-            if (COMP) {
-                const DF q = lap_finish<true>(av, lam_n, dv[k], s[k]);
-                const DF r = df_add(DF{rv[k], rl[k]}, df_neg(df_mul(df_from_double(alpha), q)));
-                rv[k] = r.hi;
-                rl[k] = r.lo;
-            } else {
-                rv[k] = fmaf(-(float)alpha, qv[k], rv[k]);
-            }
-            const bool on = valid && cb + k < I.C;
-            acc[k] = on ? df_mul_exact(rv[k], nmv.y * rv[k]) : DF{0.0f, 0.0f};
-        }
-        if (valid) {
-            stw<W>(A.y + base + v * I.Cp, yv);
-            stw<W>(A.r + base + v * I.Cp, rv);
-            if (COMP) stw<W>(A.rlo + base + v * I.Cp, rl);
-        }
-        if (single) {
-#pragma unroll
-            for (int k = 0; k < W; ++k) run[k] = df_add(run[k], acc[k]);
-        } else {
-            store_partials<W>(acc, I.C, I.ntiles, I.part_base, cb, vt.t_in_inst, out, S.red);
-        }
+        if (valid && k < I.C) run[k] = df_add(run[k], df_mul_exact(rv[k], nmv.y * rv[k]));
+    }
+    if (valid) {
+        stw<W>(A.y + off + v * W, yv);
+        stw<W>(A.r + off + v * W, rv);
+        if (COMP) stw<W>(A.rlo + off + v * W, rl);
     }
 }
 
@@ -669,30 +729,31 @@ __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I,
 {
     int P, nvc, lv, p;
     wide_lane(I, P, nvc, lv, p);
-    const int cb = 4 * p;
-    const int64_t base = pass_base(I, cb);
+    const int cb = 4 * p, Cp = I.Cp;
+    const float* __restrict__ rb = A.r + pass_base(I, cb);
+    const float* __restrict__ ob = dold + pass_base(I, cb);
     float beta[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) beta[k] = S.sf[min(cb + k, kMaxChannels - 1)];
     const int nverts = (int)(vt.v1 - vt.v0);
     for (int c0 = 0; c0 < nverts; c0 += nvc) {
-        const int64_t v = vt.v0 + c0 + lv;
+        const int v = (int)vt.v0 + c0 + lv;
         const bool valid = lv < nvc && c0 + lv < nverts;
-        const int64_t vs = valid ? v : vt.v0;
+        const int vs = valid ? v : (int)vt.v0;
         const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
         const float av = valid ? A.a[v] : 0.0f;
         const float lam_n = I.lam * nmv.x;
-        int32_t nb[10];
+        int nb[10];
 #pragma unroll
         for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
         float rv[4], dv[4];
-        ldw<4, CO>(A.r + base + vs * I.Cp, rv);
+        ldw<4, CO>(rb + vs * Cp, rv);
         if (first) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) dv[k] = nmv.y * rv[k];
         } else {
             float ov[4];
-            ldw<4, CO>(dold + base + vs * I.Cp, ov);
+            ldw<4, CO>(ob + vs * Cp, ov);
 #pragma unroll
             for (int k = 0; k < 4; ++k) dv[k] = fmaf(beta[k], ov[k], nmv.y * rv[k]);
         }
@@ -701,16 +762,16 @@ __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I,
         for (int k = 0; k < 4; ++k) sacc[k] = {0.0f, 0.0f};
 #pragma unroll
         for (int j = 0; j < 10; ++j) {
-            const int64_t u = nb[j] >= 0 ? nb[j] : vs;
+            const int u = nb[j] >= 0 ? nb[j] : vs;
             const float2 nmu = nb[j] >= 0 ? A.nm[u] : make_float2(0.0f, 0.0f);
             float ru[4], du[4];
-            ldw<4, CO>(A.r + base + u * I.Cp, ru);
+            ldw<4, CO>(rb + u * Cp, ru);
             if (first) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) du[k] = nmu.y * ru[k];
             } else {
                 float ou[4];
-                ldw<4, CO>(dold + base + u * I.Cp, ou);
+                ldw<4, CO>(ob + u * Cp, ou);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) du[k] = fmaf(beta[k], ou[k], nmu.y * ru[k]);
             }
@@ -725,8 +786,8 @@ __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I,
                 run[k] = df_add(run[k], df_mul_exact(dv[k], q.hi));
         }
         if (valid) {
-            stw<4>(dnew + base + v * I.Cp, dv);
-            if (!COMP) stw<4>(A.q + base + v * I.Cp, qh);
+            stw<4>(dnew + pass_base(I, cb) + v * Cp, dv);
+            if (!COMP) stw<4>(A.q + pass_base(I, cb) + v * Cp, qh);
         }
     }
 }
@@ -738,40 +799,40 @@ __device__ __forceinline__ void update_wide(const SolveArgs& A, const InstDev& I
 {
     int P, nvc, lv, p;
     wide_lane(I, P, nvc, lv, p);
-    const int cb = 4 * p;
+    const int cb = 4 * p, Cp = I.Cp;
     const int64_t base = pass_base(I, cb);
     double alpha[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) alpha[k] = S.sa[min(cb + k, kMaxChannels - 1)];
     const int nverts = (int)(vt.v1 - vt.v0);
     for (int c0 = 0; c0 < nverts; c0 += nvc) {
-        const int64_t v = vt.v0 + c0 + lv;
+        const int v = (int)vt.v0 + c0 + lv;
         const bool valid = lv < nvc && c0 + lv < nverts;
-        const int64_t vs = valid ? v : vt.v0;
+        const int vs = valid ? v : (int)vt.v0;
         const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
         float dv[4], yv[4], rv[4], rl[4], qv[4];
-        ldw<4, CO>(d + base + vs * I.Cp, dv);
-        ldw<4, CO>(A.y + base + vs * I.Cp, yv);
-        ldw<4, CO>(A.r + base + vs * I.Cp, rv);
+        ldw<4, CO>(d + base + vs * Cp, dv);
+        ldw<4, CO>(A.y + base + vs * Cp, yv);
+        ldw<4, CO>(A.r + base + vs * Cp, rv);
         DF sacc[4];
         float av = 0.0f, lam_n = 0.0f;
         if (COMP) {
             av = valid ? A.a[v] : 0.0f;
             lam_n = I.lam * nmv.x;
-            ldw<4, CO>(A.rlo + base + vs * I.Cp, rl);
+            ldw<4, CO>(A.rlo + base + vs * Cp, rl);
 #pragma unroll
             for (int k = 0; k < 4; ++k) sacc[k] = {0.0f, 0.0f};
 #pragma unroll
             for (int j = 0; j < 10; ++j) {
-                const int32_t u0 = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
-                const int64_t u = u0 >= 0 ? u0 : vs;
+                const int u0 = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+                const int u = u0 >= 0 ? u0 : vs;
                 const float nu = u0 >= 0 ? A.nm[u].x : 0.0f;
                 float du[4];
-                ldw<4, CO>(d + base + u * I.Cp, du);
+                ldw<4, CO>(d + base + u * Cp, du);
                 lap_acc<4, true>(sacc, nu, dv, du);
             }
         } else {
-            ldw<4, CO>(A.q + base + vs * I.Cp, qv);
+            ldw<4, CO>(A.q + base + vs * Cp, qv);
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -787,9 +848,9 @@ __device__ __forceinline__ void update_wide(const SolveArgs& A, const InstDev& I
             if (valid && cb + k < I.C) run[k] = df_add(run[k], df_mul_exact(rv[k], nmv.y * rv[k]));
         }
         if (valid) {
-            stw<4>(A.y + base + v * I.Cp, yv);
-            stw<4>(A.r + base + v * I.Cp, rv);
-            if (COMP) stw<4>(A.rlo + base + v * I.Cp, rl);
+            stw<4>(A.y + base + v * Cp, yv);
+            stw<4>(A.r + base + v * Cp, rv);
+            if (COMP) stw<4>(A.rlo + base + v * Cp, rl);
         }
     }
 }
@@ -861,7 +922,7 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
     const float2* const in = PHASE == 1 ? A.part_rs[slot] : A.part_dq;
     int cur = -1, run_tile = 0, run_C = 0, run_Cp = 1, run_W = 1, run_ntiles = 0;
     int64_t run_base = 0;
-    bool single = false;
+    bool fetch = false;
     DF run[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) run[k] = {0.0f, 0.0f};
@@ -869,37 +930,13 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
         const VTile vt = A.vt[tile];
         const InstDev I = A.inst[vt.inst];
         if (vt.inst != cur) {
-            if (cur >= 0 && single) {
+            if (cur >= 0) {
                 if (WMAX == 4 && run_Cp > 4)
                     flush_wide(run, run_Cp, run_C, run_ntiles, run_base, run_tile, out, Wd);
                 else
                     flush_run(run, run_W, run_C, run_ntiles, run_base, run_tile, out, S);
             }
-            __syncthreads();
-            reduce_instance_partials(in, I, S.sd);
-            __syncthreads();
-            for (int ch = threadIdx.x; ch < I.Cp; ch += blockDim.x) {
-                if (ch >= I.C) {            // padding channels: scalars 0 keep them at 0
-                    S.sf[ch] = 0.0f;
-                    S.sa[ch] = 0.0;
-                } else if (PHASE == 1) {
-                    const double dnow = S.sd[ch];
-                    double beta = 0.0;
-                    if (!first) {
-                        const double dprev = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1])
-                                                : A.scal[I.pc + ch].delta[slot ^ 1];
-                        beta = dprev != 0.0 ? dnow / dprev : 0.0;
-                    }
-                    S.sf[ch] = (float)beta;
-                    A.scal[I.pc + ch].delta[slot] = dnow;   // same value from every block
-                } else {
-                    const double delta = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot])
-                                            : A.scal[I.pc + ch].delta[slot];
-                    const double dq = S.sd[ch];
-                    S.sa[ch] = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
-                }
-            }
-            __syncthreads();
+            fetch = true;
             cur = vt.inst;
             run_tile = vt.t_in_inst;
             run_C = I.C;
@@ -907,31 +944,32 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
             run_W = I.Cp < 4 ? I.Cp : 4;
             run_ntiles = I.ntiles;
             run_base = I.part_base;
-            single = true;
-        } else if (single && (int)threadIdx.x < I.C) {
+        } else if ((int)threadIdx.x < I.C) {
             out[I.part_base + (int64_t)threadIdx.x * I.ntiles + vt.t_in_inst] =
                 make_float2(0.0f, 0.0f);
         }
         if (WMAX == 4 && I.Cp > 4) {
+            if (fetch) phase_scalars<PHASE, CO, 4>(A, I, in, it, S);
             if (PHASE == 1) apply_wide<COMP, CO>(A, I, vt, dsrc, ddst, first, S, run);
             else update_wide<COMP, CO>(A, I, vt, dsrc, S, run);
         } else if (PHASE == 1) {
             if (WMAX == 1 || I.Cp == 1)
-                apply_tile<1, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
+                apply_tile<1, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
             else if (WMAX == 2 || I.Cp == 2)
-                apply_tile<2, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
+                apply_tile<2, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
             else
-                apply_tile<4, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, single);
+                apply_tile<4, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
         } else {
             if (WMAX == 1 || I.Cp == 1)
-                update_tile<1, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
+                update_tile<1, COMP, CO>(A, I, vt, dsrc, S, run, fetch, in, it);
             else if (WMAX == 2 || I.Cp == 2)
-                update_tile<2, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
+                update_tile<2, COMP, CO>(A, I, vt, dsrc, S, run, fetch, in, it);
             else
-                update_tile<4, COMP, CO>(A, I, vt, dsrc, out, S, run, single);
+                update_tile<4, COMP, CO>(A, I, vt, dsrc, S, run, fetch, in, it);
         }
+        fetch = false;
     }
-    if (cur >= 0 && single) {
+    if (cur >= 0) {
         if (WMAX == 4 && run_Cp > 4)
             flush_wide(run, run_Cp, run_C, run_ntiles, run_base, run_tile, out, Wd);
         else
@@ -1049,48 +1087,6 @@ pcg_loop_kernel(SolveArgs A, int iters, unsigned* bar)
 // writing d and r for the neighbours and y once at the end.  Neighbour
 // gathers use a safe index (the vertex itself when a neighbour is absent) so
 // they issue together with the reduction of the previous phase's partials.
-
-// All threads sum the partials of one instance for all its (<= W) channels
-// (thread t takes slots t, t + blockDim, ...), then a block tree; out[ch].
-template <int W>
-__device__ void reduce_partials_all(const float2* __restrict__ part, const InstDev& I,
-                                    double* out, DF (*red)[kVTile / 32])
-{
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    DF acc[W];
-#pragma unroll
-    for (int k = 0; k < W; ++k) acc[k] = {0.0f, 0.0f};
-    constexpr int H = W == 4 ? 1 : 2;    // slots in flight per thread and channel
-    for (int j0 = threadIdx.x; j0 < I.ntiles; j0 += H * blockDim.x) {
-        float2 v[W][H];
-#pragma unroll
-        for (int k = 0; k < W; ++k)
-#pragma unroll
-            for (int h = 0; h < H; ++h) {
-                const int j = j0 + h * blockDim.x;
-                v[k][h] = (k < I.C && j < I.ntiles)
-                              ? __ldcg(part + I.part_base + (int64_t)k * I.ntiles + j)
-                              : make_float2(0.0f, 0.0f);
-            }
-#pragma unroll
-        for (int k = 0; k < W; ++k)
-#pragma unroll
-            for (int h = 0; h < H; ++h) acc[k] = df_add(acc[k], DF{v[k][h].x, v[k][h].y});
-    }
-#pragma unroll
-    for (int k = 0; k < W; ++k) {
-        const DF t = df_warp_sum(acc[k]);
-        if (lane == 0) red[k][w] = t;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < W && (int)threadIdx.x < I.C) {
-        const int k = threadIdx.x;
-        DF t = red[k][0];
-        for (int j = 1; j < nw; ++j) t = df_add(t, red[k][j]);
-        out[k] = df_to_double(t);
-    }
-    __syncthreads();
-}
 
 template <int W, bool COMP, int NG = (W == 4 ? 5 : 10)>
 __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile& vt, int iters,
