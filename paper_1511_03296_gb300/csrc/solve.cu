@@ -602,9 +602,14 @@ __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I,
     const float* __restrict__ ob = dold + off;
     const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
     const float av = valid ? A.a[v] : 0.0f;
+    // neighbour ids (an absent neighbour is replaced by the vertex itself:
+    // its term n_u (d_v - d_u) is then exactly 0, so no masking is needed)
     int nb[10];
 #pragma unroll
-    for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+    for (int j = 0; j < 10; ++j) {
+        const int u = A.nbr[(int64_t)j * A.Vtot + vs];
+        nb[j] = u >= 0 ? u : vs;
+    }
     float rv[W], ov[W];
     ldw<W, CO>(rb + vs * W, rv);
     if (!first) ldw<W, CO>(ob + vs * W, ov);
@@ -620,9 +625,8 @@ __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I,
     for (int k = 0; k < W; ++k) sacc[k] = 0.0f;
 #pragma unroll
     for (int j = 0; j < 10; ++j) {
-        const bool has = nb[j] >= 0;
-        const int u = has ? nb[j] : vs;
-        const float2 nm = has ? A.nm[u] : make_float2(0.0f, 0.0f);
+        const int u = nb[j];
+        const float2 nm = A.nm[u];
         float ru[W], ou[W];
         ldw<W, CO>(rb + u * W, ru);
         if (!first) ldw<W, CO>(ob + u * W, ou);
@@ -676,9 +680,9 @@ __device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I
         for (int k = 0; k < W; ++k) sacc[k] = {0.0f, 0.0f};
 #pragma unroll
         for (int j = 0; j < 10; ++j) {
-            const int u0 = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
-            const int u = u0 >= 0 ? u0 : vs;
-            const float nu = u0 >= 0 ? A.nm[u].x : 0.0f;
+            const int u0 = A.nbr[(int64_t)j * A.Vtot + vs];
+            const int u = u0 >= 0 ? u0 : vs;     // absent: the vertex itself, term 0
+            const float nu = A.nm[u].x;
             float du[W];
             ldw<W, CO>(d + off + u * W, du);
             lap_acc<W, true>(sacc, nu, dv, du);
@@ -745,7 +749,10 @@ __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I,
         const float lam_n = I.lam * nmv.x;
         int nb[10];
 #pragma unroll
-        for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+        for (int j = 0; j < 10; ++j) {
+            const int u = A.nbr[(int64_t)j * A.Vtot + vs];
+            nb[j] = u >= 0 ? u : vs;             // absent: the vertex itself, term 0
+        }
         float rv[4], dv[4];
         ldw<4, CO>(rb + vs * Cp, rv);
         if (first) {
@@ -762,8 +769,8 @@ __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I,
         for (int k = 0; k < 4; ++k) sacc[k] = {0.0f, 0.0f};
 #pragma unroll
         for (int j = 0; j < 10; ++j) {
-            const int u = nb[j] >= 0 ? nb[j] : vs;
-            const float2 nmu = nb[j] >= 0 ? A.nm[u] : make_float2(0.0f, 0.0f);
+            const int u = nb[j];
+            const float2 nmu = A.nm[u];
             float ru[4], du[4];
             ldw<4, CO>(rb + u * Cp, ru);
             if (first) {
@@ -824,9 +831,9 @@ __device__ __forceinline__ void update_wide(const SolveArgs& A, const InstDev& I
             for (int k = 0; k < 4; ++k) sacc[k] = {0.0f, 0.0f};
 #pragma unroll
             for (int j = 0; j < 10; ++j) {
-                const int u0 = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
-                const int u = u0 >= 0 ? u0 : vs;
-                const float nu = u0 >= 0 ? A.nm[u].x : 0.0f;
+                const int u0 = A.nbr[(int64_t)j * A.Vtot + vs];
+                const int u = u0 >= 0 ? u0 : vs;   // absent: the vertex itself, term 0
+                const float nu = A.nm[u].x;
                 float du[4];
                 ldw<4, CO>(d + base + u * Cp, du);
                 lap_acc<4, true>(sacc, nu, dv, du);
