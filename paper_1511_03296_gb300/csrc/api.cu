@@ -354,6 +354,9 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
         im.sxy = d.sigma_xy;
         im.sl = d.sigma_l;
         im.suv = d.sigma_uv;
+        im.isxy = 1.0f / d.sigma_xy;
+        im.isl = 1.0f / d.sigma_l;
+        im.isuv = 1.0f / d.sigma_uv;
         im.ncx = kx_max + 1;
         im.ncy = ky_max + 1;
         im.pix_base = pix;

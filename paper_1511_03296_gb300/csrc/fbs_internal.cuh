@@ -43,6 +43,7 @@ struct ImgDev {
     const float* yuv;       // 3 x H x W
     int H, W;
     float sxy, sl, suv;
+    float isxy, isl, isuv;  // 1 / sigma (FP32), for the quantiser's first estimate
     int ncx, ncy;           // number of cell columns / rows
     int64_t pix_base;       // first pixel in the concatenated pixel order
     int64_t cell_base;      // first cell in the concatenated cell order
@@ -107,10 +108,11 @@ enum SplatMode : int {
 // sign of 2p - (2k +- 1) sigma, which one fused multiply-add evaluates with
 // a single rounding (sign-exact).  Returns false when k is outside
 // [0, kFieldMax] or p is NaN.
-__device__ __forceinline__ bool quantise_exact(float p, float sigma, int& k)
+__device__ __forceinline__ bool quantise_exact(float p, float sigma, float inv_sigma, int& k)
 {
-    float q = __fdiv_rn(p, sigma);
-    float kf = floorf(__fadd_rn(q, 0.5f));
+    // estimate: within one of the exact result (|p / sigma| <= 4097, so the
+    // two roundings of p * (1 / sigma) + 1/2 move it by far less than 1/2)
+    float kf = floorf(__fmaf_rn(p, inv_sigma, 0.5f));
     if (!(kf >= -1.0f && kf <= (float)(kFieldMax + 2))) return false;
     float twop = __fmul_rn(2.0f, p);
     if (__fmaf_rn(-(2.0f * kf + 1.0f), sigma, twop) >= 0.0f) kf += 1.0f;

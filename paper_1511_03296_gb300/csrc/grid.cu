@@ -7,8 +7,8 @@
 // (row / sigma_xy, col / sigma_xy) equal (ky, kx) -- form a small rectangle,
 // and their vertices are contiguous in the canonical order.  One CTA takes a
 // run of consecutive cells of one cell row (a "grid tile"), quantises its
-// pixels, sorts (cell, colour, pixel) items in shared memory and
-// de-duplicates them.  A scan over tiles gives every tile its first vertex
+// pixels, radix-sorts them in shared memory by a dense (cell, colour) key
+// (stable, so equal keys keep pixel order) and de-duplicates them.  A scan over tiles gives every tile its first vertex
 // id.  No global hash table and no global sort are needed; every pixel is
 // read once per pass with coalesced row segments.
 #include "fbs_internal.cuh"
@@ -17,33 +17,8 @@ namespace fbs {
 
 namespace {
 
-constexpr uint64_t kPad = ~0ull;
-constexpr int kPixBits = 14;                       // pixel index inside a tile
-constexpr uint64_t kPixMask = (1ull << kPixBits) - 1;
-constexpr int kColourShift = kPixBits;             // 36 colour bits above it
-constexpr int kCellShift = kPixBits + 36;          // cell index inside the tile
 
 // -------------------------------------------------------------- sorting ---
-// Bitonic sort of n (power of two) keys in shared memory, ascending.
-__device__ void bitonic_sort(uint64_t* s, int n)
-{
-    for (int k = 2; k <= n; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int p = threadIdx.x; p < (n >> 1); p += blockDim.x) {
-                int i = ((p & ~(j - 1)) << 1) | (p & (j - 1));
-                int l = i + j;
-                uint64_t a = s[i], b = s[l];
-                bool asc = (i & k) == 0;
-                if ((a > b) == asc) {
-                    s[i] = b;
-                    s[l] = a;
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
 // Exclusive block scan of one int per thread; *total receives the block sum.
 __device__ int block_exclusive_scan(int v, int* warp_buf, int* total)
 {
@@ -72,44 +47,183 @@ __device__ int block_exclusive_scan(int v, int* warp_buf, int* total)
     return prefix;
 }
 
-// Quantise the pixels of one tile into sortable items:
-//   cell index in tile << 50 | (l << 24 | u << 12 | v) << 14 | pixel index in tile.
-// Pads [P, P2) with kPad.
-__device__ void load_tile_items(const GTile& t, const ImgDev& im, uint64_t* items, int P, int P2,
-                                uint32_t* err)
+// ---------------------------------------------------------- radix sort ---
+// Stable LSD radix sort of a tile's pixels, 4 bits per pass, on a dense key
+// made of only the bits that vary inside the tile: the cell index and each
+// colour field minus its tile minimum, in the significance order of the
+// packed vertex key (cell, l, u, v).  The pixels start in pixel order and
+// the sort is stable, so equal keys keep their pixel order.  Pixel indices
+// (16-bit) are moved, not the keys.
+struct DenseKey {
+    int wl, wu, wv;          // bit widths of the l, u, v offsets
+    int minl, minu, minv;
+};
+
+__device__ __forceinline__ int bit_width(uint32_t x) { return x ? 32 - __clz(x) : 0; }
+
+// 16 counters of 16 bits packed in four 64-bit words
+__device__ __forceinline__ void packed_add(uint64_t (&c)[4], int d, uint64_t v)
 {
-    const int tw = t.x1 - t.x0;
-    const int64_t plane = (int64_t)im.H * im.W;
-    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
-        uint64_t item = kPad;
-        if (i < P) {
-            int r = i / tw, cl = i - r * tw;
-            int y = t.y0 + r, x = t.x0 + cl;
-            int64_t pix = (int64_t)y * im.W + x;
-            float L = __ldg(im.yuv + pix), U = __ldg(im.yuv + plane + pix),
-                  Vv = __ldg(im.yuv + 2 * plane + pix);
-            int kx = 0, ky = 0, kl = 0, ku = 0, kv = 0;
-            bool okg = quantise_exact((float)x, im.sxy, kx) & quantise_exact((float)y, im.sxy, ky);
-            bool okc = quantise_exact(L, im.sl, kl) & quantise_exact(U, im.suv, ku) &
-                       quantise_exact(Vv, im.suv, kv);
-            if (!okc) {
-                atomicOr(err, kErrRange);
-                kl = ku = kv = 0;
-            }
-            if (!okg || ky != t.ky || kx < t.kx0 || kx >= t.kx0 + t.nkx) {
-                atomicOr(err, kErrGeometry);
-                kx = t.kx0;
-            }
-            uint64_t colour = ((uint64_t)kl << 24) | ((uint64_t)ku << 12) | (uint64_t)kv;
-            item = ((uint64_t)(kx - t.kx0) << kCellShift) | (colour << kColourShift) | (uint64_t)i;
+    const uint64_t inc = v << (16 * (d & 3));
+    const int q = d >> 2;
+    c[0] += q == 0 ? inc : 0ull;
+    c[1] += q == 1 ? inc : 0ull;
+    c[2] += q == 2 ? inc : 0ull;
+    c[3] += q == 3 ? inc : 0ull;
+}
+
+__device__ __forceinline__ uint32_t packed_get(const uint64_t (&c)[4], int d)
+{
+    const int q = d >> 2;
+    const uint64_t w = q == 0 ? c[0] : q == 1 ? c[1] : q == 2 ? c[2] : c[3];
+    return (uint32_t)(w >> (16 * (d & 3))) & 0xffffu;
+}
+
+// Exclusive block scan of four packed words per thread (fields never carry:
+// every count stays below 2^16); tot receives the block totals.
+__device__ void block_scan_packed(const uint64_t (&x)[4], uint64_t (*wbuf)[4],
+                                  uint64_t (&ex)[4], uint64_t (&tot)[4])
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t in[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        in[k] = x[k];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, in[k], off);
+            if (lane >= off) in[k] += y;
         }
-        items[i] = item;
+        if (lane == 31) wbuf[w][k] = in[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint64_t t = lane < nw ? wbuf[lane][k] : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, t, off);
+                if (lane >= off) t += y;
+            }
+            wbuf[lane][k] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        ex[k] = (w > 0 ? wbuf[w - 1][k] : 0ull) + in[k] - x[k];
+        tot[k] = wbuf[nw - 1][k];
+    }
+    __syncthreads();
+}
+
+// Sorts ord[0..P) (pixel indices, initially 0..P-1) by key[ord[.]]; tmp is
+// scratch of P entries.  Each thread takes a contiguous run of positions.
+__device__ void radix_sort_tile(const uint64_t* key, uint16_t* ord, uint16_t* tmp, int P,
+                                int nbits, uint64_t (*wbuf)[4], uint32_t* base)
+{
+    const int E = (P + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int p0 = (int)threadIdx.x * E, p1 = min(p0 + E, P);
+    uint16_t* a = ord;
+    uint16_t* b = tmp;
+    for (int sh = 0; sh < nbits; sh += 4) {
+        uint64_t c[4] = {0ull, 0ull, 0ull, 0ull};
+        for (int p = p0; p < p1; ++p) packed_add(c, (int)(key[a[p]] >> sh) & 15, 1ull);
+        uint64_t ex[4], tot[4];
+        block_scan_packed(c, wbuf, ex, tot);
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (int d = 0; d < 16; ++d) {
+                base[d] = acc;
+                acc += packed_get(tot, d);
+            }
+        }
+        __syncthreads();
+        for (int p = p0; p < p1; ++p) {
+            const uint16_t j = a[p];
+            const int d = (int)(key[j] >> sh) & 15;
+            b[base[d] + packed_get(ex, d)] = j;
+            packed_add(ex, d, 1ull);
+        }
+        __syncthreads();
+        uint16_t* t = a;
+        a = b;
+        b = t;
+    }
+    if (a != ord) {
+        for (int p = threadIdx.x; p < P; p += blockDim.x) ord[p] = a[p];
+        __syncthreads();
     }
 }
 
-__device__ __forceinline__ bool is_head(const uint64_t* items, int i)
+// x / d for 0 <= x, d <= 2^14, from m = floor(2^32 / d) + 1 (exact in that range)
+__device__ __forceinline__ int div_small(int x, uint32_t m) { return (int)__umulhi((uint32_t)x, m); }
+
+// Quantise the pixels of one tile: key[i] = cell index in tile << 36 |
+// l << 24 | u << 12 | v for tile pixel i (row-major in the tile rectangle);
+// also the block minima and maxima of l, u, v into mm[0..5].
+__device__ void quantise_tile(const GTile& t, const ImgDev& im, uint64_t* key, int P,
+                              uint32_t* err, int* mm)
 {
-    return i == 0 || (items[i] >> kColourShift) != (items[i - 1] >> kColourShift);
+    const int tw = t.x1 - t.x0;
+    const int64_t plane = (int64_t)im.H * im.W;
+    int lo[3] = {4096, 4096, 4096}, hi[3] = {-1, -1, -1};
+    // pixel i = r tw + cl, advanced by blockDim.x without division
+    const int step = (int)blockDim.x;
+    const int dq = step / tw, dr = step - dq * tw;
+    int r = (int)threadIdx.x / tw, cl = (int)threadIdx.x - r * tw;
+    for (int i = threadIdx.x; i < P; i += step) {
+        const int y = t.y0 + r, x = t.x0 + cl;
+        const int64_t pix = (int64_t)y * im.W + x;
+        const float L = __ldg(im.yuv + pix), U = __ldg(im.yuv + plane + pix),
+                    Vv = __ldg(im.yuv + 2 * plane + pix);
+        int kx = 0, ky = 0, kl = 0, ku = 0, kv = 0;
+        const bool okg = quantise_exact((float)x, im.sxy, im.isxy, kx) &
+                         quantise_exact((float)y, im.sxy, im.isxy, ky);
+        const bool okc = quantise_exact(L, im.sl, im.isl, kl) &
+                         quantise_exact(U, im.suv, im.isuv, ku) &
+                         quantise_exact(Vv, im.suv, im.isuv, kv);
+        if (!okc) {
+            atomicOr(err, kErrRange);
+            kl = ku = kv = 0;
+        }
+        if (!okg || ky != t.ky || kx < t.kx0 || kx >= t.kx0 + t.nkx) {
+            atomicOr(err, kErrGeometry);
+            kx = t.kx0;
+        }
+        lo[0] = min(lo[0], kl); hi[0] = max(hi[0], kl);
+        lo[1] = min(lo[1], ku); hi[1] = max(hi[1], ku);
+        lo[2] = min(lo[2], kv); hi[2] = max(hi[2], kv);
+        key[i] = ((uint64_t)(kx - t.kx0) << 36) | ((uint64_t)kl << 24) | ((uint64_t)ku << 12) |
+                 (uint64_t)kv;
+        cl += dr;
+        r += dq;
+        if (cl >= tw) {
+            cl -= tw;
+            ++r;
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            lo[f] = min(lo[f], __shfl_xor_sync(0xffffffffu, lo[f], off));
+            hi[f] = max(hi[f], __shfl_xor_sync(0xffffffffu, hi[f], off));
+        }
+    }
+    if (threadIdx.x == 0)
+        for (int f = 0; f < 3; ++f) {
+            mm[f] = 4096;
+            mm[3 + f] = -1;
+        }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+        for (int f = 0; f < 3; ++f) {
+            atomicMin(&mm[f], lo[f]);
+            atomicMax(&mm[3 + f], hi[f]);
+        }
+    __syncthreads();
 }
 
 // ------------------------------------------------------------- kernels ---
@@ -120,7 +234,11 @@ __device__ __forceinline__ bool is_head(const uint64_t* items, int i)
 //   tkey/tm/tps[sort_off + r] = key, count and first sorted slot of local vertex r
 //   cell_voff[cell]      = tile-local first vertex of the cell, cell_nv = its count
 //   tile_nv[tile]        = number of distinct keys in the tile
-__global__ void __launch_bounds__(kGridThreads)
+// CTA size of the tile sort (measured: 256 beats 128 and 512 -- fewer warps
+// per barrier than 512, enough threads per tile for the passes)
+constexpr int kSortThreads = 256;
+
+__global__ void __launch_bounds__(kSortThreads, 6)
 grid_sort_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ imgs,
                  int* __restrict__ tile_nv, uint32_t* err, int P2, int max_cells,
                  uint32_t* __restrict__ vid, uint32_t* __restrict__ perm,
@@ -129,57 +247,84 @@ grid_sort_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ img
                  uint32_t* __restrict__ cell_nv)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t* items = reinterpret_cast<uint64_t*>(smem_raw);
-    int* headpos = reinterpret_cast<int*>(items + P2);
-    int* cellcnt = headpos + P2;
+    uint64_t* key = reinterpret_cast<uint64_t*>(smem_raw);
+    uint16_t* ord = reinterpret_cast<uint16_t*>(key + P2);     // sorted position -> pixel
+    uint16_t* tmp = ord + P2;                                   // radix scratch, then head positions
+    int* cellcnt = reinterpret_cast<int*>(tmp + P2);
     __shared__ int warp_buf[32];
+    __shared__ uint64_t wbuf[32][4];
+    __shared__ uint32_t base[16];
+    __shared__ int mm[6];
 
     const GTile t = tiles[blockIdx.x];
     const ImgDev im = imgs[t.img];
     const int tw = t.x1 - t.x0;
     const int P = (t.y1 - t.y0) * tw;
+    const uint32_t mtw = (uint32_t)((1ull << 32) / (uint64_t)tw + 1);
 
     for (int c = threadIdx.x; c < t.nkx && c < max_cells; c += blockDim.x) cellcnt[c] = 0;
-    load_tile_items(t, im, items, P, P2, err);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) ord[i] = (uint16_t)i;
+    quantise_tile(t, im, key, P, err, mm);      // ends with a barrier
+
+    // dense keys in place (each thread rewrites the keys it wrote)
+    DenseKey dk;
+    dk.minl = mm[0];
+    dk.minu = mm[1];
+    dk.minv = mm[2];
+    dk.wl = bit_width((uint32_t)max(mm[3] - mm[0], 0));
+    dk.wu = bit_width((uint32_t)max(mm[4] - mm[1], 0));
+    dk.wv = bit_width((uint32_t)max(mm[5] - mm[2], 0));
+    const int wuv = dk.wu + dk.wv, wluv = dk.wl + wuv;
+    const int nbits = bit_width((uint32_t)max(t.nkx - 1, 0)) + wluv;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const uint64_t it = key[i];
+        const uint64_t cell = it >> 36;
+        const uint64_t l = ((it >> 24) & 0xfff) - dk.minl, u = ((it >> 12) & 0xfff) - dk.minu,
+                       v = (it & 0xfff) - dk.minv;
+        key[i] = (cell << wluv) | (l << wuv) | (u << dk.wv) | v;
+    }
     __syncthreads();
-    bitonic_sort(items, P2);
+    radix_sort_tile(key, ord, tmp, P, nbits, wbuf, base);
+    uint16_t* headpos = tmp;
 
     // each thread owns a contiguous chunk of the sorted items
-    const int E = P2 / blockDim.x;
-    const int i0 = threadIdx.x * E;
+    const int E = (P + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int i0 = threadIdx.x * E, i1 = min(i0 + E, P);
     int cnt = 0;
-    for (int i = i0; i < i0 + E && i < P; ++i) cnt += is_head(items, i) ? 1 : 0;
+    for (int i = i0; i < i1; ++i) cnt += (i == 0 || key[ord[i]] != key[ord[i - 1]]) ? 1 : 0;
     int nv;
     int run = block_exclusive_scan(cnt, warp_buf, &nv);
-    for (int i = i0; i < i0 + E && i < P; ++i) {
-        const uint64_t it = items[i];
-        const bool head = is_head(items, i);
+    const uint64_t mwl = (1ull << dk.wl) - 1, mwu = (1ull << dk.wu) - 1, mwv = (1ull << dk.wv) - 1;
+    for (int i = i0; i < i1; ++i) {
+        const int pl = ord[i];
+        const uint64_t k = key[pl];
+        const bool head = i == 0 || k != key[ord[i - 1]];
         if (head) ++run;
         const int rank = run - 1;
-        const int pl = (int)(it & kPixMask);
-        const int r = pl / tw;
+        const int r = div_small(pl, mtw);
         const int64_t gpix = im.pix_base + (int64_t)(t.y0 + r) * im.W + (t.x0 + pl - r * tw);
         vid[gpix] = (uint32_t)rank;
         perm[t.sort_off + i] = (uint32_t)gpix;
         if (head) {
-            const int cell = (int)(it >> kCellShift);
-            const uint64_t colour = (it >> kColourShift) & ((1ull << 36) - 1);
-            tkey[t.sort_off + rank] =
-                ((uint64_t)t.ky << 48) | ((uint64_t)(t.kx0 + cell) << 36) | colour;
+            const int cell = (int)(k >> wluv);
+            const uint64_t l = ((k >> wuv) & mwl) + dk.minl, u = ((k >> dk.wv) & mwu) + dk.minu,
+                           v = (k & mwv) + dk.minv;
+            tkey[t.sort_off + rank] = ((uint64_t)t.ky << 48) | ((uint64_t)(t.kx0 + cell) << 36) |
+                                      (l << 24) | (u << 12) | v;
             tps[t.sort_off + rank] = (uint32_t)(t.sort_off + i);
-            headpos[rank] = i;
+            headpos[rank] = (uint16_t)i;
             atomicAdd(&cellcnt[cell], 1);
         }
     }
     __syncthreads();
     for (int r = threadIdx.x; r < nv; r += blockDim.x)
-        tm[t.sort_off + r] = (uint32_t)((r + 1 < nv ? headpos[r + 1] : P) - headpos[r]);
+        tm[t.sort_off + r] = (uint32_t)((r + 1 < nv ? (int)headpos[r + 1] : P) - (int)headpos[r]);
     if (threadIdx.x == 0) tile_nv[blockIdx.x] = nv;
     // per-cell vertex ranges, tile-local (cells of a tile are consecutive in key order)
     const int64_t cell0 = im.cell_base + (int64_t)t.ky * im.ncx + t.kx0;
     int carry = 0;
-    for (int base = 0; base < t.nkx; base += blockDim.x) {
-        int c = base + threadIdx.x;
+    for (int base_c = 0; base_c < t.nkx; base_c += blockDim.x) {
+        int c = base_c + threadIdx.x;
         int v = c < t.nkx ? cellcnt[c] : 0;
         int tot;
         int ex = block_exclusive_scan(v, warp_buf, &tot);
@@ -325,7 +470,7 @@ bistoch_kernel(const double* __restrict__ nold, double* __restrict__ nnew,
 // ------------------------------------------------------ host launchers ---
 size_t grid_smem_sort(int P2, int max_cells)
 {
-    return (size_t)P2 * (sizeof(uint64_t) + sizeof(int)) + (size_t)max_cells * sizeof(int);
+    return (size_t)P2 * (sizeof(uint64_t) + 2 * sizeof(uint16_t)) + (size_t)max_cells * sizeof(int);
 }
 
 cudaError_t launch_grid_sort(const GTile* tiles, int ntiles, const ImgDev* imgs, int* tile_nv,
@@ -339,7 +484,7 @@ cudaError_t launch_grid_sort(const GTile* tiles, int ntiles, const ImgDev* imgs,
     if (e != cudaSuccess) return e;
     static int fam = prof_family("grid_sort");
     prof_begin(fam, s);
-    grid_sort_kernel<<<ntiles, kGridThreads, smem, s>>>(tiles, imgs, tile_nv, err, P2, max_cells,
+    grid_sort_kernel<<<ntiles, kSortThreads, smem, s>>>(tiles, imgs, tile_nv, err, P2, max_cells,
                                                         vid, perm, tkey, tm, tps, cell_voff,
                                                         cell_nv);
     prof_end(fam, s);
