@@ -9,9 +9,9 @@ the paper's equations and algorithms); this module only marshals numpy
 arrays through ctypes and compiles the C file on first use.
 
 Parity status per function (what pins each one is in ``tests/test_oracle_pins.py``):
-  keys, grid, bistochastize, splat, diag, apply_A, flat_init, pcg, slice,
-  solve, solve_robust, backward -- all pinned (closed forms, brute force,
-  dense linear algebra, invariants, finite differences).
+  keys, grid, bistochastize, splat, diag, apply_A, flat_init, pcg,
+  pcg_single, slice, solve, solve_robust, backward -- all pinned (closed
+  forms, brute force, dense linear algebra, invariants, finite differences).
 """
 from __future__ import annotations
 
@@ -28,6 +28,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fbs_oracle.c")
 _SO = os.path.join(_HERE, "_build", "libfbs_oracle.so")
 _lock = threading.Lock()
+_form_lock = threading.Lock()
 _lib = None
 
 _P = ctypes.c_void_p
@@ -69,6 +70,10 @@ def lib():
             L.fbso_flat_init.restype = None
             L.fbso_pcg.argtypes = [_I64, _P, _P, _P, _P, _D, _P, _P, _I]
             L.fbso_pcg.restype = _I
+            L.fbso_pcg_single.argtypes = [_I64, _P, _P, _P, _P, _D, _P, _P, _I]
+            L.fbso_pcg_single.restype = _I
+            L.fbso_set_pcg_form.argtypes = [_I]
+            L.fbso_set_pcg_form.restype = None
             L.fbso_slice.argtypes = [_I64, _I64, _I, _P, _P, _P]
             L.fbso_slice.restype = None
             L.fbso_solve.argtypes = [_I64, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P]
@@ -178,6 +183,38 @@ def pcg(nbr, n, a, minv, lam, b, y0, iters):
     _check(lib().fbso_pcg(b.size, _ptr(nbr), _ptr(n), _ptr(a), _ptr(minv), float(lam), _ptr(b),
                           _ptr(y), int(iters)))
     return y
+
+
+def pcg_single(nbr, n, a, minv, lam, b, y0, iters):
+    """The single-reduction form of the same PCG (one global reduction per
+    iteration); equal iterates to ``pcg`` in exact arithmetic."""
+    nbr = _c(nbr, np.int32); n = _c(n, np.float64); a = _c(a, np.float64)
+    minv = _c(minv, np.float64); b = _c(b, np.float64)
+    y = np.array(y0, dtype=np.float64, copy=True, order="C")
+    _check(lib().fbso_pcg_single(b.size, _ptr(nbr), _ptr(n), _ptr(a), _ptr(minv), float(lam),
+                                 _ptr(b), _ptr(y), int(iters)))
+    return y
+
+
+PCG_FORMS = {"standard": 0, "single": 1}
+
+
+class pcg_form:
+    """``with oracle.pcg_form("single"): ...`` -- the solves inside use the
+    single-reduction PCG; the standard form is restored afterwards."""
+
+    def __init__(self, form: str):
+        self.form = PCG_FORMS[form]
+
+    def __enter__(self):
+        L = lib()
+        _form_lock.acquire()
+        L.fbso_set_pcg_form(self.form)
+        return self
+
+    def __exit__(self, *exc):
+        lib().fbso_set_pcg_form(0)
+        _form_lock.release()
 
 
 def slice_(vid, y):

@@ -271,6 +271,77 @@ int fbso_pcg(int64_t V, const int32_t* nbr, const double* n, const double* a,
 }
 
 /* slice (Eq. (8)): x = S^T y */
+/* Single-reduction form of the same PCG (Chronopoulos and Gear, 1989): the
+ * iterates equal those of Alg. 2 in exact arithmetic, but both inner
+ * products of an iteration are taken at one point, so a parallel
+ * implementation needs one global reduction per iteration instead of two.
+ * With u = M^-1 r and w = A u kept alongside r, and the search direction p
+ * and s = A p updated by recurrences:
+ *   gamma = r^T u (Alg. 2's delta),  mu = w^T u,
+ *   beta_i = gamma_i / gamma_(i-1),  alpha_i = gamma_i / (mu_i - beta_i gamma_i / alpha_(i-1)),
+ *   p <- u + beta p,  s <- w + beta s,  y <- y + alpha p,  r <- r - alpha s,
+ *   u <- M^-1 r,  w <- A u.
+ * The denominator mu_i - beta_i gamma_i / alpha_(i-1) is p_i^T A p_i.  Guards
+ * matching Alg. 2's: beta = 0 when gamma_(i-1) = 0; the correction term is
+ * dropped when beta = 0 or alpha_(i-1) = 0; alpha = 0 when gamma = 0 or the
+ * denominator is not positive. */
+int fbso_pcg_single(int64_t V, const int32_t* nbr, const double* n, const double* a,
+                    const double* minv, double lam, const double* b, double* y, int iters)
+{
+    size_t sz = (size_t)(V > 0 ? V : 1) * sizeof(double);
+    double* r = (double*)malloc(sz);
+    double* u = (double*)malloc(sz);
+    double* w = (double*)malloc(sz);
+    double* p = (double*)malloc(sz);
+    double* s = (double*)malloc(sz);
+    if (!r || !u || !w || !p || !s) {
+        free(r); free(u); free(w); free(p); free(s);
+        return FBSO_ERR_OOM;
+    }
+    fbso_apply_A(V, nbr, n, a, lam, y, w);
+    for (int64_t v = 0; v < V; ++v) r[v] = b[v] - w[v];
+    for (int64_t v = 0; v < V; ++v) u[v] = minv[v] * r[v];
+    fbso_apply_A(V, nbr, n, a, lam, u, w);
+    double gamma = dot(V, r, u), mu = dot(V, w, u);
+    double gamma_old = 0.0, alpha_old = 0.0;
+    for (int i = 0; i < iters; ++i) {
+        double beta = 0.0, den = mu;
+        if (i > 0) {
+            beta = gamma_old != 0.0 ? gamma / gamma_old : 0.0;
+            if (beta != 0.0 && alpha_old != 0.0) den = mu - beta * gamma / alpha_old;
+        }
+        double alpha = (gamma != 0.0 && den > 0.0) ? gamma / den : 0.0;
+        for (int64_t v = 0; v < V; ++v) {
+            p[v] = (i > 0 ? u[v] + beta * p[v] : u[v]);
+            s[v] = (i > 0 ? w[v] + beta * s[v] : w[v]);
+            y[v] += alpha * p[v];
+            r[v] -= alpha * s[v];
+            u[v] = minv[v] * r[v];
+        }
+        fbso_apply_A(V, nbr, n, a, lam, u, w);
+        gamma_old = gamma;
+        alpha_old = alpha;
+        gamma = dot(V, r, u);
+        mu = dot(V, w, u);
+    }
+    free(r); free(u); free(w); free(p); free(s);
+    return FBSO_OK;
+}
+
+/* Which form the solves below use: 0 = Alg. 2 as printed (fbso_pcg),
+ * 1 = the single-reduction form (fbso_pcg_single).  Process-wide; the test
+ * suite sets it around the calls that need it. */
+static int g_pcg_form = 0;
+
+void fbso_set_pcg_form(int form) { g_pcg_form = form; }
+
+static int pcg_run(int64_t V, const int32_t* nbr, const double* n, const double* a,
+                   const double* minv, double lam, const double* b, double* y, int iters)
+{
+    return g_pcg_form == 1 ? fbso_pcg_single(V, nbr, n, a, minv, lam, b, y, iters)
+                           : fbso_pcg(V, nbr, n, a, minv, lam, b, y, iters);
+}
+
 void fbso_slice(int64_t N, int64_t V, int C, const uint32_t* vid, const double* y, double* x)
 {
     for (int ch = 0; ch < C; ++ch)
@@ -295,7 +366,7 @@ static int solve_impl(int64_t N, int64_t V, int C, const uint32_t* vid, const ui
     int st = FBSO_OK;
     for (int ch = 0; ch < C && !st; ++ch) {
         fbso_flat_init(V, b + (int64_t)ch * V, sc, y + (int64_t)ch * V);
-        st = fbso_pcg(V, nbr, n, a, minv, lam, b + (int64_t)ch * V, y + (int64_t)ch * V, pcg_iters);
+        st = pcg_run(V, nbr, n, a, minv, lam, b + (int64_t)ch * V, y + (int64_t)ch * V, pcg_iters);
     }
     if (!st && x) fbso_slice(N, V, C, vid, y, x);
     free(b); free(sc); free(a); free(minv);
@@ -370,7 +441,7 @@ int fbso_backward(int64_t N, int64_t V, int C, const uint32_t* vid, const uint32
     int st = FBSO_OK;
     for (int ch = 0; ch < C && !st; ++ch) {
         fbso_flat_init(V, g + (int64_t)ch * V, sc, z + (int64_t)ch * V);
-        st = fbso_pcg(V, nbr, n, a, minv, lam, g + (int64_t)ch * V, z + (int64_t)ch * V, pcg_iters);
+        st = pcg_run(V, nbr, n, a, minv, lam, g + (int64_t)ch * V, z + (int64_t)ch * V, pcg_iters);
     }
     if (!st) {
         for (int64_t i = 0; i < N; ++i) dc[i] = 0.0;

@@ -412,3 +412,43 @@ def test_backward_matches_finite_differences():
         cm[i] -= h
         fd = (loss(t64, cp)[0] - loss(t64, cm)[0]) / (2 * h)
         assert np.isclose(dc[i], fd, rtol=1e-5, atol=1e-12), (i, dc[i], fd)
+
+
+# ---- single-reduction PCG (Chronopoulos-Gear form of the same iteration) ----
+
+def test_pcg_single_equals_standard_iterates():
+    # the two forms produce the same iterates in exact arithmetic; compare
+    # every iteration count against the pinned standard form
+    inst, g, S, B, A, b, sc = _problem(iters=2, lam=16.0, C=1)
+    a, minv = oracle.diag(g.m, g.nbr, g.n, sc, inst.lam)
+    y0 = oracle.flat_init(b[0], sc)
+    for k in range(0, 16):
+        ys = oracle.pcg(g.nbr, g.n, a, minv, inst.lam, b[0], y0, k)
+        y1 = oracle.pcg_single(g.nbr, g.n, a, minv, inst.lam, b[0], y0, k)
+        assert np.allclose(y1, ys, rtol=1e-9, atol=1e-9 * np.abs(ys).max()), k
+
+
+def test_pcg_single_converged_matches_dense_solve():
+    inst, g, S, B, A, b, sc = _problem(iters=2, lam=16.0)
+    with oracle.pcg_form("single"):
+        y, _ = oracle.solve(g, inst.t, inst.c, inst.lam, 600)
+    ystar = np.linalg.solve(A, b.T).T
+    assert np.allclose(y, ystar, rtol=1e-9, atol=1e-9 * np.abs(ystar).max())
+
+
+def test_pcg_single_zero_right_hand_side_stays_zero():
+    inst, g, S, B, A, b, sc = _problem(iters=2, lam=16.0, C=1)
+    a, minv = oracle.diag(g.m, g.nbr, g.n, sc, inst.lam)
+    z = np.zeros_like(b[0])
+    y = oracle.pcg_single(g.nbr, g.n, a, minv, inst.lam, z, z, 25)
+    assert np.all(y == 0.0)
+
+
+def test_pcg_form_context_restores_standard():
+    inst, g, S, B, A, b, sc = _problem(iters=2, lam=16.0, C=1)
+    y_std, _ = oracle.solve(g, inst.t, inst.c, inst.lam, 5)
+    with oracle.pcg_form("single"):
+        y_one, _ = oracle.solve(g, inst.t, inst.c, inst.lam, 5)
+    y_again, _ = oracle.solve(g, inst.t, inst.c, inst.lam, 5)
+    assert np.array_equal(y_std, y_again)
+    assert np.allclose(y_one, y_std, rtol=1e-9, atol=1e-9 * np.abs(y_std).max())
