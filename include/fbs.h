@@ -167,14 +167,27 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *                            is being captured.
  *   FBS_PCG_PER_PHASE        two launches per iteration (replayed from a CUDA
  *                            graph when the same solve repeats).
+ * FBS_OPT_PCG_FORM: which form of the Jacobi PCG (supplement Alg. 2) runs:
+ *   FBS_PCG_FORM_STANDARD    (default) Alg. 2 as printed: two phases, two
+ *                            global reductions per iteration.
+ *   FBS_PCG_FORM_SINGLE      the single-reduction (Chronopoulos-Gear) form,
+ *                            with the same iterates in exact arithmetic: u =
+ *                            M^-1 r, w = A u and s = A p are carried along and
+ *                            both inner products of an iteration are taken
+ *                            together, so an iteration is one launch.  Used
+ *                            for FP32 vectors when no image has more than 4
+ *                            channels (per-phase launches); other solves keep
+ *                            the standard form.
  * FBS_OPT_INJECT_BARRIER_TIMEOUT: value 1 makes the next persistent PCG
  *   loop start with its barrier counter preset so that no barrier can
  *   complete; every block waits out its bounded spin, latches
  *   FBS_ERR_TIMEOUT and returns (a test of the failure path; one-shot).
  */
-enum { FBS_OPT_VECTOR_PRECISION = 1, FBS_OPT_PCG_LAUNCH = 2, FBS_OPT_INJECT_BARRIER_TIMEOUT = 3 };
+enum { FBS_OPT_VECTOR_PRECISION = 1, FBS_OPT_PCG_LAUNCH = 2, FBS_OPT_INJECT_BARRIER_TIMEOUT = 3,
+       FBS_OPT_PCG_FORM = 4 };
 enum { FBS_VECTORS_AUTO = 0, FBS_VECTORS_FP32 = 1, FBS_VECTORS_COMPENSATED = 2 };
 enum { FBS_PCG_AUTO = 0, FBS_PCG_PERSISTENT = 1, FBS_PCG_PER_PHASE = 2 };
+enum { FBS_PCG_FORM_STANDARD = 0, FBS_PCG_FORM_SINGLE = 1 };
 fbs_status fbs_set_option(fbs_grid* g, int option, int value);
 
 /*

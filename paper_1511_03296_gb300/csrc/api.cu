@@ -249,10 +249,11 @@ struct fbs_grid {
     int bistoch_iters = 0;
     // solve workspace
     size_t cap_vec = 0;                 // floats per vector
-    float* vec = nullptr;               // 6 x cap_vec: y, r, r_lo, d0, d1, q
+    float* vec = nullptr;               // 8 x cap_vec: y, r, r_lo, d0, d1, q, s0, s1
     int precision = FBS_VECTORS_AUTO;
     int persistent = 1;
     int force_persistent = 0;
+    int pcg_form = FBS_PCG_FORM_STANDARD;
     int inject_timeout = 0;
     float* a = nullptr;
     float2* nm = nullptr;
@@ -677,7 +678,10 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     else plan.comp = plan.mode == kSplatBackward ? 1 : 0;
     // the whole PCG loop as one cooperative launch, except inside a caller's
     // stream capture (per-phase launches are captured instead)
-    plan.persistent = g->persistent && !capturing(s) ? 1 : 0;
+    // the single-reduction form for FP32 vectors and images of at most 4
+    // channels; it runs as per-phase launches
+    plan.single = g->pcg_form == FBS_PCG_FORM_SINGLE && !plan.comp && cmax <= 4 ? 1 : 0;
+    plan.persistent = g->persistent && !capturing(s) && !plan.single ? 1 : 0;
     plan.force_persistent = g->force_persistent;
     plan.inject_timeout = plan.persistent ? g->inject_timeout : 0;
     if (plan.persistent) g->inject_timeout = 0;
@@ -693,11 +697,11 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
         g->cap_vec = (size_t)std::max<int64_t>(cv, 32);
         g->cap_scal = (size_t)std::max(pc, 1);
         g->cap_part = (size_t)std::max<int64_t>(cpart, 1);
-        if ((e = dalloc(&g->vec, 6 * g->cap_vec, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = dalloc(&g->vec, 8 * g->cap_vec, s)) != cudaSuccess) return cuda_status(e);
         if ((e = dalloc(&g->a, g->Vtot, s)) != cudaSuccess) return cuda_status(e);
         if ((e = dalloc(&g->nm, g->Vtot, s)) != cudaSuccess) return cuda_status(e);
         if ((e = dalloc(&g->scal, g->cap_scal, s)) != cudaSuccess) return cuda_status(e);
-        if ((e = dalloc(&g->part, 3 * g->cap_part, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = dalloc(&g->part, 4 * g->cap_part, s)) != cudaSuccess) return cuda_status(e);
         if (!g->barrier && (e = dalloc(&g->barrier, kBarrierWords, s)) != cudaSuccess)
             return cuda_status(e);
         if ((e = dalloc(&g->inst, (size_t)g->n_images, s)) != cudaSuccess) return cuda_status(e);
@@ -729,11 +733,15 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.d[0] = g->vec + 3 * g->cap_vec;
     A.d[1] = g->vec + 4 * g->cap_vec;
     A.q = g->vec + 5 * g->cap_vec;
+    A.aux[0] = g->vec + 6 * g->cap_vec;
+    A.aux[1] = g->vec + 7 * g->cap_vec;
     A.scal = g->scal;
     plan.barrier = g->barrier;
     A.part_rs[0] = g->part;
     A.part_rs[1] = g->part + g->cap_part;
     A.part_dq = g->part + 2 * g->cap_part;
+    A.part_mu[0] = A.part_dq;
+    A.part_mu[1] = g->part + 3 * g->cap_part;
     A.err = g->err;
     // AUTO: the resident loop for small batches; per-phase (graph) otherwise
     if (plan.persistent && !plan.force_persistent && !resident_preferred(A, plan))
@@ -834,6 +842,11 @@ fbs_status fbs_set_option(fbs_grid* g, int option, int value)
     if (option == FBS_OPT_INJECT_BARRIER_TIMEOUT) {
         if (value != 0 && value != 1) return FBS_ERR_ARG;
         g->inject_timeout = value;
+        return FBS_OK;
+    }
+    if (option == FBS_OPT_PCG_FORM) {
+        if (value != FBS_PCG_FORM_STANDARD && value != FBS_PCG_FORM_SINGLE) return FBS_ERR_ARG;
+        g->pcg_form = value;
         return FBS_OK;
     }
     if (option == FBS_OPT_PCG_LAUNCH) {

@@ -93,6 +93,7 @@ __host__ __device__ inline int padded_channels(int C) { return C <= 2 ? C : (C +
 // r^T M^-1 r of iteration `it` in slot it % 2
 struct Scal {
     double delta[2];
+    double gam[2], alp[2];  // single-reduction form: gamma_i and alpha_i by iteration parity
 };
 
 // splat modes

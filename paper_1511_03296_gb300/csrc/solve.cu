@@ -87,6 +87,7 @@ __device__ __forceinline__ void stw(float* p, const float (&v)[W])
 struct PhaseSmem {
     DF red[4][kVTile / 32];
     double sd[kMaxChannels];     // reduced inner products
+    double sd2[kMaxChannels];    // second inner product (single-reduction form)
     float sf[kMaxChannels];      // beta (phase 1)
     double sa[kMaxChannels];     // alpha (phase 2)
 };
@@ -324,6 +325,8 @@ __device__ __forceinline__ void splat_finish(const SolveArgs& A, const InstDev& 
         A.d[0][idx] = 0.0f;
         A.d[1][idx] = 0.0f;
         A.q[idx] = 0.0f;
+        A.aux[0][idx] = 0.0f;
+        A.aux[1][idx] = 0.0f;
     }
     vertex_epilogue(A, I, v, cnt, sc);
 }
@@ -1015,6 +1018,242 @@ pcg_update_kernel(SolveArgs A, const float* __restrict__ d, int it)
     phase_run<2, COMP, false, WMAX>(A, d, nullptr, it, t0, t1, S, Wd);
 }
 
+// ------------------------------------------ single-reduction PCG form ---
+// The Chronopoulos-Gear form of Alg. 2 (same iterates in exact arithmetic):
+// with u = M^-1 r, w = A u and s = A p carried along, iteration i is
+//   beta = gamma_i / gamma_(i-1),  alpha = gamma_i / (mu_i - beta gamma_i / alpha_(i-1)),
+//   s_i = w_i + beta s_(i-1),  p_i = u_i + beta p_(i-1),  y += alpha p_i,
+//   r_(i+1) = r_i - alpha s_i,  u_(i+1) = M^-1 r_(i+1),  w_(i+1) = A u_(i+1),
+//   gamma_(i+1) = r_(i+1)^T u_(i+1),  mu_(i+1) = w_(i+1)^T u_(i+1),
+// one launch per iteration: each thread forms s_i, r_(i+1), u_(i+1) for its
+// vertex and, from gathered (r_i, w_i, s_(i-1)), for each neighbour, so no
+// second pass is needed; both inner products go to one set of partials.
+// Buffers by iteration parity: r in r / r_lo, w in d[0] / d[1], s in aux[];
+// p (in q) and y are updated in place.  Guards as Alg. 2's: beta = 0 when
+// gamma_(i-1) = 0; the correction term is dropped when beta = 0 or
+// alpha_(i-1) = 0; alpha = 0 when gamma = 0 or the denominator is not
+// positive.  FP32 vectors, images with at most 4 channels.
+__device__ __forceinline__ float* cg_r(const SolveArgs& A, int k) { return k ? A.rlo : A.r; }
+
+// beta (S.sf) and alpha (S.sa) of iteration it for image I, from the
+// partials of gamma_it and mu_it and the stored gamma, alpha of iteration
+// it - 1; stores gamma_it and alpha_it.  Whole block; ends with a barrier.
+template <int W>
+__device__ void cg_scalars(const SolveArgs& A, const InstDev& I, int it, PhaseSmem& S)
+{
+    constexpr int H = W == 1 ? 8 : W == 2 ? 4 : 2;
+    const int slot = it & 1;
+    __syncthreads();
+    reduce_partials_all<W, H>(A.part_rs[slot], I, S.sd, S.red);
+    reduce_partials_all<W, H>(A.part_mu[slot], I, S.sd2, S.red);
+    for (int ch = threadIdx.x; ch < I.Cp; ch += blockDim.x) {
+        if (ch >= I.C) {
+            S.sf[ch] = 0.0f;
+            S.sa[ch] = 0.0;
+            continue;
+        }
+        const double gamma = S.sd[ch], mu = S.sd2[ch];
+        double beta = 0.0, den = mu;
+        if (it > 0) {
+            const double gold = A.scal[I.pc + ch].gam[slot ^ 1];
+            const double aold = A.scal[I.pc + ch].alp[slot ^ 1];
+            beta = gold != 0.0 ? gamma / gold : 0.0;
+            if (beta != 0.0 && aold != 0.0) den = mu - beta * gamma / aold;
+        }
+        const double alpha = (gamma != 0.0 && den > 0.0) ? gamma / den : 0.0;
+        S.sf[ch] = (float)beta;
+        S.sa[ch] = alpha;
+        A.scal[I.pc + ch].gam[slot] = gamma;   // same values from every block
+        A.scal[I.pc + ch].alp[slot] = alpha;
+    }
+    __syncthreads();
+}
+
+// Iteration it on one tile (Cp = W).  last: only p and y are needed.
+template <int W>
+__device__ __forceinline__ void cg_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
+                                        int it, bool last, PhaseSmem& S, DF (&rg)[4],
+                                        DF (&rm)[4], bool fetch)
+{
+    const int v = (int)vt.v0 + (int)threadIdx.x;
+    const bool valid = v < (int)vt.v1;
+    const int vs = valid ? v : (int)vt.v0;
+    const int cur = it & 1, nxt = cur ^ 1;
+    const int64_t off = I.vec_base - I.voff * W;
+    const float* __restrict__ rb = cg_r(A, cur) + off;      // r_i
+    const float* __restrict__ wb = A.d[cur] + off;          // w_i
+    const float* __restrict__ sb = A.aux[nxt] + off;        // s_(i-1)
+    const bool first = it == 0;
+    const float2 nmv = A.nm[vs];
+    const float av = A.a[vs];
+    float rv[W], wv[W], so[W], pv[W], yv[W];
+    ldw<W, false>(rb + vs * W, rv);
+    ldw<W, false>(wb + vs * W, wv);
+    ldw<W, false>(A.y + off + vs * W, yv);
+    if (!first) {
+        ldw<W, false>(sb + vs * W, so);
+        ldw<W, false>(A.q + off + vs * W, pv);
+    }
+    if (fetch) cg_scalars<W>(A, I, it, S);
+    float beta[W], alpha[W], r1[W], u1[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        beta[k] = S.sf[k];
+        alpha[k] = (float)S.sa[k];
+        const float si = first ? wv[k] : fmaf(beta[k], so[k], wv[k]);
+        const float ui = nmv.y * rv[k];
+        pv[k] = first ? ui : fmaf(beta[k], pv[k], ui);
+        yv[k] = fmaf(alpha[k], pv[k], yv[k]);
+        r1[k] = fmaf(-alpha[k], si, rv[k]);
+        u1[k] = nmv.y * r1[k];
+        so[k] = si;
+    }
+    if (valid) {
+        stw<W>(A.y + off + v * W, yv);
+        stw<W>(A.q + off + v * W, pv);
+    }
+    if (last) return;
+    float lap[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) lap[k] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 10; ++j) {
+        const int u0 = A.nbr[(int64_t)j * A.Vtot + vs];
+        const int u = u0 >= 0 ? u0 : vs;        // absent: the vertex itself, term 0
+        const float2 nm = A.nm[u];
+        float ru[W], wu[W], su[W];
+        ldw<W, false>(rb + u * W, ru);
+        ldw<W, false>(wb + u * W, wu);
+        if (!first) ldw<W, false>(sb + u * W, su);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const float s_u = first ? wu[k] : fmaf(beta[k], su[k], wu[k]);
+            const float u_u = nm.y * fmaf(-alpha[k], s_u, ru[k]);
+            lap[k] = fmaf(nm.x, u1[k] - u_u, lap[k]);
+        }
+    }
+    const float lam_n = I.lam * nmv.x;
+    float w1[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        w1[k] = fmaf(av, u1[k], lam_n * lap[k]);
+        if (valid && k < I.C) {
+            rg[k] = df_add(rg[k], df_mul_exact(r1[k], u1[k]));
+            rm[k] = df_add(rm[k], df_mul_exact(w1[k], u1[k]));
+        }
+    }
+    if (valid) {
+        stw<W>(A.aux[cur] + off + v * W, so);
+        stw<W>(cg_r(A, nxt) + off + v * W, r1);
+        stw<W>(A.d[nxt] + off + v * W, w1);
+    }
+}
+
+// Set-up on one tile: w_0 = A M^-1 r_0 into d[0] and the products w_0^T u_0
+// into rm (gamma_0 = r_0^T M^-1 r_0 comes from the initial residual).
+template <int W>
+__device__ __forceinline__ void cg_w0_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
+                                           DF (&rm)[4])
+{
+    const int v = (int)vt.v0 + (int)threadIdx.x;
+    const bool valid = v < (int)vt.v1;
+    const int vs = valid ? v : (int)vt.v0;
+    const int64_t off = I.vec_base - I.voff * W;
+    const float* __restrict__ rb = A.r + off;
+    const float2 nmv = A.nm[vs];
+    const float av = A.a[vs];
+    float rv[W], u0[W], lap[W];
+    ldw<W, false>(rb + vs * W, rv);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        u0[k] = nmv.y * rv[k];
+        lap[k] = 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 10; ++j) {
+        const int u0i = A.nbr[(int64_t)j * A.Vtot + vs];
+        const int u = u0i >= 0 ? u0i : vs;
+        const float2 nm = A.nm[u];
+        float ru[W];
+        ldw<W, false>(rb + u * W, ru);
+#pragma unroll
+        for (int k = 0; k < W; ++k) lap[k] = fmaf(nm.x, u0[k] - nm.y * ru[k], lap[k]);
+    }
+    const float lam_n = I.lam * nmv.x;
+    float w0[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        w0[k] = fmaf(av, u0[k], lam_n * lap[k]);
+        if (valid && k < I.C) rm[k] = df_add(rm[k], df_mul_exact(w0[k], u0[k]));
+    }
+    if (valid) stw<W>(A.d[0] + off + v * W, w0);
+}
+
+// A block's chunk of tiles for one single-reduction iteration (it >= 0) or
+// the set-up (it < 0): per image, the CG scalars at the start and the
+// products accumulated over the block's run of the image's tiles.
+template <int WMAX>
+__device__ void cg_run(const SolveArgs& A, int it, bool last, int t0, int t1, PhaseSmem& S)
+{
+    const int nxt = (it + 1) & 1;              // set-up (it = -1) writes slot 0
+    float2* const out_g = A.part_rs[nxt];
+    float2* const out_m = A.part_mu[nxt];
+    int cur = -1, run_tile = 0, run_C = 0, run_W = 1, run_ntiles = 0;
+    int64_t run_base = 0;
+    bool fetch = false;
+    DF rg[4], rm[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rg[k] = rm[k] = {0.0f, 0.0f};
+    for (int tile = t0; tile < t1; ++tile) {
+        const VTile vt = A.vt[tile];
+        const InstDev I = A.inst[vt.inst];
+        if (vt.inst != cur) {
+            if (cur >= 0 && !last) {
+                if (it >= 0) flush_run(rg, run_W, run_C, run_ntiles, run_base, run_tile, out_g, S);
+                flush_run(rm, run_W, run_C, run_ntiles, run_base, run_tile, out_m, S);
+            }
+            fetch = it >= 0;
+            cur = vt.inst;
+            run_tile = vt.t_in_inst;
+            run_C = I.C;
+            run_W = I.Cp < 4 ? I.Cp : 4;
+            run_ntiles = I.ntiles;
+            run_base = I.part_base;
+        } else if (!last && (int)threadIdx.x < I.C) {
+            const int64_t o = I.part_base + (int64_t)threadIdx.x * I.ntiles + vt.t_in_inst;
+            if (it >= 0) out_g[o] = make_float2(0.0f, 0.0f);
+            out_m[o] = make_float2(0.0f, 0.0f);
+        }
+        if (it < 0) {
+            if (WMAX == 1 || I.Cp == 1) cg_w0_tile<1>(A, I, vt, rm);
+            else if (WMAX == 2 || I.Cp == 2) cg_w0_tile<2>(A, I, vt, rm);
+            else cg_w0_tile<4>(A, I, vt, rm);
+        } else {
+            if (WMAX == 1 || I.Cp == 1) cg_tile<1>(A, I, vt, it, last, S, rg, rm, fetch);
+            else if (WMAX == 2 || I.Cp == 2) cg_tile<2>(A, I, vt, it, last, S, rg, rm, fetch);
+            else cg_tile<4>(A, I, vt, it, last, S, rg, rm, fetch);
+        }
+        fetch = false;
+    }
+    if (cur >= 0 && !last) {
+        if (it >= 0) flush_run(rg, run_W, run_C, run_ntiles, run_base, run_tile, out_g, S);
+        flush_run(rm, run_W, run_C, run_ntiles, run_base, run_tile, out_m, S);
+    }
+}
+
+template <int WMAX>
+constexpr int single_min_blocks() { return WMAX <= 2 ? 3 : 2; }
+
+template <int WMAX>
+__global__ void __launch_bounds__(kVTile, single_min_blocks<WMAX>())
+pcg_single_kernel(SolveArgs A, int it, int last)
+{
+    __shared__ PhaseSmem S;
+    int t0, t1;
+    block_chunk(A.nvt, t0, t1);
+    cg_run<WMAX>(A, it, last != 0, t0, t1, S);
+}
+
 // ------------------------------------------------- persistent PCG loop ---
 // Grid barrier for a cooperative launch.  Thread 0 of each block arrives on
 // its group's counter (groups of consecutive blocks, each counter on its own
@@ -1402,6 +1641,23 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
             if (e == cudaSuccess) return cudaGetLastError();
             cudaGetLastError();   // clear, and fall back to per-phase launches
         }
+    }
+    if (P.single) {
+        static int f_single = prof_family("pcg_single");
+        static const void* const fn_s[3] = {(const void*)pcg_single_kernel<1>,
+                                            (const void*)pcg_single_kernel<2>,
+                                            (const void*)pcg_single_kernel<4>};
+        static const int occ_s[3] = {occupancy(fn_s[0]), occupancy(fn_s[1]), occupancy(fn_s[2])};
+        const int nb = persistent_blocks(occ_s[wi], A.nvt);
+        for (int it = -1; it < P.pcg_iters; ++it) {
+            const int last = it == P.pcg_iters - 1 ? 1 : 0;
+            prof_begin(f_single, s);
+            if (wi == 0) pcg_single_kernel<1><<<nb, kVTile, 0, s>>>(A, it, last);
+            else if (wi == 1) pcg_single_kernel<2><<<nb, kVTile, 0, s>>>(A, it, last);
+            else pcg_single_kernel<4><<<nb, kVTile, 0, s>>>(A, it, last);
+            prof_end(f_single, s);
+        }
+        return cudaGetLastError();
     }
     const int nb_p = persistent_blocks(occ_p[wi], A.nvt);
     const int nb_u = persistent_blocks(occ_u[wi], A.nvt);

@@ -27,10 +27,12 @@ struct SolveArgs {
     float* rlo;                // low part of r (compensated variant)
     float* d[2];
     float* q;
+    float* aux[2];             // single-reduction form: s = A p by iteration parity
     // reductions
     Scal* scal;                // sum_k C_k
     float2* part_rs[2];        // sum_k C_k * ntiles_k double-float tile partials of r^T M^-1 r
     float2* part_dq;           // ... of d^T A d
+    float2* part_mu[2];        // single-reduction form: partials of w^T u by parity
     uint32_t* err;
 };
 
@@ -50,6 +52,7 @@ struct SolvePlan {
     int force_persistent;
     unsigned* barrier;         // kBarrierWords words of grid-barrier state (persistent loop)
     int inject_timeout;        // preset the barrier counter so no wait completes (test)
+    int single;                // 1: single-reduction PCG form (FP32, Cp <= 4, per-phase)
 };
 
 // A solve runs as segments: for each outer (IRLS) iteration a setup (splat,

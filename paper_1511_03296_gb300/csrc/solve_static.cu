@@ -70,11 +70,11 @@ StaticLayout layout(int n_images, int64_t cv, int64_t Vtot, int pc, int64_t cpar
     StaticLayout L;
     size_t o = 0;
     L.inst = o;    o = align256(o + sizeof(InstDev) * (size_t)n_images);
-    L.vec = o;     o = align256(o + sizeof(float) * 6 * (size_t)cv);
+    L.vec = o;     o = align256(o + sizeof(float) * 8 * (size_t)cv);
     L.a = o;       o = align256(o + sizeof(float) * (size_t)Vtot);
     L.nm = o;      o = align256(o + sizeof(float2) * (size_t)Vtot);
     L.scal = o;    o = align256(o + sizeof(Scal) * (size_t)pc);
-    L.part = o;    o = align256(o + sizeof(float2) * 3 * (size_t)cpart);
+    L.part = o;    o = align256(o + sizeof(float2) * 4 * (size_t)cpart);
     L.barrier = o; o = align256(o + sizeof(unsigned) * kBarrierWords);
     L.total = o;
     return L;
@@ -182,10 +182,14 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
     A.d[0] = vec + 3 * cv;
     A.d[1] = vec + 4 * cv;
     A.q = vec + 5 * cv;
+    A.aux[0] = vec + 6 * cv;
+    A.aux[1] = vec + 7 * cv;
     A.scal = reinterpret_cast<Scal*>(base + L.scal);
     A.part_rs[0] = part;
     A.part_rs[1] = part + cpart;
     A.part_dq = part + 2 * cpart;
+    A.part_mu[0] = A.part_dq;
+    A.part_mu[1] = part + 3 * cpart;
     A.err = G.err;
 
     SolvePlan P;

@@ -26,9 +26,10 @@ EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robus
             "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read",
             "fbs_set_option", "fbs_solve_static"]
 
-OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT = 1, 2, 3
+OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT, OPT_PCG_FORM = 1, 2, 3, 4
 VECTORS_AUTO, VECTORS_FP32, VECTORS_COMPENSATED = 0, 1, 2
 PCG_AUTO, PCG_PERSISTENT, PCG_PER_PHASE = 0, 1, 2
+PCG_FORM_STANDARD, PCG_FORM_SINGLE = 0, 1
 
 
 class FbsError(RuntimeError):

@@ -20,6 +20,7 @@ def to_dev(a):
 
 
 PCG_LAUNCH = {"mode": 0}    # fbs.PCG_AUTO; tests may switch to PCG_PERSISTENT / PCG_PER_PHASE
+PCG_FORM = {"form": 0}      # fbs.PCG_FORM_STANDARD; tests may switch to PCG_FORM_SINGLE
 
 
 def gpu_grid(insts, bistoch_iters=2):
@@ -28,6 +29,7 @@ def gpu_grid(insts, bistoch_iters=2):
     g = fbs.grid_build(yuv, [i.sigma_xy for i in insts], [i.sigma_l for i in insts],
                        [i.sigma_uv for i in insts])
     fbs.set_option(g, fbs.OPT_PCG_LAUNCH, PCG_LAUNCH["mode"])
+    fbs.set_option(g, fbs.OPT_PCG_FORM, PCG_FORM["form"])
     if bistoch_iters:
         fbs.bistochastize(g, bistoch_iters)
     return g

@@ -1,0 +1,120 @@
+"""Parity of the single-reduction (Chronopoulos-Gear) PCG form on the GPU
+with the oracle's single-reduction form, at equal iteration counts (rel-L2
+1e-5 on y and x, FP32 vectors against FP64).  Solves that the form does not
+cover (more than 4 channels, compensated vectors) fall back to the standard
+form and are compared with the standard oracle."""
+import numpy as np
+import pytest
+
+from paper_1511_03296_gb300 import synth
+from tests.gpu_util import PCG_FORM, REL_L2_TOL, gpu_grid, gpu_solve, oracle_grid, rel_l2, to_dev
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _single_form():
+    import torch
+    from paper_1511_03296_gb300 import build, fbs
+    build.build()
+    fbs.load()
+    assert torch.cuda.is_available()
+    PCG_FORM["form"] = fbs.PCG_FORM_SINGLE
+    yield
+    PCG_FORM["form"] = fbs.PCG_FORM_STANDARD
+
+
+def _inst(seed, h, w, sig, C=1, lam=128.0, npoly=4):
+    return synth.make_tiny(seed, h, w, npoly, C, sig, lam)
+
+
+def _check(insts, iters=25, tol=REL_L2_TOL, form="single"):
+    g = gpu_grid(insts, 2)
+    xs, ys = gpu_solve(g, insts, iters)
+    errs = []
+    for k, inst in enumerate(insts):
+        og = oracle_grid(inst, 2)
+        with oracle.pcg_form(form):
+            oy, ox = oracle.solve(og, inst.t, inst.c, inst.lam, iters)
+        ey, ex = rel_l2(ys[k], oy), rel_l2(xs[k].reshape(inst.channels, -1), ox)
+        errs.append((ey, ex))
+        assert ey <= tol and ex <= tol, (k, ey, ex)
+    return errs
+
+
+def test_single_plain_64x48():
+    _check(synth.plain_64x48().instances)
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2, 5, 50])
+def test_single_iteration_counts(iters):
+    _check([_inst(10, 70, 90, (8.0, 4.0, 3.0), C=2, npoly=6)], iters)
+
+
+def test_single_lambda_zero_is_weighted_mean():
+    inst = _inst(11, 40, 56, (8.0, 4.0, 3.0), C=2, lam=0.0)
+    g = gpu_grid([inst], 2)
+    xs, ys = gpu_solve(g, [inst], 25)
+    og = oracle_grid(inst, 2)
+    c = inst.c.reshape(-1).astype(np.float64)
+    for ch in range(2):
+        t = inst.t[ch].reshape(-1).astype(np.float64)
+        num = np.bincount(og.vid, weights=c * t, minlength=og.V)
+        den = np.bincount(og.vid, weights=c, minlength=og.V)
+        want = np.where(den > 0, num / np.where(den > 0, den, 1), 0.0)
+        assert np.allclose(ys[0][ch], want, rtol=1e-6, atol=1e-5)
+
+
+def test_single_zero_confidence_channels_and_vertices():
+    inst = _inst(12, 48, 64, (8.0, 4.0, 3.0), C=3)
+    inst.c[:, 20:] = 0.0
+    inst.t[1] = 0.0
+    _check([inst])
+
+
+def test_single_batched_uneven_images():
+    insts = [_inst(20, 37, 53, (3.3, 5.0, 7.7), C=1, lam=32.0),
+             _inst(21, 120, 160, (8.0, 4.0, 3.0), C=2, lam=128.0, npoly=8),
+             _inst(22, 9, 300, (16.0, 8.0, 8.0), C=3, lam=4.0),
+             _inst(23, 64, 48, (8.0, 4.0, 3.0), C=1, lam=0.0),
+             _inst(24, 200, 150, (16.0, 8.0, 8.0), C=2, lam=128.0, npoly=10)]
+    _check(insts)
+
+
+def test_single_full_1080p():
+    inst = synth.plain_1080p().instances[0]
+    print("single form 1080p rel-L2 (y, x):", _check([inst]))
+
+
+def test_single_deterministic():
+    inst = _inst(30, 120, 160, (8.0, 4.0, 3.0), C=2, npoly=8)
+    g = gpu_grid([inst], 2)
+    a = gpu_solve(g, [inst], 25)
+    b = gpu_solve(g, [inst], 25)
+    assert np.array_equal(a[0][0], b[0][0]) and np.array_equal(a[1][0], b[1][0])
+
+
+def test_single_robust_small():
+    import torch
+    from paper_1511_03296_gb300 import fbs
+    rng = np.random.Generator(np.random.PCG64(31))
+    inst = synth.robust_instance(rng, 120, 160, 8, (8.0, 8.0, 8.0), 4.0)
+    g = gpu_grid([inst], 2)
+    t, c = to_dev(inst.t), to_dev(inst.c)
+    x = torch.empty_like(t)
+    y = torch.empty((1, g.vertex_counts[0]), device="cuda")
+    fbs.solve_robust(g, [t], [c], inst.lam, 8.0, 4, 25, x=[x], y=[y])
+    fbs.grid_sync(g)
+    og = oracle_grid(inst, 2)
+    with oracle.pcg_form("single"):
+        oy, ox = oracle.solve_robust(og, inst.t, inst.c, inst.lam, 8.0, 4, 25)
+    ey = rel_l2(y.cpu().numpy(), oy)
+    ex = rel_l2(x.cpu().numpy().reshape(1, -1), ox)
+    assert ey <= REL_L2_TOL and ex <= REL_L2_TOL, (ey, ex)
+
+
+def test_wide_images_fall_back_to_standard_form():
+    # 5 channels (padded to 8): the single form does not cover it
+    _check([_inst(40, 60, 80, (8.0, 4.0, 3.0), C=5, npoly=6)], form="standard")
