@@ -157,8 +157,9 @@ __device__ void radix_sort_tile(const uint64_t* key, uint16_t* ord, uint16_t* tm
     }
 }
 
-// x / d for 0 <= x, d <= 2^14, from m = floor(2^32 / d) + 1 (exact in that range)
-__device__ __forceinline__ int div_small(int x, uint32_t m) { return (int)__umulhi((uint32_t)x, m); }
+// x / d for 0 <= x < 2^14 and 1 <= d <= 2^14, from m = floor(2^32 / d) + 1
+// (exact in that range; m needs 33 bits for d = 1)
+__device__ __forceinline__ int div_small(int x, uint64_t m) { return (int)(((uint64_t)x * m) >> 32); }
 
 // Quantise the pixels of one tile: key[i] = cell index in tile << 36 |
 // l << 24 | u << 12 | v for tile pixel i (row-major in the tile rectangle);
@@ -260,7 +261,7 @@ grid_sort_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ img
     const ImgDev im = imgs[t.img];
     const int tw = t.x1 - t.x0;
     const int P = (t.y1 - t.y0) * tw;
-    const uint32_t mtw = (uint32_t)((1ull << 32) / (uint64_t)tw + 1);
+    const uint64_t mtw = (1ull << 32) / (uint64_t)tw + 1;
 
     for (int c = threadIdx.x; c < t.nkx && c < max_cells; c += blockDim.x) cellcnt[c] = 0;
     for (int i = threadIdx.x; i < P; i += blockDim.x) ord[i] = (uint16_t)i;

@@ -38,6 +38,9 @@ GRID_CASES = [
     ("large cells", lambda: _inst(6, 250, 301, (100.0, 8.0, 8.0))),
     ("sigma_xy 127 (127x127 cells)", lambda: _inst(7, 256, 256, (127.0, 16.0, 16.0))),
     ("ragged 257x385", lambda: _inst(8, 257, 385, (16.0, 8.0, 8.0), npoly=12)),
+    # W = 249 at sigma_xy = 16: the last cell column is one pixel wide and the
+    # tiler puts it in a tile of its own (tile width 1)
+    ("one-pixel last tile 64x249", lambda: _inst(13, 64, 249, (16.0, 8.0, 8.0), npoly=5)),
 ]
 
 
