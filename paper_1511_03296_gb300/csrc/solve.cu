@@ -489,16 +489,28 @@ splat_kernel(SolveArgs A, int mode, float sigma_gm, int comp, unsigned* work)
 }
 
 // ------------------------------------------------- Laplacian-form apply ---
-// Accumulates, for W channels, sum_u n_u (z_v - z_u) over the neighbours;
-// with COMP every product is exact and the sums are double-float pairs.
+// Accumulates, for W channels, sum_u n_u (z_v - z_u) over the neighbours.
+// COMP: each product n_u (z_v - z_u) is split exactly into p + e; p enters
+// the running high part through an error-free two-sum and both errors are
+// added to the low part (the cascaded "Sum2" scheme of Ogita, Rump and
+// Oishi, 2005: as accurate as summing in twice the working precision); the
+// pair is renormalised in lap_finish.
 template <int W, bool COMP>
 __device__ __forceinline__ void lap_acc(DF (&s)[W], float nu, const float (&zv)[W],
                                         const float (&zu)[W])
 {
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        if (COMP) s[k] = df_add(s[k], df_mul_exact(nu, zv[k] - zu[k]));
-        else s[k].hi = fmaf(nu, zv[k] - zu[k], s[k].hi);
+        if (COMP) {
+            const float dz = zv[k] - zu[k];
+            const float p = __fmul_rn(nu, dz);
+            const float e = __fmaf_rn(nu, dz, -p);
+            const DF t = df_two_sum(s[k].hi, p);
+            s[k].hi = t.hi;
+            s[k].lo = __fadd_rn(s[k].lo, __fadd_rn(t.lo, e));
+        } else {
+            s[k].hi = fmaf(nu, zv[k] - zu[k], s[k].hi);
+        }
     }
 }
 
@@ -506,7 +518,7 @@ __device__ __forceinline__ void lap_acc(DF (&s)[W], float nu, const float (&zv)[
 template <bool COMP>
 __device__ __forceinline__ DF lap_finish(float av, float lam_n, float zv, DF s)
 {
-    return COMP ? df_add(df_mul_exact(av, zv), df_mul_f(s, lam_n))
+    return COMP ? df_add(df_mul_exact(av, zv), df_mul_f(df_two_sum(s.hi, s.lo), lam_n))
                 : DF{fmaf(av, zv, lam_n * s.hi), 0.0f};
 }
 
