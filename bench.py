@@ -262,6 +262,17 @@ def time_steps(step, steps, warmup, flush, stream):
     return [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
 
 
+# DRAM traffic of one PCG iteration (both phases) from one ncu capture of the
+# current kernels (dram__bytes_read.sum + dram__bytes_write.sum; the summaries
+# and commands are in profiles/pcg_1080p.md and profiles/pcg_*_batched16.md).
+# ncu flushes the caches before each captured launch, so at 1080p this is the
+# cold-start traffic of an L2-resident working set.  The 64-image batch is too
+# large to capture under the profiling size rule: its 16-image prefix was
+# captured and the traffic is scaled by its ratio to the algorithmic bytes.
+PCG_TRAFFIC_1080P = 9.004032e6 + 7.723520e6
+PCG_TRAFFIC_RATIO_BATCHED = (173.014272e6 + 16.165376e6 + 66.415360e6 + 0.599040e6) / 235835472
+
+
 def pcg_roofline(regions, solves_per_step, steps, bytes_per_iter, peak):
     """Achieved GB/s of the PCG iteration from the region events of the
     timed steps (all PCG iterations of a step share the same byte count)."""
@@ -321,7 +332,10 @@ def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, seq
             "one_at_a_time_ms": ms1,
             "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
                             for k, v in regions.items() if v[0]},
-            "pcg_roofline": pcg_roofline(regions, 1, steps, bytes_iter, peak)}
+            "pcg_roofline": dict(pcg_roofline(regions, 1, steps, bytes_iter, peak) or {},
+                                 traffic=PCG_TRAFFIC_RATIO_BATCHED * bytes_iter,
+                                 traffic_source="ncu of the first 16 images, scaled by "
+                                                "traffic / algorithmic bytes")}
 
 
 def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
@@ -370,7 +384,8 @@ def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
             "fwd_bwd_mpix_s": whole_job_mpix(dist.world, npix, m), "ms_per_step": m,
             "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
                             for k, v in regions.items() if v[0]},
-            "pcg_roofline": pcg_roofline(regions, 2, steps, bytes_iter, peak)}
+            "pcg_roofline": dict(pcg_roofline(regions, 2, steps, bytes_iter, peak) or {},
+                                 traffic=None)}
 
 
 def run_only(args, dist):
@@ -506,7 +521,9 @@ def run_ours(args, dist):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
         "roofline": dict(roof or {}, kernel="pcg iteration (both CG phases)",
-                         traffic=None, peak_source="measured" if peaks else "fallback",
+                         traffic=PCG_TRAFFIC_1080P,
+                         traffic_source="ncu, cold caches, one iteration (apply + update)",
+                         peak_source="measured" if peaks else "fallback",
                          note="working set L2-resident at this size; see batched / fwd_bwd "
                               "for the HBM-bound sizes"),
         "phase_share": region_share,
