@@ -725,6 +725,51 @@ __device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I
     }
 }
 
+// FP32 phase 2 on two consecutive tiles of one image (Cp = W <= 4): the same
+// arithmetic as update_tile, with the loads of both tiles issued together
+// (a streaming pass; this doubles the loads in flight per thread).  The
+// products enter run[] tile by tile, in the same order as two single calls.
+template <int W, bool CO>
+__device__ __forceinline__ void update_pair(const SolveArgs& A, const InstDev& I,
+                                            const VTile& va, const VTile& vb,
+                                            const float* __restrict__ d, PhaseSmem& S,
+                                            DF (&run)[4], bool fetch, const float2* in, int it)
+{
+    const int64_t off = I.vec_base - I.voff * W;
+    int v[2], vs[2];
+    bool valid[2];
+    float2 nmv[2];
+    float dv[2][W], yv[2][W], rv[2][W], qv[2][W];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const VTile& vt = t == 0 ? va : vb;
+        v[t] = (int)vt.v0 + (int)threadIdx.x;
+        valid[t] = v[t] < (int)vt.v1;
+        vs[t] = valid[t] ? v[t] : (int)vt.v0;
+        nmv[t] = A.nm[vs[t]];
+        ldw<W, CO>(d + off + vs[t] * W, dv[t]);
+        ldw<W, CO>(A.y + off + vs[t] * W, yv[t]);
+        ldw<W, CO>(A.r + off + vs[t] * W, rv[t]);
+        ldw<W, CO>(A.q + off + vs[t] * W, qv[t]);
+    }
+    if (fetch) phase_scalars<2, CO, W>(A, I, in, it, S);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            const float alpha = (float)S.sa[k];
+            yv[t][k] = fmaf(alpha, dv[t][k], yv[t][k]);
+            rv[t][k] = fmaf(-alpha, qv[t][k], rv[t][k]);
+            if (valid[t] && k < I.C)
+                run[k] = df_add(run[k], df_mul_exact(rv[t][k], nmv[t].y * rv[t][k]));
+        }
+        if (valid[t]) {
+            stw<W>(A.y + off + v[t] * W, yv[t]);
+            stw<W>(A.r + off + v[t] * W, rv[t]);
+        }
+    }
+}
+
 // ------------------------------------------------ wide images (Cp > 4) ---
 // The Cp / 4 consecutive threads of a vertex each take one float4 of its
 // channel row (thread p: channels 4p .. 4p+3), so a neighbour's whole row is
@@ -969,6 +1014,23 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
         } else if ((int)threadIdx.x < I.C) {
             out[I.part_base + (int64_t)threadIdx.x * I.ntiles + vt.t_in_inst] =
                 make_float2(0.0f, 0.0f);
+        }
+        if (PHASE == 2 && !COMP && !(WMAX == 4 && I.Cp > 4) && tile + 1 < t1 &&
+            A.vt[tile + 1].inst == vt.inst) {
+            // two tiles of the same image at once (the second is never a run start)
+            const VTile vb = A.vt[tile + 1];
+            if ((int)threadIdx.x < I.C)
+                out[I.part_base + (int64_t)threadIdx.x * I.ntiles + vb.t_in_inst] =
+                    make_float2(0.0f, 0.0f);
+            if (WMAX == 1 || I.Cp == 1)
+                update_pair<1, CO>(A, I, vt, vb, dsrc, S, run, fetch, in, it);
+            else if (WMAX == 2 || I.Cp == 2)
+                update_pair<2, CO>(A, I, vt, vb, dsrc, S, run, fetch, in, it);
+            else
+                update_pair<4, CO>(A, I, vt, vb, dsrc, S, run, fetch, in, it);
+            fetch = false;
+            ++tile;
+            continue;
         }
         if (WMAX == 4 && I.Cp > 4) {
             if (fetch) phase_scalars<PHASE, CO, 4>(A, I, in, it, S);
