@@ -22,6 +22,7 @@ cudaError_t launch_scan_tiles(const int*, int64_t*, int, cudaStream_t);
 cudaError_t launch_grid_finalize(const GTile*, int, const ImgDev*, const int64_t*, uint32_t*,
                                  const uint64_t*, const uint32_t*, const uint32_t*, uint64_t*,
                                  uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
+cudaError_t launch_pack_neighbours(const int32_t*, uint32_t*, int64_t, cudaStream_t);
 cudaError_t launch_grid_neighbours(const GTile*, int, const ImgDev*, const int64_t*,
                                    const uint64_t*, const uint32_t*, const uint32_t*, int32_t*,
                                    int64_t, cudaStream_t);
@@ -234,6 +235,7 @@ struct fbs_grid {
     uint32_t* pstart = nullptr;
     uint32_t* m = nullptr;
     int32_t* nbr = nullptr;
+    uint32_t* nbrp = nullptr;           // 5 x Vtot packed 16-bit neighbour offsets
     double* n64 = nullptr;
     double* n64b = nullptr;
     float* nf = nullptr;
@@ -291,7 +293,7 @@ void free_grid_memory(fbs_grid* g, cudaStream_t s)
         g->cap_stream = nullptr;
     }
     dfree(g->vkey, s); dfree(g->vid, s); dfree(g->perm, s); dfree(g->pstart, s);
-    dfree(g->m, s); dfree(g->nbr, s); dfree(g->n64, s); dfree(g->n64b, s); dfree(g->nf, s);
+    dfree(g->m, s); dfree(g->nbr, s); dfree(g->nbrp, s); dfree(g->n64, s); dfree(g->n64b, s); dfree(g->nf, s);
     dfree(g->cell_voff, s); dfree(g->cell_nv, s); dfree(g->err, s); dfree(g->vt, s);
     dfree(g->gt, s); dfree(g->gt_voff, s);
     dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s); dfree(g->part, s);
@@ -472,6 +474,7 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
         FBS_TRY(dalloc(&g->pstart, V, s));
         FBS_TRY(dalloc(&g->m, V, s));
         FBS_TRY(dalloc(&g->nbr, (size_t)V * 10, s));
+        FBS_TRY(dalloc(&g->nbrp, (size_t)V * 5, s));
         FBS_TRY(dalloc(&g->n64, V, s));
         FBS_TRY(dalloc(&g->n64b, V, s));
         FBS_TRY(dalloc(&g->nf, V, s));
@@ -479,6 +482,7 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
                                      d_tps, g->vkey, g->m, g->pstart, g->cell_voff, s));
         FBS_TRY(launch_grid_neighbours(d_tiles, ntiles, d_img, d_tile_voff, g->vkey, g->cell_voff,
                                        g->cell_nv, g->nbr, V, s));
+        FBS_TRY(launch_pack_neighbours(g->nbr, g->nbrp, V, s));
         // vertex tiles for the vertex kernels
         std::vector<VTile> vt;
         g->vt0.resize(n_images);
@@ -719,6 +723,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.inst = g->inst;
     A.ninst = g->n_images;
     A.nbr = g->nbr;
+    A.nbrp = g->nbrp;
     A.Vtot = g->Vtot;
     A.n64 = g->n64;
     A.m = g->m;
@@ -999,6 +1004,7 @@ bool grid_view(const fbs_grid* g, GridView* out)
     out->nvt_img = g->nvt_img.data();
     out->vt = g->vt;
     out->nbr = g->nbr;
+    out->nbrp = g->nbrp;
     out->n64 = g->n64;
     out->m = g->m;
     out->pstart = g->pstart;

@@ -20,6 +20,8 @@ constexpr int kChanBlock = 4;            // channels processed per pass of a PCG
 constexpr int kMaxChannels = 64;         // channels per image
 constexpr unsigned kBarrierGroups = 32;            // first-level counters of the grid barrier
 constexpr unsigned kBarrierWords = 32 * (kBarrierGroups + 1);
+constexpr int kNbrOffMax = 32767;          // packed neighbour offsets: |offset| <= this
+constexpr int kNbrEscape = -32768;         // ... else this, and the 32-bit table holds the id
 constexpr unsigned kWorkCounterWord = 2;   // in the barrier block, unused by the barrier:
                                            // the splat's work counter
 constexpr unsigned kBarrierSpinLimit = 1u << 20;   // polls of >= 64 ns: >= 67 ms before a time-out

@@ -468,6 +468,34 @@ bistoch_kernel(const double* __restrict__ nold, double* __restrict__ nnew,
 
 }  // namespace
 
+// Packed neighbour table: for dimension d, one 32-bit word per vertex holding
+// the -1 and +1 neighbours as 16-bit signed offsets from the vertex (low and
+// high half); an absent neighbour is offset 0 (the vertex itself, whose
+// Laplacian term is exactly 0), and an offset outside [-32767, 32767] is the
+// escape value -32768 (read the 32-bit table instead).  Spatial order keeps
+// offsets small: l, u, v neighbours share the cell, x neighbours are in the
+// next cell, y neighbours one cell row away.
+__global__ void __launch_bounds__(256)
+pack_neighbours_kernel(const int32_t* __restrict__ nbr, uint32_t* __restrict__ nbrp, int64_t V)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            uint32_t w = 0;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int32_t u = nbr[(int64_t)(2 * d + s) * V + v];
+                const int64_t off = u >= 0 ? (int64_t)u - v : 0;
+                const int32_t h = (off >= -kNbrOffMax && off <= kNbrOffMax) ? (int32_t)off
+                                                                             : kNbrEscape;
+                w |= ((uint32_t)h & 0xffffu) << (16 * s);
+            }
+            nbrp[(int64_t)d * V + v] = w;
+        }
+    }
+}
+
 // ------------------------------------------------------ host launchers ---
 size_t grid_smem_sort(int P2, int max_cells)
 {
@@ -537,6 +565,14 @@ cudaError_t launch_bistoch(const double* nold, double* nnew, float* nf, const ui
     prof_begin(fam, s);
     bistoch_kernel<<<blocks, 256, 0, s>>>(nold, nnew, nf, m, nbr, V, first, last);
     prof_end(fam, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_neighbours(const int32_t* nbr, uint32_t* nbrp, int64_t V, cudaStream_t s)
+{
+    if (V == 0) return cudaSuccess;
+    const int blocks = (int)std::min<int64_t>((V + 255) / 256, (int64_t)device_info().sms * 8);
+    pack_neighbours_kernel<<<blocks, 256, 0, s>>>(nbr, nbrp, V);
     return cudaGetLastError();
 }
 

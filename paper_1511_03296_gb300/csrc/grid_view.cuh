@@ -20,6 +20,7 @@ struct GridView {
     const int* nvt_img;        // host, n_images
     const VTile* vt;           // device
     const int32_t* nbr;        // device
+    const uint32_t* nbrp;      // device, packed offsets
     const double* n64;
     const uint32_t* m;
     const uint32_t* pstart;

@@ -83,6 +83,34 @@ __device__ __forceinline__ void stw(float* p, const float (&v)[W])
     }
 }
 
+// The ten neighbours of vertex v (order: -1, +1 per dimension) from the
+// packed table (16-bit offsets; absent: v itself, whose Laplacian term is
+// exactly 0).  Escaped offsets are rare (more than 32767 vertices between a
+// vertex and its y neighbour): the 32-bit table is read only in a
+// warp-uniform branch when some lane of the warp has one, so the common
+// path has no load in the id chain.  All lanes of the warp must call it.
+__device__ __forceinline__ void load_neighbours(const SolveArgs& A, int v, int (&nb)[10])
+{
+    uint32_t w[5];
+#pragma unroll
+    for (int d = 0; d < 5; ++d) w[d] = A.nbrp[(int64_t)d * A.Vtot + v];
+    bool esc = false;
+#pragma unroll
+    for (int d = 0; d < 5; ++d) {
+        const int om = (int)(int16_t)(w[d] & 0xffffu), op = (int)(int16_t)(w[d] >> 16);
+        nb[2 * d] = v + om;
+        nb[2 * d + 1] = v + op;
+        esc |= (om == kNbrEscape) | (op == kNbrEscape);
+    }
+    if (__any_sync(0xffffffffu, esc)) {
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            const int o = (int)(int16_t)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+            if (o == kNbrEscape) nb[j] = A.nbr[(int64_t)j * A.Vtot + v];
+        }
+    }
+}
+
 // -------------------------------------------------------- inner products ---
 struct PhaseSmem {
     DF red[4][kVTile / 32];
@@ -620,11 +648,7 @@ __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I,
     // neighbour ids (an absent neighbour is replaced by the vertex itself:
     // its term n_u (d_v - d_u) is then exactly 0, so no masking is needed)
     int nb[10];
-#pragma unroll
-    for (int j = 0; j < 10; ++j) {
-        const int u = A.nbr[(int64_t)j * A.Vtot + vs];
-        nb[j] = u >= 0 ? u : vs;
-    }
+    load_neighbours(A, vs, nb);
     float rv[W], ov[W];
     ldw<W, CO>(rb + vs * W, rv);
     if (!first) ldw<W, CO>(ob + vs * W, ov);
@@ -693,10 +717,11 @@ __device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I
         av = valid ? A.a[v] : 0.0f;
 #pragma unroll
         for (int k = 0; k < W; ++k) sacc[k] = {0.0f, 0.0f};
+        int nb[10];
+        load_neighbours(A, vs, nb);
 #pragma unroll
         for (int j = 0; j < 10; ++j) {
-            const int u0 = A.nbr[(int64_t)j * A.Vtot + vs];
-            const int u = u0 >= 0 ? u0 : vs;     // absent: the vertex itself, term 0
+            const int u = nb[j];
             const float nu = A.nm[u].x;
             float du[W];
             ldw<W, CO>(d + off + u * W, du);
@@ -808,11 +833,7 @@ __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I,
         const float av = valid ? A.a[v] : 0.0f;
         const float lam_n = I.lam * nmv.x;
         int nb[10];
-#pragma unroll
-        for (int j = 0; j < 10; ++j) {
-            const int u = A.nbr[(int64_t)j * A.Vtot + vs];
-            nb[j] = u >= 0 ? u : vs;             // absent: the vertex itself, term 0
-        }
+        load_neighbours(A, vs, nb);
         float rv[4], dv[4];
         ldw<4, CO>(rb + vs * Cp, rv);
         if (first) {
@@ -889,10 +910,11 @@ __device__ __forceinline__ void update_wide(const SolveArgs& A, const InstDev& I
             ldw<4, CO>(A.rlo + base + vs * Cp, rl);
 #pragma unroll
             for (int k = 0; k < 4; ++k) sacc[k] = {0.0f, 0.0f};
+            int nb[10];
+            load_neighbours(A, vs, nb);
 #pragma unroll
             for (int j = 0; j < 10; ++j) {
-                const int u0 = A.nbr[(int64_t)j * A.Vtot + vs];
-                const int u = u0 >= 0 ? u0 : vs;   // absent: the vertex itself, term 0
+                const int u = nb[j];
                 const float nu = A.nm[u].x;
                 float du[4];
                 ldw<4, CO>(d + base + u * Cp, du);

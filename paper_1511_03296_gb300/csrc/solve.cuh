@@ -12,6 +12,7 @@ struct SolveArgs {
     int ninst;
     // grid
     const int32_t* nbr;        // 10 x Vtot, global vertex ids, -1 if absent
+    const uint32_t* nbrp;      // 5 x Vtot, packed 16-bit offsets (-1 and +1 per dimension)
     int64_t Vtot;
     const double* n64;         // bistochastisation vector n
     const uint32_t* m;         // counts

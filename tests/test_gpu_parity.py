@@ -385,3 +385,17 @@ def test_bad_arguments():
         fbs.solve(g, [t], [c], -1.0, 5)
     with pytest.raises(fbs.FbsError, match="ARG"):
         fbs.solve_robust(g, [to_dev(np.concatenate([inst.t, inst.t]))], [c], 1.0, 1.0, 2, 5)
+
+
+def test_solve_with_escaped_neighbour_offsets():
+    # 16 x 16384 at sigma_xy = 8 with unit colour sigmas: over 100 k vertices
+    # per cell row, so y-neighbour offsets exceed the packed table's 16 bits
+    # and the PCG reads those neighbours from the 32-bit table
+    from paper_1511_03296_gb300 import fbs
+    inst = synth.make_tiny(41, 16, 16384, 40, 1, (8.0, 1.0, 1.0), 128.0)
+    g = gpu_grid([inst], 2)
+    _, _, _, nbr, _ = fbs.grid_export(g, 0, with_n=False)
+    v = np.arange(nbr.shape[0])[:, None]
+    far = (nbr >= 0) & (np.abs(nbr.astype(np.int64) - v) > 32767)
+    assert far.sum() > 0, "no escaped offsets: the case does not cover the path"
+    _check_solve([inst])
