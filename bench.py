@@ -91,6 +91,16 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+def tune(fbs, yuv, sig, t, c, lam, x):
+    """The library's autotuner on one grid of the workload (its choice is then
+    set on every step's grid; tuning happens outside the timed region)."""
+    g = fbs.grid_build(yuv, *sig)
+    fbs.bistochastize(g, BISTOCH_ITERS)
+    r = fbs.autotune(g, t, c, lam, PCG_ITERS, x=x)
+    g.destroy()
+    return r
+
+
 def rank_seed(base: int, rank: int) -> int:
     """Each rank draws its own independent problems (weak scaling)."""
     return base + rank
@@ -268,9 +278,11 @@ def time_steps(step, steps, warmup, flush, stream):
 # ncu flushes the caches before each captured launch, so at 1080p this is the
 # cold-start traffic of an L2-resident working set.  The 64-image batch is too
 # large to capture under the profiling size rule: its 16-image prefix was
-# captured and the traffic is scaled by its ratio to the algorithmic bytes.
-PCG_TRAFFIC_1080P = 9.004032e6 + 7.723520e6
-PCG_TRAFFIC_RATIO_BATCHED = (173.014272e6 + 16.165376e6 + 66.415360e6 + 0.599040e6) / 235835472
+# captured and the traffic is scaled by its ratio to the algorithmic bytes
+# (below 1: the gathers read 16-bit packed neighbour offsets, not the 32-bit
+# ids the algorithmic count assumes).
+PCG_TRAFFIC_1080P = 6.887424e6 + 7.724544e6
+PCG_TRAFFIC_RATIO_BATCHED = (108.712960e6 + 10.696704e6 + 66.429952e6 + 0.733440e6) / 235835472
 
 
 def pcg_roofline(regions, solves_per_step, steps, bytes_per_iter, peak):
@@ -300,9 +312,11 @@ def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, seq
     sig = ([i.sigma_xy for i in insts], [i.sigma_l for i in insts], [i.sigma_uv for i in insts])
     lam = [i.lam for i in insts]
     info = {}
+    tuning = tune(fbs, yuv, sig, t, c, lam, x)
 
     def batched():
         g = fbs.grid_build(yuv, *sig)
+        fbs.apply_tuning(g, tuning)
         fbs.bistochastize(g, BISTOCH_ITERS)
         fbs.solve(g, t, c, lam, PCG_ITERS, x=x)
         info["V"] = g.vertex_counts
@@ -328,6 +342,7 @@ def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, seq
                         "chroma (C=2, c=1 on 2% of pixels), sigma_xy in {8,16}, lambda in {32,128}",
             "pixels": npix, "vertices": int(sum(info["V"])),
             "batched_mpix_s": whole_job_mpix(dist.world, npix, mb), "batched_ms": mb,
+            "tuning": tuning,
             "one_at_a_time_mpix_s": whole_job_mpix(dist.world, npix, ms1),
             "one_at_a_time_ms": ms1,
             "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
@@ -358,9 +373,11 @@ def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
     lam = [i.lam for i in insts]
     numel = sum(tt.numel() for tt in t)
     info = {}
+    tuning = tune(fbs, yuv, sig, t, c, lam, x)
 
     def step():
         g = fbs.grid_build(yuv, *sig)
+        fbs.apply_tuning(g, tuning)
         fbs.bistochastize(g, BISTOCH_ITERS)
         y = [torch.empty((i.channels, g.vertex_counts[k]), device="cuda")
              for k, i in enumerate(insts)]
@@ -382,6 +399,7 @@ def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
                         "lambda=128, forward + backward (2 x 25 PCG iterations)",
             "pixels": npix, "vertices": int(sum(info["V"])),
             "fwd_bwd_mpix_s": whole_job_mpix(dist.world, npix, m), "ms_per_step": m,
+            "tuning": tuning,
             "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
                             for k, v in regions.items() if v[0]},
             "pcg_roofline": dict(pcg_roofline(regions, 2, steps, bytes_iter, peak) or {},
@@ -430,8 +448,12 @@ def run_ours(args, dist):
 
     V_holder = {}
 
+    tuning = tune(fbs, [d_yuv], (inst.sigma_xy, inst.sigma_l, inst.sigma_uv), [d_t], [d_c],
+                  inst.lam, [d_x])
+
     def step(yuv, t, c, x):
         g = fbs.grid_build([yuv], inst.sigma_xy, inst.sigma_l, inst.sigma_uv)
+        fbs.apply_tuning(g, tuning)
         fbs.bistochastize(g, BISTOCH_ITERS)
         fbs.solve(g, [t], [c], inst.lam, PCG_ITERS, x=[x])
         V_holder["V"] = g.vertex_counts[0]
@@ -515,7 +537,8 @@ def run_ours(args, dist):
                    "channels": inst.channels, "parallelism": f"replicas x{dist.world}",
                    "l2": "flushed between steps (256 MiB write outside the step events)",
                    "precision": "FP32 vectors, FP64-accurate CG dot products, FP64 "
-                                "bistochastisation"},
+                                "bistochastisation",
+                   "tuning": tuning},
         "clocks": clk.summary(),
         "e2e": {"value": whole_job_mpix(dist.world, inst.n_pixels, e2e_ms), "unit": "Mpix/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

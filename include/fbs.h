@@ -178,17 +178,47 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *                            for FP32 vectors when no image has more than 4
  *                            channels (per-phase launches); other solves keep
  *                            the standard form.
+ * FBS_OPT_PHASE_BLOCKS: 1 (default), 2 or 4 -- the per-phase PCG kernels
+ *   launch min(tiles, SMs x resident blocks per SM x value) blocks; above 1
+ *   the blocks take shorter runs of tiles in several waves.
  * FBS_OPT_INJECT_BARRIER_TIMEOUT: value 1 makes the next persistent PCG
  *   loop start with its barrier counter preset so that no barrier can
  *   complete; every block waits out its bounded spin, latches
  *   FBS_ERR_TIMEOUT and returns (a test of the failure path; one-shot).
  */
 enum { FBS_OPT_VECTOR_PRECISION = 1, FBS_OPT_PCG_LAUNCH = 2, FBS_OPT_INJECT_BARRIER_TIMEOUT = 3,
-       FBS_OPT_PCG_FORM = 4 };
+       FBS_OPT_PCG_FORM = 4, FBS_OPT_PHASE_BLOCKS = 5 };
 enum { FBS_VECTORS_AUTO = 0, FBS_VECTORS_FP32 = 1, FBS_VECTORS_COMPENSATED = 2 };
 enum { FBS_PCG_AUTO = 0, FBS_PCG_PERSISTENT = 1, FBS_PCG_PER_PHASE = 2 };
 enum { FBS_PCG_FORM_STANDARD = 0, FBS_PCG_FORM_SINGLE = 1 };
 fbs_status fbs_set_option(fbs_grid* g, int option, int value);
+
+/*
+ * fbs_autotune -- picks the PCG launch configuration for this grid and
+ * problem shape by timing it.  The paper has no counterpart (it runs one CPU
+ * configuration); it serves the batched solves (tile and block shapes
+ * chosen by measurement rather than fixed).
+ *
+ * Runs fbs_solve(g, probs, pcg_iters) under each candidate -- launch style
+ * (per-phase launches, or the persistent loop where its cooperative launch
+ * fits), PCG form (standard or single-reduction) and the per-phase block
+ * count (FBS_OPT_PHASE_BLOCKS 1, 2, 4) -- each warmed up twice (so graph
+ * replay is what gets timed) and timed over three solves with CUDA events on
+ * `stream`, then leaves the fastest set on the grid (fbs_set_option values)
+ * and solves once more with it, so the output buffers in probs hold that
+ * configuration's result.  *out, if not null, receives the choice and its
+ * median solve time.  Synchronises `stream`.  Errors: as fbs_solve;
+ * FBS_ERR_STATE while `stream` is being captured.
+ */
+typedef struct {
+    int pcg_launch;        /* FBS_PCG_PER_PHASE or FBS_PCG_PERSISTENT */
+    int pcg_form;          /* FBS_PCG_FORM_* */
+    int phase_blocks;      /* FBS_OPT_PHASE_BLOCKS value */
+    float solve_ms;        /* median time of one solve with this choice */
+    int candidates;        /* configurations timed */
+} fbs_tune_result;
+fbs_status fbs_autotune(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters, void* stream,
+                        fbs_tune_result* out);
 
 /*
  * fbs_solve_static -- fbs_solve for callers that cannot allocate device

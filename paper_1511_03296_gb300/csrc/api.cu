@@ -256,6 +256,7 @@ struct fbs_grid {
     int persistent = 1;
     int force_persistent = 0;
     int pcg_form = FBS_PCG_FORM_STANDARD;
+    int phase_blocks = 1;
     int inject_timeout = 0;
     float* a = nullptr;
     float2* nm = nullptr;
@@ -686,6 +687,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     // channels; it runs as per-phase launches
     plan.single = g->pcg_form == FBS_PCG_FORM_SINGLE && !plan.comp && cmax <= 4 ? 1 : 0;
     plan.persistent = g->persistent && !capturing(s) && !plan.single ? 1 : 0;
+    plan.block_mult = g->phase_blocks;
     plan.force_persistent = g->force_persistent;
     plan.inject_timeout = plan.persistent ? g->inject_timeout : 0;
     if (plan.persistent) g->inject_timeout = 0;
@@ -849,6 +851,11 @@ fbs_status fbs_set_option(fbs_grid* g, int option, int value)
         g->inject_timeout = value;
         return FBS_OK;
     }
+    if (option == FBS_OPT_PHASE_BLOCKS) {
+        if (value != 1 && value != 2 && value != 4) return FBS_ERR_ARG;
+        g->phase_blocks = value;
+        return FBS_OK;
+    }
     if (option == FBS_OPT_PCG_FORM) {
         if (value != FBS_PCG_FORM_STANDARD && value != FBS_PCG_FORM_SINGLE) return FBS_ERR_ARG;
         g->pcg_form = value;
@@ -862,6 +869,75 @@ fbs_status fbs_set_option(fbs_grid* g, int option, int value)
         return FBS_OK;
     }
     return FBS_ERR_ARG;
+}
+
+fbs_status fbs_autotune(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters, void* stream,
+                        fbs_tune_result* out)
+{
+    if (!g) return FBS_ERR_ARG;
+    fbs_status st = check_problems(g, probs, pcg_iters);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s)) return FBS_ERR_STATE;
+    struct Cand {
+        int launch, form, blocks;
+    };
+    const Cand cands[] = {{FBS_PCG_PER_PHASE, FBS_PCG_FORM_STANDARD, 1},
+                          {FBS_PCG_PER_PHASE, FBS_PCG_FORM_STANDARD, 2},
+                          {FBS_PCG_PER_PHASE, FBS_PCG_FORM_STANDARD, 4},
+                          {FBS_PCG_PER_PHASE, FBS_PCG_FORM_SINGLE, 1},
+                          {FBS_PCG_PER_PHASE, FBS_PCG_FORM_SINGLE, 2},
+                          {FBS_PCG_PERSISTENT, FBS_PCG_FORM_STANDARD, 1}};
+    const int n = (int)(sizeof(cands) / sizeof(cands[0]));
+    const int saved_persistent = g->persistent, saved_force = g->force_persistent,
+              saved_form = g->pcg_form, saved_blocks = g->phase_blocks;
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; ++k)
+        if (cudaEventCreate(&ev[k]) != cudaSuccess) return FBS_ERR_CUDA;
+    int best = -1;
+    float best_ms = 0.0f;
+    for (int c = 0; c < n && !st; ++c) {
+        g->persistent = cands[c].launch == FBS_PCG_PER_PHASE ? 0 : 1;
+        g->force_persistent = cands[c].launch == FBS_PCG_PERSISTENT ? 1 : 0;
+        g->pcg_form = cands[c].form;
+        g->phase_blocks = cands[c].blocks;
+        for (int w = 0; w < 2 && !st; ++w) st = fbs_solve(g, probs, pcg_iters, stream);
+        float t[3] = {0.0f, 0.0f, 0.0f};
+        for (int r = 0; r < 3 && !st; ++r) {
+            if (cudaEventRecord(ev[0], s) != cudaSuccess) st = FBS_ERR_CUDA;
+            if (!st) st = fbs_solve(g, probs, pcg_iters, stream);
+            if (!st && cudaEventRecord(ev[1], s) != cudaSuccess) st = FBS_ERR_CUDA;
+            if (!st && cudaEventSynchronize(ev[1]) != cudaSuccess) st = FBS_ERR_CUDA;
+            if (!st && cudaEventElapsedTime(&t[r], ev[0], ev[1]) != cudaSuccess) st = FBS_ERR_CUDA;
+        }
+        if (st) break;
+        std::sort(t, t + 3);
+        if (best < 0 || t[1] < best_ms) {
+            best = c;
+            best_ms = t[1];
+        }
+    }
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+    if (st || best < 0) {
+        g->persistent = saved_persistent;
+        g->force_persistent = saved_force;
+        g->pcg_form = saved_form;
+        g->phase_blocks = saved_blocks;
+        return st ? st : FBS_ERR_STATE;
+    }
+    g->persistent = cands[best].launch == FBS_PCG_PER_PHASE ? 0 : 1;
+    g->force_persistent = cands[best].launch == FBS_PCG_PERSISTENT ? 1 : 0;
+    g->pcg_form = cands[best].form;
+    g->phase_blocks = cands[best].blocks;
+    st = fbs_solve(g, probs, pcg_iters, stream);
+    if (out) {
+        out->pcg_launch = cands[best].launch;
+        out->pcg_form = cands[best].form;
+        out->phase_blocks = cands[best].blocks;
+        out->solve_ms = best_ms;
+        out->candidates = n;
+    }
+    return st;
 }
 
 fbs_status fbs_grid_info(const fbs_grid* g, int image, int64_t* n_vertices, int64_t* vertex_offset)

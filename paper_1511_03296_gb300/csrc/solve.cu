@@ -1744,7 +1744,7 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
                                             (const void*)pcg_single_kernel<2>,
                                             (const void*)pcg_single_kernel<4>};
         static const int occ_s[3] = {occupancy(fn_s[0]), occupancy(fn_s[1]), occupancy(fn_s[2])};
-        const int nb = persistent_blocks(occ_s[wi], A.nvt);
+        const int nb = persistent_blocks(occ_s[wi] * (P.block_mult > 1 ? P.block_mult : 1), A.nvt);
         for (int it = -1; it < P.pcg_iters; ++it) {
             const int last = it == P.pcg_iters - 1 ? 1 : 0;
             prof_begin(f_single, s);
@@ -1755,8 +1755,9 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
         }
         return cudaGetLastError();
     }
-    const int nb_p = persistent_blocks(occ_p[wi], A.nvt);
-    const int nb_u = persistent_blocks(occ_u[wi], A.nvt);
+    const int mult = P.block_mult > 1 ? P.block_mult : 1;
+    const int nb_p = persistent_blocks(occ_p[wi] * mult, A.nvt);
+    const int nb_u = persistent_blocks(occ_u[wi] * mult, A.nvt);
     for (int it = 0; it < P.pcg_iters; ++it) {
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];

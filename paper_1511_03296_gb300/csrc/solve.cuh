@@ -54,6 +54,7 @@ struct SolvePlan {
     unsigned* barrier;         // kBarrierWords words of grid-barrier state (persistent loop)
     int inject_timeout;        // preset the barrier counter so no wait completes (test)
     int single;                // 1: single-reduction PCG form (FP32, Cp <= 4, per-phase)
+    int block_mult;            // per-phase kernels: blocks = min(tiles, SMs x occupancy x this)
 };
 
 // A solve runs as segments: for each outer (IRLS) iteration a setup (splat,

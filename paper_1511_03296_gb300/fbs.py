@@ -24,9 +24,10 @@ STATUS_NAMES = {0: "FBS_OK", 1: "FBS_ERR_ARG", 2: "FBS_ERR_RANGE", 3: "FBS_ERR_O
 EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robust",
             "fbs_solve_backward", "fbs_grid_info", "fbs_grid_export", "fbs_grid_sync",
             "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read",
-            "fbs_set_option", "fbs_solve_static"]
+            "fbs_set_option", "fbs_solve_static", "fbs_autotune"]
 
 OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT, OPT_PCG_FORM = 1, 2, 3, 4
+OPT_PHASE_BLOCKS = 5
 VECTORS_AUTO, VECTORS_FP32, VECTORS_COMPENSATED = 0, 1, 2
 PCG_AUTO, PCG_PERSISTENT, PCG_PER_PHASE = 0, 1, 2
 PCG_FORM_STANDARD, PCG_FORM_SINGLE = 0, 1
@@ -203,6 +204,33 @@ def _problems(grid, t, c, lam, x, y):
     return probs
 
 
+class _TuneResult(ctypes.Structure):
+    _fields_ = [("pcg_launch", ctypes.c_int), ("pcg_form", ctypes.c_int),
+                ("phase_blocks", ctypes.c_int), ("solve_ms", ctypes.c_float),
+                ("candidates", ctypes.c_int)]
+
+
+def autotune(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25, x: Optional[List] = None,
+             y: Optional[List] = None, stream=None) -> dict:
+    """fbs_autotune: times the PCG launch configurations on this problem, leaves
+    the fastest set on the grid and returns it (the outputs hold its result).
+    The same settings can be applied to another grid of the same shape with
+    ``apply_tuning``."""
+    probs = _problems(grid, t, c, lam, x, y)
+    r = _TuneResult()
+    _check(load().fbs_autotune(grid.handle, probs, int(pcg_iters), _stream_ptr(stream),
+                               ctypes.byref(r)), "fbs_autotune")
+    return {"pcg_launch": r.pcg_launch, "pcg_form": r.pcg_form, "phase_blocks": r.phase_blocks,
+            "solve_ms": r.solve_ms, "candidates": r.candidates}
+
+
+def apply_tuning(grid: Grid, tuning: dict) -> None:
+    """Sets an autotune result's options on a grid."""
+    set_option(grid, OPT_PCG_LAUNCH, tuning["pcg_launch"])
+    set_option(grid, OPT_PCG_FORM, tuning["pcg_form"])
+    set_option(grid, OPT_PHASE_BLOCKS, tuning["phase_blocks"])
+
+
 def solve(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25, x: Optional[List] = None,
           y: Optional[List] = None, stream=None) -> None:
     """Forward solve; writes x (C x H x W) and/or y (C x V) per image."""
@@ -243,7 +271,9 @@ def solve_backward(grid: Grid, t: List, c: List, lam, yhat: List, dL_dx: List, d
 
 def set_option(grid: Grid, option: int, value: int) -> None:
     """OPT_VECTOR_PRECISION: VECTORS_AUTO / VECTORS_FP32 / VECTORS_COMPENSATED;
-    OPT_PCG_LAUNCH: PCG_PERSISTENT / PCG_PER_PHASE (see include/fbs.h)."""
+    OPT_PCG_LAUNCH: PCG_AUTO / PCG_PERSISTENT / PCG_PER_PHASE; OPT_PCG_FORM:
+    PCG_FORM_STANDARD / PCG_FORM_SINGLE; OPT_PHASE_BLOCKS: 1, 2, 4 (see
+    include/fbs.h)."""
     _check(load().fbs_set_option(grid.handle, int(option), int(value)), "fbs_set_option")
 
 

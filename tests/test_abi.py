@@ -64,6 +64,9 @@ def test_argument_errors_need_no_gpu(lib):
     lib.fbs_grid_info.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_void_p]
     assert lib.fbs_grid_info(None, 0, None, None) == 1
+    lib.fbs_autotune.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.c_void_p]
+    assert lib.fbs_autotune(None, None, 25, None, None) == 1
 
 
 def test_binding_fails_loudly_without_library(tmp_path):

@@ -399,3 +399,34 @@ def test_solve_with_escaped_neighbour_offsets():
     far = (nbr >= 0) & (np.abs(nbr.astype(np.int64) - v) > 32767)
     assert far.sum() > 0, "no escaped offsets: the case does not cover the path"
     _check_solve([inst])
+
+
+def test_autotune_picks_a_configuration_and_keeps_parity():
+    # the tuned configuration is left on the grid and its result is in the
+    # outputs; a later solve with it still matches the oracle
+    import torch
+    from paper_1511_03296_gb300 import fbs
+    insts = [_inst(50, 120, 160, (8.0, 4.0, 3.0), C=1, npoly=8),
+             _inst(51, 90, 200, (16.0, 8.0, 8.0), C=2, npoly=6)]
+    g = gpu_grid(insts, 2)
+    t = [to_dev(i.t) for i in insts]
+    c = [to_dev(i.c) for i in insts]
+    x = [torch.empty_like(tt) for tt in t]
+    r = fbs.autotune(g, t, c, [i.lam for i in insts], 25, x=x)
+    assert r["candidates"] >= 5 and r["solve_ms"] > 0
+    assert r["pcg_launch"] in (fbs.PCG_PER_PHASE, fbs.PCG_PERSISTENT)
+    assert r["pcg_form"] in (fbs.PCG_FORM_STANDARD, fbs.PCG_FORM_SINGLE)
+    assert r["phase_blocks"] in (1, 2, 4)
+    fbs.grid_sync(g)
+    for k, inst in enumerate(insts):
+        og = oracle_grid(inst, 2)
+        form = "single" if r["pcg_form"] == fbs.PCG_FORM_SINGLE else "standard"
+        with oracle.pcg_form(form):
+            _, ox = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
+        assert rel_l2(x[k].cpu().numpy().reshape(inst.channels, -1), ox) <= REL_L2_TOL
+    # the choice can be set on another grid of the same shape
+    g2 = gpu_grid(insts, 2)
+    fbs.apply_tuning(g2, r)
+    xs, ys = gpu_solve(g2, insts, 25)
+    for k in range(2):
+        assert np.array_equal(xs[k], x[k].cpu().numpy())
