@@ -201,6 +201,40 @@ def cpu_baseline(inst, seconds: float):
                       f"{sum(times):.1f} s, single-threaded FP64 C"}
 
 
+def _oracle_worker(args):
+    """One host process: repeats the oracle's 1080p step for `seconds`."""
+    seconds, = args
+    from paper_1511_03296_gb300 import synth
+    inst = synth.plain_1080p().instances[0]
+    n, t_all = 0, 0.0
+    t_end = time.perf_counter() + seconds
+    while True:
+        t0 = time.perf_counter()
+        oracle_step(inst)
+        t_all += time.perf_counter() - t0
+        n += 1
+        if time.perf_counter() >= t_end:
+            break
+    return n * inst.n_pixels, t_all
+
+
+def cpu_baseline_all_cores(seconds: float):
+    """The oracle on every host core at once, one independent image per process
+    (spawned: the parent holds a CUDA context).  Whole-host Mpix/s."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(seconds,)] * cores)
+    wall = time.perf_counter() - t0
+    pix = sum(r[0] for r in res)
+    busy = max(r[1] for r in res)
+    return {"value": pix / busy / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} processes, each repeating the 1920x1080 C=3 step for about "
+                      f"{seconds:.0f} s ({pix / 2073600:.0f} steps in all, {wall:.1f} s wall)"}
+
+
 def run_reference(args, dist):
     if dist.rank != 0:
         return
@@ -351,6 +385,41 @@ def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, seq
                                  traffic=PCG_TRAFFIC_RATIO_BATCHED * bytes_iter,
                                  traffic_source="ncu of the first 16 images, scaled by "
                                                 "traffic / algorithmic bytes")}
+
+
+def run_extra_robust(dist, flush, stream, peak, steps, warmup):
+    """The robust solver on a 1400 x 1000 disparity target (5 % outliers, c = 0
+    on a 10 % mask): grid, 2 bistochastisation sweeps, 10 IRLS x 25 PCG."""
+    import torch
+    from paper_1511_03296_gb300 import fbs, synth
+    wl = synth.robust_1400x1000(seed=rank_seed(3, dist.rank))
+    inst = wl.instances[0]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    yuv, t, c = dev(inst.yuv), dev(inst.t), dev(inst.c)
+    x = torch.empty_like(t)
+    info = {}
+
+    def step():
+        g = fbs.grid_build([yuv], inst.sigma_xy, inst.sigma_l, inst.sigma_uv)
+        fbs.bistochastize(g, BISTOCH_ITERS)
+        fbs.solve_robust(g, [t], [c], inst.lam, wl.sigma_gm, wl.irls_iters, PCG_ITERS, x=[x])
+        info["V"] = g.vertex_counts[0]
+        g.destroy()
+
+    fbs.profile_enable(2)
+    ms = time_steps(step, steps, warmup, flush, stream)
+    regions = fbs.profile_read()
+    fbs.profile_enable(0)
+    m = dist.max(sum(ms) / len(ms))
+    bytes_iter = algorithmic_bytes_per_pcg_iteration(info["V"], 1)
+    return {"workload": "robust 1400x1000, C=1, sigma=(4,4,4), lambda=0.25, sigma_gm=1, "
+                        "10 IRLS x 25 PCG iterations",
+            "pixels": inst.n_pixels, "vertices": info["V"],
+            "robust_mpix_s": whole_job_mpix(dist.world, inst.n_pixels, m), "ms_per_step": m,
+            "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
+                            for k, v in regions.items() if v[0]},
+            "pcg_roofline": dict(pcg_roofline(regions, wl.irls_iters, steps, bytes_iter, peak)
+                                 or {}, traffic=None)}
 
 
 def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
@@ -556,8 +625,10 @@ def run_ours(args, dist):
         xs = max(3, min(args.steps // 10, 20))
         line["batched"] = run_extra_batched(dist, flush, stream, peak, xs, 3)
         line["fwd_bwd"] = run_extra_fwd_bwd(dist, flush, stream, peak, xs, 3)
+        line["robust"] = run_extra_robust(dist, flush, stream, peak, max(3, xs // 2), 3)
     if dist.rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(synth.plain_1080p().instances[0], args.cpu_seconds)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.cpu_seconds / 2)
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
 
