@@ -10,8 +10,9 @@ arrays through ctypes and compiles the C file on first use.
 
 Parity status per function (what pins each one is in ``tests/test_oracle_pins.py``):
   keys, grid, bistochastize, splat, diag, apply_A, flat_init, pcg,
-  pcg_single, slice, solve, solve_robust, backward -- all pinned (closed
-  forms, brute force, dense linear algebra, invariants, finite differences).
+  pcg_single, pyramid, hierarchical (preconditioner and initialisation),
+  slice, solve, solve_robust, backward -- all pinned (closed forms, brute
+  force, dense linear algebra, invariants, finite differences).
 """
 from __future__ import annotations
 
@@ -74,6 +75,14 @@ def lib():
             L.fbso_pcg_single.restype = _I
             L.fbso_set_pcg_form.argtypes = [_I]
             L.fbso_set_pcg_form.restype = None
+            L.fbso_pyramid.argtypes = [_I64, _P, _I, _P, _P]
+            L.fbso_pyramid.restype = _I
+            L.fbso_set_hierarchical.argtypes = [_I, _I, _P, _P, _D, _D, _D, _D]
+            L.fbso_set_hierarchical.restype = None
+            L.fbso_hier_precond.argtypes = [_P, _P, _P]
+            L.fbso_hier_precond.restype = _I
+            L.fbso_hier_init.argtypes = [_P, _P, _P]
+            L.fbso_hier_init.restype = _I
             L.fbso_slice.argtypes = [_I64, _I64, _I, _P, _P, _P]
             L.fbso_slice.restype = None
             L.fbso_solve.argtypes = [_I64, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P]
@@ -215,6 +224,60 @@ class pcg_form:
     def __exit__(self, *exc):
         lib().fbso_set_pcg_form(0)
         _form_lock.release()
+
+
+MAX_LEVELS = 64
+
+
+def pyramid(vkey):
+    """Bilateral-space pyramid of a grid's vertex keys: (sizes, parent), with
+    sizes[k] the vertex count of level k (level 0 = the grid, the last level
+    one vertex) and parent the concatenated parent indices of levels
+    0..K-2."""
+    vkey = _c(vkey, np.uint64)
+    V = vkey.size
+    sizes = np.zeros(MAX_LEVELS, np.int64)
+    parent = np.zeros(max(2 * V, 1), np.int32)
+    K = lib().fbso_pyramid(V, _ptr(vkey), MAX_LEVELS, _ptr(sizes), _ptr(parent))
+    if K < 0:
+        raise OracleError(f"fbso_pyramid failed ({-K})")
+    sizes = sizes[:K].copy()
+    return sizes, parent[:int(sizes[:-1].sum())].copy()
+
+
+class hierarchical:
+    """``with oracle.hierarchical(grid): ...`` -- the solves inside use the
+    hierarchical preconditioner and initialisation of Sec. 4 on the grid's
+    bilateral-space pyramid; Jacobi and the flat initialisation afterwards."""
+
+    def __init__(self, g, prec=(2.0, 5.0), init=(4.0, 0.0)):
+        self.sizes, self.parent = pyramid(g.vkey)
+        self.prec, self.init_ab = prec, init
+
+    def __enter__(self):
+        L = lib()
+        _form_lock.acquire()
+        L.fbso_set_hierarchical(1, len(self.sizes), _ptr(self.sizes), _ptr(self.parent),
+                                self.prec[0], self.prec[1], self.init_ab[0], self.init_ab[1])
+        return self
+
+    def __exit__(self, *exc):
+        lib().fbso_set_hierarchical(0, 0, None, None, 0.0, 0.0, 0.0, 0.0)
+        _form_lock.release()
+
+    def precond(self, a, r):
+        """M_hier^-1 r for diag(A) = a (inside the context)."""
+        a = _c(a, np.float64); r = _c(r, np.float64)
+        s = np.empty_like(r)
+        _check(lib().fbso_hier_precond(_ptr(a), _ptr(r), _ptr(s)))
+        return s
+
+    def init(self, b, sc):
+        """The hierarchical initialisation of b with weights sc (inside the context)."""
+        b = _c(b, np.float64); sc = _c(sc, np.float64)
+        y = np.empty_like(b)
+        _check(lib().fbso_hier_init(_ptr(b), _ptr(sc), _ptr(y)))
+        return y
 
 
 def slice_(vid, y):

@@ -328,6 +328,247 @@ int fbso_pcg_single(int64_t V, const int32_t* nbr, const double* n, const double
     return FBSO_OK;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Bilateral-space pyramid (supplement, bilateral-space pyramids) and the  */
+/* hierarchical preconditioner and initialisation of Sec. 4.               */
+/* ---------------------------------------------------------------------- */
+/* Level 0 is the grid itself.  Level k+1 halves every key field of level  */
+/* k (reading: integer halving, floor -- it reaches a single vertex, as    */
+/* the pyramid's top must), de-duplicates in ascending packed order, and   */
+/* maps each level-k vertex to its parent.  Returns the number of levels K */
+/* (the last has one vertex), or -FBSO_ERR_OOM / -FBSO_ERR_ARG.  sizes[k]  */
+/* receives level k's size; parent receives, level after level, the      */
+/* parent index of every vertex of levels 0..K-2 (room for 2 V entries     */
+/* suffices: every level is at most as large as the one below).           */
+static uint64_t halve_key(uint64_t k)
+{
+    uint64_t out = 0;
+    for (int d = 0; d < 5; ++d) {
+        uint64_t f = (k >> kShift[d]) & FBSO_FIELD_MAX;
+        out |= (f >> 1) << kShift[d];
+    }
+    return out;
+}
+
+int fbso_pyramid(int64_t V, const uint64_t* vkey, int max_levels, int64_t* sizes,
+                 int32_t* parent)
+{
+    if (V <= 0 || max_levels < 1) return -FBSO_ERR_ARG;
+    uint64_t* cur = (uint64_t*)malloc((size_t)V * sizeof(uint64_t));
+    uint64_t* nxt = (uint64_t*)malloc((size_t)V * sizeof(uint64_t));
+    if (!cur || !nxt) { free(cur); free(nxt); return -FBSO_ERR_OOM; }
+    memcpy(cur, vkey, (size_t)V * sizeof(uint64_t));
+    int64_t L = V, off = 0;
+    int K = 1;
+    sizes[0] = V;
+    while (L > 1) {
+        if (K >= max_levels) { free(cur); free(nxt); return -FBSO_ERR_ARG; }
+        for (int64_t i = 0; i < L; ++i) nxt[i] = halve_key(cur[i]);
+        uint64_t* h = (uint64_t*)malloc((size_t)L * sizeof(uint64_t));
+        if (!h) { free(cur); free(nxt); return -FBSO_ERR_OOM; }
+        memcpy(h, nxt, (size_t)L * sizeof(uint64_t));
+        qsort(nxt, (size_t)L, sizeof(uint64_t), cmp_u64);
+        int64_t L2 = 0;
+        for (int64_t i = 0; i < L; ++i)
+            if (i == 0 || nxt[i] != nxt[i - 1]) nxt[L2++] = nxt[i];
+        for (int64_t i = 0; i < L; ++i) parent[off + i] = (int32_t)find_key(nxt, L2, h[i]);
+        free(h);
+        off += L;
+        sizes[K++] = L2;
+        uint64_t* t = cur; cur = nxt; nxt = t;
+        L = L2;
+    }
+    free(cur); free(nxt);
+    return K;
+}
+
+/* The pyramid the solves use while the hierarchical preconditioner is on. */
+static struct {
+    int on;
+    int K;
+    const int64_t* sizes;
+    const int32_t* parent;
+    double pa, pb, ia, ib;   /* (alpha, beta) of the preconditioner and of the initialisation */
+} g_pyr;
+
+/* The paper uses (alpha, beta) = (2, 5) for the preconditioner and (4, 0)
+ * for the initialisation. */
+void fbso_set_hierarchical(int on, int K, const int64_t* sizes, const int32_t* parent,
+                           double prec_alpha, double prec_beta, double init_alpha,
+                           double init_beta)
+{
+    g_pyr.on = on;
+    g_pyr.K = K;
+    g_pyr.sizes = sizes;
+    g_pyr.parent = parent;
+    g_pyr.pa = prec_alpha;
+    g_pyr.pb = prec_beta;
+    g_pyr.ia = init_alpha;
+    g_pyr.ib = init_beta;
+}
+
+/* P: level values z[0..K) from bilateral-space y (level 0 = y; level k+1
+ * sums its children), into one array of sum(sizes) entries. */
+static void pyr_lift(const double* y, double* z)
+{
+    int64_t off = 0;
+    for (int64_t i = 0; i < g_pyr.sizes[0]; ++i) z[i] = y[i];
+    for (int k = 0; k + 1 < g_pyr.K; ++k) {
+        const int64_t L = g_pyr.sizes[k], up = off + L;
+        for (int64_t j = 0; j < g_pyr.sizes[k + 1]; ++j) z[up + j] = 0.0;
+        for (int64_t i = 0; i < L; ++i) z[up + g_pyr.parent[off + i]] += z[off + i];
+        off = up;
+    }
+}
+
+/* P^T: y = sum over levels of the level values broadcast down to level 0
+ * (top down: each level adds its parent's accumulated value). */
+static void pyr_collapse(double* z, double* y)
+{
+    int64_t offs[64];
+    offs[0] = 0;
+    for (int k = 1; k < g_pyr.K; ++k) offs[k] = offs[k - 1] + g_pyr.sizes[k - 1];
+    for (int k = g_pyr.K - 2; k >= 0; --k)
+        for (int64_t i = 0; i < g_pyr.sizes[k]; ++i)
+            z[offs[k] + i] += z[offs[k + 1] + g_pyr.parent[offs[k] + i]];
+    for (int64_t i = 0; i < g_pyr.sizes[0]; ++i) y[i] = z[i];
+}
+
+static int64_t pyr_total(void)
+{
+    int64_t t = 0;
+    for (int k = 0; k < g_pyr.K; ++k) t += g_pyr.sizes[k];
+    return t;
+}
+
+/* level weight: 1 at level 0, alpha^-(beta + k) above */
+static double level_weight(int k, double alpha, double beta)
+{
+    return k == 0 ? 1.0 : pow(alpha, -(beta + k));
+}
+
+/* Per-coefficient scale of M_hier^-1 = P^T(w o P(1) o P(.) / P(diag A))
+ * (Sec. 4); 0 where P(diag A) <= 0. */
+static int hier_coef(const double* a, double* coef)
+{
+    const int64_t T = pyr_total(), V = g_pyr.sizes[0];
+    double* one = (double*)malloc((size_t)V * sizeof(double));
+    double* cnt = (double*)malloc((size_t)T * sizeof(double));
+    if (!one || !cnt) { free(one); free(cnt); return FBSO_ERR_OOM; }
+    for (int64_t i = 0; i < V; ++i) one[i] = 1.0;
+    pyr_lift(one, cnt);
+    pyr_lift(a, coef);
+    int64_t off = 0;
+    for (int k = 0; k < g_pyr.K; ++k) {
+        const double w = level_weight(k, g_pyr.pa, g_pyr.pb);
+        for (int64_t i = 0; i < g_pyr.sizes[k]; ++i) {
+            const double dA = coef[off + i];
+            coef[off + i] = dA > 0.0 ? w * cnt[off + i] / dA : 0.0;
+        }
+        off += g_pyr.sizes[k];
+    }
+    free(one); free(cnt);
+    return FBSO_OK;
+}
+
+/* s = M_hier^-1 r */
+static void hier_apply(const double* coef, const double* r, double* s, double* work)
+{
+    const int64_t T = pyr_total();
+    pyr_lift(r, work);
+    for (int64_t i = 0; i < T; ++i) work[i] *= coef[i];
+    pyr_collapse(work, s);
+}
+
+/* y = P^T(w o P(b) / P(1)) / P^T(w o P(sc) / P(1)) (the push-pull
+ * initialisation of Sec. 4); 0 where the denominator is 0. */
+static int hier_init(const double* b, const double* sc, double* y)
+{
+    const int64_t T = pyr_total(), V = g_pyr.sizes[0];
+    double* one = (double*)malloc((size_t)V * sizeof(double));
+    double* cnt = (double*)malloc((size_t)T * sizeof(double));
+    double* zn = (double*)malloc((size_t)T * sizeof(double));
+    double* zd = (double*)malloc((size_t)T * sizeof(double));
+    double* den = (double*)malloc((size_t)V * sizeof(double));
+    if (!one || !cnt || !zn || !zd || !den) {
+        free(one); free(cnt); free(zn); free(zd); free(den);
+        return FBSO_ERR_OOM;
+    }
+    for (int64_t i = 0; i < V; ++i) one[i] = 1.0;
+    pyr_lift(one, cnt);
+    pyr_lift(b, zn);
+    pyr_lift(sc, zd);
+    int64_t off = 0;
+    for (int k = 0; k < g_pyr.K; ++k) {
+        const double w = level_weight(k, g_pyr.ia, g_pyr.ib);
+        for (int64_t i = 0; i < g_pyr.sizes[k]; ++i) {
+            zn[off + i] *= w / cnt[off + i];
+            zd[off + i] *= w / cnt[off + i];
+        }
+        off += g_pyr.sizes[k];
+    }
+    pyr_collapse(zn, y);
+    pyr_collapse(zd, den);
+    for (int64_t i = 0; i < V; ++i) y[i] = den[i] > 0.0 ? y[i] / den[i] : 0.0;
+    free(one); free(cnt); free(zn); free(zd); free(den);
+    return FBSO_OK;
+}
+
+/* Alg. 2 with M^-1 = M_hier^-1. */
+static int pcg_hier(int64_t V, const int32_t* nbr, const double* n, const double* a, double lam,
+                    const double* b, double* y, int iters)
+{
+    const int64_t T = pyr_total();
+    size_t sz = (size_t)(V > 0 ? V : 1) * sizeof(double);
+    double* r = (double*)malloc(sz);
+    double* d = (double*)malloc(sz);
+    double* q = (double*)malloc(sz);
+    double* s = (double*)malloc(sz);
+    double* coef = (double*)malloc((size_t)T * sizeof(double));
+    double* work = (double*)malloc((size_t)T * sizeof(double));
+    int st = (!r || !d || !q || !s || !coef || !work) ? FBSO_ERR_OOM : hier_coef(a, coef);
+    if (!st) {
+        fbso_apply_A(V, nbr, n, a, lam, y, q);
+        for (int64_t v = 0; v < V; ++v) r[v] = b[v] - q[v];
+        hier_apply(coef, r, d, work);
+        double delta = dot(V, r, d);
+        for (int i = 0; i < iters; ++i) {
+            fbso_apply_A(V, nbr, n, a, lam, d, q);
+            double dq = dot(V, d, q);
+            double alpha = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
+            for (int64_t v = 0; v < V; ++v) y[v] += alpha * d[v];
+            for (int64_t v = 0; v < V; ++v) r[v] -= alpha * q[v];
+            hier_apply(coef, r, s, work);
+            double delta_old = delta;
+            delta = dot(V, r, s);
+            double beta = delta_old != 0.0 ? delta / delta_old : 0.0;
+            for (int64_t v = 0; v < V; ++v) d[v] = s[v] + beta * d[v];
+        }
+    }
+    free(r); free(d); free(q); free(s); free(coef); free(work);
+    return st;
+}
+
+/* The hierarchical preconditioner applied to r (tests) */
+int fbso_hier_precond(const double* a, const double* r, double* s)
+{
+    if (!g_pyr.on) return FBSO_ERR_ARG;
+    const int64_t T = pyr_total();
+    double* coef = (double*)malloc((size_t)T * sizeof(double));
+    double* work = (double*)malloc((size_t)T * sizeof(double));
+    int st = (!coef || !work) ? FBSO_ERR_OOM : hier_coef(a, coef);
+    if (!st) hier_apply(coef, r, s, work);
+    free(coef); free(work);
+    return st;
+}
+
+/* The hierarchical initialisation of b with weights sc (tests) */
+int fbso_hier_init(const double* b, const double* sc, double* y)
+{
+    if (!g_pyr.on) return FBSO_ERR_ARG;
+    return hier_init(b, sc, y);
+}
+
 /* Which form the solves below use: 0 = Alg. 2 as printed (fbso_pcg),
  * 1 = the single-reduction form (fbso_pcg_single).  Process-wide; the test
  * suite sets it around the calls that need it. */
@@ -338,8 +579,17 @@ void fbso_set_pcg_form(int form) { g_pcg_form = form; }
 static int pcg_run(int64_t V, const int32_t* nbr, const double* n, const double* a,
                    const double* minv, double lam, const double* b, double* y, int iters)
 {
+    if (g_pyr.on) return pcg_hier(V, nbr, n, a, lam, b, y, iters);
     return g_pcg_form == 1 ? fbso_pcg_single(V, nbr, n, a, minv, lam, b, y, iters)
                            : fbso_pcg(V, nbr, n, a, minv, lam, b, y, iters);
+}
+
+/* initial state: the flat initialisation, or the hierarchical one */
+static int init_run(int64_t V, const double* b, const double* sc, double* y)
+{
+    if (g_pyr.on) return hier_init(b, sc, y);
+    fbso_flat_init(V, b, sc, y);
+    return FBSO_OK;
 }
 
 void fbso_slice(int64_t N, int64_t V, int C, const uint32_t* vid, const double* y, double* x)
@@ -365,8 +615,8 @@ static int solve_impl(int64_t N, int64_t V, int C, const uint32_t* vid, const ui
     fbso_diag(V, m, nbr, n, sc, lam, a, minv);
     int st = FBSO_OK;
     for (int ch = 0; ch < C && !st; ++ch) {
-        fbso_flat_init(V, b + (int64_t)ch * V, sc, y + (int64_t)ch * V);
-        st = pcg_run(V, nbr, n, a, minv, lam, b + (int64_t)ch * V, y + (int64_t)ch * V, pcg_iters);
+        st = init_run(V, b + (int64_t)ch * V, sc, y + (int64_t)ch * V);
+        if (!st) st = pcg_run(V, nbr, n, a, minv, lam, b + (int64_t)ch * V, y + (int64_t)ch * V, pcg_iters);
     }
     if (!st && x) fbso_slice(N, V, C, vid, y, x);
     free(b); free(sc); free(a); free(minv);
@@ -440,8 +690,10 @@ int fbso_backward(int64_t N, int64_t V, int C, const uint32_t* vid, const uint32
     fbso_diag(V, m, nbr, n, sc, lam, a, minv);
     int st = FBSO_OK;
     for (int ch = 0; ch < C && !st; ++ch) {
-        fbso_flat_init(V, g + (int64_t)ch * V, sc, z + (int64_t)ch * V);
-        st = pcg_run(V, nbr, n, a, minv, lam, g + (int64_t)ch * V, z + (int64_t)ch * V, pcg_iters);
+        st = init_run(V, g + (int64_t)ch * V, sc, z + (int64_t)ch * V);
+        if (!st)
+            st = pcg_run(V, nbr, n, a, minv, lam, g + (int64_t)ch * V, z + (int64_t)ch * V,
+                         pcg_iters);
     }
     if (!st) {
         for (int64_t i = 0; i < N; ++i) dc[i] = 0.0;

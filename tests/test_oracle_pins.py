@@ -452,3 +452,93 @@ def test_pcg_form_context_restores_standard():
     y_again, _ = oracle.solve(g, inst.t, inst.c, inst.lam, 5)
     assert np.array_equal(y_std, y_again)
     assert np.allclose(y_one, y_std, rtol=1e-9, atol=1e-9 * np.abs(y_std).max())
+
+
+# ---- bilateral-space pyramid and the hierarchical preconditioner (Sec. 4) ----
+
+def _halve(keys):
+    out = np.zeros_like(keys)
+    for shift in (48, 36, 24, 12, 0):
+        out |= ((keys >> np.uint64(shift)) & np.uint64(4095)) >> np.uint64(1) << np.uint64(shift)
+    return out
+
+
+def test_pyramid_matches_brute_force():
+    inst = synth.make_tiny(60, 40, 56, 5, 1)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    sizes, parent = oracle.pyramid(g.vkey)
+    keys, off = g.vkey.astype(np.uint64), 0
+    for k in range(len(sizes) - 1):
+        assert keys.size == sizes[k]
+        h = _halve(keys)
+        up = np.unique(h)
+        assert np.array_equal(parent[off:off + keys.size], np.searchsorted(up, h))
+        off += keys.size
+        keys = up
+    assert sizes[-1] == 1 and keys.size == 1
+
+
+def _hier_problem(seed=61, h=24, w=32, C=1):
+    inst = synth.make_tiny(seed, h, w, 4, C)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    b, sc = oracle.splat(g.vid, inst.t, inst.c, g.V)
+    a, minv = oracle.diag(g.m, g.nbr, g.n, sc, inst.lam)
+    return inst, g, b, sc, a, minv
+
+
+def test_hier_preconditioner_is_symmetric_positive_definite():
+    inst, g, b, sc, a, minv = _hier_problem()
+    with oracle.hierarchical(g) as H:
+        M = np.stack([H.precond(a, e) for e in np.eye(g.V)], axis=1)
+    assert np.allclose(M, M.T, rtol=1e-12, atol=1e-14 * np.abs(M).max())
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_hier_preconditioner_degenerates_to_jacobi():
+    # coarse levels weighted by alpha^-(beta + k): with beta large only the
+    # finest level (Jacobi) remains
+    inst, g, b, sc, a, minv = _hier_problem()
+    r = np.random.default_rng(1).normal(size=g.V)
+    with oracle.hierarchical(g, prec=(2.0, 80.0), init=(4.0, 80.0)) as H:
+        s = H.precond(a, r)
+        y = H.init(b[0], sc)
+    assert np.allclose(s, minv * r, rtol=1e-12, atol=0)
+    assert np.allclose(y, oracle.flat_init(b[0], sc), rtol=1e-12, atol=0)
+
+
+def test_hier_init_keeps_a_target_proportional_to_confidence():
+    # b = kappa S c: numerator and denominator of the push-pull differ by kappa
+    inst, g, b, sc, a, minv = _hier_problem()
+    with oracle.hierarchical(g) as H:
+        y = H.init(37.5 * sc, sc)
+    assert np.allclose(y[sc > 0], 37.5, rtol=1e-12, atol=0)
+
+
+def test_hier_pcg_converged_matches_dense_solve():
+    inst, g, S, B, A, b, sc = _problem(iters=2, lam=16.0)
+    with oracle.hierarchical(g):
+        y, _ = oracle.solve(g, inst.t, inst.c, inst.lam, 400)
+    ystar = np.linalg.solve(A, b.T).T
+    assert np.allclose(y, ystar, rtol=1e-9, atol=1e-9 * np.abs(ystar).max())
+
+
+def test_hier_converges_faster_than_jacobi():
+    # the paper's claim (Sec. 4, figure on preconditioning and initialisation):
+    # at equal iteration counts the hierarchical preconditioner and
+    # initialisation leave a smaller objective gap than Jacobi with the flat
+    # initialisation
+    sig, lam = (8.0, 4.0, 3.0), 128.0
+    inst = synth.make_tiny(70, 120, 160, 10, 1, sig, lam)
+    g = oracle.build_grid(inst.yuv, *sig, 2)
+    b, sc = oracle.splat(g.vid, inst.t, inst.c, g.V)
+    a, minv = oracle.diag(g.m, g.nbr, g.n, sc, lam)
+
+    def loss(y):
+        return 0.5 * y @ oracle.apply_A(g.nbr, g.n, a, lam, y) - b[0] @ y
+
+    f_star = loss(oracle.solve(g, inst.t, inst.c, lam, 2000)[0][0])
+    for k in (10, 25):
+        yj, _ = oracle.solve(g, inst.t, inst.c, lam, k)
+        with oracle.hierarchical(g):
+            yh, _ = oracle.solve(g, inst.t, inst.c, lam, k)
+        assert loss(yh[0]) - f_star < 0.5 * (loss(yj[0]) - f_star), k
