@@ -178,6 +178,19 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *                            for FP32 vectors when no image has more than 4
  *                            channels (per-phase launches); other solves keep
  *                            the standard form.
+ * FBS_OPT_PRECONDITIONER: the preconditioner and initial state (Sec. 4):
+ *   FBS_PRECOND_JACOBI        (default) M^-1 = diag(A)^-1 and the flat
+ *                             initialisation y0 = S(c o t) / S c.
+ *   FBS_PRECOND_HIERARCHICAL  the bilateral-space pyramid (supplement):
+ *                             M^-1 = P^T(w o P(1) o P(.) / P(diag A)) with
+ *                             (alpha, beta) = (2, 5) and the push-pull
+ *                             initialisation with (4, 0).  The pyramid is
+ *                             built on the host on first use (one device
+ *                             synchronisation; FBS_ERR_STATE if that first
+ *                             use is inside a stream capture).  Applies when
+ *                             every image has the same channel count of at
+ *                             most 4; other solves use Jacobi.  Per-phase
+ *                             launches, standard PCG form.
  * FBS_OPT_PHASE_BLOCKS: 1 (default), 2 or 4 -- the per-phase PCG kernels
  *   launch min(tiles, SMs x resident blocks per SM x value) blocks; above 1
  *   the blocks take shorter runs of tiles in several waves.
@@ -187,7 +200,8 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *   FBS_ERR_TIMEOUT and returns (a test of the failure path; one-shot).
  */
 enum { FBS_OPT_VECTOR_PRECISION = 1, FBS_OPT_PCG_LAUNCH = 2, FBS_OPT_INJECT_BARRIER_TIMEOUT = 3,
-       FBS_OPT_PCG_FORM = 4, FBS_OPT_PHASE_BLOCKS = 5 };
+       FBS_OPT_PCG_FORM = 4, FBS_OPT_PHASE_BLOCKS = 5, FBS_OPT_PRECONDITIONER = 6 };
+enum { FBS_PRECOND_JACOBI = 0, FBS_PRECOND_HIERARCHICAL = 1 };
 enum { FBS_VECTORS_AUTO = 0, FBS_VECTORS_FP32 = 1, FBS_VECTORS_COMPENSATED = 2 };
 enum { FBS_PCG_AUTO = 0, FBS_PCG_PERSISTENT = 1, FBS_PCG_PER_PHASE = 2 };
 enum { FBS_PCG_FORM_STANDARD = 0, FBS_PCG_FORM_SINGLE = 1 };

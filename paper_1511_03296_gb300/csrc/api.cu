@@ -257,6 +257,21 @@ struct fbs_grid {
     int force_persistent = 0;
     int pcg_form = FBS_PCG_FORM_STANDARD;
     int phase_blocks = 1;
+    int precond = FBS_PRECOND_JACOBI;
+    // bilateral-space pyramid (built on the first hierarchical solve)
+    int pyr_K = 0;
+    int64_t pyr_off[kMaxLevels + 1] = {0};
+    int32_t* pyr_parent = nullptr;
+    int32_t* pyr_child_off = nullptr;
+    int32_t* pyr_child_idx = nullptr;
+    uint16_t* pyr_vimg = nullptr;
+    float* pyr_cnt = nullptr;
+    float* pyr_cinit = nullptr;
+    float* pyr_coef = nullptr;
+    float* pyr_dg = nullptr;
+    float* pyr_scv = nullptr;
+    float* pyr_buf = nullptr;
+    float* pyr_buf2 = nullptr;
     int inject_timeout = 0;
     float* a = nullptr;
     float2* nm = nullptr;
@@ -299,6 +314,9 @@ void free_grid_memory(fbs_grid* g, cudaStream_t s)
     dfree(g->gt, s); dfree(g->gt_voff, s);
     dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s); dfree(g->part, s);
     dfree(g->inst, s); dfree(g->barrier, s);
+    dfree(g->pyr_parent, s); dfree(g->pyr_child_off, s); dfree(g->pyr_child_idx, s);
+    dfree(g->pyr_vimg, s); dfree(g->pyr_cnt, s); dfree(g->pyr_cinit, s); dfree(g->pyr_coef, s); dfree(g->pyr_dg, s);
+    dfree(g->pyr_scv, s); dfree(g->pyr_buf, s); dfree(g->pyr_buf2, s);
 }
 
 fbs_status latched(uint32_t bits)
@@ -648,6 +666,138 @@ fbs_status run_segments(fbs_grid* g, const SolveArgs& A, const SolvePlan& P, cud
     return cuda_status(e);
 }
 
+// halves every 12-bit key field (floor): the parent key one pyramid level up
+uint64_t halve_key(uint64_t k)
+{
+    static const int shift[5] = {48, 36, 24, 12, 0};
+    uint64_t out = 0;
+    for (int d = 0; d < 5; ++d) out |= (((k >> shift[d]) & kFieldMax) >> 1) << shift[d];
+    return out;
+}
+
+// The bilateral-space pyramid of the grid (supplement, bilateral-space
+// pyramids), built once on the host from the vertex keys: per image, level
+// k+1 is the sorted distinct halved keys of level k (floor halving reaches a
+// single vertex); the images' levels are concatenated level by level (an
+// image that reached its top keeps one vertex), with each vertex's parent,
+// each vertex's children in ascending order (so the device sums are
+// deterministic), the counts P(1) and the initialisation weights
+// w_init(k) / P(1), w_init(k) = 4^-k (alpha = 4, beta = 0).
+fbs_status build_pyramid(fbs_grid* g, cudaStream_t s)
+{
+    const int64_t V = g->Vtot;
+    std::vector<uint64_t> keys(V);
+    cudaError_t e = cudaMemcpyAsync(keys.data(), g->vkey, V * sizeof(uint64_t),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int n = g->n_images;
+    // per image, per level: sorted keys and the parent of each vertex
+    std::vector<std::vector<std::vector<uint64_t>>> lk(n);
+    std::vector<std::vector<std::vector<int32_t>>> lp(n);
+    int K = 1;
+    for (int im = 0; im < n; ++im) {
+        lk[im].push_back(std::vector<uint64_t>(keys.begin() + g->voff[im],
+                                               keys.begin() + g->voff[im + 1]));
+        while (lk[im].back().size() > 1) {
+            const std::vector<uint64_t>& cur = lk[im].back();
+            std::vector<uint64_t> h(cur.size());
+            for (size_t i = 0; i < cur.size(); ++i) h[i] = halve_key(cur[i]);
+            std::vector<uint64_t> up(h);
+            std::sort(up.begin(), up.end());
+            up.erase(std::unique(up.begin(), up.end()), up.end());
+            std::vector<int32_t> par(cur.size());
+            for (size_t i = 0; i < cur.size(); ++i)
+                par[i] = (int32_t)(std::lower_bound(up.begin(), up.end(), h[i]) - up.begin());
+            lp[im].push_back(std::move(par));
+            lk[im].push_back(std::move(up));
+        }
+        K = std::max(K, (int)lk[im].size());
+    }
+    if (K > kMaxLevels) return FBS_ERR_ARG;
+    // level sizes per image (an image past its top keeps its single vertex)
+    auto lsize = [&](int im, int k) -> int64_t {
+        return k < (int)lk[im].size() ? (int64_t)lk[im][k].size() : 1;
+    };
+    std::vector<std::vector<int64_t>> ioff(K, std::vector<int64_t>(n + 1, 0));   // image offsets in a level
+    int64_t off[kMaxLevels + 1];
+    off[0] = 0;
+    for (int k = 0; k < K; ++k) {
+        for (int im = 0; im < n; ++im) ioff[k][im + 1] = ioff[k][im] + lsize(im, k);
+        off[k + 1] = off[k] + ioff[k][n];
+    }
+    const int64_t T = off[K];
+    std::vector<int32_t> parent(off[K - 1] > 0 ? off[K - 1] : 1, 0);
+    for (int k = 0; k + 1 < K; ++k)
+        for (int im = 0; im < n; ++im)
+            for (int64_t i = 0; i < lsize(im, k); ++i) {
+                const int32_t pl = k < (int)lp[im].size() ? lp[im][k][i] : 0;
+                parent[off[k] + ioff[k][im] + i] = (int32_t)(ioff[k + 1][im] + pl);
+            }
+    // children lists (counting sort by parent keeps children ascending)
+    std::vector<int32_t> child_off(T - off[1] + 1, 0), child_idx(std::max<int64_t>(off[K - 1], 1));
+    for (int k = 0; k + 1 < K; ++k)
+        for (int64_t i = 0; i < off[k + 1] - off[k]; ++i)
+            ++child_off[off[k + 1] - off[1] + parent[off[k] + i] + 1];
+    for (int64_t g2 = 0; g2 < T - off[1]; ++g2) child_off[g2 + 1] += child_off[g2];
+    {
+        std::vector<int32_t> fill(child_off.begin(), child_off.end() - 1);
+        for (int k = 0; k + 1 < K; ++k)
+            for (int64_t i = 0; i < off[k + 1] - off[k]; ++i)
+                child_idx[fill[off[k + 1] - off[1] + parent[off[k] + i]]++] = (int32_t)i;
+    }
+    // counts and initialisation weights
+    std::vector<double> cnt(T, 1.0);
+    for (int k = 1; k < K; ++k)
+        for (int64_t p = 0; p < off[k + 1] - off[k]; ++p) {
+            double c = 0.0;
+            const int64_t gg = off[k] + p - off[1];
+            for (int32_t j = child_off[gg]; j < child_off[gg + 1]; ++j)
+                c += cnt[off[k - 1] + child_idx[j]];
+            cnt[off[k] + p] = c;
+        }
+    std::vector<float> cinit(T), cntf(T);
+    for (int64_t i = 0; i < T; ++i) cntf[i] = (float)cnt[i];   // integers below 2^24: exact
+    for (int k = 0; k < K; ++k) {
+        const double w = k == 0 ? 1.0 : pow(4.0, -(double)k);
+        for (int64_t i = off[k]; i < off[k + 1]; ++i) cinit[i] = (float)(w / cnt[i]);
+    }
+    std::vector<uint16_t> vimg(V);
+    for (int im = 0; im < n; ++im)
+        for (int64_t v = g->voff[im]; v < g->voff[im + 1]; ++v) vimg[v] = (uint16_t)im;
+    // device copies
+    if ((e = dalloc(&g->pyr_parent, parent.size(), s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_child_off, child_off.size(), s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_child_idx, child_idx.size(), s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_vimg, (size_t)V, s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_cnt, (size_t)T, s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_cinit, (size_t)T, s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_coef, (size_t)T, s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_dg, (size_t)V, s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_scv, (size_t)V, s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_buf, (size_t)std::max<int64_t>(T - V, 1) * 4, s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_buf2, (size_t)std::max<int64_t>(T - V, 1), s)) != cudaSuccess)
+        return cuda_status(e);
+    const struct {
+        void* dst;
+        const void* src;
+        size_t bytes;
+    } cp[] = {{g->pyr_parent, parent.data(), parent.size() * sizeof(int32_t)},
+              {g->pyr_child_off, child_off.data(), child_off.size() * sizeof(int32_t)},
+              {g->pyr_child_idx, child_idx.data(), child_idx.size() * sizeof(int32_t)},
+              {g->pyr_vimg, vimg.data(), vimg.size() * sizeof(uint16_t)},
+              {g->pyr_cnt, cntf.data(), cntf.size() * sizeof(float)},
+              {g->pyr_cinit, cinit.data(), cinit.size() * sizeof(float)}};
+    for (const auto& c : cp)
+        if ((e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess)
+            return cuda_status(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e);
+    g->pyr_K = K;
+    for (int k = 0; k <= K; ++k) g->pyr_off[k] = off[k];
+    return FBS_OK;
+}
+
 // Sizes the workspace, uploads the image descriptors (if they changed) and
 // runs one solve plan.
 fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStream_t s)
@@ -686,7 +836,15 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     // the single-reduction form for FP32 vectors and images of at most 4
     // channels; it runs as per-phase launches
     plan.single = g->pcg_form == FBS_PCG_FORM_SINGLE && !plan.comp && cmax <= 4 ? 1 : 0;
-    plan.persistent = g->persistent && !capturing(s) && !plan.single ? 1 : 0;
+    // hierarchical preconditioner: every image with the same Cp <= 4
+    plan.hier = 0;
+    if (g->precond == FBS_PRECOND_HIERARCHICAL && cmax <= 4) {
+        bool uniform = true;
+        for (int k = 1; k < g->n_images; ++k) uniform &= inst[k].Cp == inst[0].Cp;
+        plan.hier = uniform ? 1 : 0;
+    }
+    if (plan.hier) plan.single = 0;
+    plan.persistent = g->persistent && !capturing(s) && !plan.single && !plan.hier ? 1 : 0;
     plan.block_mult = g->phase_blocks;
     plan.force_persistent = g->force_persistent;
     plan.inject_timeout = plan.persistent ? g->inject_timeout : 0;
@@ -750,6 +908,28 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.part_mu[0] = A.part_dq;
     A.part_mu[1] = g->part + 3 * g->cap_part;
     A.err = g->err;
+    if (plan.hier) {
+        if (g->pyr_K == 0) {
+            if (cap) return FBS_ERR_STATE;          // first hierarchical solve inside capture
+            fbs_status pst = build_pyramid(g, s);
+            if (pst) return pst;
+        }
+        A.pyr.K = g->pyr_K;
+        A.pyr.W = inst[0].Cp;
+        for (int k = 0; k <= g->pyr_K; ++k) A.pyr.off[k] = g->pyr_off[k];
+        A.pyr.parent = g->pyr_parent;
+        A.pyr.child_off = g->pyr_child_off;
+        A.pyr.child_idx = g->pyr_child_idx;
+        A.pyr.vimg = g->pyr_vimg;
+        A.pyr.cnt = g->pyr_cnt;
+        A.pyr.cinit = g->pyr_cinit;
+        A.pyr.coef = g->pyr_coef;
+        A.pyr.dg = g->pyr_dg;
+        A.pyr.scv = g->pyr_scv;
+        A.pyr.buf = g->pyr_buf;
+        A.pyr.buf2 = g->pyr_buf2;
+        A.pyr.z = A.aux[0];
+    }
     // AUTO: the resident loop for small batches; per-phase (graph) otherwise
     if (plan.persistent && !plan.force_persistent && !resident_preferred(A, plan))
         plan.persistent = 0;
@@ -849,6 +1029,11 @@ fbs_status fbs_set_option(fbs_grid* g, int option, int value)
     if (option == FBS_OPT_INJECT_BARRIER_TIMEOUT) {
         if (value != 0 && value != 1) return FBS_ERR_ARG;
         g->inject_timeout = value;
+        return FBS_OK;
+    }
+    if (option == FBS_OPT_PRECONDITIONER) {
+        if (value != FBS_PRECOND_JACOBI && value != FBS_PRECOND_HIERARCHICAL) return FBS_ERR_ARG;
+        g->precond = value;
         return FBS_OK;
     }
     if (option == FBS_OPT_PHASE_BLOCKS) {

@@ -290,6 +290,10 @@ __device__ __forceinline__ void vertex_epilogue(const SolveArgs& A, const InstDe
     const double diag = has_nbr ? lam * ((double)cnt - 10.0 * nv * nv) + scd : scd;
     A.a[v] = (float)(rem + scd);
     A.nm[v] = make_float2((float)nv, diag > 0.0 ? (float)(1.0 / diag) : 0.0f);
+    if (A.pyr.K > 0) {                  // hierarchical preconditioner: diag(A) and S c
+        A.pyr.dg[v] = (float)diag;
+        A.pyr.scv[v] = (float)scd;
+    }
 }
 
 // Splat weight and value of one pixel (index i within its image) for channel
@@ -631,17 +635,19 @@ residual_kernel(SolveArgs A)
 // (phase 2 recomputes it exactly from d).  With fetch (the tile starts the
 // block's run over an image) the CG scalars are formed first, after the
 // tile's neighbour ids and own values have been requested.
-template <int W, bool COMP, bool CO>
+template <int W, bool COMP, bool CO, bool HIER = false>
 __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
                                            const float* __restrict__ dold,
                                            float* __restrict__ dnew, bool first, PhaseSmem& S,
                                            DF (&run)[4], bool fetch, const float2* in, int it)
 {
+    // HIER: the preconditioned residual z = M_hier^-1 r is a vector of its own
+    // (the pyramid passes after each update), read in place of M^-1 r
     const int v = (int)vt.v0 + (int)threadIdx.x;
     const bool valid = v < (int)vt.v1;
     const int vs = valid ? v : (int)vt.v0;
     const int64_t off = I.vec_base - I.voff * W;        // element (ch, u) at off + u W + ch
-    const float* __restrict__ rb = A.r + off;
+    const float* __restrict__ rb = (HIER ? A.pyr.z : A.r) + off;
     const float* __restrict__ ob = dold + off;
     const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
     const float av = valid ? A.a[v] : 0.0f;
@@ -654,10 +660,11 @@ __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I,
     if (!first) ldw<W, CO>(ob + vs * W, ov);
     if (fetch) phase_scalars<1, CO, W>(A, I, in, it, S);
     float beta[W], dv[W];
+    const float mv = HIER ? 1.0f : nmv.y;
 #pragma unroll
     for (int k = 0; k < W; ++k) {
         beta[k] = S.sf[k];
-        dv[k] = first ? nmv.y * rv[k] : fmaf(beta[k], ov[k], nmv.y * rv[k]);
+        dv[k] = first ? mv * rv[k] : fmaf(beta[k], ov[k], mv * rv[k]);
     }
     float sacc[W];
 #pragma unroll
@@ -669,9 +676,10 @@ __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I,
         float ru[W], ou[W];
         ldw<W, CO>(rb + u * W, ru);
         if (!first) ldw<W, CO>(ob + u * W, ou);
+        const float mu = HIER ? 1.0f : nm.y;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            const float du = first ? nm.y * ru[k] : fmaf(beta[k], ou[k], nm.y * ru[k]);
+            const float du = first ? mu * ru[k] : fmaf(beta[k], ou[k], mu * ru[k]);
             sacc[k] = fmaf(nm.x, dv[k] - du, sacc[k]);
         }
     }
@@ -1000,7 +1008,7 @@ __device__ __forceinline__ void flush_run(DF (&run)[4], int W, int C, int ntiles
 // scalars (phase 1: delta_it and beta; phase 2: alpha), then dispatches each
 // tile on the image's pass width.  When an image's channels fit one pass the
 // products are accumulated over the run of its tiles in this chunk.
-template <int PHASE, bool COMP, bool CO, int WMAX>
+template <int PHASE, bool COMP, bool CO, int WMAX, bool HIER = false>
 __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
                           float* __restrict__ ddst, int it, int t0, int t1, PhaseSmem& S,
                           WideSmem& Wd)
@@ -1060,11 +1068,11 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
             else update_wide<COMP, CO>(A, I, vt, dsrc, S, run);
         } else if (PHASE == 1) {
             if (WMAX == 1 || I.Cp == 1)
-                apply_tile<1, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
+                apply_tile<1, COMP, CO, HIER>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
             else if (WMAX == 2 || I.Cp == 2)
-                apply_tile<2, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
+                apply_tile<2, COMP, CO, HIER>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
             else
-                apply_tile<4, COMP, CO>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
+                apply_tile<4, COMP, CO, HIER>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
         } else {
             if (WMAX == 1 || I.Cp == 1)
                 update_tile<1, COMP, CO>(A, I, vt, dsrc, S, run, fetch, in, it);
@@ -1092,7 +1100,7 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
 template <int WMAX>
 constexpr int phase_min_blocks() { return WMAX <= 2 ? 4 : 2; }
 
-template <int WMAX, bool COMP>
+template <int WMAX, bool COMP, bool HIER = false>
 __global__ void __launch_bounds__(kVTile, phase_min_blocks<WMAX>())
 pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict__ dnew, int it)
 {
@@ -1100,7 +1108,7 @@ pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict_
     __shared__ WideSmem Wd;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
-    phase_run<1, COMP, false, WMAX>(A, dold, dnew, it, t0, t1, S, Wd);
+    phase_run<1, COMP, false, WMAX, HIER>(A, dold, dnew, it, t0, t1, S, Wd);
 }
 
 template <int WMAX, bool COMP>
@@ -1348,6 +1356,221 @@ pcg_single_kernel(SolveArgs A, int it, int last)
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
     cg_run<WMAX>(A, it, last != 0, t0, t1, S);
+}
+
+// ------------------------------------- hierarchical preconditioner ---
+// The bilateral-space pyramid passes of Sec. 4 (levels built on the host;
+// see PyrDev).  P sums children into parents level by level (children in
+// ascending order: deterministic sums); P^T broadcasts parents back down
+// and adds them to each level's own scaled value:
+//   M_hier^-1 r = P^T(coef o P(r)),  coef = w(k) P(1) / P(diag A),
+//   y_hier = P^T(cinit o P(b)) / P^T(cinit o P(S c)),  cinit = w_init(k) / P(1).
+
+// global vector offset of channel 0 of grid vertex v (the image's layout)
+__device__ __forceinline__ int64_t pyr_vec0(const SolveArgs& A, int64_t v)
+{
+    const InstDev& I = A.inst[A.pyr.vimg[v]];
+    return I.vec_base + (v - I.voff) * I.Cp;
+}
+
+// Level k -> k+1: each parent sums its children's w values.  At k = 0 the
+// children's values come from the CG vector src0 (w = W channels) or, when
+// scal0 is set, from the per-vertex array scal0 (w = 1); above, from lv.
+__global__ void __launch_bounds__(256)
+pyr_up_kernel(SolveArgs A, int k, const float* __restrict__ src0, const float* __restrict__ scal0,
+              float* __restrict__ lv, int w)
+{
+    const PyrDev& P = A.pyr;
+    const int64_t np = P.off[k + 2] - P.off[k + 1];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t gp = P.off[k + 1] + p - P.off[1];
+        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int32_t j = P.child_off[gp]; j < P.child_off[gp + 1]; ++j) {
+            const int64_t c = P.child_idx[j];
+            if (k == 0) {
+                if (scal0) {
+                    acc[0] += scal0[c];
+                } else {
+                    const int64_t o = pyr_vec0(A, c);
+                    for (int ch = 0; ch < w; ++ch) acc[ch] += src0[o + ch];
+                }
+            } else {
+                const float* x = lv + (P.off[k] + c - P.off[1]) * w;
+                for (int ch = 0; ch < w; ++ch) acc[ch] += x[ch];
+            }
+        }
+        float* dst = lv + gp * w;
+        for (int ch = 0; ch < w; ++ch) dst[ch] = acc[ch];
+    }
+}
+
+// Level k >= 1, top down: value <- weight o value + (parent's final value)
+__global__ void __launch_bounds__(256)
+pyr_down_kernel(SolveArgs A, int k, const float* __restrict__ weight, float* __restrict__ lv, int w)
+{
+    const PyrDev& P = A.pyr;
+    const int64_t nk = P.off[k + 1] - P.off[k];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nk;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = P.off[k] + i;
+        const float wt = weight[g];
+        float* x = lv + (g - P.off[1]) * w;
+        const bool top = k == P.K - 1;
+        const float* up = top ? nullptr : lv + (P.off[k + 1] + P.parent[g] - P.off[1]) * w;
+        for (int ch = 0; ch < w; ++ch) x[ch] = wt * x[ch] + (top ? 0.0f : up[ch]);
+    }
+}
+
+// coef = w(k) P(1) / P(diag A) on every pyramid vertex (w(0) = 1,
+// w(k) = 2^-(5 + k)); 0 where P(diag A) <= 0.  P(diag A) of levels >= 1 is
+// in buf2 (an up-sweep of dg).
+__global__ void __launch_bounds__(256)
+pyr_coef_kernel(SolveArgs A)
+{
+    const PyrDev& P = A.pyr;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < P.off[P.K];
+         g += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (g >= P.off[k + 1]) ++k;
+        const float D = k == 0 ? P.dg[g] : P.buf2[g - P.off[1]];
+        const float w = k == 0 ? 1.0f : exp2f(-(float)(5 + k));
+        P.coef[g] = D > 0.0f ? w * P.cnt[g] / D : 0.0f;
+    }
+}
+
+// Level 0 of the preconditioner, per vertex tile: z = coef r + (level-1
+// parent's value); partials of r^T z into `out` for every tile.
+template <int W>
+__device__ __forceinline__ void pyr_precond_tile(const SolveArgs& A, const InstDev& I,
+                                                 const VTile& vt, float2* out, PhaseSmem& S)
+{
+    const PyrDev& P = A.pyr;
+    const int v = (int)vt.v0 + (int)threadIdx.x;
+    const bool valid = v < (int)vt.v1;
+    const int vs = valid ? v : (int)vt.v0;
+    const int64_t off = I.vec_base - I.voff * W;
+    float rv[W], zv[W];
+    ldw<W, false>(A.r + off + vs * W, rv);
+    const float c0 = P.coef[vs];
+    float up[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) up[k] = 0.0f;
+    if (P.K > 1) {
+        const float* u = P.buf + (int64_t)P.parent[vs] * W;   // level 1 starts at buf[0]
+#pragma unroll
+        for (int k = 0; k < W; ++k) up[k] = u[k];
+    }
+    DF acc[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        zv[k] = fmaf(c0, rv[k], up[k]);
+        acc[k] = valid && k < I.C ? df_mul_exact(rv[k], zv[k]) : DF{0.0f, 0.0f};
+    }
+    if (valid) stw<W>(P.z + off + v * W, zv);
+    store_partials<W>(acc, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst, out, S.red);
+}
+
+__global__ void __launch_bounds__(kVTile)
+pyr_precond0_kernel(SolveArgs A, float2* out)
+{
+    __shared__ PhaseSmem S;
+    int t0, t1;
+    block_chunk(A.nvt, t0, t1);
+    for (int tile = t0; tile < t1; ++tile) {
+        const VTile vt = A.vt[tile];
+        const InstDev I = A.inst[vt.inst];
+        if (I.Cp == 1) pyr_precond_tile<1>(A, I, vt, out, S);
+        else if (I.Cp == 2) pyr_precond_tile<2>(A, I, vt, out, S);
+        else pyr_precond_tile<4>(A, I, vt, out, S);
+    }
+}
+
+// Level 0 of the initialisation: y = (cinit b + Tb) / (cinit S c + Ts), 0
+// where the denominator is 0; b is in r after the splat (its high part).
+__global__ void __launch_bounds__(256)
+pyr_init0_kernel(SolveArgs A)
+{
+    const PyrDev& P = A.pyr;
+    const int W = P.W;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < P.off[1];
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = pyr_vec0(A, v);
+        const float ci = P.cinit[v];
+        const float den = fmaf(ci, P.scv[v], P.K > 1 ? P.buf2[P.parent[v]] : 0.0f);
+        for (int ch = 0; ch < W; ++ch) {
+            const float num = fmaf(ci, A.r[o + ch], P.K > 1 ? P.buf[(int64_t)P.parent[v] * W + ch] : 0.0f);
+            A.y[o + ch] = den > 0.0f ? num / den : 0.0f;
+        }
+    }
+}
+
+int pyr_blocks(int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)device_info().sms * 8));
+}
+
+// full up-sweep of a level-0 vector (src0, W channels) or scalar (scal0) into lv
+cudaError_t pyr_up_all(const SolveArgs& A, const float* src0, const float* scal0, float* lv, int w,
+                       cudaStream_t s)
+{
+    for (int k = 0; k + 1 < A.pyr.K; ++k)
+        pyr_up_kernel<<<pyr_blocks(A.pyr.off[k + 2] - A.pyr.off[k + 1]), 256, 0, s>>>(
+            A, k, src0, scal0, lv, w);
+    return cudaGetLastError();
+}
+
+// down-sweep of levels K-1 .. 1 with the given per-vertex weights
+cudaError_t pyr_down_all(const SolveArgs& A, const float* weight, float* lv, int w, cudaStream_t s)
+{
+    for (int k = A.pyr.K - 1; k >= 1; --k)
+        pyr_down_kernel<<<pyr_blocks(A.pyr.off[k + 1] - A.pyr.off[k]), 256, 0, s>>>(A, k, weight,
+                                                                                    lv, w);
+    return cudaGetLastError();
+}
+
+// z = M_hier^-1 r and the partials of r^T z into out
+cudaError_t pyr_precond(const SolveArgs& A, float2* out, cudaStream_t s)
+{
+    static int fam = prof_family("pyr_precond");
+    static const int occ = [] {
+        int o = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pyr_precond0_kernel, kVTile, 0);
+        return o > 0 ? o : 1;
+    }();
+    prof_begin(fam, s);
+    cudaError_t e = pyr_up_all(A, A.r, nullptr, A.pyr.buf, A.pyr.W, s);
+    if (e == cudaSuccess) e = pyr_down_all(A, A.pyr.coef, A.pyr.buf, A.pyr.W, s);
+    if (e == cudaSuccess) {
+        const int nb = std::min(A.nvt, device_info().sms * occ);
+        pyr_precond0_kernel<<<nb, kVTile, 0, s>>>(A, out);
+        e = cudaGetLastError();
+    }
+    prof_end(fam, s);
+    return e;
+}
+
+// the preconditioner's scale (after the splat) and the initial state y0
+cudaError_t pyr_setup(const SolveArgs& A, cudaStream_t s)
+{
+    static int fam = prof_family("pyr_setup");
+    prof_begin(fam, s);
+    const int64_t T = A.pyr.off[A.pyr.K];
+    cudaError_t e = pyr_up_all(A, nullptr, A.pyr.dg, A.pyr.buf2, 1, s);
+    if (e == cudaSuccess) {
+        pyr_coef_kernel<<<pyr_blocks(T), 256, 0, s>>>(A);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = pyr_up_all(A, A.r, nullptr, A.pyr.buf, A.pyr.W, s);
+    if (e == cudaSuccess) e = pyr_up_all(A, nullptr, A.pyr.scv, A.pyr.buf2, 1, s);
+    if (e == cudaSuccess) e = pyr_down_all(A, A.pyr.cinit, A.pyr.buf, A.pyr.W, s);
+    if (e == cudaSuccess) e = pyr_down_all(A, A.pyr.cinit, A.pyr.buf2, 1, s);
+    if (e == cudaSuccess) {
+        pyr_init0_kernel<<<pyr_blocks(A.pyr.off[1]), 256, 0, s>>>(A);
+        e = cudaGetLastError();
+    }
+    prof_end(fam, s);
+    return e;
 }
 
 // ------------------------------------------------- persistent PCG loop ---
@@ -1762,15 +1985,25 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
         prof_begin(f_apply, s);
-        if (wi == 0) pcg_apply_kernel<1, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
-        else if (wi == 1) pcg_apply_kernel<2, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
-        else pcg_apply_kernel<4, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+        if (P.hier) {
+            if (wi == 0) pcg_apply_kernel<1, COMP, true><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+            else if (wi == 1) pcg_apply_kernel<2, COMP, true><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+            else pcg_apply_kernel<4, COMP, true><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+        } else {
+            if (wi == 0) pcg_apply_kernel<1, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+            else if (wi == 1) pcg_apply_kernel<2, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+            else pcg_apply_kernel<4, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+        }
         prof_end(f_apply, s);
         prof_begin(f_update, s);
         if (wi == 0) pcg_update_kernel<1, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
         else if (wi == 1) pcg_update_kernel<2, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
         else pcg_update_kernel<4, COMP><<<nb_u, kVTile, 0, s>>>(A, dnew, it);
         prof_end(f_update, s);
+        if (P.hier) {                       // z = M_hier^-1 r and the next delta's partials
+            cudaError_t e = pyr_precond(A, A.part_rs[(it + 1) & 1], s);
+            if (e != cudaSuccess) return e;
+        }
     }
     return cudaGetLastError();
 }
@@ -1827,13 +2060,16 @@ cudaError_t launch_segment(const SolveArgs& A, const SolvePlan& P, int seg, int 
         }
         prof_end(f_splat, s);
         if (e != cudaSuccess) return e;
+        if (P.hier && (e = pyr_setup(A, s)) != cudaSuccess) return e;   // coef, y0
         prof_begin(f_res, s);
         if (P.comp)
             residual_kernel<true><<<persistent_blocks(occ_rt, A.nvt), kVTile, 0, s>>>(A);
         else
             residual_kernel<false><<<persistent_blocks(occ_rf, A.nvt), kVTile, 0, s>>>(A);
         prof_end(f_res, s);
-        return cudaGetLastError();
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (P.hier) return pyr_precond(A, A.part_rs[0], s);        // z0, delta_0
+        return cudaSuccess;
     }
     if (seg == kSegLoop) return P.comp ? launch_loop<true>(A, P, s) : launch_loop<false>(A, P, s);
     const dim3 pix_grid((unsigned)std::min<int64_t>((P.max_pixels + 255) / 256,

@@ -5,6 +5,31 @@
 
 namespace fbs {
 
+constexpr int kMaxLevels = 16;     // bilateral-space pyramid levels (12-bit fields: at most 13)
+
+// The bilateral-space pyramid of a grid (supplement) and the per-solve
+// arrays of the hierarchical preconditioner (Sec. 4).  Pyramid vertices are
+// numbered level by level: level k occupies [off[k], off[k+1]), level 0 is
+// the grid's vertices.  Values of levels >= 1 live in buf (W per vertex).
+struct PyrDev {
+    int K;                     // levels; the last has one vertex per image
+    int W;                     // channels per vertex (the batch's common Cp)
+    int64_t off[kMaxLevels + 1];
+    const int32_t* parent;     // [off[K-1]]: level-local parent (in level k+1) of each vertex below the top
+    const int32_t* child_off;  // [off[K] - off[1] + 1]: children of level >= 1 vertex g are
+    const int32_t* child_idx;  //   child_idx[child_off[g - off[1]] .. child_off[g - off[1] + 1])
+                               //   (level-local indices in the level below, ascending)
+    const uint16_t* vimg;      // [off[1]]: image of each grid vertex
+    const float* cnt;          // [off[K]]: P(1), grid vertices below each pyramid vertex
+    const float* cinit;        // [off[K]]: initialisation weight w_init(k) / P(1)
+    float* coef;               // [off[K]]: preconditioner scale w(k) P(1) / P(diag A) (per solve)
+    float* dg;                 // [off[1]]: diag(A) (per solve)
+    float* scv;                // [off[1]]: S c (per solve)
+    float* buf;                // [(off[K] - off[1]) * W]: level values
+    float* buf2;               // [off[K] - off[1]]: second (1-channel) level values
+    float* z;                  // CG vector layout: z = M_hier^-1 r
+};
+
 struct SolveArgs {
     const VTile* vt;
     int nvt;
@@ -35,6 +60,7 @@ struct SolveArgs {
     float2* part_dq;           // ... of d^T A d
     float2* part_mu[2];        // single-reduction form: partials of w^T u by parity
     uint32_t* err;
+    PyrDev pyr;                // hierarchical preconditioner (pyr.K = 0 when off)
 };
 
 struct SolvePlan {
@@ -55,6 +81,7 @@ struct SolvePlan {
     int inject_timeout;        // preset the barrier counter so no wait completes (test)
     int single;                // 1: single-reduction PCG form (FP32, Cp <= 4, per-phase)
     int block_mult;            // per-phase kernels: blocks = min(tiles, SMs x occupancy x this)
+    int hier;                  // 1: hierarchical preconditioner and initialisation (per-phase)
 };
 
 // A solve runs as segments: for each outer (IRLS) iteration a setup (splat,

@@ -27,7 +27,8 @@ EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robus
             "fbs_set_option", "fbs_solve_static", "fbs_autotune"]
 
 OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT, OPT_PCG_FORM = 1, 2, 3, 4
-OPT_PHASE_BLOCKS = 5
+OPT_PHASE_BLOCKS, OPT_PRECONDITIONER = 5, 6
+PRECOND_JACOBI, PRECOND_HIERARCHICAL = 0, 1
 VECTORS_AUTO, VECTORS_FP32, VECTORS_COMPENSATED = 0, 1, 2
 PCG_AUTO, PCG_PERSISTENT, PCG_PER_PHASE = 0, 1, 2
 PCG_FORM_STANDARD, PCG_FORM_SINGLE = 0, 1

@@ -21,6 +21,7 @@ def to_dev(a):
 
 PCG_LAUNCH = {"mode": 0}    # fbs.PCG_AUTO; tests may switch to PCG_PERSISTENT / PCG_PER_PHASE
 PCG_FORM = {"form": 0}      # fbs.PCG_FORM_STANDARD; tests may switch to PCG_FORM_SINGLE
+PRECOND = {"kind": 0}       # fbs.PRECOND_JACOBI; tests may switch to PRECOND_HIERARCHICAL
 
 
 def gpu_grid(insts, bistoch_iters=2):
@@ -30,6 +31,7 @@ def gpu_grid(insts, bistoch_iters=2):
                        [i.sigma_uv for i in insts])
     fbs.set_option(g, fbs.OPT_PCG_LAUNCH, PCG_LAUNCH["mode"])
     fbs.set_option(g, fbs.OPT_PCG_FORM, PCG_FORM["form"])
+    fbs.set_option(g, fbs.OPT_PRECONDITIONER, PRECOND["kind"])
     if bistoch_iters:
         fbs.bistochastize(g, bistoch_iters)
     return g
