@@ -75,7 +75,7 @@ def lib():
             L.fbso_pcg_single.restype = _I
             L.fbso_set_pcg_form.argtypes = [_I]
             L.fbso_set_pcg_form.restype = None
-            L.fbso_pyramid.argtypes = [_I64, _P, _I, _P, _P]
+            L.fbso_pyramid.argtypes = [_I64, _P, _I, _P, _P, _I64]
             L.fbso_pyramid.restype = _I
             L.fbso_set_hierarchical.argtypes = [_I, _I, _P, _P, _D, _D, _D, _D]
             L.fbso_set_hierarchical.restype = None
@@ -237,12 +237,16 @@ def pyramid(vkey):
     vkey = _c(vkey, np.uint64)
     V = vkey.size
     sizes = np.zeros(MAX_LEVELS, np.int64)
-    parent = np.zeros(max(2 * V, 1), np.int32)
-    K = lib().fbso_pyramid(V, _ptr(vkey), MAX_LEVELS, _ptr(sizes), _ptr(parent))
+    # first pass: level sizes only; second: the parents, into an exact buffer
+    K = lib().fbso_pyramid(V, _ptr(vkey), MAX_LEVELS, _ptr(sizes), None, 0)
     if K < 0:
         raise OracleError(f"fbso_pyramid failed ({-K})")
-    sizes = sizes[:K].copy()
-    return sizes, parent[:int(sizes[:-1].sum())].copy()
+    n_par = int(sizes[:K - 1].sum())
+    parent = np.zeros(max(n_par, 1), np.int32)
+    K2 = lib().fbso_pyramid(V, _ptr(vkey), MAX_LEVELS, _ptr(sizes), _ptr(parent), n_par)
+    if K2 != K:
+        raise OracleError(f"fbso_pyramid failed ({-K2})")
+    return sizes[:K].copy(), parent[:n_par].copy()
 
 
 class hierarchical:

@@ -351,7 +351,7 @@ static uint64_t halve_key(uint64_t k)
 }
 
 int fbso_pyramid(int64_t V, const uint64_t* vkey, int max_levels, int64_t* sizes,
-                 int32_t* parent)
+                 int32_t* parent, int64_t parent_cap)
 {
     if (V <= 0 || max_levels < 1) return -FBSO_ERR_ARG;
     uint64_t* cur = (uint64_t*)malloc((size_t)V * sizeof(uint64_t));
@@ -371,7 +371,10 @@ int fbso_pyramid(int64_t V, const uint64_t* vkey, int max_levels, int64_t* sizes
         int64_t L2 = 0;
         for (int64_t i = 0; i < L; ++i)
             if (i == 0 || nxt[i] != nxt[i - 1]) nxt[L2++] = nxt[i];
-        for (int64_t i = 0; i < L; ++i) parent[off + i] = (int32_t)find_key(nxt, L2, h[i]);
+        if (parent) {
+            if (off + L > parent_cap) { free(h); free(cur); free(nxt); return -FBSO_ERR_ARG; }
+            for (int64_t i = 0; i < L; ++i) parent[off + i] = (int32_t)find_key(nxt, L2, h[i]);
+        }
         free(h);
         off += L;
         sizes[K++] = L2;

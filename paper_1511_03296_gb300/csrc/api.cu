@@ -265,13 +265,14 @@ struct fbs_grid {
     int32_t* pyr_child_off = nullptr;
     int32_t* pyr_child_idx = nullptr;
     uint16_t* pyr_vimg = nullptr;
+    int64_t* pyr_ioff = nullptr;
+    uint8_t* pyr_kimg = nullptr;
     float* pyr_cnt = nullptr;
     float* pyr_cinit = nullptr;
     float* pyr_coef = nullptr;
     float* pyr_dg = nullptr;
     float* pyr_scv = nullptr;
-    float* pyr_buf = nullptr;
-    float* pyr_buf2 = nullptr;
+    float2* pyr_lv = nullptr;
     int inject_timeout = 0;
     float* a = nullptr;
     float2* nm = nullptr;
@@ -315,8 +316,9 @@ void free_grid_memory(fbs_grid* g, cudaStream_t s)
     dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s); dfree(g->part, s);
     dfree(g->inst, s); dfree(g->barrier, s);
     dfree(g->pyr_parent, s); dfree(g->pyr_child_off, s); dfree(g->pyr_child_idx, s);
-    dfree(g->pyr_vimg, s); dfree(g->pyr_cnt, s); dfree(g->pyr_cinit, s); dfree(g->pyr_coef, s); dfree(g->pyr_dg, s);
-    dfree(g->pyr_scv, s); dfree(g->pyr_buf, s); dfree(g->pyr_buf2, s);
+    dfree(g->pyr_vimg, s); dfree(g->pyr_ioff, s); dfree(g->pyr_kimg, s); dfree(g->pyr_cnt, s);
+    dfree(g->pyr_cinit, s); dfree(g->pyr_coef, s); dfree(g->pyr_dg, s); dfree(g->pyr_scv, s);
+    dfree(g->pyr_lv, s);
 }
 
 fbs_status latched(uint32_t bits)
@@ -679,7 +681,8 @@ uint64_t halve_key(uint64_t k)
 // pyramids), built once on the host from the vertex keys: per image, level
 // k+1 is the sorted distinct halved keys of level k (floor halving reaches a
 // single vertex); the images' levels are concatenated level by level (an
-// image that reached its top keeps one vertex), with each vertex's parent,
+// image that reached its top keeps one vertex, with count and weights 0, so
+// each image's result is that of its own pyramid), with each vertex's parent,
 // each vertex's children in ascending order (so the device sums are
 // deterministic), the counts P(1) and the initialisation weights
 // w_init(k) / P(1), w_init(k) = 4^-k (alpha = 4, beta = 0).
@@ -762,21 +765,39 @@ fbs_status build_pyramid(fbs_grid* g, cudaStream_t s)
         const double w = k == 0 ? 1.0 : pow(4.0, -(double)k);
         for (int64_t i = off[k]; i < off[k + 1]; ++i) cinit[i] = (float)(w / cnt[i]);
     }
-    std::vector<uint16_t> vimg(V);
-    for (int im = 0; im < n; ++im)
-        for (int64_t v = g->voff[im]; v < g->voff[im + 1]; ++v) vimg[v] = (uint16_t)im;
+    // the single vertex an image keeps past its own top is not a level of
+    // its pyramid: count 0 and weight 0 make its terms vanish exactly
+    for (int k = 1; k < K; ++k)
+        for (int im = 0; im < n; ++im)
+            if (k >= (int)lk[im].size()) {
+                cntf[off[k] + ioff[k][im]] = 0.0f;
+                cinit[off[k] + ioff[k][im]] = 0.0f;
+            }
+    // absolute per-image level ranges and each image's own level count
+    std::vector<int64_t> ioffa((size_t)K * (n + 1));
+    for (int k = 0; k < K; ++k)
+        for (int im = 0; im <= n; ++im) ioffa[(size_t)k * (n + 1) + im] = off[k] + ioff[k][im];
+    std::vector<uint8_t> kimg(n);
+    for (int im = 0; im < n; ++im) kimg[im] = (uint8_t)lk[im].size();
+    std::vector<uint16_t> vimg(T);
+    for (int k = 0; k < K; ++k)
+        for (int im = 0; im < n; ++im)
+            for (int64_t i = 0; i < lsize(im, k); ++i)
+                vimg[off[k] + ioff[k][im] + i] = (uint16_t)im;
     // device copies
     if ((e = dalloc(&g->pyr_parent, parent.size(), s)) != cudaSuccess ||
         (e = dalloc(&g->pyr_child_off, child_off.size(), s)) != cudaSuccess ||
         (e = dalloc(&g->pyr_child_idx, child_idx.size(), s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_vimg, (size_t)V, s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_vimg, (size_t)T, s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_ioff, ioffa.size(), s)) != cudaSuccess ||
+        (e = dalloc(&g->pyr_kimg, kimg.size(), s)) != cudaSuccess ||
         (e = dalloc(&g->pyr_cnt, (size_t)T, s)) != cudaSuccess ||
         (e = dalloc(&g->pyr_cinit, (size_t)T, s)) != cudaSuccess ||
         (e = dalloc(&g->pyr_coef, (size_t)T, s)) != cudaSuccess ||
         (e = dalloc(&g->pyr_dg, (size_t)V, s)) != cudaSuccess ||
         (e = dalloc(&g->pyr_scv, (size_t)V, s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_buf, (size_t)std::max<int64_t>(T - V, 1) * 4, s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_buf2, (size_t)std::max<int64_t>(T - V, 1), s)) != cudaSuccess)
+        (e = dalloc(&g->pyr_lv, (size_t)std::max<int64_t>(T - V, 1) * kPyrMaxNc, s)) !=
+            cudaSuccess)
         return cuda_status(e);
     const struct {
         void* dst;
@@ -786,6 +807,8 @@ fbs_status build_pyramid(fbs_grid* g, cudaStream_t s)
               {g->pyr_child_off, child_off.data(), child_off.size() * sizeof(int32_t)},
               {g->pyr_child_idx, child_idx.data(), child_idx.size() * sizeof(int32_t)},
               {g->pyr_vimg, vimg.data(), vimg.size() * sizeof(uint16_t)},
+              {g->pyr_ioff, ioffa.data(), ioffa.size() * sizeof(int64_t)},
+              {g->pyr_kimg, kimg.data(), kimg.size() * sizeof(uint8_t)},
               {g->pyr_cnt, cntf.data(), cntf.size() * sizeof(float)},
               {g->pyr_cinit, cinit.data(), cinit.size() * sizeof(float)}};
     for (const auto& c : cp)
@@ -836,13 +859,8 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     // the single-reduction form for FP32 vectors and images of at most 4
     // channels; it runs as per-phase launches
     plan.single = g->pcg_form == FBS_PCG_FORM_SINGLE && !plan.comp && cmax <= 4 ? 1 : 0;
-    // hierarchical preconditioner: every image with the same Cp <= 4
-    plan.hier = 0;
-    if (g->precond == FBS_PRECOND_HIERARCHICAL && cmax <= 4) {
-        bool uniform = true;
-        for (int k = 1; k < g->n_images; ++k) uniform &= inst[k].Cp == inst[0].Cp;
-        plan.hier = uniform ? 1 : 0;
-    }
+    // hierarchical preconditioner: images of at most 4 channels
+    plan.hier = g->precond == FBS_PRECOND_HIERARCHICAL && cmax <= 4 ? 1 : 0;
     if (plan.hier) plan.single = 0;
     plan.persistent = g->persistent && !capturing(s) && !plan.single && !plan.hier ? 1 : 0;
     plan.block_mult = g->phase_blocks;
@@ -915,19 +933,21 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
             if (pst) return pst;
         }
         A.pyr.K = g->pyr_K;
-        A.pyr.W = inst[0].Cp;
+        A.pyr.W = 1;
+        for (const InstDev& d : inst) A.pyr.W = std::max(A.pyr.W, d.Cp);
         for (int k = 0; k <= g->pyr_K; ++k) A.pyr.off[k] = g->pyr_off[k];
         A.pyr.parent = g->pyr_parent;
         A.pyr.child_off = g->pyr_child_off;
         A.pyr.child_idx = g->pyr_child_idx;
         A.pyr.vimg = g->pyr_vimg;
+        A.pyr.ioff = g->pyr_ioff;
+        A.pyr.kimg = g->pyr_kimg;
         A.pyr.cnt = g->pyr_cnt;
         A.pyr.cinit = g->pyr_cinit;
         A.pyr.coef = g->pyr_coef;
         A.pyr.dg = g->pyr_dg;
         A.pyr.scv = g->pyr_scv;
-        A.pyr.buf = g->pyr_buf;
-        A.pyr.buf2 = g->pyr_buf2;
+        A.pyr.lv = g->pyr_lv;
         A.pyr.z = A.aux[0];
     }
     // AUTO: the resident loop for small batches; per-phase (graph) otherwise

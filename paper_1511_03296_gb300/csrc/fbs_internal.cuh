@@ -95,8 +95,20 @@ __host__ __device__ inline int padded_channels(int C) { return C <= 2 ? C : (C +
 // r^T M^-1 r of iteration `it` in slot it % 2
 struct Scal {
     double delta[2];
+    double delta0;          // r_0^T M^-1 r_0 (both forms): the stall test's scale
     double gam[2], alp[2];  // single-reduction form: gamma_i and alpha_i by iteration parity
 };
+
+// FP32-vector safeguard of the CG scalars: a channel whose r^T M^-1 r has
+// fallen to 2^-96 of its first value (the preconditioned residual down by
+// 2^-48, far below what FP32 vectors resolve) takes alpha = beta = 0 from
+// then on.  Without it the recursive FP32 residual keeps shrinking, over
+// thousands of iterations, into the subnormal range, where beta overflows
+// and 0 * inf turns y into NaN.  Also true for now = 0 (or NaN).
+__device__ __forceinline__ bool cg_stalled(double now, double first)
+{
+    return !(now > first * 0x1p-96);
+}
 
 // splat modes
 enum SplatMode : int {
@@ -143,6 +155,15 @@ __device__ __forceinline__ DF df_add(DF a, DF b)
 {
     DF s = df_two_sum(a.hi, b.hi);
     float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    float h = __fadd_rn(s.hi, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s.hi))};
+}
+
+// a + b for a double-float a and a float b
+__device__ __forceinline__ DF df_add_f(DF a, float b)
+{
+    DF s = df_two_sum(a.hi, b);
+    float e = __fadd_rn(s.lo, a.lo);
     float h = __fadd_rn(s.hi, e);
     return {h, __fsub_rn(e, __fsub_rn(h, s.hi))};
 }

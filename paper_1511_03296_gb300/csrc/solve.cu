@@ -246,15 +246,19 @@ __device__ void phase_scalars(const SolveArgs& A, const InstDev& I, const float2
             if (it > 0) {
                 const double dprev = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot ^ 1])
                                         : A.scal[I.pc + ch].delta[slot ^ 1];
-                beta = dprev != 0.0 ? dnow / dprev : 0.0;
+                const double d0 = CO ? __ldcg(&A.scal[I.pc + ch].delta0) : A.scal[I.pc + ch].delta0;
+                beta = dprev != 0.0 && !cg_stalled(dnow, d0) ? dnow / dprev : 0.0;
+            } else {
+                A.scal[I.pc + ch].delta0 = dnow;
             }
             S.sf[ch] = (float)beta;
             A.scal[I.pc + ch].delta[slot] = dnow;   // same value from every block
         } else {
             const double delta = CO ? __ldcg(&A.scal[I.pc + ch].delta[slot])
                                     : A.scal[I.pc + ch].delta[slot];
+            const double d0 = CO ? __ldcg(&A.scal[I.pc + ch].delta0) : A.scal[I.pc + ch].delta0;
             const double dq = S.sd[ch];
-            S.sa[ch] = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
+            S.sa[ch] = (dq > 0.0 && !cg_stalled(delta, d0)) ? delta / dq : 0.0;
         }
     }
     __syncthreads();
@@ -1158,13 +1162,17 @@ __device__ void cg_scalars(const SolveArgs& A, const InstDev& I, int it, PhaseSm
         }
         const double gamma = S.sd[ch], mu = S.sd2[ch];
         double beta = 0.0, den = mu;
+        bool stalled = gamma == 0.0;
         if (it > 0) {
             const double gold = A.scal[I.pc + ch].gam[slot ^ 1];
             const double aold = A.scal[I.pc + ch].alp[slot ^ 1];
-            beta = gold != 0.0 ? gamma / gold : 0.0;
+            stalled = cg_stalled(gamma, A.scal[I.pc + ch].delta0);
+            beta = gold != 0.0 && !stalled ? gamma / gold : 0.0;
             if (beta != 0.0 && aold != 0.0) den = mu - beta * gamma / aold;
+        } else {
+            A.scal[I.pc + ch].delta0 = gamma;
         }
-        const double alpha = (gamma != 0.0 && den > 0.0) ? gamma / den : 0.0;
+        const double alpha = (!stalled && den > 0.0) ? gamma / den : 0.0;
         S.sf[ch] = (float)beta;
         S.sa[ch] = alpha;
         A.scal[I.pc + ch].gam[slot] = gamma;   // same values from every block
@@ -1360,87 +1368,209 @@ pcg_single_kernel(SolveArgs A, int it, int last)
 
 // ------------------------------------- hierarchical preconditioner ---
 // The bilateral-space pyramid passes of Sec. 4 (levels built on the host;
-// see PyrDev).  P sums children into parents level by level (children in
-// ascending order: deterministic sums); P^T broadcasts parents back down
-// and adds them to each level's own scaled value:
+// see PyrDev).  P sums children into parents level by level, in ascending
+// child order and in double-float arithmetic: deterministic, and free of
+// the cancellation error that FP32 sums of a converging, oscillating
+// residual would feed back into CG as a changing preconditioner.  P^T
+// broadcasts parents back down, adding each level's own scaled value:
 //   M_hier^-1 r = P^T(coef o P(r)),  coef = w(k) P(1) / P(diag A),
 //   y_hier = P^T(cinit o P(b)) / P^T(cinit o P(S c)),  cinit = w_init(k) / P(1).
+// The weights are FP32 (a rounded weight leaves M_hier^-1 linear and
+// symmetric).  Launches: level 1 from the grid (pyr_gather0), level 2 from
+// level 1 (pyr_gather), levels >= 3 of each image up and back down in one
+// block per image (pyr_tail), levels 2 and 1 down (pyr_down12), and level 0
+// (pyr_precond0 / pyr_init0).  A level
+// vector holds nc double-float values per vertex: W channels (the widest
+// image's Cp; an image uses its first Cp), plus S c and diag(A) in the setup
+// pass (nc = W + 2).
 
-// global vector offset of channel 0 of grid vertex v (the image's layout)
-__device__ __forceinline__ int64_t pyr_vec0(const SolveArgs& A, int64_t v)
-{
-    const InstDev& I = A.inst[A.pyr.vimg[v]];
-    return I.vec_base + (v - I.voff) * I.Cp;
-}
+__device__ __forceinline__ DF pyr_ld(const float2* p) { const float2 v = *p; return {v.x, v.y}; }
+__device__ __forceinline__ void pyr_st(float2* p, DF v) { *p = make_float2(v.hi, v.lo); }
 
-// Level k -> k+1: each parent sums its children's w values.  At k = 0 the
-// children's values come from the CG vector src0 (w = W channels) or, when
-// scal0 is set, from the per-vertex array scal0 (w = 1); above, from lv.
+// Level 1 parents sum their grid children: channels [0, cp) from the CG
+// vector src (the child image's layout), and with scal, S c into channel W
+// and diag(A) into channel W + 1.
 __global__ void __launch_bounds__(256)
-pyr_up_kernel(SolveArgs A, int k, const float* __restrict__ src0, const float* __restrict__ scal0,
-              float* __restrict__ lv, int w)
+pyr_gather0_kernel(SolveArgs A, const float* __restrict__ src, int nc, int scal)
 {
     const PyrDev& P = A.pyr;
-    const int64_t np = P.off[k + 2] - P.off[k + 1];
+    const int W = P.W;
+    const int64_t np = P.off[2] - P.off[1];
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t gp = P.off[k + 1] + p - P.off[1];
-        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int32_t j = P.child_off[gp]; j < P.child_off[gp + 1]; ++j) {
+        DF acc[4], asc = {0.0f, 0.0f}, adg = {0.0f, 0.0f};
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) acc[ch] = DF{0.0f, 0.0f};
+        // a parent's children are grid vertices of its own image
+        const InstDev& I = A.inst[P.vimg[P.off[1] + p]];
+        const int cp = I.Cp;
+        const float* base = src + I.vec_base - I.voff * cp;
+        const int32_t j1 = P.child_off[p + 1];
+#pragma unroll 4
+        for (int32_t j = P.child_off[p]; j < j1; ++j) {
             const int64_t c = P.child_idx[j];
-            if (k == 0) {
-                if (scal0) {
-                    acc[0] += scal0[c];
-                } else {
-                    const int64_t o = pyr_vec0(A, c);
-                    for (int ch = 0; ch < w; ++ch) acc[ch] += src0[o + ch];
-                }
-            } else {
-                const float* x = lv + (P.off[k] + c - P.off[1]) * w;
-                for (int ch = 0; ch < w; ++ch) acc[ch] += x[ch];
+            const float* x = base + c * cp;
+#pragma unroll
+            for (int ch = 0; ch < 4; ++ch)
+                if (ch < cp) acc[ch] = df_add_f(acc[ch], x[ch]);
+            if (scal) {
+                asc = df_add_f(asc, P.scv[c]);
+                adg = df_add_f(adg, P.dg[c]);
             }
         }
-        float* dst = lv + gp * w;
-        for (int ch = 0; ch < w; ++ch) dst[ch] = acc[ch];
+        float2* dst = P.lv + p * nc;
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch)
+            if (ch < W) pyr_st(dst + ch, acc[ch]);
+        if (scal) {
+            pyr_st(dst + W, asc);
+            pyr_st(dst + W + 1, adg);
+        }
     }
 }
 
-// Level k >= 1, top down: value <- weight o value + (parent's final value)
+// one parent g (absolute, level k + 1 >= 2) sums its level-k children
+__device__ __forceinline__ void pyr_sum_children(const PyrDev& P, int k, int64_t g, int nc)
+{
+    DF acc[kPyrMaxNc];
+#pragma unroll
+    for (int ch = 0; ch < kPyrMaxNc; ++ch) acc[ch] = DF{0.0f, 0.0f};
+    const int64_t gl = g - P.off[1];
+    const int32_t j1 = P.child_off[gl + 1];
+#pragma unroll 4
+    for (int32_t j = P.child_off[gl]; j < j1; ++j) {
+        const float2* x = P.lv + (P.off[k] + P.child_idx[j] - P.off[1]) * nc;
+#pragma unroll
+        for (int ch = 0; ch < kPyrMaxNc; ++ch)
+            if (ch < nc) acc[ch] = df_add(acc[ch], pyr_ld(x + ch));
+    }
+    float2* dst = P.lv + gl * nc;
+#pragma unroll
+    for (int ch = 0; ch < kPyrMaxNc; ++ch)
+        if (ch < nc) pyr_st(dst + ch, acc[ch]);
+}
+
+// Level k + 1 from level k, every image.
 __global__ void __launch_bounds__(256)
-pyr_down_kernel(SolveArgs A, int k, const float* __restrict__ weight, float* __restrict__ lv, int w)
+pyr_gather_kernel(SolveArgs A, int k, int nc)
 {
     const PyrDev& P = A.pyr;
-    const int64_t nk = P.off[k + 1] - P.off[k];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nk;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t g = P.off[k] + i;
-        const float wt = weight[g];
-        float* x = lv + (g - P.off[1]) * w;
-        const bool top = k == P.K - 1;
-        const float* up = top ? nullptr : lv + (P.off[k + 1] + P.parent[g] - P.off[1]) * w;
-        for (int ch = 0; ch < w; ++ch) x[ch] = wt * x[ch] + (top ? 0.0f : up[ch]);
+    const int64_t n = P.off[k + 2] - P.off[k + 1];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        pyr_sum_children(P, k, P.off[k + 1] + p, nc);
+}
+
+// Levels >= 3 of one image per block: with up, parents of levels 3 .. top
+// sum their children; with wt, levels top .. 3 take x <- wt o x + (parent's
+// x) (the image's top has no parent).  Images whose own pyramid has at most
+// three levels have nothing here.
+__global__ void __launch_bounds__(kPyrTailThreads)
+pyr_tail_kernel(SolveArgs A, int nc, int up, const float* __restrict__ wt)
+{
+    const PyrDev& P = A.pyr;
+    const int n = A.ninst;
+    for (int im = blockIdx.x; im < n; im += gridDim.x) {
+        const int Ki = P.kimg[im];
+        if (up) {
+            for (int k = 2; k + 1 < Ki; ++k) {
+                const int64_t g0 = P.ioff[(k + 1) * (n + 1) + im];
+                const int64_t g1 = P.ioff[(k + 1) * (n + 1) + im + 1];
+                for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x)
+                    pyr_sum_children(P, k, g, nc);
+                __syncthreads();
+            }
+        }
+        if (wt) {
+            for (int k = Ki - 1; k >= 3; --k) {
+                const int64_t g0 = P.ioff[k * (n + 1) + im];
+                const int64_t g1 = P.ioff[k * (n + 1) + im + 1];
+                const bool top = k == Ki - 1;
+                for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+                    float2* x = P.lv + (g - P.off[1]) * nc;
+                    const float2* u =
+                        top ? nullptr : P.lv + (P.off[k + 1] + P.parent[g] - P.off[1]) * nc;
+                    const float w = wt[g];
+#pragma unroll
+                    for (int ch = 0; ch < kPyrMaxNc; ++ch)
+                        if (ch < nc) {
+                            const DF xv = df_mul_f(pyr_ld(x + ch), w);
+                            pyr_st(x + ch, top ? xv : df_add(xv, pyr_ld(u + ch)));
+                        }
+                }
+                __syncthreads();
+            }
+        }
     }
 }
 
 // coef = w(k) P(1) / P(diag A) on every pyramid vertex (w(0) = 1,
-// w(k) = 2^-(5 + k)); 0 where P(diag A) <= 0.  P(diag A) of levels >= 1 is
-// in buf2 (an up-sweep of dg).
+// w(k) = 2^-(5 + k)); 0 where P(diag A) <= 0 and on the vertices an image
+// keeps past its own top (P(1) = 0 there).  P(diag A) of levels >= 1 is the
+// setup pass's channel W + 1.
 __global__ void __launch_bounds__(256)
 pyr_coef_kernel(SolveArgs A)
 {
     const PyrDev& P = A.pyr;
+    const int nc = P.W + 2;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < P.off[P.K];
          g += (int64_t)gridDim.x * blockDim.x) {
         int k = 0;
         while (g >= P.off[k + 1]) ++k;
-        const float D = k == 0 ? P.dg[g] : P.buf2[g - P.off[1]];
+        float D;
+        if (k == 0) {
+            D = P.dg[g];
+        } else {
+            const float2 d = P.lv[(g - P.off[1]) * nc + P.W + 1];
+            D = d.x + d.y;
+        }
         const float w = k == 0 ? 1.0f : exp2f(-(float)(5 + k));
         P.coef[g] = D > 0.0f ? w * P.cnt[g] / D : 0.0f;
     }
 }
 
-// Level 0 of the preconditioner, per vertex tile: z = coef r + (level-1
-// parent's value); partials of r^T z into `out` for every tile.
+// The down-sweep of levels 2 and 1, finished for each level-1 vertex in
+// place (weights wt): x1 = wt o l1 + x2, with x2 = wt o l2 of the level-2
+// ancestor plus its level-3 ancestor's final value from pyr_tail, each while
+// the image's own pyramid reaches that level (the image's top has no
+// parent).  Level-2 values are read, not written, so every level-1 vertex
+// sees them whole.
+__global__ void __launch_bounds__(256)
+pyr_down12_kernel(SolveArgs A, int nc, const float* __restrict__ wt)
+{
+    const PyrDev& P = A.pyr;
+    const int64_t n1 = P.off[2] - P.off[1];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n1;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g1 = P.off[1] + p;
+        const int Ki = P.kimg[P.vimg[g1]];
+        float2* x1 = P.lv + p * nc;
+        const float w1 = wt[g1];
+        const float2* l2 = nullptr;
+        const float2* l3 = nullptr;
+        float w2 = 0.0f;
+        if (Ki > 2) {
+            const int64_t g2 = P.off[2] + P.parent[g1];
+            w2 = wt[g2];
+            l2 = P.lv + (g2 - P.off[1]) * nc;
+            if (Ki > 3) l3 = P.lv + (P.off[3] + P.parent[g2] - P.off[1]) * nc;
+        }
+#pragma unroll
+        for (int ch = 0; ch < kPyrMaxNc; ++ch)
+            if (ch < nc) {
+                DF x = df_mul_f(pyr_ld(x1 + ch), w1);
+                if (Ki > 2) {
+                    DF x2 = df_mul_f(pyr_ld(l2 + ch), w2);
+                    if (Ki > 3) x2 = df_add(x2, pyr_ld(l3 + ch));
+                    x = df_add(x, x2);
+                }
+                pyr_st(x1 + ch, x);
+            }
+    }
+}
+
+// Level 0 of the preconditioner, per vertex tile: z = coef r + x1(ancestors);
+// partials of r^T z into `out` for every tile.
 template <int W>
 __device__ __forceinline__ void pyr_precond_tile(const SolveArgs& A, const InstDev& I,
                                                  const VTile& vt, float2* out, PhaseSmem& S)
@@ -1453,18 +1583,21 @@ __device__ __forceinline__ void pyr_precond_tile(const SolveArgs& A, const InstD
     float rv[W], zv[W];
     ldw<W, false>(A.r + off + vs * W, rv);
     const float c0 = P.coef[vs];
-    float up[W];
+    float x[W];
 #pragma unroll
-    for (int k = 0; k < W; ++k) up[k] = 0.0f;
-    if (P.K > 1) {
-        const float* u = P.buf + (int64_t)P.parent[vs] * W;   // level 1 starts at buf[0]
+    for (int k = 0; k < W; ++k) x[k] = 0.0f;
+    if (P.K > 1) {                      // level-1 ancestor's final value (pyr_down12)
+        const float2* x1 = P.lv + (int64_t)P.parent[vs] * P.W;
 #pragma unroll
-        for (int k = 0; k < W; ++k) up[k] = u[k];
+        for (int k = 0; k < W; ++k) {
+            const float2 t = x1[k];
+            x[k] = t.x + t.y;
+        }
     }
     DF acc[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) {
-        zv[k] = fmaf(c0, rv[k], up[k]);
+        zv[k] = fmaf(c0, rv[k], x[k]);
         acc[k] = valid && k < I.C ? df_mul_exact(rv[k], zv[k]) : DF{0.0f, 0.0f};
     }
     if (valid) stw<W>(P.z + off + v * W, zv);
@@ -1486,20 +1619,24 @@ pyr_precond0_kernel(SolveArgs A, float2* out)
     }
 }
 
-// Level 0 of the initialisation: y = (cinit b + Tb) / (cinit S c + Ts), 0
-// where the denominator is 0; b is in r after the splat (its high part).
+// Level 0 of the initialisation: y = (cinit b + x1_b) / (cinit S c + x1_Sc),
+// 0 where the denominator is not positive; b is in r after the splat.
 __global__ void __launch_bounds__(256)
 pyr_init0_kernel(SolveArgs A)
 {
     const PyrDev& P = A.pyr;
-    const int W = P.W;
+    const int W = P.W, nc = W + 2;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < P.off[1];
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t o = pyr_vec0(A, v);
+        const int im = P.vimg[v];
+        const InstDev& I = A.inst[im];
+        const int64_t o = I.vec_base + (v - I.voff) * I.Cp;
+        // level-1 ancestor's final values (pyr_down12): channels, then S c
+        const float2* x1 = P.K > 1 ? P.lv + (int64_t)P.parent[v] * nc : nullptr;
         const float ci = P.cinit[v];
-        const float den = fmaf(ci, P.scv[v], P.K > 1 ? P.buf2[P.parent[v]] : 0.0f);
-        for (int ch = 0; ch < W; ++ch) {
-            const float num = fmaf(ci, A.r[o + ch], P.K > 1 ? P.buf[(int64_t)P.parent[v] * W + ch] : 0.0f);
+        const float den = fmaf(ci, P.scv[v], x1 ? x1[W].x + x1[W].y : 0.0f);
+        for (int ch = 0; ch < I.Cp; ++ch) {
+            const float num = fmaf(ci, A.r[o + ch], x1 ? x1[ch].x + x1[ch].y : 0.0f);
             A.y[o + ch] = den > 0.0f ? num / den : 0.0f;
         }
     }
@@ -1510,22 +1647,23 @@ int pyr_blocks(int64_t n)
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)device_info().sms * 8));
 }
 
-// full up-sweep of a level-0 vector (src0, W channels) or scalar (scal0) into lv
-cudaError_t pyr_up_all(const SolveArgs& A, const float* src0, const float* scal0, float* lv, int w,
-                       cudaStream_t s)
+// P of a level-0 vector (levels 1 .. top of every image) into lv: level 1
+// from src (with scal, S c and diag(A) too), level 2, then each image's
+// levels above; with wt, the down-sweep to level 1 as well (each image's
+// levels top .. 3 in pyr_tail, levels 2 and 1 in pyr_down12).
+cudaError_t pyr_sweep(const SolveArgs& A, const float* src, int nc, int scal, int up,
+                      const float* wt, cudaStream_t s)
 {
-    for (int k = 0; k + 1 < A.pyr.K; ++k)
-        pyr_up_kernel<<<pyr_blocks(A.pyr.off[k + 2] - A.pyr.off[k + 1]), 256, 0, s>>>(
-            A, k, src0, scal0, lv, w);
-    return cudaGetLastError();
-}
-
-// down-sweep of levels K-1 .. 1 with the given per-vertex weights
-cudaError_t pyr_down_all(const SolveArgs& A, const float* weight, float* lv, int w, cudaStream_t s)
-{
-    for (int k = A.pyr.K - 1; k >= 1; --k)
-        pyr_down_kernel<<<pyr_blocks(A.pyr.off[k + 1] - A.pyr.off[k]), 256, 0, s>>>(A, k, weight,
-                                                                                    lv, w);
+    const PyrDev& P = A.pyr;
+    if (P.K < 2) return cudaSuccess;
+    if (up) {
+        pyr_gather0_kernel<<<pyr_blocks(P.off[2] - P.off[1]), 256, 0, s>>>(A, src, nc, scal);
+        if (P.K > 2)
+            pyr_gather_kernel<<<pyr_blocks(P.off[3] - P.off[2]), 256, 0, s>>>(A, 1, nc);
+    }
+    if (P.K > 3 && (up || wt))
+        pyr_tail_kernel<<<A.ninst, kPyrTailThreads, 0, s>>>(A, nc, up, wt);
+    if (wt) pyr_down12_kernel<<<pyr_blocks(P.off[2] - P.off[1]), 256, 0, s>>>(A, nc, wt);
     return cudaGetLastError();
 }
 
@@ -1539,8 +1677,7 @@ cudaError_t pyr_precond(const SolveArgs& A, float2* out, cudaStream_t s)
         return o > 0 ? o : 1;
     }();
     prof_begin(fam, s);
-    cudaError_t e = pyr_up_all(A, A.r, nullptr, A.pyr.buf, A.pyr.W, s);
-    if (e == cudaSuccess) e = pyr_down_all(A, A.pyr.coef, A.pyr.buf, A.pyr.W, s);
+    cudaError_t e = pyr_sweep(A, A.r, A.pyr.W, 0, 1, A.pyr.coef, s);
     if (e == cudaSuccess) {
         const int nb = std::min(A.nvt, device_info().sms * occ);
         pyr_precond0_kernel<<<nb, kVTile, 0, s>>>(A, out);
@@ -1550,21 +1687,19 @@ cudaError_t pyr_precond(const SolveArgs& A, float2* out, cudaStream_t s)
     return e;
 }
 
-// the preconditioner's scale (after the splat) and the initial state y0
+// the preconditioner's scale (after the splat) and the initial state y0:
+// one up-sweep of (b, S c, diag A), coef, one down-sweep with cinit
 cudaError_t pyr_setup(const SolveArgs& A, cudaStream_t s)
 {
     static int fam = prof_family("pyr_setup");
     prof_begin(fam, s);
-    const int64_t T = A.pyr.off[A.pyr.K];
-    cudaError_t e = pyr_up_all(A, nullptr, A.pyr.dg, A.pyr.buf2, 1, s);
+    const int nc = A.pyr.W + 2;
+    cudaError_t e = pyr_sweep(A, A.r, nc, 1, 1, nullptr, s);
     if (e == cudaSuccess) {
-        pyr_coef_kernel<<<pyr_blocks(T), 256, 0, s>>>(A);
+        pyr_coef_kernel<<<pyr_blocks(A.pyr.off[A.pyr.K]), 256, 0, s>>>(A);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = pyr_up_all(A, A.r, nullptr, A.pyr.buf, A.pyr.W, s);
-    if (e == cudaSuccess) e = pyr_up_all(A, nullptr, A.pyr.scv, A.pyr.buf2, 1, s);
-    if (e == cudaSuccess) e = pyr_down_all(A, A.pyr.cinit, A.pyr.buf, A.pyr.W, s);
-    if (e == cudaSuccess) e = pyr_down_all(A, A.pyr.cinit, A.pyr.buf2, 1, s);
+    if (e == cudaSuccess) e = pyr_sweep(A, nullptr, nc, 0, 0, A.pyr.cinit, s);
     if (e == cudaSuccess) {
         pyr_init0_kernel<<<pyr_blocks(A.pyr.off[1]), 256, 0, s>>>(A);
         e = cudaGetLastError();
@@ -1724,7 +1859,11 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
                         if (tx < I.C) {
                             if (it > 0) {
                                 const double dprev = __ldcg(&A.scal[I.pc + tx].delta[slot ^ 1]);
-                                beta = dprev != 0.0 ? S.sd[tx] / dprev : 0.0;
+                                const double d0 = __ldcg(&A.scal[I.pc + tx].delta0);
+                                beta = dprev != 0.0 && !cg_stalled(S.sd[tx], d0) ? S.sd[tx] / dprev
+                                                                                 : 0.0;
+                            } else {
+                                A.scal[I.pc + tx].delta0 = S.sd[tx];
                             }
                             A.scal[I.pc + tx].delta[slot] = S.sd[tx];
                         }
@@ -1782,8 +1921,9 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
                         double alpha = 0.0;
                         if (tx < I.C) {
                             const double delta = __ldcg(&A.scal[I.pc + tx].delta[slot]);
+                            const double d0 = __ldcg(&A.scal[I.pc + tx].delta0);
                             const double dq = S.sd[tx];
-                            alpha = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
+                            alpha = (dq > 0.0 && !cg_stalled(delta, d0)) ? delta / dq : 0.0;
                         }
                         S.sa[tx] = alpha;
                     }

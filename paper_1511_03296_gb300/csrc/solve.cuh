@@ -6,27 +6,33 @@
 namespace fbs {
 
 constexpr int kMaxLevels = 16;     // bilateral-space pyramid levels (12-bit fields: at most 13)
+constexpr int kPyrMaxNc = 6;       // level-vector values per vertex: 4 channels, S c, diag A
+constexpr int kPyrTailThreads = 1024;
 
 // The bilateral-space pyramid of a grid (supplement) and the per-solve
 // arrays of the hierarchical preconditioner (Sec. 4).  Pyramid vertices are
 // numbered level by level: level k occupies [off[k], off[k+1]), level 0 is
 // the grid's vertices.  Values of levels >= 1 live in buf (W per vertex).
 struct PyrDev {
-    int K;                     // levels; the last has one vertex per image
-    int W;                     // channels per vertex (the batch's common Cp)
+    int K;                     // levels of the deepest image's pyramid (level 0 = the grid)
+    int W;                     // channels of a level vector: the widest image's Cp (<= 4)
     int64_t off[kMaxLevels + 1];
+    const int64_t* ioff;       // [K * (n_images + 1)]: image i's vertices on level k are
+                               //   [ioff[k (n+1) + i], ioff[k (n+1) + i + 1]) (absolute)
+    const uint8_t* kimg;       // [n_images]: levels of each image's own pyramid
     const int32_t* parent;     // [off[K-1]]: level-local parent (in level k+1) of each vertex below the top
     const int32_t* child_off;  // [off[K] - off[1] + 1]: children of level >= 1 vertex g are
     const int32_t* child_idx;  //   child_idx[child_off[g - off[1]] .. child_off[g - off[1] + 1])
                                //   (level-local indices in the level below, ascending)
-    const uint16_t* vimg;      // [off[1]]: image of each grid vertex
+    const uint16_t* vimg;      // [off[K]]: image of each pyramid vertex
     const float* cnt;          // [off[K]]: P(1), grid vertices below each pyramid vertex
-    const float* cinit;        // [off[K]]: initialisation weight w_init(k) / P(1)
+                               //   (0 on the vertex an image keeps past its own top)
+    const float* cinit;        // [off[K]]: initialisation weight w_init(k) / P(1) (0 likewise)
     float* coef;               // [off[K]]: preconditioner scale w(k) P(1) / P(diag A) (per solve)
     float* dg;                 // [off[1]]: diag(A) (per solve)
     float* scv;                // [off[1]]: S c (per solve)
-    float* buf;                // [(off[K] - off[1]) * W]: level values
-    float* buf2;               // [off[K] - off[1]]: second (1-channel) level values
+    float2* lv;                // [(off[K] - off[1]) * (W + 2)]: level values (double-float
+                               //   hi, lo), nc per vertex
     float* z;                  // CG vector layout: z = M_hier^-1 r
 };
 

@@ -463,10 +463,16 @@ def _halve(keys):
     return out
 
 
-def test_pyramid_matches_brute_force():
-    inst = synth.make_tiny(60, 40, 56, 5, 1)
+@pytest.mark.parametrize("h,w,sig", [(40, 56, (8.0, 4.0, 3.0)),
+                                     # sparse: levels shrink by less than half, so
+                                     # the parents outnumber twice the vertices
+                                     (30, 400, (1.0, 4.0, 3.0))])
+def test_pyramid_matches_brute_force(h, w, sig):
+    inst = synth.make_tiny(60, h, w, 5, 1, sig)
     g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
     sizes, parent = oracle.pyramid(g.vkey)
+    if sig[0] == 1.0:
+        assert parent.size > 2 * g.V
     keys, off = g.vkey.astype(np.uint64), 0
     for k in range(len(sizes) - 1):
         assert keys.size == sizes[k]
