@@ -112,6 +112,30 @@ fbs_status fbs_bistochastize(fbs_grid* g, int iters, void* stream);
 fbs_status fbs_solve(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters, void* stream);
 
 /*
+ * fbs_solve_lowrank -- the forward pass of a wide target through the
+ * low-rank reduction of the supplement (multiple output channels):
+ * for each image, B = S(c o t) (V x C) is factored by a column-pivoted QR
+ * B P = Q R; the rows of R P^T are ranked by their squared norm ("mass",
+ * ties in pivot order) and the fewest leading rows whose mass reaches
+ * (1 - eps) of |B|_F^2 are kept (t of them, the image's rank); the reduced
+ * system A Y~ = Q~ (the kept columns of Q) is solved with `pcg_iters`
+ * Jacobi-PCG iterations per column, exactly as fbs_solve solves a t-channel
+ * target, and x = S^T (Y~ R~) with R~ the kept rows.  R and P are formed on
+ * the host from the pivoted Cholesky factorisation of the Gram matrix
+ * B^T B (accumulated on the GPU with FP64 accuracy); a pivot at or below
+ * 1e-13 of the largest column mass ends the factorisation (numerically
+ * dependent columns have mass 0).  probs[k].x (C x N, device) receives x;
+ * probs[k].y must be NULL.  eps in [1e-12, 1); the paper uses 0.01.
+ * ranks: host array of n_images receiving t per image (0 when B = 0, then
+ * x = 0), or NULL.  SYNCHRONISES `stream` (twice: to read the Gram matrices
+ * back and at the end).  Errors: FBS_ERR_ARG (as fbs_solve, plus eps out of
+ * range, a NULL x or a non-NULL y), FBS_ERR_STATE (inside a stream capture,
+ * or before fbs_bistochastize), FBS_ERR_OOM, FBS_ERR_CUDA.
+ */
+fbs_status fbs_solve_lowrank(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters,
+                             double eps, int* ranks, void* stream);
+
+/*
  * fbs_solve_robust -- robust bilateral solver with the Geman-McClure loss
  * (supplement Sec. 3, Alg. 3): c <- c_init (probs[k].c); repeat irls_iters
  * times { x <- solve(t, c); e <- x - t; c <- 2 s^2 / (s^2 + e^2)^2 } with

@@ -11,8 +11,9 @@ arrays through ctypes and compiles the C file on first use.
 Parity status per function (what pins each one is in ``tests/test_oracle_pins.py``):
   keys, grid, bistochastize, splat, diag, apply_A, flat_init, pcg,
   pcg_single, pyramid, hierarchical (preconditioner and initialisation),
-  slice, solve, solve_robust, backward -- all pinned (closed forms, brute
-  force, dense linear algebra, invariants, finite differences).
+  slice, solve, solve_robust, backward, lowrank_factors, solve_lowrank --
+  all pinned (closed forms, brute force, dense linear algebra, invariants,
+  finite differences).
 """
 from __future__ import annotations
 
@@ -360,6 +361,53 @@ def backward(g: Grid, t, c, lam, pcg_iters, yhat, dx):
                                _ptr(t), _ptr(c), float(lam), int(pcg_iters), _ptr(yhat), _ptr(dx),
                                _ptr(dt), _ptr(dc)))
     return dt, dc
+
+
+def lowrank_factors(B, eps):
+    """The reduction of a wide right-hand side (supplement, multiple output
+    channels): B (V x C) = Q R P^T by a column-pivoted QR (LAPACK's
+    Businger-Golub pivoting, the library step); R' = R P^T; row masses
+    m_i = |R'_i|^2; rows ranked by mass (stable); the fewest leading rows
+    whose mass reaches (1 - eps) of the total are kept.  Returns
+    (Q~ V x t, R~ t x C, t); t = 0 when B = 0.  (The printed cut-off reads
+    "largest t with sum_{i<t} m_i <= (1 - eps) sum m_i", which can keep
+    nothing; the reading here keeps enough rows that the dropped mass is at
+    most eps of the total, the stated intent.)"""
+    import scipy.linalg
+    B = np.asarray(B, np.float64)
+    V, C = B.shape
+    Q, R, piv = scipy.linalg.qr(B, mode="economic", pivoting=True)
+    Rp = np.empty_like(R)
+    Rp[:, piv] = R                       # R P^T: columns back in input order
+    mass = (Rp ** 2).sum(axis=1)
+    total = float(mass.sum())
+    if total <= 0.0:
+        return Q[:, :0], Rp[:0], 0
+    order = np.argsort(-mass, kind="stable")
+    csum = np.cumsum(mass[order])
+    t = min(int(np.searchsorted(csum, (1.0 - eps) * total, side="left")) + 1, len(order))
+    keep = order[:t]
+    return Q[:, keep], Rp[keep, :], t
+
+
+def solve_lowrank(g: Grid, t, c, lam, pcg_iters, eps):
+    """Forward solve of a wide target through the low-rank reduction:
+    B = S(c o t) (Eq. 7's b, one column per channel), B ~ Q~ R~
+    (``lowrank_factors``), Y~ = A^-1 Q~ by Jacobi-PCG from the flat
+    initialisation per column (the same solve as every channel of
+    ``solve``), Y = Y~ R~, x = S^T Y.  Returns (y C x V, x C x N, t)."""
+    t = _c(t, np.float32).reshape(-1, g.N)
+    c = _c(c, np.float32).reshape(g.N)
+    C = t.shape[0]
+    b, sc = splat(g.vid, t, c, g.V)
+    Qt, Rt, r = lowrank_factors(b.T, eps)
+    a, minv = diag(g.m, g.nbr, g.n, sc, lam)
+    y = np.zeros((C, g.V), np.float64)
+    for q in range(r):
+        bq = np.ascontiguousarray(Qt[:, q])
+        yq = pcg(g.nbr, g.n, a, minv, lam, bq, flat_init(bq, sc), pcg_iters)
+        y += np.outer(Rt[q], yq)
+    return y, slice_(g.vid, y), r
 
 
 def run_instance(inst, bistoch_iters=2, pcg_iters=25):

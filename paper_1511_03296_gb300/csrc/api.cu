@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fbs_internal.cuh"
+#include "lowrank.cuh"
 #include "solve.cuh"
 
 namespace fbs {
@@ -973,9 +974,229 @@ std::vector<InstDev> base_instances(const fbs_grid* g, const fbs_problem_desc* p
     return inst;
 }
 
+// ------------------------------------------------ low-rank reduction ---
+// The reduction of a wide B = S(c o T) (V x C) by a column-pivoted QR
+// B P = Q R (supplement, multiple output channels).  R and P come from the
+// pivoted Cholesky factorisation of G = B^T B: pivoting on the largest
+// remaining diagonal of the Schur complement is pivoting on the largest
+// remaining column norm, so R^T R = P^T G P gives the same R (rows with
+// positive diagonal) as the QR.  Rows of R are ranked by their mass
+// m_i = |R_i|^2 (stable: ties in pivot order); the t kept are the fewest
+// leading ones whose mass reaches (1 - eps) of the total |B|_F^2 = trace G.
+// Q's kept columns are Q_k = B P R^-1 e_k, so the reduced right-hand sides
+// are B W with W = P R^-1 restricted to the kept columns (C x t), and
+// Y = Y_reduced R~ with R~ = the kept rows of R P^T (t x C).
+struct LrChoice {
+    int t = 0;                  // rows kept (0: B = 0)
+    std::vector<float> W;       // C x max(t, 1), row-major
+    std::vector<float> Rt;      // max(t, 1) x C, row-major
+};
+
+LrChoice lr_choose(const double* G, int ld, int C, double eps)
+{
+    std::vector<double> S((size_t)C * C), R((size_t)C * C, 0.0);
+    for (int i = 0; i < C; ++i)
+        for (int j = 0; j < C; ++j) S[(size_t)i * C + j] = G[(size_t)i * ld + j];
+    std::vector<int> piv(C);
+    for (int j = 0; j < C; ++j) piv[j] = j;
+    double dmax = 0.0, total = 0.0;
+    for (int j = 0; j < C; ++j) {
+        dmax = std::max(dmax, S[(size_t)j * C + j]);
+        total += S[(size_t)j * C + j];
+    }
+    // numerical rank: a pivot at or below 1e-13 of the largest column mass
+    // is rounding noise of an exactly dependent column
+    const double tol = dmax * 1e-13;
+    int r = 0;
+    for (int k = 0; k < C; ++k) {
+        int p = k;
+        for (int j = k + 1; j < C; ++j)
+            if (S[(size_t)j * C + j] > S[(size_t)p * C + p]) p = j;
+        if (!(S[(size_t)p * C + p] > tol)) break;
+        if (p != k) {
+            std::swap(piv[k], piv[p]);
+            for (int j = 0; j < C; ++j) std::swap(S[(size_t)k * C + j], S[(size_t)p * C + j]);
+            for (int i = 0; i < C; ++i) std::swap(S[(size_t)i * C + k], S[(size_t)i * C + p]);
+            for (int i = 0; i < k; ++i) std::swap(R[(size_t)i * C + k], R[(size_t)i * C + p]);
+        }
+        const double rkk = sqrt(S[(size_t)k * C + k]);
+        R[(size_t)k * C + k] = rkk;
+        for (int j = k + 1; j < C; ++j) R[(size_t)k * C + j] = S[(size_t)k * C + j] / rkk;
+        for (int i = k + 1; i < C; ++i)
+            for (int j = k + 1; j < C; ++j)
+                S[(size_t)i * C + j] -= R[(size_t)k * C + i] * R[(size_t)k * C + j];
+        r = k + 1;
+    }
+    LrChoice out;
+    std::vector<double> mass(r, 0.0);
+    for (int k = 0; k < r; ++k)
+        for (int j = k; j < C; ++j) mass[k] += R[(size_t)k * C + j] * R[(size_t)k * C + j];
+    std::vector<int> order(r);
+    for (int k = 0; k < r; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mass[a] > mass[b]; });
+    int t = 0;
+    if (total > 0.0) {
+        double acc = 0.0;
+        while (t < r && acc < (1.0 - eps) * total) acc += mass[order[t++]];
+    }
+    out.t = t;
+    const int tc = std::max(t, 1);
+    out.W.assign((size_t)C * tc, 0.0f);
+    out.Rt.assign((size_t)tc * C, 0.0f);
+    if (t == 0) return out;
+    // R^-1 of the leading r x r block (upper triangular), column by column
+    std::vector<double> Ri((size_t)r * r, 0.0);
+    for (int k = 0; k < r; ++k) {
+        Ri[(size_t)k * r + k] = 1.0 / R[(size_t)k * C + k];
+        for (int i = k - 1; i >= 0; --i) {
+            double acc = 0.0;
+            for (int j = i + 1; j <= k; ++j) acc += R[(size_t)i * C + j] * Ri[(size_t)j * r + k];
+            Ri[(size_t)i * r + k] = -acc / R[(size_t)i * C + i];
+        }
+    }
+    for (int q = 0; q < t; ++q) {
+        const int k = order[q];
+        for (int j = 0; j <= k; ++j) out.W[(size_t)piv[j] * tc + q] = (float)Ri[(size_t)j * r + k];
+        for (int j = k; j < C; ++j) out.Rt[(size_t)q * C + piv[j]] = (float)R[(size_t)k * C + j];
+    }
+    return out;
+}
+
 }  // namespace
 
 extern "C" {
+
+fbs_status fbs_solve_lowrank(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters,
+                             double eps, int* ranks, void* stream)
+{
+    fbs_status st = check_problems(g, probs, pcg_iters);
+    if (st) return st;
+    if (!(eps >= 1e-12 && eps < 1.0)) return FBS_ERR_ARG;
+    const int n = g->n_images;
+    for (int k = 0; k < n; ++k)
+        if (!probs[k].x || probs[k].y) return FBS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (capturing(s)) return FBS_ERR_STATE;
+    int cmax = 1;
+    for (int k = 0; k < n; ++k) cmax = std::max(cmax, probs[k].channels);
+    // B and its Gram matrices
+    std::vector<LrImg> li(n);
+    int64_t bfl = 0;
+    for (int k = 0; k < n; ++k) {
+        LrImg& L = li[k];
+        memset(&L, 0, sizeof(L));
+        L.t = probs[k].t;
+        L.c = probs[k].c;
+        L.C = probs[k].channels;
+        L.N = (int64_t)g->img[k].H * g->img[k].W;
+        L.pix_base = g->img[k].pix_base;
+        L.v0 = g->voff[k];
+        L.nv = g->voff[k + 1] - g->voff[k];
+        L.boff = bfl;
+        bfl += L.nv * L.C;
+    }
+    LrImg* d_li = nullptr;
+    int64_t* d_voff = nullptr;
+    float* B = nullptr;
+    float2* part = nullptr;
+    double* G = nullptr;
+    float *d_M = nullptr, *d_tr = nullptr, *d_xr = nullptr;
+    std::vector<double> hG((size_t)n * cmax * cmax);
+    std::vector<LrChoice> ch(n);
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        dfree(d_li, s); dfree(d_voff, s); dfree(B, s); dfree(part, s); dfree(G, s);
+        dfree(d_M, s); dfree(d_tr, s); dfree(d_xr, s);
+    };
+#define LR_TRY(x)                          \
+    do {                                   \
+        if ((e = (x)) != cudaSuccess) {    \
+            cleanup();                     \
+            return cuda_status(e);         \
+        }                                  \
+    } while (0)
+    LR_TRY(dalloc(&d_li, (size_t)n, s));
+    LR_TRY(dalloc(&d_voff, (size_t)n + 1, s));
+    LR_TRY(dalloc(&B, (size_t)bfl, s));
+    LR_TRY(dalloc(&part, (size_t)n * kLrGramBlocks * (cmax * (cmax + 1) / 2), s));
+    LR_TRY(dalloc(&G, hG.size(), s));
+    LR_TRY(cudaMemcpyAsync(d_li, li.data(), n * sizeof(LrImg), cudaMemcpyHostToDevice, s));
+    LR_TRY(cudaMemcpyAsync(d_voff, g->voff.data(), (n + 1) * sizeof(int64_t),
+                           cudaMemcpyHostToDevice, s));
+    LR_TRY(lr_splat(d_li, n, g->Vtot, d_voff, g->pstart, g->m, g->perm, B, s));
+    LR_TRY(lr_gram(d_li, n, B, part, G, cmax, s));
+    LR_TRY(cudaMemcpyAsync(hG.data(), G, hG.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LR_TRY(cudaStreamSynchronize(s));
+    // ranks and the maps in and out of the reduced system
+    int64_t mfl = 0, rfl = 0;
+    std::vector<int64_t> moff(n), roff(n);
+    for (int k = 0; k < n; ++k) {
+        ch[k] = lr_choose(hG.data() + (size_t)k * cmax * cmax, cmax, li[k].C, eps);
+        if (ranks) ranks[k] = ch[k].t;
+        moff[k] = mfl;
+        mfl += 2 * (int64_t)ch[k].W.size();
+        roff[k] = rfl;
+        rfl += li[k].N * std::max(ch[k].t, 1);
+    }
+    std::vector<float> hM((size_t)mfl);
+    for (int k = 0; k < n; ++k) {
+        std::copy(ch[k].W.begin(), ch[k].W.end(), hM.begin() + moff[k]);
+        std::copy(ch[k].Rt.begin(), ch[k].Rt.end(), hM.begin() + moff[k] + ch[k].W.size());
+    }
+    LR_TRY(dalloc(&d_M, (size_t)mfl, s));
+    LR_TRY(dalloc(&d_tr, (size_t)rfl, s));
+    LR_TRY(dalloc(&d_xr, (size_t)rfl, s));
+    LR_TRY(cudaMemcpyAsync(d_M, hM.data(), mfl * sizeof(float), cudaMemcpyHostToDevice, s));
+    // reduced targets T W
+    int64_t max_pixels = 1;
+    for (int k = 0; k < n; ++k) {
+        li[k].Cout = std::max(ch[k].t, 1);
+        li[k].M = d_M + moff[k];
+        li[k].out = d_tr + roff[k];
+        max_pixels = std::max(max_pixels, li[k].N);
+    }
+    LR_TRY(cudaMemcpyAsync(d_li, li.data(), n * sizeof(LrImg), cudaMemcpyHostToDevice, s));
+    LR_TRY(lr_map(d_li, n, max_pixels, s));
+    // the reduced solve
+    std::vector<fbs_problem_desc> rp(probs, probs + n);
+    for (int k = 0; k < n; ++k) {
+        rp[k].t = d_tr + roff[k];
+        rp[k].x = d_xr + roff[k];
+        rp[k].y = nullptr;
+        rp[k].channels = li[k].Cout;
+    }
+    std::vector<InstDev> inst = base_instances(g, rp.data());
+    SolvePlan plan;
+    memset(&plan, 0, sizeof(plan));
+    plan.mode = kSplatConfidence;
+    plan.outer_iters = 1;
+    plan.pcg_iters = pcg_iters;
+    plan.sigma_gm = 1.0f;
+    st = run(g, inst, plan, s);
+    if (st) {
+        cleanup();
+        return st;
+    }
+    // x = x_reduced R~
+    for (int k = 0; k < n; ++k) {
+        li[k].t = d_xr + roff[k];
+        li[k].C = li[k].Cout;
+        li[k].Cout = probs[k].channels;
+        li[k].M = d_M + moff[k] + ch[k].W.size();
+        li[k].out = probs[k].x;
+    }
+    // (stream-ordered after the first map, which read the previous copy)
+    if ((e = cudaMemcpyAsync(d_li, li.data(), n * sizeof(LrImg), cudaMemcpyHostToDevice, s)) ==
+        cudaSuccess)
+        e = lr_map(d_li, n, max_pixels, s);
+    // the host copies above are stream-ordered: finish them before the
+    // host vectors go out of scope
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cleanup();
+#undef LR_TRY
+    if (e != cudaSuccess) return cuda_status(e);
+    return e2 == cudaSuccess ? FBS_OK : cuda_status(e2);
+}
 
 fbs_status fbs_solve(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters, void* stream)
 {

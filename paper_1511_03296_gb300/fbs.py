@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "FBS_OK", 1: "FBS_ERR_ARG", 2: "FBS_ERR_RANGE", 3: "FBS_ERR_O
 EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robust",
             "fbs_solve_backward", "fbs_grid_info", "fbs_grid_export", "fbs_grid_sync",
             "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read",
-            "fbs_set_option", "fbs_solve_static", "fbs_autotune"]
+            "fbs_set_option", "fbs_solve_static", "fbs_autotune", "fbs_solve_lowrank"]
 
 OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT, OPT_PCG_FORM = 1, 2, 3, 4
 OPT_PHASE_BLOCKS, OPT_PRECONDITIONER = 5, 6
@@ -73,6 +73,8 @@ def load(path: Optional[str] = None):
         L.fbs_bistochastize.argtypes = [P, I, P]
         L.fbs_solve.argtypes = [P, ctypes.POINTER(ProblemDesc), I, P]
         L.fbs_solve_robust.argtypes = [P, ctypes.POINTER(ProblemDesc), F, I, I, P]
+        L.fbs_solve_lowrank.argtypes = [P, ctypes.POINTER(ProblemDesc), I, ctypes.c_double,
+                                        ctypes.POINTER(I), P]
         L.fbs_solve_backward.argtypes = [P, ctypes.POINTER(ProblemDesc), ctypes.POINTER(P),
                                          ctypes.POINTER(P), ctypes.POINTER(P), I, P]
         L.fbs_grid_info.argtypes = [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64)]
@@ -247,6 +249,19 @@ def solve_static(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25,
     probs = _problems(grid, t, c, lam, x, y)
     _check(load().fbs_solve_static(grid.handle, probs, int(pcg_iters), _stream_ptr(stream)),
            "fbs_solve_static")
+
+
+def solve_lowrank(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25, eps: float = 0.01,
+                  x: Optional[List] = None, stream=None) -> List[int]:
+    """fbs_solve_lowrank: a wide target solved through the low-rank
+    reduction of B = S(c o t) (column-pivoted QR, rows kept by mass down to
+    a residual fraction eps); writes x (C x H x W) per image and returns the
+    rank each image was solved at.  Synchronises the stream."""
+    probs = _problems(grid, t, c, lam, x, None)
+    ranks = (ctypes.c_int * grid.n_images)()
+    _check(load().fbs_solve_lowrank(grid.handle, probs, int(pcg_iters), float(eps), ranks,
+                                    _stream_ptr(stream)), "fbs_solve_lowrank")
+    return list(ranks)
 
 
 def solve_robust(grid: Grid, t: List, c: List, lam, sigma_gm: float, irls_iters: int = 10,

@@ -197,16 +197,29 @@ def _smooth_field(rng, h, w, sigma, step=8):
     return zoom(coarse, (h / hs, w / ws), order=1)[:h, :w]
 
 
-def segmentation_instance(rng, h, w, n_classes, sigmas, lam, blob_sigma=24.0):
-    """Label blobs = argmax over smoothed random fields; t = softmax of smoothed noisy logits."""
+def segmentation_instance(rng, h, w, n_classes, sigmas, lam, blob_sigma=24.0, n_present=None):
+    """Label blobs = argmax over smoothed random fields; t = softmax of smoothed noisy logits.
+
+    With n_present, only that many classes (drawn at random) occur in the
+    label map and the others get logits 8 lower (probability ~3e-4 of a
+    present class's), as a CNN assigns next to nothing to classes absent
+    from a scene: B = S(c o t) is then close to rank n_present."""
     step = 8 if blob_sigma >= 16 else 1
     fields = np.stack([_smooth_field(rng, h, w, blob_sigma, step) for _ in range(n_classes)])
+    absent = None
+    if n_present is not None:
+        present = rng.choice(n_classes, size=n_present, replace=False)
+        absent = np.ones(n_classes, bool)
+        absent[present] = False
+        fields[absent] = -np.inf
     labels = np.argmax(fields, axis=0)
     colours = rng.integers(0, 256, size=(n_classes, 3))
     rgb = colours[labels].astype(np.uint8)
     yuv = rgb_to_yuv_planar(add_noise_u8(rng, rgb, 4.0))
     onehot = (labels[None] == np.arange(n_classes)[:, None, None]).astype(np.float64)
     logits = 4.0 * onehot + rng.normal(size=onehot.shape)
+    if absent is not None:
+        logits[absent] -= 8.0
     logits = _smooth_stack(logits, 2.0)
     logits -= logits.max(axis=0, keepdims=True)
     e = np.exp(logits)
@@ -291,6 +304,17 @@ def segmentation_16(seed: int = 5, n_images: int = 16, h: int = 480, w: int = 64
     rng = np.random.Generator(np.random.PCG64(seed))
     insts = [segmentation_instance(rng, h, w, 21, (8.0, 4.0, 3.0), 128.0) for _ in range(n_images)]
     return Workload(f"segmentation {n_images}x{w}x{h} C=21", insts, backward=True)
+
+
+def segmentation_scenes_16(seed: int = 6, n_images: int = 16, h: int = 480, w: int = 640,
+                           n_present=(2, 6)) -> Workload:
+    """16 images 640x480, C = 21 softmax targets of which 2-6 classes occur
+    per image (the regime of the low-rank reduction), c ~ U[0, 1]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    insts = [segmentation_instance(rng, h, w, 21, (8.0, 4.0, 3.0), 128.0,
+                                   n_present=int(rng.integers(n_present[0], n_present[1] + 1)))
+             for _ in range(n_images)]
+    return Workload(f"segmentation scenes {n_images}x{w}x{h} C=21", insts)
 
 
 def crop(inst: Instance, y0: int, x0: int, h: int, w: int) -> Instance:

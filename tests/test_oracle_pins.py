@@ -548,3 +548,71 @@ def test_hier_converges_faster_than_jacobi():
         with oracle.hierarchical(g):
             yh, _ = oracle.solve(g, inst.t, inst.c, lam, k)
         assert loss(yh[0]) - f_star < 0.5 * (loss(yj[0]) - f_star), k
+
+
+# ---- low-rank reduction of a wide target (supplement, multiple output channels) ----
+
+def test_lowrank_rank_rule_closed_form():
+    # orthogonal columns of norms 3, 0, 4, 1: the pivoted QR takes them in the
+    # order 4, 3, 1 with a diagonal R, so the row masses are 16, 9, 1, 0 of a
+    # total 26; the kept rows are the fewest whose mass reaches (1 - eps) 26
+    rng = np.random.default_rng(0)
+    U, _ = np.linalg.qr(rng.standard_normal((50, 4)))
+    B = U * np.array([3.0, 0.0, 4.0, 1.0])
+    for eps, t_exp in ((0.5, 1), (0.1, 2), (0.05, 2), (0.01, 3), (1e-9, 3)):
+        Qt, Rt, t = oracle.lowrank_factors(B, eps)
+        assert t == t_exp, (eps, t)
+        # Q~ R~ keeps exactly the kept columns of B
+        kept = np.argsort(-np.array([9.0, 0.0, 16.0, 1.0]), kind="stable")[:t]
+        expect = np.zeros_like(B)
+        expect[:, kept] = B[:, kept]
+        assert np.allclose(Qt @ Rt, expect, atol=1e-12)
+
+
+def test_lowrank_factors_invariants():
+    # Q~ orthonormal; the dropped mass is at most eps of |B|_F^2; one row
+    # fewer would drop more (t is minimal)
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((400, 9)) @ np.diag(2.0 ** -np.arange(9)) @ rng.standard_normal((9, 9))
+    total = (B ** 2).sum()
+    for eps in (0.2, 0.01, 1e-4):
+        Qt, Rt, t = oracle.lowrank_factors(B, eps)
+        assert np.allclose(Qt.T @ Qt, np.eye(t), atol=1e-12)
+        assert ((B - Qt @ Rt) ** 2).sum() <= eps * total * (1 + 1e-9)
+        if t > 1:
+            assert ((B - Qt[:, :t - 1] @ Rt[:t - 1]) ** 2).sum() > eps * total
+
+
+def test_lowrank_exact_rank_converged_equals_full_solve():
+    # a 5-channel target of rank 2 (pixel-level combinations of two channels):
+    # B = S(c o T) has rank 2, the reduction keeps 2 columns for any small
+    # eps, and converged solves agree, as A^-1 B = (A^-1 Q~) R~ exactly
+    inst = synth.make_tiny(71, 40, 56, 5, 2)
+    t1, t2 = inst.t[0].astype(np.float64), inst.t[1].astype(np.float64)
+    T = np.stack([t1, t2, t1 + t2, 0.0 * t1, 2.0 * t1 - t2]).astype(np.float32)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    y, x, t = oracle.solve_lowrank(g, T, inst.c, inst.lam, 600, 1e-9)
+    assert t == 2
+    yf, xf = oracle.solve(g, T, inst.c, inst.lam, 600)
+    assert np.linalg.norm(x - xf) <= 1e-8 * np.linalg.norm(xf)
+    assert np.abs(x[3]).max() == 0.0 or np.abs(x[3]).max() <= 1e-10 * np.abs(xf).max()
+
+
+def test_lowrank_zero_target():
+    inst = synth.make_tiny(72, 24, 32, 3, 3)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    y, x, t = oracle.solve_lowrank(g, np.zeros_like(inst.t), inst.c, inst.lam, 25, 0.01)
+    assert t == 0 and not x.any() and not y.any()
+
+
+def test_lowrank_tiny_eps_equals_full_solve_at_any_iteration_count_for_one_channel():
+    # one channel: Q~ = b / |b| and R~ = |b|, and PCG is homogeneous of
+    # degree 1 in b, so the reduced solve equals the plain one at every
+    # iteration count
+    inst = synth.make_tiny(73, 40, 56, 5, 1)
+    g = oracle.build_grid(inst.yuv, inst.sigma_xy, inst.sigma_l, inst.sigma_uv, 2)
+    for it in (0, 3, 25):
+        _, x, t = oracle.solve_lowrank(g, inst.t, inst.c, inst.lam, it, 0.01)
+        _, xf = oracle.solve(g, inst.t, inst.c, inst.lam, it)
+        assert t == 1
+        assert np.linalg.norm(x - xf) <= 1e-12 * np.linalg.norm(xf)
