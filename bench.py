@@ -49,7 +49,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the batched and forward+backward workloads")
-    p.add_argument("--only", choices=["batched", "fwd_bwd"], default=None,
+    p.add_argument("--only", choices=["batched", "fwd_bwd", "lowrank"], default=None,
                    help="run one extra workload alone (for profiling) and print its line")
     p.add_argument("--images", type=int, default=None,
                    help="image count of the --only workload (default: its full size)")
@@ -475,6 +475,77 @@ def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
                                  traffic=None)}
 
 
+def run_extra_lowrank(dist, flush, stream, steps, warmup, n_images=16, eps=0.01):
+    """16 scenes 640x480 with 21-channel softmax targets of which 2-6 classes
+    occur: the full 21-channel forward solve against the low-rank reduction
+    (eps = 0.01), each with its grid build and bistochastisation."""
+    import torch
+    from paper_1511_03296_gb300 import fbs, synth
+    wl = synth.segmentation_scenes_16(seed=rank_seed(6, dist.rank), n_images=n_images)
+    insts = wl.instances
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    yuv = [dev(i.yuv) for i in insts]
+    t = [dev(i.t) for i in insts]
+    c = [dev(i.c) for i in insts]
+    x_full = [torch.empty_like(tt) for tt in t]
+    x_lr = [torch.empty_like(tt) for tt in t]
+    sig = ([i.sigma_xy for i in insts], [i.sigma_l for i in insts], [i.sigma_uv for i in insts])
+    lam = [i.lam for i in insts]
+    info = {}
+
+    def full():
+        g = fbs.grid_build(yuv, *sig)
+        fbs.bistochastize(g, BISTOCH_ITERS)
+        fbs.solve(g, t, c, lam, PCG_ITERS, x=x_full)
+        g.destroy()
+
+    def lowrank():
+        g = fbs.grid_build(yuv, *sig)
+        fbs.bistochastize(g, BISTOCH_ITERS)
+        info["ranks"] = fbs.solve_lowrank(g, t, c, lam, PCG_ITERS, eps, x=x_lr)
+        g.destroy()
+
+    ms_f = time_steps(full, steps, warmup, flush, stream)
+    ms_l = time_steps(lowrank, steps, warmup, flush, stream)
+    num = sum(float(((a - b) ** 2).sum()) for a, b in zip(x_lr, x_full))
+    den = sum(float((b ** 2).sum()) for b in x_full)
+    mf, ml = dist.max(sum(ms_f) / len(ms_f)), dist.max(sum(ms_l) / len(ms_l))
+    npix = wl.n_pixels
+    return {"workload": f"{n_images} scenes 640x480, C=21 softmax targets with 2-6 classes "
+                        "present, c~U[0,1], sigma=(8,4,3), lambda=128, 25 PCG iterations",
+            "pixels": npix, "eps": eps, "ranks": info["ranks"],
+            "full_ms": mf, "full_mpix_s": whole_job_mpix(dist.world, npix, mf),
+            "lowrank_ms": ml, "lowrank_mpix_s": whole_job_mpix(dist.world, npix, ml),
+            "speedup": mf / ml, "rel_l2_vs_full": (num / den) ** 0.5}
+
+
+def run_extra_dt(dist, flush, stream, steps, warmup):
+    """The domain transform post-filter on the 1080p workload's 3-channel
+    output (sigma_s = 32, sigma_r = 64, 3 iterations, the reference as the
+    guide), timed alone: the paper includes it in every runtime."""
+    import torch
+    from paper_1511_03296_gb300 import fbs, synth
+    inst = synth.plain_1080p(seed=rank_seed(2, dist.rank)).instances[0]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    guide, x0 = dev(inst.yuv), dev(inst.t)
+    x = torch.empty_like(x0)
+
+    def step():
+        x.copy_(x0)
+        fbs.domain_transform(guide, x, 32.0, 64.0, 3)
+
+    def copy_only():
+        x.copy_(x0)
+
+    ms = time_steps(step, steps, warmup, flush, stream)
+    mc = time_steps(copy_only, steps, warmup, flush, stream)
+    m = dist.max(sum(ms) / len(ms) - sum(mc) / len(mc))
+    return {"workload": "domain transform of a 1920x1080 3-channel image, sigma_s=32, "
+                        "sigma_r=64, 3 iterations (rows: parallel affine scans; columns: "
+                        "one thread per column)",
+            "ms": m, "mpix_s": whole_job_mpix(dist.world, inst.n_pixels, m)}
+
+
 def run_only(args, dist):
     """One extra workload alone (a profiling aid): prints its own JSON line."""
     import torch
@@ -490,6 +561,9 @@ def run_only(args, dist):
     if args.only == "batched":
         out = run_extra_batched(dist, flush, stream, peak, args.steps, args.warmup,
                                 n_images=args.images or 64, sequential=False)
+    elif args.only == "lowrank":
+        out = run_extra_lowrank(dist, flush, stream, args.steps, args.warmup,
+                                n_images=args.images or 16)
     else:
         out = run_extra_fwd_bwd(dist, flush, stream, peak, args.steps, args.warmup,
                                 n_images=args.images or 16)
@@ -626,6 +700,8 @@ def run_ours(args, dist):
         line["batched"] = run_extra_batched(dist, flush, stream, peak, xs, 3)
         line["fwd_bwd"] = run_extra_fwd_bwd(dist, flush, stream, peak, xs, 3)
         line["robust"] = run_extra_robust(dist, flush, stream, peak, max(3, xs // 2), 3)
+        line["lowrank"] = run_extra_lowrank(dist, flush, stream, max(3, xs // 2), 3)
+        line["domain_transform"] = run_extra_dt(dist, flush, stream, xs, 3)
     if dist.rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(synth.plain_1080p().instances[0], args.cpu_seconds)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.cpu_seconds / 2)

@@ -136,6 +136,24 @@ fbs_status fbs_solve_lowrank(fbs_grid* g, const fbs_problem_desc* probs, int pcg
                              double eps, int* ranks, void* stream);
 
 /*
+ * fbs_domain_transform -- the edge-aware post-filter the paper runs on the
+ * solver's output (Sec. 5: it smooths the blocky artefacts of the
+ * simplified grid; Gastal and Oliveira 2011, recursive formulation).
+ * guide: 3 x height x width (device, planar; its values set the edges, in
+ * the units sigma_r is given in), x: channels x height x width (device),
+ * filtered in place.  With d = 1 + (sigma_s / sigma_r) sum_c |dI_c| the
+ * step length between horizontally (vertically) adjacent pixels, iteration
+ * i = 1 .. iterations filters every row and then every column forward and
+ * backward with J[k] <- (1 - a^d) J[k] + a^d J[k -/+ 1], a = exp(-sqrt(2) /
+ * sigma_i), sigma_i = sigma_s sqrt(3) 2^(iterations - i) /
+ * sqrt(4^iterations - 1).  FP32.  Errors: FBS_ERR_ARG (NULL buffers,
+ * non-positive sizes or sigmas, iterations outside 1 .. 16, width above
+ * 29000), FBS_ERR_OOM, FBS_ERR_CUDA.
+ */
+fbs_status fbs_domain_transform(const float* guide, int height, int width, float* x, int channels,
+                                float sigma_s, float sigma_r, int iterations, void* stream);
+
+/*
  * fbs_solve_robust -- robust bilateral solver with the Geman-McClure loss
  * (supplement Sec. 3, Alg. 3): c <- c_init (probs[k].c); repeat irls_iters
  * times { x <- solve(t, c); e <- x - t; c <- 2 s^2 / (s^2 + e^2)^2 } with

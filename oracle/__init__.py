@@ -11,7 +11,8 @@ arrays through ctypes and compiles the C file on first use.
 Parity status per function (what pins each one is in ``tests/test_oracle_pins.py``):
   keys, grid, bistochastize, splat, diag, apply_A, flat_init, pcg,
   pcg_single, pyramid, hierarchical (preconditioner and initialisation),
-  slice, solve, solve_robust, backward, lowrank_factors, solve_lowrank --
+  slice, solve, solve_robust, backward, lowrank_factors, solve_lowrank,
+  domain_transform --
   all pinned (closed forms, brute force, dense linear algebra, invariants,
   finite differences).
 """
@@ -84,6 +85,8 @@ def lib():
             L.fbso_hier_precond.restype = _I
             L.fbso_hier_init.argtypes = [_P, _P, _P]
             L.fbso_hier_init.restype = _I
+            L.fbso_domain_transform.argtypes = [_I64, _I64, _I, _P, _D, _D, _I, _P]
+            L.fbso_domain_transform.restype = _I
             L.fbso_slice.argtypes = [_I64, _I64, _I, _P, _P, _P]
             L.fbso_slice.restype = None
             L.fbso_solve.argtypes = [_I64, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P]
@@ -408,6 +411,18 @@ def solve_lowrank(g: Grid, t, c, lam, pcg_iters, eps):
         yq = pcg(g.nbr, g.n, a, minv, lam, bq, flat_init(bq, sc), pcg_iters)
         y += np.outer(Rt[q], yq)
     return y, slice_(g.vid, y), r
+
+
+def domain_transform(guide, x, sigma_s, sigma_r, iters=3):
+    """The domain transform post-filter (recursive formulation of Gastal
+    and Oliveira 2011, as the paper's Sec. 5 applies it to the solver's
+    output): guide 3 x H x W, x C x H x W; returns the filtered x (FP64)."""
+    guide = _c(guide, np.float32)
+    H, W = guide.shape[1], guide.shape[2]
+    x = np.array(x, dtype=np.float64, copy=True, order="C").reshape(-1, H, W)
+    _check(lib().fbso_domain_transform(H, W, x.shape[0], _ptr(guide), float(sigma_s),
+                                       float(sigma_r), int(iters), _ptr(x)))
+    return x
 
 
 def run_instance(inst, bistoch_iters=2, pcg_iters=25):

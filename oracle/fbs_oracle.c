@@ -713,3 +713,66 @@ int fbso_backward(int64_t N, int64_t V, int C, const uint32_t* vid, const uint32
     free(g); free(z); free(sc); free(a); free(minv);
     return st;
 }
+
+/* ---------------------------------------------------------------------
+ * Domain transform post-filter (Sec. 5 runs it on the solver's output to
+ * smooth the simplified grid's blocky artefacts; the filter is Gastal and
+ * Oliveira 2011's recursive formulation, restated here from its
+ * published definition).  For a 3-channel guide I (H x W, planar) the step
+ * from a pixel to its left (upper) neighbour has length
+ *     d = 1 + (sigma_s / sigma_r) * sum_c |I_c(p) - I_c(p')|
+ * in the transformed domain.  Iteration i = 1..N filters every row and
+ * then every column with a first-order recursive filter of feedback
+ * a_i = exp(-sqrt(2) / sigma_i), sigma_i = sigma_s sqrt(3) 2^(N-i) /
+ * sqrt(4^N - 1) (the iterations' variances add up to sigma_s^2): along a
+ * line with values J and step lengths d (d[k] between k-1 and k),
+ *     forward   J[k] <- (1 - a^d[k]) J[k] + a^d[k] J[k-1],     k = 1 .. L-1
+ *     backward  J[k] <- (1 - a^d[k+1]) J[k] + a^d[k+1] J[k+1], k = L-2 .. 0.
+ * x (C x H x W) is filtered in place. */
+static void dt_line(double* J, const double* d, int64_t L, int64_t stride, double a)
+{
+    for (int64_t k = 1; k < L; ++k) {
+        const double w = pow(a, d[k * stride]);
+        J[k * stride] = (1.0 - w) * J[k * stride] + w * J[(k - 1) * stride];
+    }
+    for (int64_t k = L - 2; k >= 0; --k) {
+        const double w = pow(a, d[(k + 1) * stride]);
+        J[k * stride] = (1.0 - w) * J[k * stride] + w * J[(k + 1) * stride];
+    }
+}
+
+int fbso_domain_transform(int64_t H, int64_t W, int C, const float* guide, double sigma_s,
+                          double sigma_r, int iters, double* x)
+{
+    if (H < 1 || W < 1 || C < 1 || !(sigma_s > 0) || !(sigma_r > 0) || iters < 1)
+        return FBSO_ERR_ARG;
+    const int64_t N = H * W;
+    double* dh = (double*)calloc((size_t)N, sizeof(double));   /* step from (y, x-1) to (y, x) */
+    double* dv = (double*)calloc((size_t)N, sizeof(double));   /* step from (y-1, x) to (y, x) */
+    if (!dh || !dv) { free(dh); free(dv); return FBSO_ERR_OOM; }
+    const double r = sigma_s / sigma_r;
+    for (int64_t yy = 0; yy < H; ++yy)
+        for (int64_t xx = 0; xx < W; ++xx) {
+            const int64_t p = yy * W + xx;
+            double sh = 0.0, sv = 0.0;
+            for (int ch = 0; ch < 3; ++ch) {
+                const double v = guide[ch * N + p];
+                if (xx > 0) sh += fabs(v - (double)guide[ch * N + p - 1]);
+                if (yy > 0) sv += fabs(v - (double)guide[ch * N + p - W]);
+            }
+            dh[p] = 1.0 + r * sh;
+            dv[p] = 1.0 + r * sv;
+        }
+    for (int i = 1; i <= iters; ++i) {
+        const double sig_i = sigma_s * sqrt(3.0) * pow(2.0, (double)(iters - i)) /
+                             sqrt(pow(4.0, (double)iters) - 1.0);
+        const double a = exp(-sqrt(2.0) / sig_i);
+        for (int ch = 0; ch < C; ++ch) {
+            double* X = x + (int64_t)ch * N;
+            for (int64_t yy = 0; yy < H; ++yy) dt_line(X + yy * W, dh + yy * W, W, 1, a);
+            for (int64_t xx = 0; xx < W; ++xx) dt_line(X + xx, dv + xx, H, W, a);
+        }
+    }
+    free(dh); free(dv);
+    return FBSO_OK;
+}

@@ -218,6 +218,12 @@ int64_t next_pow2(int64_t x)
 }  // namespace
 }  // namespace fbs
 
+namespace fbs {
+cudaError_t domain_transform(const float* guide, int H, int W, float* x, int C, float sigma_s,
+                             float sigma_r, int iters, float* dh, float* dv, cudaStream_t s);
+int domain_transform_max_width();
+}  // namespace fbs
+
 using namespace fbs;
 
 // -------------------------------------------------------------- handle ----
@@ -1196,6 +1202,26 @@ fbs_status fbs_solve_lowrank(fbs_grid* g, const fbs_problem_desc* probs, int pcg
 #undef LR_TRY
     if (e != cudaSuccess) return cuda_status(e);
     return e2 == cudaSuccess ? FBS_OK : cuda_status(e2);
+}
+
+fbs_status fbs_domain_transform(const float* guide, int height, int width, float* x, int channels,
+                                float sigma_s, float sigma_r, int iterations, void* stream)
+{
+    if (!guide || !x || height < 1 || width < 1 || channels < 1 || channels > 65535 ||
+        !(sigma_s > 0.f) || !isfinite(sigma_s) || !(sigma_r > 0.f) || !isfinite(sigma_r) ||
+        iterations < 1 || iterations > 16 || width > domain_transform_max_width())
+        return FBS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = (size_t)height * width;
+    float *dh = nullptr, *dv = nullptr;
+    cudaError_t e = dalloc(&dh, N, s);
+    if (e == cudaSuccess) e = dalloc(&dv, N, s);
+    if (e == cudaSuccess)
+        e = domain_transform(guide, height, width, x, channels, sigma_s, sigma_r, iterations, dh,
+                             dv, s);
+    dfree(dh, s);
+    dfree(dv, s);
+    return e == cudaSuccess ? FBS_OK : cuda_status(e);
 }
 
 fbs_status fbs_solve(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters, void* stream)

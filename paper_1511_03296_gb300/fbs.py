@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "FBS_OK", 1: "FBS_ERR_ARG", 2: "FBS_ERR_RANGE", 3: "FBS_ERR_O
 EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robust",
             "fbs_solve_backward", "fbs_grid_info", "fbs_grid_export", "fbs_grid_sync",
             "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read",
-            "fbs_set_option", "fbs_solve_static", "fbs_autotune", "fbs_solve_lowrank"]
+            "fbs_set_option", "fbs_solve_static", "fbs_autotune", "fbs_solve_lowrank",
+            "fbs_domain_transform"]
 
 OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT, OPT_PCG_FORM = 1, 2, 3, 4
 OPT_PHASE_BLOCKS, OPT_PRECONDITIONER = 5, 6
@@ -75,6 +76,7 @@ def load(path: Optional[str] = None):
         L.fbs_solve_robust.argtypes = [P, ctypes.POINTER(ProblemDesc), F, I, I, P]
         L.fbs_solve_lowrank.argtypes = [P, ctypes.POINTER(ProblemDesc), I, ctypes.c_double,
                                         ctypes.POINTER(I), P]
+        L.fbs_domain_transform.argtypes = [P, I, I, P, I, F, F, I, P]
         L.fbs_solve_backward.argtypes = [P, ctypes.POINTER(ProblemDesc), ctypes.POINTER(P),
                                          ctypes.POINTER(P), ctypes.POINTER(P), I, P]
         L.fbs_grid_info.argtypes = [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64)]
@@ -262,6 +264,25 @@ def solve_lowrank(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25, eps: f
     _check(load().fbs_solve_lowrank(grid.handle, probs, int(pcg_iters), float(eps), ranks,
                                     _stream_ptr(stream)), "fbs_solve_lowrank")
     return list(ranks)
+
+
+def domain_transform(guide, x, sigma_s: float, sigma_r: float, iterations: int = 3,
+                     stream=None) -> None:
+    """fbs_domain_transform: edge-aware recursive filtering of x (C x H x W,
+    in place) guided by a 3 x H x W image -- the post-filter the paper runs
+    on the solver's output."""
+    import torch
+    if guide.dim() != 3 or guide.shape[0] != 3:
+        raise ValueError("guide must be 3 x H x W")
+    H, W = int(guide.shape[1]), int(guide.shape[2])
+    if x.dim() == 2:
+        x = x.unsqueeze(0)
+    if x.dim() != 3 or tuple(x.shape[1:]) != (H, W):
+        raise ValueError("x must be C x H x W with the guide's H and W")
+    _check(load().fbs_domain_transform(_dev_ptr(guide, "guide", torch.float32), H, W,
+                                       _dev_ptr(x, "x", torch.float32), int(x.shape[0]),
+                                       float(sigma_s), float(sigma_r), int(iterations),
+                                       _stream_ptr(stream)), "fbs_domain_transform")
 
 
 def solve_robust(grid: Grid, t: List, c: List, lam, sigma_gm: float, irls_iters: int = 10,

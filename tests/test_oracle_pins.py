@@ -616,3 +616,43 @@ def test_lowrank_tiny_eps_equals_full_solve_at_any_iteration_count_for_one_chann
         _, xf = oracle.solve(g, inst.t, inst.c, inst.lam, it)
         assert t == 1
         assert np.linalg.norm(x - xf) <= 1e-12 * np.linalg.norm(xf)
+
+
+# ---- domain transform post-filter (Sec. 5; Gastal and Oliveira 2011, recursive form) ----
+
+def test_domain_transform_keeps_constants():
+    rng = np.random.default_rng(2)
+    guide = rng.uniform(0, 255, size=(3, 17, 23)).astype(np.float32)
+    x = np.full((2, 17, 23), 3.25)
+    out = oracle.domain_transform(guide, x, 16.0, 32.0, 3)
+    assert np.allclose(out, 3.25, rtol=0, atol=1e-12)
+
+
+def test_domain_transform_impulse_response_closed_form():
+    # one iteration on a single row of a flat guide (every step of length 1):
+    # the forward then backward recursive filter of feedback a has the
+    # two-sided impulse response (1 - a) / (1 + a) a^|n| away from the ends
+    L, sig = 401, 4.0
+    guide = np.zeros((3, 1, L), np.float32)
+    x = np.zeros((1, 1, L))
+    x[0, 0, L // 2] = 1.0
+    out = oracle.domain_transform(guide, x, sig, 10.0, 1)[0, 0]
+    a = np.exp(-np.sqrt(2.0) / sig)
+    n = np.arange(L) - L // 2
+    assert np.allclose(out, (1 - a) / (1 + a) * a ** np.abs(n), rtol=1e-12, atol=1e-15)
+
+
+def test_domain_transform_stops_at_an_edge():
+    # a hard edge in the guide and a tiny range bandwidth: nothing crosses it,
+    # so each side is filtered as an image of its own
+    rng = np.random.default_rng(3)
+    H, W, k = 12, 30, 14
+    guide = np.zeros((3, H, W), np.float32)
+    guide[:, :, k + 1:] = 255.0
+    x = rng.standard_normal((2, H, W))
+    out = oracle.domain_transform(guide, x, 8.0, 1e-6, 3)
+    left = oracle.domain_transform(guide[:, :, :k + 1], x[:, :, :k + 1], 8.0, 1e-6, 3)
+    right = oracle.domain_transform(guide[:, :, k + 1:], x[:, :, k + 1:], 8.0, 1e-6, 3)
+    assert np.allclose(out[:, :, :k + 1], left, rtol=0, atol=1e-12)
+    assert np.allclose(out[:, :, k + 1:], right, rtol=0, atol=1e-12)
+    assert not np.allclose(out, x)
