@@ -49,7 +49,9 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the batched and forward+backward workloads")
-    p.add_argument("--only", choices=["batched", "fwd_bwd", "lowrank"], default=None,
+    p.add_argument("--precond", choices=["jacobi", "hierarchical"], default="jacobi",
+                   help="preconditioner of the --only batched workload")
+    p.add_argument("--only", choices=["batched", "fwd_bwd", "lowrank", "dt"], default=None,
                    help="run one extra workload alone (for profiling) and print its line")
     p.add_argument("--images", type=int, default=None,
                    help="image count of the --only workload (default: its full size)")
@@ -315,8 +317,8 @@ def time_steps(step, steps, warmup, flush, stream):
 # captured and the traffic is scaled by its ratio to the algorithmic bytes
 # (below 1: the gathers read 16-bit packed neighbour offsets, not the 32-bit
 # ids the algorithmic count assumes).
-PCG_TRAFFIC_1080P = 6.887424e6 + 7.724544e6
-PCG_TRAFFIC_RATIO_BATCHED = (108.712960e6 + 10.696704e6 + 66.429952e6 + 0.733440e6) / 235835472
+PCG_TRAFFIC_1080P = 6.887936e6 + 7.725312e6
+PCG_TRAFFIC_RATIO_BATCHED = (108.269568e6 + 11.023360e6 + 66.433024e6 + 0.849664e6) / 235835472
 
 
 def pcg_roofline(regions, solves_per_step, steps, bytes_per_iter, peak):
@@ -331,9 +333,11 @@ def pcg_roofline(regions, solves_per_step, steps, bytes_per_iter, peak):
             "frac": achieved / peak, "bytes_per_iter": bytes_per_iter, "iter_us": iter_ms * 1e3}
 
 
-def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, sequential=True):
+def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, sequential=True,
+                      precond="jacobi"):
     """64 images of uneven size in one grid and one batched solve, against the
-    same images solved one at a time."""
+    same images solved one at a time (optionally with the hierarchical
+    preconditioner instead of Jacobi)."""
     import torch
     from paper_1511_03296_gb300 import fbs, synth
     wl = synth.batched_64(seed=rank_seed(4, dist.rank), n_images=n_images)
@@ -348,9 +352,12 @@ def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, seq
     info = {}
     tuning = tune(fbs, yuv, sig, t, c, lam, x)
 
+    pc = fbs.PRECOND_HIERARCHICAL if precond == "hierarchical" else fbs.PRECOND_JACOBI
+
     def batched():
         g = fbs.grid_build(yuv, *sig)
         fbs.apply_tuning(g, tuning)
+        fbs.set_option(g, fbs.OPT_PRECONDITIONER, pc)
         fbs.bistochastize(g, BISTOCH_ITERS)
         fbs.solve(g, t, c, lam, PCG_ITERS, x=x)
         info["V"] = g.vertex_counts
@@ -374,6 +381,7 @@ def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, seq
     bytes_iter = sum(V * (48 + 40 * i.channels) for V, i in zip(info["V"], insts))
     return {"workload": "64 images, sizes U{320..1920} x U{240..1080}, half depth (C=1), half "
                         "chroma (C=2, c=1 on 2% of pixels), sigma_xy in {8,16}, lambda in {32,128}",
+            "preconditioner": precond,
             "pixels": npix, "vertices": int(sum(info["V"])),
             "batched_mpix_s": whole_job_mpix(dist.world, npix, mb), "batched_ms": mb,
             "tuning": tuning,
@@ -560,7 +568,10 @@ def run_only(args, dist):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     if args.only == "batched":
         out = run_extra_batched(dist, flush, stream, peak, args.steps, args.warmup,
-                                n_images=args.images or 64, sequential=False)
+                                n_images=args.images or 64, sequential=False,
+                                precond=args.precond)
+    elif args.only == "dt":
+        out = run_extra_dt(dist, flush, stream, args.steps, args.warmup)
     elif args.only == "lowrank":
         out = run_extra_lowrank(dist, flush, stream, args.steps, args.warmup,
                                 n_images=args.images or 16)
