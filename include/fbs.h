@@ -227,9 +227,10 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *                             M^-1 = P^T(w o P(1) o P(.) / P(diag A)) with
  *                             (alpha, beta) = (2, 5) and the push-pull
  *                             initialisation with (4, 0).  The pyramid is
- *                             built on the host on first use (one device
- *                             synchronisation; FBS_ERR_STATE if that first
- *                             use is inside a stream capture).  Applies when
+ *                             built on the GPU on first use (one
+ *                             synchronisation per level to read its size;
+ *                             FBS_ERR_STATE if that first use is inside a
+ *                             stream capture).  Applies when
  *                             every image has at most 4 channels; other
  *                             solves use Jacobi.  Per-phase launches,
  *                             standard PCG form.

@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfbs.so")
-SOURCES = ["api.cu", "dtf.cu", "grid.cu", "lowrank.cu", "solve.cu", "solve_static.cu"]
+SOURCES = ["api.cu", "dtf.cu", "grid.cu", "lowrank.cu", "pyramid.cu", "solve.cu", "solve_static.cu"]
 HEADERS = ["fbs_internal.cuh", "solve.cuh", "grid_view.cuh",
            os.path.join("..", "..", "include", "fbs.h")]
 

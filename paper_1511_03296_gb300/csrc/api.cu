@@ -12,6 +12,7 @@
 
 #include "fbs_internal.cuh"
 #include "lowrank.cuh"
+#include "pyramid.cuh"
 #include "solve.cuh"
 
 namespace fbs {
@@ -676,153 +677,167 @@ fbs_status run_segments(fbs_grid* g, const SolveArgs& A, const SolvePlan& P, cud
 }
 
 // halves every 12-bit key field (floor): the parent key one pyramid level up
-uint64_t halve_key(uint64_t k)
-{
-    static const int shift[5] = {48, 36, 24, 12, 0};
-    uint64_t out = 0;
-    for (int d = 0; d < 5; ++d) out |= (((k >> shift[d]) & kFieldMax) >> 1) << shift[d];
-    return out;
-}
-
 // The bilateral-space pyramid of the grid (supplement, bilateral-space
-// pyramids), built once on the host from the vertex keys: per image, level
-// k+1 is the sorted distinct halved keys of level k (floor halving reaches a
-// single vertex); the images' levels are concatenated level by level (an
-// image that reached its top keeps one vertex, with count and weights 0, so
-// each image's result is that of its own pyramid), with each vertex's parent,
-// each vertex's children in ascending order (so the device sums are
-// deterministic), the counts P(1) and the initialisation weights
-// w_init(k) / P(1), w_init(k) = 4^-k (alpha = 4, beta = 0).
+// pyramids), built on the GPU once per grid: per image, level k+1 is the
+// distinct floor-halved keys of level k (floor halving reaches a single
+// vertex), numbered in first-occurrence order (see pyramid.cu); the images'
+// levels are concatenated level by level (an image that reached its top
+// keeps one vertex, with count and weights 0, so each image's result is that
+// of its own pyramid), with each vertex's parent, each vertex's children in
+// ascending order (so the device sums are deterministic), the counts P(1)
+// and the initialisation weights 4^-k / P(1).  The host reads back only the
+// per-image level sizes (one synchronisation per level).
 fbs_status build_pyramid(fbs_grid* g, cudaStream_t s)
 {
-    const int64_t V = g->Vtot;
-    std::vector<uint64_t> keys(V);
-    cudaError_t e = cudaMemcpyAsync(keys.data(), g->vkey, V * sizeof(uint64_t),
-                                    cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_status(e);
     const int n = g->n_images;
-    // per image, per level: sorted keys and the parent of each vertex
-    std::vector<std::vector<std::vector<uint64_t>>> lk(n);
-    std::vector<std::vector<std::vector<int32_t>>> lp(n);
-    int K = 1;
-    for (int im = 0; im < n; ++im) {
-        lk[im].push_back(std::vector<uint64_t>(keys.begin() + g->voff[im],
-                                               keys.begin() + g->voff[im + 1]));
-        while (lk[im].back().size() > 1) {
-            const std::vector<uint64_t>& cur = lk[im].back();
-            std::vector<uint64_t> h(cur.size());
-            for (size_t i = 0; i < cur.size(); ++i) h[i] = halve_key(cur[i]);
-            std::vector<uint64_t> up(h);
-            std::sort(up.begin(), up.end());
-            up.erase(std::unique(up.begin(), up.end()), up.end());
-            std::vector<int32_t> par(cur.size());
-            for (size_t i = 0; i < cur.size(); ++i)
-                par[i] = (int32_t)(std::lower_bound(up.begin(), up.end(), h[i]) - up.begin());
-            lp[im].push_back(std::move(par));
-            lk[im].push_back(std::move(up));
-        }
-        K = std::max(K, (int)lk[im].size());
-    }
-    if (K > kMaxLevels) return FBS_ERR_ARG;
-    // level sizes per image (an image past its top keeps its single vertex)
-    auto lsize = [&](int im, int k) -> int64_t {
-        return k < (int)lk[im].size() ? (int64_t)lk[im][k].size() : 1;
+    const int64_t V = g->Vtot;
+    std::vector<std::vector<int64_t>> lstart(1, g->voff);          // level-local image starts
+    std::vector<uint64_t*> keyL(1, g->vkey);
+    std::vector<uint16_t*> imgL(1, nullptr);
+    std::vector<int32_t*> parL;
+    int64_t* d_idx = nullptr;
+    int64_t* d_out = nullptr;
+    int64_t* d_htoff = nullptr;
+    unsigned long long* hkey = nullptr;
+    int32_t *hmin = nullptr, *slot = nullptr;
+    uint32_t *flag = nullptr, *idv = nullptr, *tmp = nullptr;
+    int64_t* d_off = nullptr;
+    uint32_t *tcnt = nullptr, *tscan = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto level_tmp_free = [&]() {
+        dfree(d_htoff, s); dfree(hkey, s); dfree(hmin, s); dfree(slot, s); dfree(flag, s);
+        dfree(idv, s); dfree(tmp, s);
     };
-    std::vector<std::vector<int64_t>> ioff(K, std::vector<int64_t>(n + 1, 0));   // image offsets in a level
+    auto cleanup = [&]() {
+        level_tmp_free();
+        dfree(d_idx, s); dfree(d_out, s); dfree(d_off, s); dfree(tcnt, s); dfree(tscan, s);
+        for (size_t k = 1; k < keyL.size(); ++k) dfree(keyL[k], s);
+        for (auto*& p : imgL) dfree(p, s);
+        for (auto*& p : parL) dfree(p, s);
+    };
+#define PYR_TRY(x)                        \
+    do {                                  \
+        if ((e = (x)) != cudaSuccess) {   \
+            cleanup();                    \
+            return cuda_status(e);        \
+        }                                 \
+    } while (0)
+    PYR_TRY(dalloc(&imgL[0], (size_t)V, s));
+    PYR_TRY(dalloc(&d_idx, (size_t)n + 1, s));
+    PYR_TRY(dalloc(&d_out, (size_t)n + 1, s));
+    PYR_TRY(cudaMemcpyAsync(d_idx, g->voff.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    PYR_TRY(fill_vimg(d_idx, n, V, imgL[0], s));
+    std::vector<int64_t> hout(n + 1);
+    for (int k = 0;; ++k) {
+        const std::vector<int64_t>& ls = lstart[k];
+        bool all_top = true;
+        for (int im = 0; im < n; ++im) all_top &= ls[im + 1] - ls[im] == 1;
+        if (all_top) break;
+        if (k + 1 >= kMaxLevels) {
+            cleanup();
+            return FBS_ERR_ARG;
+        }
+        const int64_t nk = ls[n];
+        std::vector<int64_t> htoff(n + 1, 0);
+        for (int im = 0; im < n; ++im) {
+            int64_t sz = 2;
+            while (sz < 2 * (ls[im + 1] - ls[im])) sz <<= 1;
+            htoff[im + 1] = htoff[im] + sz;
+        }
+        PYR_TRY(dalloc(&d_htoff, (size_t)n + 1, s));
+        PYR_TRY(dalloc(&hkey, (size_t)htoff[n], s));
+        PYR_TRY(dalloc(&hmin, (size_t)htoff[n], s));
+        PYR_TRY(dalloc(&slot, (size_t)nk, s));
+        PYR_TRY(dalloc(&flag, (size_t)nk, s));
+        PYR_TRY(dalloc(&idv, (size_t)nk + 1, s));
+        PYR_TRY(dalloc(&tmp, (size_t)(nk / 1024 + 2), s));
+        PYR_TRY(cudaMemcpyAsync(d_htoff, htoff.data(), (n + 1) * sizeof(int64_t),
+                                cudaMemcpyHostToDevice, s));
+        PYR_TRY(cudaMemsetAsync(hkey, 0xFF, (size_t)htoff[n] * sizeof(unsigned long long), s));
+        PYR_TRY(cudaMemsetAsync(hmin, 0x7F, (size_t)htoff[n] * sizeof(int32_t), s));
+        PyrLevelArgs L;
+        L.key = keyL[k];
+        L.img = imgL[k];
+        L.n = nk;
+        L.htoff = d_htoff;
+        L.hkey = hkey;
+        L.hmin = hmin;
+        L.slot = slot;
+        L.flag = flag;
+        L.id = idv;
+        L.err = g->err;
+        PYR_TRY(pyr_level_insert(L, s));
+        PYR_TRY(scan_u32(flag, idv, nk, tmp, s));
+        // next-level image starts: the ids at this level's image starts
+        PYR_TRY(cudaMemcpyAsync(d_idx, ls.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        PYR_TRY(gather_u32(idv, d_idx, d_out, n + 1, s));
+        PYR_TRY(cudaMemcpyAsync(hout.data(), d_out, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        PYR_TRY(cudaStreamSynchronize(s));
+        lstart.push_back(hout);
+        const int64_t nk1 = hout[n];
+        keyL.push_back(nullptr);
+        imgL.push_back(nullptr);
+        parL.push_back(nullptr);
+        PYR_TRY(dalloc(&keyL[k + 1], (size_t)nk1, s));
+        PYR_TRY(dalloc(&imgL[k + 1], (size_t)nk1, s));
+        PYR_TRY(dalloc(&parL[k], (size_t)nk, s));
+        L.parent = parL[k];
+        L.key1 = keyL[k + 1];
+        L.img1 = imgL[k + 1];
+        PYR_TRY(pyr_level_finish(L, s));
+        level_tmp_free();
+    }
+    const int K = (int)lstart.size();
     int64_t off[kMaxLevels + 1];
     off[0] = 0;
-    for (int k = 0; k < K; ++k) {
-        for (int im = 0; im < n; ++im) ioff[k][im + 1] = ioff[k][im] + lsize(im, k);
-        off[k + 1] = off[k] + ioff[k][n];
-    }
+    for (int k = 0; k < K; ++k) off[k + 1] = off[k] + lstart[k][n];
     const int64_t T = off[K];
-    std::vector<int32_t> parent(off[K - 1] > 0 ? off[K - 1] : 1, 0);
-    for (int k = 0; k + 1 < K; ++k)
-        for (int im = 0; im < n; ++im)
-            for (int64_t i = 0; i < lsize(im, k); ++i) {
-                const int32_t pl = k < (int)lp[im].size() ? lp[im][k][i] : 0;
-                parent[off[k] + ioff[k][im] + i] = (int32_t)(ioff[k + 1][im] + pl);
-            }
-    // children lists (counting sort by parent keeps children ascending)
-    std::vector<int32_t> child_off(T - off[1] + 1, 0), child_idx(std::max<int64_t>(off[K - 1], 1));
-    for (int k = 0; k + 1 < K; ++k)
-        for (int64_t i = 0; i < off[k + 1] - off[k]; ++i)
-            ++child_off[off[k + 1] - off[1] + parent[off[k] + i] + 1];
-    for (int64_t g2 = 0; g2 < T - off[1]; ++g2) child_off[g2 + 1] += child_off[g2];
-    {
-        std::vector<int32_t> fill(child_off.begin(), child_off.end() - 1);
-        for (int k = 0; k + 1 < K; ++k)
-            for (int64_t i = 0; i < off[k + 1] - off[k]; ++i)
-                child_idx[fill[off[k + 1] - off[1] + parent[off[k] + i]]++] = (int32_t)i;
-    }
-    // counts and initialisation weights
-    std::vector<double> cnt(T, 1.0);
-    for (int k = 1; k < K; ++k)
-        for (int64_t p = 0; p < off[k + 1] - off[k]; ++p) {
-            double c = 0.0;
-            const int64_t gg = off[k] + p - off[1];
-            for (int32_t j = child_off[gg]; j < child_off[gg + 1]; ++j)
-                c += cnt[off[k - 1] + child_idx[j]];
-            cnt[off[k] + p] = c;
-        }
-    std::vector<float> cinit(T), cntf(T);
-    for (int64_t i = 0; i < T; ++i) cntf[i] = (float)cnt[i];   // integers below 2^24: exact
-    for (int k = 0; k < K; ++k) {
-        const double w = k == 0 ? 1.0 : pow(4.0, -(double)k);
-        for (int64_t i = off[k]; i < off[k + 1]; ++i) cinit[i] = (float)(w / cnt[i]);
-    }
-    // the single vertex an image keeps past its own top is not a level of
-    // its pyramid: count 0 and weight 0 make its terms vanish exactly
-    for (int k = 1; k < K; ++k)
-        for (int im = 0; im < n; ++im)
-            if (k >= (int)lk[im].size()) {
-                cntf[off[k] + ioff[k][im]] = 0.0f;
-                cinit[off[k] + ioff[k][im]] = 0.0f;
-            }
-    // absolute per-image level ranges and each image's own level count
     std::vector<int64_t> ioffa((size_t)K * (n + 1));
     for (int k = 0; k < K; ++k)
-        for (int im = 0; im <= n; ++im) ioffa[(size_t)k * (n + 1) + im] = off[k] + ioff[k][im];
-    std::vector<uint8_t> kimg(n);
-    for (int im = 0; im < n; ++im) kimg[im] = (uint8_t)lk[im].size();
-    std::vector<uint16_t> vimg(T);
-    for (int k = 0; k < K; ++k)
-        for (int im = 0; im < n; ++im)
-            for (int64_t i = 0; i < lsize(im, k); ++i)
-                vimg[off[k] + ioff[k][im] + i] = (uint16_t)im;
-    // device copies
-    if ((e = dalloc(&g->pyr_parent, parent.size(), s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_child_off, child_off.size(), s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_child_idx, child_idx.size(), s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_vimg, (size_t)T, s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_ioff, ioffa.size(), s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_kimg, kimg.size(), s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_cnt, (size_t)T, s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_cinit, (size_t)T, s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_coef, (size_t)T, s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_dg, (size_t)V, s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_scv, (size_t)V, s)) != cudaSuccess ||
-        (e = dalloc(&g->pyr_lv, (size_t)std::max<int64_t>(T - V, 1) * kPyrMaxNc, s)) !=
-            cudaSuccess)
-        return cuda_status(e);
-    const struct {
-        void* dst;
-        const void* src;
-        size_t bytes;
-    } cp[] = {{g->pyr_parent, parent.data(), parent.size() * sizeof(int32_t)},
-              {g->pyr_child_off, child_off.data(), child_off.size() * sizeof(int32_t)},
-              {g->pyr_child_idx, child_idx.data(), child_idx.size() * sizeof(int32_t)},
-              {g->pyr_vimg, vimg.data(), vimg.size() * sizeof(uint16_t)},
-              {g->pyr_ioff, ioffa.data(), ioffa.size() * sizeof(int64_t)},
-              {g->pyr_kimg, kimg.data(), kimg.size() * sizeof(uint8_t)},
-              {g->pyr_cnt, cntf.data(), cntf.size() * sizeof(float)},
-              {g->pyr_cinit, cinit.data(), cinit.size() * sizeof(float)}};
-    for (const auto& c : cp)
-        if ((e = cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, s)) !=
-            cudaSuccess)
-            return cuda_status(e);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_status(e);
+        for (int im = 0; im <= n; ++im) ioffa[(size_t)k * (n + 1) + im] = off[k] + lstart[k][im];
+    std::vector<uint8_t> kimg(n, (uint8_t)K);
+    for (int im = 0; im < n; ++im)
+        for (int k = 0; k < K; ++k)
+            if (lstart[k][im + 1] - lstart[k][im] == 1) {
+                kimg[im] = (uint8_t)(k + 1);
+                break;
+            }
+    // the concatenated arrays
+    PYR_TRY(dalloc(&g->pyr_parent, (size_t)std::max<int64_t>(off[K - 1], 1), s));
+    PYR_TRY(dalloc(&g->pyr_child_off, (size_t)(T - V + 1), s));
+    PYR_TRY(dalloc(&g->pyr_child_idx, (size_t)std::max<int64_t>(off[K - 1], 1), s));
+    PYR_TRY(dalloc(&g->pyr_vimg, (size_t)T, s));
+    PYR_TRY(dalloc(&g->pyr_ioff, ioffa.size(), s));
+    PYR_TRY(dalloc(&g->pyr_kimg, kimg.size(), s));
+    PYR_TRY(dalloc(&g->pyr_cnt, (size_t)T, s));
+    PYR_TRY(dalloc(&g->pyr_cinit, (size_t)T, s));
+    PYR_TRY(dalloc(&g->pyr_coef, (size_t)T, s));
+    PYR_TRY(dalloc(&g->pyr_dg, (size_t)V, s));
+    PYR_TRY(dalloc(&g->pyr_scv, (size_t)V, s));
+    PYR_TRY(dalloc(&g->pyr_lv, (size_t)std::max<int64_t>(T - V, 1) * kPyrMaxNc, s));
+    for (int k = 0; k < K; ++k) {
+        PYR_TRY(cudaMemcpyAsync(g->pyr_vimg + off[k], imgL[k], lstart[k][n] * sizeof(uint16_t),
+                                cudaMemcpyDeviceToDevice, s));
+        if (k + 1 < K)
+            PYR_TRY(cudaMemcpyAsync(g->pyr_parent + off[k], parL[k], lstart[k][n] * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, s));
+    }
+    PYR_TRY(cudaMemcpyAsync(g->pyr_ioff, ioffa.data(), ioffa.size() * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s));
+    PYR_TRY(cudaMemcpyAsync(g->pyr_kimg, kimg.data(), kimg.size(), cudaMemcpyHostToDevice, s));
+    PYR_TRY(dalloc(&d_off, (size_t)K + 1, s));
+    PYR_TRY(cudaMemcpyAsync(d_off, off, (K + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    const int64_t np = T - V;
+    PYR_TRY(dalloc(&tcnt, (size_t)3 * (np + 1), s));
+    PYR_TRY(dalloc(&tscan, (size_t)(np / 1024 + 2), s));
+    PYR_TRY(pyr_children(g->pyr_parent, d_off, K, T, V, g->pyr_child_off, g->pyr_child_idx, tcnt,
+                         tscan, s));
+    PYR_TRY(pyr_counts(g->pyr_child_off, g->pyr_child_idx, off, d_off, K, g->pyr_ioff, g->pyr_kimg, n,
+                       g->pyr_cnt, g->pyr_cinit, s));
+    // the host copies above are stream-ordered: finish before their sources go
+    PYR_TRY(cudaStreamSynchronize(s));
+    cleanup();
+#undef PYR_TRY
     g->pyr_K = K;
     for (int k = 0; k <= K; ++k) g->pyr_off[k] = off[k];
     return FBS_OK;

@@ -1367,7 +1367,7 @@ pcg_single_kernel(SolveArgs A, int it, int last)
 }
 
 // ------------------------------------- hierarchical preconditioner ---
-// The bilateral-space pyramid passes of Sec. 4 (levels built on the host;
+// The bilateral-space pyramid passes of Sec. 4 (levels built by pyramid.cu;
 // see PyrDev).  P sums children into parents level by level, in ascending
 // child order and in double-float arithmetic: deterministic, and free of
 // the cancellation error that FP32 sums of a converging, oscillating
