@@ -148,7 +148,7 @@ fbs_status fbs_solve_lowrank(fbs_grid* g, const fbs_problem_desc* probs, int pcg
  * sigma_i), sigma_i = sigma_s sqrt(3) 2^(iterations - i) /
  * sqrt(4^iterations - 1).  FP32.  Errors: FBS_ERR_ARG (NULL buffers,
  * non-positive sizes or sigmas, iterations outside 1 .. 16, width above
- * 29000), FBS_ERR_OOM, FBS_ERR_CUDA.
+ * 28000), FBS_ERR_OOM, FBS_ERR_CUDA.
  */
 fbs_status fbs_domain_transform(const float* guide, int height, int width, float* x, int channels,
                                 float sigma_s, float sigma_r, int iterations, void* stream);

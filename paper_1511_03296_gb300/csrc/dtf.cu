@@ -11,9 +11,9 @@
 // Rows: one block per (row, channel) stages the row in shared memory and
 // runs each direction as a parallel scan of the affine maps J -> A J + B
 // (each thread composes a contiguous chunk, the block scans the chunk maps,
-// each thread replays its chunk from its prefix).  Columns: one thread per
-// (column, channel) walks down and back up (a warp's loads are 32
-// consecutive floats of a row).
+// each thread replays its chunk from its prefix).  Columns: one block per 32
+// columns and channel, 8 row segments per column, the same composition
+// across the segments (a warp's loads are 32 consecutive floats of a row).
 #include <algorithm>
 #include <cmath>
 
@@ -64,13 +64,17 @@ __device__ Aff aff_block_exclusive(Aff m, Aff* s_warp)
 // direction: forward r = k, backward r = L-1-k; element r's map is
 // J -> A_r J + (1 - A_r) x with A_0 = 0 and A_r the weight of the step
 // from the previous position.
+// shared-memory slot of line element k: one pad word per 32, so that the
+// threads' contiguous chunks fall in different banks
+__device__ __forceinline__ int dt_pad(int k) { return k + (k >> 5); }
+
 template <bool BACK>
 __device__ void dt_scan(float* sx, const float* sw, int L, Aff* s_warp)
 {
     const int per = (L + kDtThreads - 1) / kDtThreads;
     const int r0 = threadIdx.x * per, r1 = min(L, r0 + per);
-    auto pos = [&](int r) { return BACK ? L - 1 - r : r; };
-    auto wgt = [&](int r) { return r == 0 ? 0.0f : sw[BACK ? L - r : r]; };
+    auto pos = [&](int r) { return dt_pad(BACK ? L - 1 - r : r); };
+    auto wgt = [&](int r) { return r == 0 ? 0.0f : sw[dt_pad(BACK ? L - r : r)]; };
     Aff m = {1.0f, 0.0f};
     for (int r = r0; r < r1; ++r) {
         const float A = wgt(r);
@@ -114,42 +118,83 @@ dt_rows_kernel(float* __restrict__ x, const float* __restrict__ dh, int H, int W
 {
     extern __shared__ float s_line[];
     __shared__ Aff s_warp[kDtThreads / 32];
+    const int Wp = dt_pad(W - 1) + 1;
     float* sx = s_line;
-    float* sw = s_line + W;
+    float* sw = s_line + Wp;
     const int y = blockIdx.x;
     float* row = x + ((int64_t)blockIdx.y * H + y) * W;
     const float* d = dh + (int64_t)y * W;
     for (int k = threadIdx.x; k < W; k += kDtThreads) {
-        sx[k] = row[k];
-        sw[k] = exp2f(kexp * d[k]);
+        sx[dt_pad(k)] = row[k];
+        sw[dt_pad(k)] = exp2f(kexp * d[k]);
     }
     __syncthreads();
     dt_scan<false>(sx, sw, W, s_warp);
     dt_scan<true>(sx, sw, W, s_warp);
-    for (int k = threadIdx.x; k < W; k += kDtThreads) row[k] = sx[k];
+    for (int k = threadIdx.x; k < W; k += kDtThreads) row[k] = sx[dt_pad(k)];
 }
 
-// thread (column, channel): down, then back up
-__global__ void __launch_bounds__(128)
-dt_cols_kernel(float* __restrict__ x, const float* __restrict__ dv, int H, int W, int C, float kexp)
+// block (32 columns, channel), 8 row segments per column: each direction
+// composes every segment's affine map, scans the 8 maps of each column in
+// shared memory and replays the segments (a warp reads 32 consecutive
+// floats of a row)
+constexpr int kDtCols = 32, kDtSegs = 8;
+
+__global__ void __launch_bounds__(kDtCols * kDtSegs)
+dt_cols_kernel(float* __restrict__ x, const float* __restrict__ dv, int H, int W, float kexp)
 {
-    const int64_t n = (int64_t)W * C;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int col = (int)(q % W), ch = (int)(q / W);
-        float* X = x + (int64_t)ch * H * W + col;
-        const float* d = dv + col;
-        float J = X[0];
-#pragma unroll 4
-        for (int y = 1; y < H; ++y) {
-            const float w = exp2f(kexp * d[(int64_t)y * W]);
-            J = fmaf(w, J, (1.0f - w) * X[(int64_t)y * W]);
+    __shared__ Aff s_map[kDtSegs][kDtCols];
+    const int lane = threadIdx.x % kDtCols, seg = threadIdx.x / kDtCols;
+    const int col = blockIdx.x * kDtCols + lane;
+    const bool valid = col < W;
+    const int per = (H + kDtSegs - 1) / kDtSegs;
+    const int y0 = min(H, seg * per), y1 = min(H, y0 + per);
+    float* X = x + (int64_t)blockIdx.y * H * W + (valid ? col : 0);
+    const float* d = dv + (valid ? col : 0);
+    auto wdown = [&](int y) { return y == 0 ? 0.0f : exp2f(kexp * d[(int64_t)y * W]); };
+    auto wup = [&](int y) { return y == H - 1 ? 0.0f : exp2f(kexp * d[(int64_t)(y + 1) * W]); };
+    // down
+    Aff m = {1.0f, 0.0f};
+    if (valid)
+        for (int y = y0; y < y1; ++y) {
+            const float A = wdown(y);
+            m = aff_then(Aff{A, (1.0f - A) * X[(int64_t)y * W]}, m);
+        }
+    s_map[seg][lane] = m;
+    __syncthreads();
+    Aff P = {1.0f, 0.0f};
+    for (int q = 0; q < seg; ++q) P = aff_then(s_map[q][lane], P);
+    if (valid) {
+        float J = P.b;
+        float xn = y0 < y1 ? X[(int64_t)y0 * W] : 0.0f;
+        for (int y = y0; y < y1; ++y) {
+            const float xv = xn;
+            if (y + 1 < y1) xn = X[(int64_t)(y + 1) * W];     // the next row's load goes first
+            const float A = wdown(y);
+            J = fmaf(A, J, (1.0f - A) * xv);
             X[(int64_t)y * W] = J;
         }
-#pragma unroll 4
-        for (int y = H - 2; y >= 0; --y) {
-            const float w = exp2f(kexp * d[(int64_t)(y + 1) * W]);
-            J = fmaf(w, J, (1.0f - w) * X[(int64_t)y * W]);
+    }
+    __syncthreads();
+    // up: segments in the order 7 .. 0, rows descending
+    m = {1.0f, 0.0f};
+    if (valid)
+        for (int y = y1 - 1; y >= y0; --y) {
+            const float A = wup(y);
+            m = aff_then(Aff{A, (1.0f - A) * X[(int64_t)y * W]}, m);
+        }
+    s_map[seg][lane] = m;
+    __syncthreads();
+    P = {1.0f, 0.0f};
+    for (int q = kDtSegs - 1; q > seg; --q) P = aff_then(s_map[q][lane], P);
+    if (valid) {
+        float J = P.b;
+        float xn = y0 < y1 ? X[(int64_t)(y1 - 1) * W] : 0.0f;
+        for (int y = y1 - 1; y >= y0; --y) {
+            const float xv = xn;
+            if (y - 1 >= y0) xn = X[(int64_t)(y - 1) * W];
+            const float A = wup(y);
+            J = fmaf(A, J, (1.0f - A) * xv);
             X[(int64_t)y * W] = J;
         }
     }
@@ -158,7 +203,7 @@ dt_cols_kernel(float* __restrict__ x, const float* __restrict__ dv, int H, int W
 }  // namespace
 
 // Rows longer than this do not fit the row kernel's shared memory.
-constexpr int kDtMaxWidth = 29000;   // 2 x 4 B per pixel of a row: 232000 B of shared memory
+constexpr int kDtMaxWidth = 28000;   // 2 x 4 B x 33/32 per pixel of a row: 231008 B of shared memory
 
 cudaError_t domain_transform(const float* guide, int H, int W, float* x, int C, float sigma_s,
                              float sigma_r, int iters, float* dh, float* dv, cudaStream_t s)
@@ -167,7 +212,7 @@ cudaError_t domain_transform(const float* guide, int H, int W, float* x, int C, 
     const int sms = device_info().sms;
     dt_steps_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, sms * 8)), 256, 0,
                       s>>>(guide, H, W, sigma_s / sigma_r, dh, dv);
-    const size_t smem = (size_t)2 * W * sizeof(float);
+    const size_t smem = (size_t)2 * (W + W / 32 + 1) * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(dt_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)std::max<size_t>(smem, 1));
     if (e != cudaSuccess) return e;
@@ -177,9 +222,8 @@ cudaError_t domain_transform(const float* guide, int H, int W, float* x, int C, 
                            sqrt(pow(4.0, (double)iters) - 1.0);
         const float kexp = (float)(-sqrt(2.0) * log2e / sig);
         dt_rows_kernel<<<dim3((unsigned)H, (unsigned)C), kDtThreads, smem, s>>>(x, dh, H, W, kexp);
-        const int64_t nc = (int64_t)W * C;
-        dt_cols_kernel<<<(int)std::max<int64_t>(1, std::min<int64_t>((nc + 127) / 128, sms * 16)), 128,
-                         0, s>>>(x, dv, H, W, C, kexp);
+        dt_cols_kernel<<<dim3((unsigned)((W + kDtCols - 1) / kDtCols), (unsigned)C),
+                         kDtCols * kDtSegs, 0, s>>>(x, dv, H, W, kexp);
     }
     return cudaGetLastError();
 }
