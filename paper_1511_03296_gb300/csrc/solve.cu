@@ -1376,9 +1376,9 @@ pcg_single_kernel(SolveArgs A, int it, int last)
 //   M_hier^-1 r = P^T(coef o P(r)),  coef = w(k) P(1) / P(diag A),
 //   y_hier = P^T(cinit o P(b)) / P^T(cinit o P(S c)),  cinit = w_init(k) / P(1).
 // The weights are FP32 (a rounded weight leaves M_hier^-1 linear and
-// symmetric).  Launches: level 1 from the grid (pyr_gather0), level 2 from
-// level 1 (pyr_gather), levels >= 3 of each image up and back down in one
-// block per image (pyr_tail), levels 2 and 1 down (pyr_down12), and level 0
+// symmetric).  Launches: level 1 from the grid (pyr_gather0), levels 2 and
+// 3 (pyr_gather), levels >= 4 of each image up and back down in one block
+// per image (pyr_tail), levels 3 .. 1 down (pyr_down_low), and level 0
 // (pyr_precond0 / pyr_init0).  A level
 // vector holds nc double-float values per vertex: W channels (the widest
 // image's Cp; an image uses its first Cp), plus S c and diag(A) in the setup
@@ -1461,10 +1461,10 @@ pyr_gather_kernel(SolveArgs A, int k, int nc)
         pyr_sum_children(P, k, P.off[k + 1] + p, nc);
 }
 
-// Levels >= 3 of one image per block: with up, parents of levels 3 .. top
-// sum their children; with wt, levels top .. 3 take x <- wt o x + (parent's
+// Levels >= 4 of one image per block: with up, parents of levels 4 .. top
+// sum their children; with wt, levels top .. 4 take x <- wt o x + (parent's
 // x) (the image's top has no parent).  Images whose own pyramid has at most
-// three levels have nothing here.
+// four levels have nothing here.
 __global__ void __launch_bounds__(kPyrTailThreads)
 pyr_tail_kernel(SolveArgs A, int nc, int up, const float* __restrict__ wt)
 {
@@ -1473,7 +1473,7 @@ pyr_tail_kernel(SolveArgs A, int nc, int up, const float* __restrict__ wt)
     for (int im = blockIdx.x; im < n; im += gridDim.x) {
         const int Ki = P.kimg[im];
         if (up) {
-            for (int k = 2; k + 1 < Ki; ++k) {
+            for (int k = 3; k + 1 < Ki; ++k) {
                 const int64_t g0 = P.ioff[(k + 1) * (n + 1) + im];
                 const int64_t g1 = P.ioff[(k + 1) * (n + 1) + im + 1];
                 for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x)
@@ -1482,7 +1482,7 @@ pyr_tail_kernel(SolveArgs A, int nc, int up, const float* __restrict__ wt)
             }
         }
         if (wt) {
-            for (int k = Ki - 1; k >= 3; --k) {
+            for (int k = Ki - 1; k >= 4; --k) {
                 const int64_t g0 = P.ioff[k * (n + 1) + im];
                 const int64_t g1 = P.ioff[k * (n + 1) + im + 1];
                 const bool top = k == Ki - 1;
@@ -1529,14 +1529,14 @@ pyr_coef_kernel(SolveArgs A)
     }
 }
 
-// The down-sweep of levels 2 and 1, finished for each level-1 vertex in
-// place (weights wt): x1 = wt o l1 + x2, with x2 = wt o l2 of the level-2
-// ancestor plus its level-3 ancestor's final value from pyr_tail, each while
-// the image's own pyramid reaches that level (the image's top has no
-// parent).  Level-2 values are read, not written, so every level-1 vertex
-// sees them whole.
+// The down-sweep of levels 3, 2 and 1, finished for each level-1 vertex in
+// place (weights wt): x1 = wt o l1 + x2, x2 = wt o l2 + x3 and x3 = wt o l3
+// + x4 along the vertex's ancestors, with x4 the level-4 ancestor's final
+// value from pyr_tail, each while the image's own pyramid reaches that
+// level (the image's top has no parent).  Levels 2 and 3 are read, not
+// written, so every level-1 vertex sees them whole.
 __global__ void __launch_bounds__(256)
-pyr_down12_kernel(SolveArgs A, int nc, const float* __restrict__ wt)
+pyr_down_low_kernel(SolveArgs A, int nc, const float* __restrict__ wt)
 {
     const PyrDev& P = A.pyr;
     const int64_t n1 = P.off[2] - P.off[1];
@@ -1546,14 +1546,18 @@ pyr_down12_kernel(SolveArgs A, int nc, const float* __restrict__ wt)
         const int Ki = P.kimg[P.vimg[g1]];
         float2* x1 = P.lv + p * nc;
         const float w1 = wt[g1];
-        const float2* l2 = nullptr;
-        const float2* l3 = nullptr;
-        float w2 = 0.0f;
+        const float2 *l2 = nullptr, *l3 = nullptr, *l4 = nullptr;
+        float w2 = 0.0f, w3 = 0.0f;
         if (Ki > 2) {
             const int64_t g2 = P.off[2] + P.parent[g1];
             w2 = wt[g2];
             l2 = P.lv + (g2 - P.off[1]) * nc;
-            if (Ki > 3) l3 = P.lv + (P.off[3] + P.parent[g2] - P.off[1]) * nc;
+            if (Ki > 3) {
+                const int64_t g3 = P.off[3] + P.parent[g2];
+                w3 = wt[g3];
+                l3 = P.lv + (g3 - P.off[1]) * nc;
+                if (Ki > 4) l4 = P.lv + (P.off[4] + P.parent[g3] - P.off[1]) * nc;
+            }
         }
 #pragma unroll
         for (int ch = 0; ch < kPyrMaxNc; ++ch)
@@ -1561,7 +1565,11 @@ pyr_down12_kernel(SolveArgs A, int nc, const float* __restrict__ wt)
                 DF x = df_mul_f(pyr_ld(x1 + ch), w1);
                 if (Ki > 2) {
                     DF x2 = df_mul_f(pyr_ld(l2 + ch), w2);
-                    if (Ki > 3) x2 = df_add(x2, pyr_ld(l3 + ch));
+                    if (Ki > 3) {
+                        DF x3 = df_mul_f(pyr_ld(l3 + ch), w3);
+                        if (Ki > 4) x3 = df_add(x3, pyr_ld(l4 + ch));
+                        x2 = df_add(x2, x3);
+                    }
                     x = df_add(x, x2);
                 }
                 pyr_st(x1 + ch, x);
@@ -1586,7 +1594,7 @@ __device__ __forceinline__ void pyr_precond_tile(const SolveArgs& A, const InstD
     float x[W];
 #pragma unroll
     for (int k = 0; k < W; ++k) x[k] = 0.0f;
-    if (P.K > 1) {                      // level-1 ancestor's final value (pyr_down12)
+    if (P.K > 1) {                      // level-1 ancestor's final value (pyr_down_low)
         const float2* x1 = P.lv + (int64_t)P.parent[vs] * P.W;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
@@ -1631,7 +1639,7 @@ pyr_init0_kernel(SolveArgs A)
         const int im = P.vimg[v];
         const InstDev& I = A.inst[im];
         const int64_t o = I.vec_base + (v - I.voff) * I.Cp;
-        // level-1 ancestor's final values (pyr_down12): channels, then S c
+        // level-1 ancestor's final values (pyr_down_low): channels, then S c
         const float2* x1 = P.K > 1 ? P.lv + (int64_t)P.parent[v] * nc : nullptr;
         const float ci = P.cinit[v];
         const float den = fmaf(ci, P.scv[v], x1 ? x1[W].x + x1[W].y : 0.0f);
@@ -1648,9 +1656,9 @@ int pyr_blocks(int64_t n)
 }
 
 // P of a level-0 vector (levels 1 .. top of every image) into lv: level 1
-// from src (with scal, S c and diag(A) too), level 2, then each image's
-// levels above; with wt, the down-sweep to level 1 as well (each image's
-// levels top .. 3 in pyr_tail, levels 2 and 1 in pyr_down12).
+// from src (with scal, S c and diag(A) too), levels 2 and 3, then each
+// image's levels above; with wt, the down-sweep to level 1 as well (each
+// image's levels top .. 4 in pyr_tail, levels 3 .. 1 in pyr_down_low).
 cudaError_t pyr_sweep(const SolveArgs& A, const float* src, int nc, int scal, int up,
                       const float* wt, cudaStream_t s)
 {
@@ -1660,10 +1668,12 @@ cudaError_t pyr_sweep(const SolveArgs& A, const float* src, int nc, int scal, in
         pyr_gather0_kernel<<<pyr_blocks(P.off[2] - P.off[1]), 256, 0, s>>>(A, src, nc, scal);
         if (P.K > 2)
             pyr_gather_kernel<<<pyr_blocks(P.off[3] - P.off[2]), 256, 0, s>>>(A, 1, nc);
+        if (P.K > 3)
+            pyr_gather_kernel<<<pyr_blocks(P.off[4] - P.off[3]), 256, 0, s>>>(A, 2, nc);
     }
-    if (P.K > 3 && (up || wt))
+    if (P.K > 4 && (up || wt))
         pyr_tail_kernel<<<A.ninst, kPyrTailThreads, 0, s>>>(A, nc, up, wt);
-    if (wt) pyr_down12_kernel<<<pyr_blocks(P.off[2] - P.off[1]), 256, 0, s>>>(A, nc, wt);
+    if (wt) pyr_down_low_kernel<<<pyr_blocks(P.off[2] - P.off[1]), 256, 0, s>>>(A, nc, wt);
     return cudaGetLastError();
 }
 

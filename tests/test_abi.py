@@ -67,6 +67,24 @@ def test_argument_errors_need_no_gpu(lib):
     lib.fbs_autotune.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                  ctypes.c_void_p]
     assert lib.fbs_autotune(None, None, 25, None, None) == 1
+    lib.fbs_solve_lowrank.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.fbs_solve_lowrank(None, None, 25, 0.01, None, None) == 1
+    # the domain transform checks every argument before touching the device
+    lib.fbs_domain_transform.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_float,
+                                         ctypes.c_float, ctypes.c_int, ctypes.c_void_p]
+    fake = ctypes.c_void_p(0x1000)     # never dereferenced: each call fails validation first
+    for args in ((None, 8, 8, fake, 1, 32.0, 64.0, 3),          # no guide
+                 (fake, 8, 8, None, 1, 32.0, 64.0, 3),          # no x
+                 (fake, 0, 8, fake, 1, 32.0, 64.0, 3),          # empty image
+                 (fake, 8, 8, fake, 0, 32.0, 64.0, 3),          # no channels
+                 (fake, 8, 8, fake, 1, 0.0, 64.0, 3),           # sigma_s
+                 (fake, 8, 8, fake, 1, 32.0, float("inf"), 3),  # sigma_r
+                 (fake, 8, 8, fake, 1, 32.0, 64.0, 0),          # iterations
+                 (fake, 8, 8, fake, 1, 32.0, 64.0, 17),
+                 (fake, 8, 28001, fake, 1, 32.0, 64.0, 3)):     # row wider than shared memory
+        assert lib.fbs_domain_transform(*args, None) == 1, args
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
