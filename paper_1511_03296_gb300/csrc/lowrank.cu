@@ -37,12 +37,27 @@ lr_splat_kernel(const LrImg* __restrict__ imgs, int n, int64_t Vtot, const int64
             DF acc[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) acc[k] = DF{0.0f, 0.0f};
-            for (uint32_t j = 0; j < cnt; ++j) {
-                const int64_t i = (int64_t)perm[p0 + j] - I.pix_base;
-                const float w = I.c[i];
+            // 4 pixels' loads in flight, then their sums in pixel order
+            for (uint32_t j0 = 0; j0 < cnt; j0 += 4) {
+                int64_t ii[4];
+                float w[4], val[8][4];
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (cb + k < I.C) acc[k] = df_add(acc[k], df_mul_exact(w, I.t[(cb + k) * I.N + i]));
+                for (int u = 0; u < 4; ++u)
+                    ii[u] = j0 + u < cnt ? (int64_t)perm[p0 + j0 + u] - I.pix_base : 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    w[u] = j0 + u < cnt ? I.c[ii[u]] : 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k)
+                        val[k][u] = cb + k < I.C ? I.t[(cb + k) * I.N + ii[u]] : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (j0 + u < cnt) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            if (cb + k < I.C) acc[k] = df_add(acc[k], df_mul_exact(w[u], val[k][u]));
+                    }
             }
 #pragma unroll
             for (int k = 0; k < 8; ++k)

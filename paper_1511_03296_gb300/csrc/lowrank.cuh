@@ -7,7 +7,7 @@
 
 namespace fbs {
 
-constexpr int kLrGramBlocks = 64;      // Gram partial sums per image
+constexpr int kLrGramBlocks = 256;     // Gram partial sums per image
 constexpr int kLrMaxEntries = 2080;    // C (C + 1) / 2 for C = 64
 
 // one image of a low-rank pass
