@@ -288,7 +288,10 @@ fbs_status fbs_autotune(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iter
  * The grid (built earlier by fbs_grid_build) and all inputs and outputs
  * are the caller's, with the same meaning as for fbs_solve; the CG state is
  * FP32 unless FBS_OPT_VECTOR_PRECISION selects the compensated variant, and
- * no CUDA graph is used.
+ * no CUDA graph is used.  It always solves with the Jacobi preconditioner
+ * and the flat initialisation in the standard PCG form
+ * (FBS_OPT_PRECONDITIONER and FBS_OPT_PCG_FORM do not apply: the pyramid
+ * needs its own device arrays).
  *
  * Limits and sharing: the array holds 6 float vectors of sum_k C_k V_k
  * entries plus per-vertex and per-tile terms; a problem that does not fit
@@ -320,6 +323,29 @@ fbs_status fbs_grid_info(const fbs_grid* g, int image, int64_t* n_vertices,
 fbs_status fbs_grid_export(const fbs_grid* g, int image, void* stream, uint64_t* host_keys,
                            uint32_t* host_vid, uint32_t* host_counts, int32_t* host_nbr,
                            double* host_n);
+
+/*
+ * fbs_pyramid_export -- copy one level of one image's bilateral-space
+ * pyramid (the hierarchical preconditioner's, supplement) to HOST buffers
+ * for inspection (parity checks).  Builds the pyramid first if no
+ * hierarchical solve has (SYNCHRONISES `stream`; FBS_ERR_STATE inside a
+ * stream capture).  *levels receives the number of levels K of the grid's
+ * deepest image (an image past its own top keeps one vertex, with count 0).
+ * Level 0 is the grid.  Outputs (any may be NULL):
+ *   *n_vertices      the image's vertex count on that level (V_level)
+ *   host_keys        uint64[V_level]  packed keys, fields floor-halved
+ *                                     `level` times; vertices in the
+ *                                     library's order (first occurrence)
+ *   host_parent      int32[V_level]   index of each vertex's parent among
+ *                                     the image's vertices of level + 1
+ *                                     (-1 on the top level)
+ *   host_count       float[V_level]   P(1): grid vertices below each vertex
+ * Errors: FBS_ERR_ARG (bad image or level), FBS_ERR_STATE, FBS_ERR_OOM,
+ * FBS_ERR_CUDA.
+ */
+fbs_status fbs_pyramid_export(fbs_grid* g, int image, int level, void* stream, int* levels,
+                              int64_t* n_vertices, uint64_t* host_keys, int32_t* host_parent,
+                              float* host_count);
 
 /* Wait for the handle's work on `stream` and return (then clear) any latched
  * device-side error. */

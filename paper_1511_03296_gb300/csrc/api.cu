@@ -275,6 +275,8 @@ struct fbs_grid {
     uint16_t* pyr_vimg = nullptr;
     int64_t* pyr_ioff = nullptr;
     uint8_t* pyr_kimg = nullptr;
+    uint64_t* pyr_key = nullptr;        // packed keys of every pyramid vertex (for export)
+    std::vector<int64_t> pyr_ioff_host; // K x (n_images + 1), absolute
     float* pyr_cnt = nullptr;
     float* pyr_cinit = nullptr;
     float* pyr_coef = nullptr;
@@ -324,7 +326,8 @@ void free_grid_memory(fbs_grid* g, cudaStream_t s)
     dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s); dfree(g->part, s);
     dfree(g->inst, s); dfree(g->barrier, s);
     dfree(g->pyr_parent, s); dfree(g->pyr_child_off, s); dfree(g->pyr_child_idx, s);
-    dfree(g->pyr_vimg, s); dfree(g->pyr_ioff, s); dfree(g->pyr_kimg, s); dfree(g->pyr_cnt, s);
+    dfree(g->pyr_vimg, s); dfree(g->pyr_ioff, s); dfree(g->pyr_kimg, s); dfree(g->pyr_key, s);
+    dfree(g->pyr_cnt, s);
     dfree(g->pyr_cinit, s); dfree(g->pyr_coef, s); dfree(g->pyr_dg, s); dfree(g->pyr_scv, s);
     dfree(g->pyr_lv, s);
 }
@@ -807,6 +810,7 @@ fbs_status build_pyramid(fbs_grid* g, cudaStream_t s)
     PYR_TRY(dalloc(&g->pyr_child_off, (size_t)(T - V + 1), s));
     PYR_TRY(dalloc(&g->pyr_child_idx, (size_t)std::max<int64_t>(off[K - 1], 1), s));
     PYR_TRY(dalloc(&g->pyr_vimg, (size_t)T, s));
+    PYR_TRY(dalloc(&g->pyr_key, (size_t)T, s));
     PYR_TRY(dalloc(&g->pyr_ioff, ioffa.size(), s));
     PYR_TRY(dalloc(&g->pyr_kimg, kimg.size(), s));
     PYR_TRY(dalloc(&g->pyr_cnt, (size_t)T, s));
@@ -817,6 +821,8 @@ fbs_status build_pyramid(fbs_grid* g, cudaStream_t s)
     PYR_TRY(dalloc(&g->pyr_lv, (size_t)std::max<int64_t>(T - V, 1) * kPyrMaxNc, s));
     for (int k = 0; k < K; ++k) {
         PYR_TRY(cudaMemcpyAsync(g->pyr_vimg + off[k], imgL[k], lstart[k][n] * sizeof(uint16_t),
+                                cudaMemcpyDeviceToDevice, s));
+        PYR_TRY(cudaMemcpyAsync(g->pyr_key + off[k], keyL[k], lstart[k][n] * sizeof(uint64_t),
                                 cudaMemcpyDeviceToDevice, s));
         if (k + 1 < K)
             PYR_TRY(cudaMemcpyAsync(g->pyr_parent + off[k], parL[k], lstart[k][n] * sizeof(int32_t),
@@ -840,6 +846,7 @@ fbs_status build_pyramid(fbs_grid* g, cudaStream_t s)
 #undef PYR_TRY
     g->pyr_K = K;
     for (int k = 0; k <= K; ++k) g->pyr_off[k] = off[k];
+    g->pyr_ioff_host = ioffa;
     return FBS_OK;
 }
 
@@ -1451,6 +1458,45 @@ fbs_status fbs_grid_export(const fbs_grid* g, int image, void* stream, uint64_t*
                 const int32_t u = soa[(size_t)k * V + v];
                 host_nbr[v * 10 + k] = u >= 0 ? (int32_t)(u - v0) : -1;
             }
+    return FBS_OK;
+}
+
+fbs_status fbs_pyramid_export(fbs_grid* g, int image, int level, void* stream, int* levels,
+                              int64_t* n_vertices, uint64_t* host_keys, int32_t* host_parent,
+                              float* host_count)
+{
+    if (!g || image < 0 || image >= g->n_images || level < 0) return FBS_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->pyr_K == 0) {
+        if (capturing(s)) return FBS_ERR_STATE;
+        const fbs_status st = build_pyramid(g, s);
+        if (st) return st;
+    }
+    const int K = g->pyr_K, n = g->n_images;
+    if (levels) *levels = K;
+    if (level >= K) return FBS_ERR_ARG;
+    const int64_t g0 = g->pyr_ioff_host[(size_t)level * (n + 1) + image];
+    const int64_t nv = g->pyr_ioff_host[(size_t)level * (n + 1) + image + 1] - g0;
+    if (n_vertices) *n_vertices = nv;
+    cudaError_t e = cudaSuccess;
+    if (host_keys)
+        e = cudaMemcpyAsync(host_keys, g->pyr_key + g0, nv * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+    if (host_count && e == cudaSuccess)
+        e = cudaMemcpyAsync(host_count, g->pyr_cnt + g0, nv * sizeof(float), cudaMemcpyDeviceToHost, s);
+    const bool top = level + 1 >= K;
+    if (host_parent && !top && e == cudaSuccess)
+        e = cudaMemcpyAsync(host_parent, g->pyr_parent + g0, nv * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (host_parent) {
+        // level-local ids of level + 1 -> indices within the image's range there
+        const int64_t base = top ? 0
+                                 : g->pyr_ioff_host[(size_t)(level + 1) * (n + 1) + image] -
+                                       g->pyr_off[level + 1];
+        for (int64_t i = 0; i < nv; ++i)
+            host_parent[i] = top ? -1 : (int32_t)(host_parent[i] - base);
+    }
     return FBS_OK;
 }
 

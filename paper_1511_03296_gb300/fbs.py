@@ -25,7 +25,7 @@ EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robus
             "fbs_solve_backward", "fbs_grid_info", "fbs_grid_export", "fbs_grid_sync",
             "fbs_grid_destroy", "fbs_status_string", "fbs_profile_enable", "fbs_profile_read",
             "fbs_set_option", "fbs_solve_static", "fbs_autotune", "fbs_solve_lowrank",
-            "fbs_domain_transform"]
+            "fbs_domain_transform", "fbs_pyramid_export"]
 
 OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT, OPT_PCG_FORM = 1, 2, 3, 4
 OPT_PHASE_BLOCKS, OPT_PRECONDITIONER = 5, 6
@@ -77,6 +77,8 @@ def load(path: Optional[str] = None):
         L.fbs_solve_lowrank.argtypes = [P, ctypes.POINTER(ProblemDesc), I, ctypes.c_double,
                                         ctypes.POINTER(I), P]
         L.fbs_domain_transform.argtypes = [P, I, I, P, I, F, F, I, P]
+        L.fbs_pyramid_export.argtypes = [P, I, I, P, ctypes.POINTER(I), ctypes.POINTER(I64), P, P,
+                                         P]
         L.fbs_solve_backward.argtypes = [P, ctypes.POINTER(ProblemDesc), ctypes.POINTER(P),
                                          ctypes.POINTER(P), ctypes.POINTER(P), I, P]
         L.fbs_grid_info.argtypes = [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64)]
@@ -264,6 +266,30 @@ def solve_lowrank(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25, eps: f
     _check(load().fbs_solve_lowrank(grid.handle, probs, int(pcg_iters), float(eps), ranks,
                                     _stream_ptr(stream)), "fbs_solve_lowrank")
     return list(ranks)
+
+
+def pyramid_export(grid: Grid, image: int = 0, stream=None) -> list:
+    """The bilateral-space pyramid of one image, level by level: a list of
+    dicts {keys, parent, count} (numpy arrays), level 0 first; built on the
+    GPU first if no hierarchical solve has built it."""
+    import numpy as np
+    L = load()
+    levels, n = ctypes.c_int(0), ctypes.c_int64(0)
+    _check(L.fbs_pyramid_export(grid.handle, int(image), 0, _stream_ptr(stream),
+                                ctypes.byref(levels), ctypes.byref(n), None, None, None),
+           "fbs_pyramid_export")
+    out = []
+    for k in range(levels.value):
+        _check(L.fbs_pyramid_export(grid.handle, int(image), k, _stream_ptr(stream), None,
+                                    ctypes.byref(n), None, None, None), "fbs_pyramid_export")
+        keys = np.empty(n.value, np.uint64)
+        parent = np.empty(n.value, np.int32)
+        count = np.empty(n.value, np.float32)
+        _check(L.fbs_pyramid_export(grid.handle, int(image), k, _stream_ptr(stream), None,
+                                    ctypes.byref(n), keys.ctypes.data, parent.ctypes.data,
+                                    count.ctypes.data), "fbs_pyramid_export")
+        out.append({"keys": keys, "parent": parent, "count": count})
+    return out
 
 
 def domain_transform(guide, x, sigma_s: float, sigma_r: float, iterations: int = 3,

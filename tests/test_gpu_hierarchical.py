@@ -208,3 +208,51 @@ def test_image_alone_equals_image_in_a_deeper_batch(hier):
     fs = f(ys)
     gap_gpu, gap_or = f(y2[1]) - fs, f(oy) - fs
     assert gap_or > 0 and 0.8 <= gap_gpu / gap_or <= 1.25, (gap_gpu, gap_or)
+
+
+def _halve(keys):
+    out = np.zeros_like(keys)
+    for shift in (48, 36, 24, 12, 0):
+        out |= ((keys >> np.uint64(shift)) & np.uint64(4095)) >> np.uint64(1) << np.uint64(shift)
+    return out
+
+
+def test_gpu_pyramid_equals_the_oracles_level_by_level():
+    # index work, compared exactly: per image and level the set of keys (the
+    # oracle's level sizes, numpy halving + unique), every parent link (the
+    # parent's key is the halved key), and the counts P(1) by brute force;
+    # the vertex order on levels >= 1 is the library's first-occurrence
+    # order, so sets are compared, not sequences
+    from paper_1511_03296_gb300 import fbs
+    insts = [_inst(101, 120, 160, (8.0, 4.0, 3.0), C=1, npoly=8),
+             synth.make_tiny(7, 100, 1000, 8, 1, (1.0, 4.0, 3.0), 128.0),
+             _inst(102, 1, 1, (8.0, 4.0, 3.0), C=2),
+             _inst(103, 37, 53, (3.3, 5.0, 7.7), C=2)]
+    g = gpu_grid(insts, 2)
+    for k_img, inst in enumerate(insts):
+        og = oracle_grid(inst, 2)
+        sizes, _ = oracle.pyramid(og.vkey)
+        levels = fbs.pyramid_export(g, k_img)
+        K = len(levels)
+        assert K >= len(sizes)
+        keys0 = og.vkey.astype(np.uint64)
+        ref = keys0
+        for k in range(K):
+            L = levels[k]
+            if k < len(sizes):
+                assert L["keys"].size == sizes[k], (k_img, k)
+                assert np.array_equal(np.sort(L["keys"]), ref), (k_img, k)
+                # P(1): grid vertices whose k-fold halved key is this key
+                anc = keys0
+                for _ in range(k):
+                    anc = _halve(anc)
+                u, cnt = np.unique(anc, return_counts=True)
+                assert np.array_equal(cnt[np.searchsorted(u, L["keys"])], L["count"].astype(np.int64))
+            else:                           # past the image's own top: one vertex, count 0
+                assert L["keys"].size == 1 and L["count"][0] == 0.0
+            if k + 1 < K:
+                up = levels[k + 1]["keys"]
+                assert np.array_equal(up[L["parent"]], _halve(L["keys"])), (k_img, k)
+            else:
+                assert np.all(L["parent"] == -1)
+            ref = np.unique(_halve(ref))
