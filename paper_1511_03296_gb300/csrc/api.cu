@@ -501,20 +501,23 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
             while (ti < ntiles && tiles[ti].img < k) ++ti;
             g->voff[k] = tile_voff[ti];
         }
+        // the GPU idles from the synchronisation until the next launch:
+        // allocate what the finalize pass writes, launch it, and do the rest
+        // of the host work while it runs
         const int64_t V = g->Vtot;
         FBS_TRY(dalloc(&g->vkey, V, s));
         FBS_TRY(dalloc(&g->pstart, V, s));
         FBS_TRY(dalloc(&g->m, V, s));
-        FBS_TRY(dalloc(&g->nbr, (size_t)V * 10, s));
-        FBS_TRY(dalloc(&g->nbrp, (size_t)V * 5, s));
-        FBS_TRY(dalloc(&g->n64, V, s));
-        FBS_TRY(dalloc(&g->n64b, V, s));
-        FBS_TRY(dalloc(&g->nf, V, s));
         FBS_TRY(launch_grid_finalize(d_tiles, ntiles, d_img, d_tile_voff, g->vid, d_tkey, d_tm,
                                      d_tps, g->vkey, g->m, g->pstart, g->cell_voff, s));
+        FBS_TRY(dalloc(&g->nbr, (size_t)V * 10, s));
+        FBS_TRY(dalloc(&g->nbrp, (size_t)V * 5, s));
         FBS_TRY(launch_grid_neighbours(d_tiles, ntiles, d_img, d_tile_voff, g->vkey, g->cell_voff,
                                        g->cell_nv, g->nbr, V, s));
         FBS_TRY(launch_pack_neighbours(g->nbr, g->nbrp, V, s));
+        FBS_TRY(dalloc(&g->n64, V, s));
+        FBS_TRY(dalloc(&g->n64b, V, s));
+        FBS_TRY(dalloc(&g->nf, V, s));
         // vertex tiles for the vertex kernels
         std::vector<VTile> vt;
         g->vt0.resize(n_images);
