@@ -80,6 +80,12 @@ def test_dt_many_channels_and_determinism():
     assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
 
 
+def test_dt_widest_row():
+    # 28000 pixels: the row kernel's largest shared-memory staging (231 KB)
+    guide, x = _case(14, 3, 28000, 1)
+    _check(guide, x, 32.0, 64.0, 2)
+
+
 def test_dt_argument_errors():
     from paper_1511_03296_gb300 import fbs
     guide, x = _case(13, 8, 8, 1)

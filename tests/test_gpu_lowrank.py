@@ -82,6 +82,17 @@ def test_lowrank_exact_rank_target():
     _check([inst], 25, 1e-6, expect_ranks=[2])
 
 
+def test_lowrank_sixty_four_channels():
+    # the widest target (64 channels, the Gram blocks' largest stride), of
+    # rank 3: pixel-level combinations of three channels
+    inst = synth.make_tiny(74, 48, 64, 5, 3)
+    rng = np.random.default_rng(4)
+    mix = rng.standard_normal((64, 3))
+    mix[10:20] = 0.0
+    inst.t = np.einsum("kc,chw->khw", mix, inst.t.astype(np.float64)).astype(np.float32)
+    _check([inst], 25, 1e-6, expect_ranks=[3])
+
+
 def test_lowrank_full_size_scenes_sampled():
     w = synth.segmentation_scenes_16(n_images=4)
     ranks = _check(w.instances, 25, 0.01)
