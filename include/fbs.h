@@ -84,8 +84,9 @@ typedef struct {
  * imgs: host array of n_images descriptors (the yuv buffers are device
  * memory and only need to live until this call returns).  *out receives a
  * new handle.  SYNCHRONISES `stream` once (to size the vertex arrays).
- * Errors: FBS_ERR_ARG (null, n_images < 1, non-positive size or sigma, a
- * grid cell of more than 16384 pixels, i.e. sigma_xy > 127), FBS_ERR_RANGE
+ * Errors: FBS_ERR_ARG (null, n_images outside 1 .. 65535, non-positive
+ * size or sigma, a grid cell of more than 16384 pixels, i.e. sigma_xy >
+ * 127), FBS_ERR_RANGE
  * (a key field out of [0, 4095], including NaN / negative colours),
  * FBS_ERR_OOM, FBS_ERR_CUDA.  On error *out is NULL.
  */

@@ -364,7 +364,8 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
 {
     if (!out) return FBS_ERR_ARG;
     *out = nullptr;
-    if (!imgs || n_images < 1) return FBS_ERR_ARG;
+    // image ids are 16-bit in the pyramid and index grid.y of per-image launches
+    if (!imgs || n_images < 1 || n_images > 65535) return FBS_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
 
     // ---- host geometry: cells, cell-row / cell-column pixel ranges, tiles

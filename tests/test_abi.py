@@ -57,6 +57,9 @@ def test_argument_errors_need_no_gpu(lib):
     out = ctypes.c_void_p(1)
     assert lib.fbs_grid_build(None, 1, None, ctypes.byref(out)) == 1
     assert out.value is None
+    descs = ctypes.c_void_p(0x1000)    # never read: the image count is checked first
+    assert lib.fbs_grid_build(descs, 65536, None, ctypes.byref(out)) == 1
+    assert lib.fbs_grid_build(descs, 0, None, ctypes.byref(out)) == 1
     lib.fbs_bistochastize.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
     assert lib.fbs_bistochastize(None, 2, None) == 1
     lib.fbs_solve.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
