@@ -751,6 +751,10 @@ fbs_status build_pyramid(fbs_grid* g, cudaStream_t s)
             while (sz < 2 * (ls[im + 1] - ls[im])) sz <<= 1;
             htoff[im + 1] = htoff[im] + sz;
         }
+        if (htoff[n] > INT32_MAX) {           // hash slots are 32-bit
+            cleanup();
+            return FBS_ERR_ARG;
+        }
         PYR_TRY(dalloc(&d_htoff, (size_t)n + 1, s));
         PYR_TRY(dalloc(&hkey, (size_t)htoff[n], s));
         PYR_TRY(dalloc(&hmin, (size_t)htoff[n], s));
