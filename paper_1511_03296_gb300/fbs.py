@@ -335,7 +335,8 @@ def solve_backward(grid: Grid, t: List, c: List, lam, yhat: List, dL_dx: List, d
 def set_option(grid: Grid, option: int, value: int) -> None:
     """OPT_VECTOR_PRECISION: VECTORS_AUTO / VECTORS_FP32 / VECTORS_COMPENSATED;
     OPT_PCG_LAUNCH: PCG_AUTO / PCG_PERSISTENT / PCG_PER_PHASE; OPT_PCG_FORM:
-    PCG_FORM_STANDARD / PCG_FORM_SINGLE; OPT_PHASE_BLOCKS: 1, 2, 4 (see
+    PCG_FORM_STANDARD / PCG_FORM_SINGLE; OPT_PHASE_BLOCKS: 1, 2, 4;
+    OPT_PRECONDITIONER: PRECOND_JACOBI / PRECOND_HIERARCHICAL (see
     include/fbs.h)."""
     _check(load().fbs_set_option(grid.handle, int(option), int(value)), "fbs_set_option")
 
