@@ -231,10 +231,8 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *                             built on the GPU on first use (one
  *                             synchronisation per level to read its size;
  *                             FBS_ERR_STATE if that first use is inside a
- *                             stream capture).  Applies when
- *                             every image has at most 4 channels; other
- *                             solves use Jacobi.  Per-phase launches,
- *                             standard PCG form.
+ *                             stream capture).  Any channel count;
+ *                             per-phase launches, standard PCG form.
  * FBS_OPT_PHASE_BLOCKS: 1 (default), 2 or 4 -- the per-phase PCG kernels
  *   launch min(tiles, SMs x resident blocks per SM x value) blocks; above 1
  *   the blocks take shorter runs of tiles in several waves.

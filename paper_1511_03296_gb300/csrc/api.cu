@@ -283,6 +283,7 @@ struct fbs_grid {
     float* pyr_dg = nullptr;
     float* pyr_scv = nullptr;
     float2* pyr_lv = nullptr;
+    int pyr_lv_nc = 0;                  // level-vector values per vertex pyr_lv holds
     int inject_timeout = 0;
     float* a = nullptr;
     float2* nm = nullptr;
@@ -827,6 +828,7 @@ fbs_status build_pyramid(fbs_grid* g, cudaStream_t s)
     PYR_TRY(dalloc(&g->pyr_dg, (size_t)V, s));
     PYR_TRY(dalloc(&g->pyr_scv, (size_t)V, s));
     PYR_TRY(dalloc(&g->pyr_lv, (size_t)std::max<int64_t>(T - V, 1) * kPyrMaxNc, s));
+    g->pyr_lv_nc = kPyrMaxNc;
     for (int k = 0; k < K; ++k) {
         PYR_TRY(cudaMemcpyAsync(g->pyr_vimg + off[k], imgL[k], lstart[k][n] * sizeof(uint16_t),
                                 cudaMemcpyDeviceToDevice, s));
@@ -896,8 +898,8 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     // the single-reduction form for FP32 vectors and images of at most 4
     // channels; it runs as per-phase launches
     plan.single = g->pcg_form == FBS_PCG_FORM_SINGLE && !plan.comp && cmax <= 4 ? 1 : 0;
-    // hierarchical preconditioner: images of at most 4 channels
-    plan.hier = g->precond == FBS_PRECOND_HIERARCHICAL && cmax <= 4 ? 1 : 0;
+    // hierarchical preconditioner: any channel count
+    plan.hier = g->precond == FBS_PRECOND_HIERARCHICAL ? 1 : 0;
     if (plan.hier) plan.single = 0;
     plan.persistent = g->persistent && !capturing(s) && !plan.single && !plan.hier ? 1 : 0;
     plan.block_mult = g->phase_blocks;
@@ -972,6 +974,16 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
         A.pyr.K = g->pyr_K;
         A.pyr.W = 1;
         for (const InstDev& d : inst) A.pyr.W = std::max(A.pyr.W, d.Cp);
+        if (A.pyr.W + 2 > g->pyr_lv_nc) {           // level vectors of a wider solve
+            if (cap) return FBS_ERR_STATE;
+            dfree(g->pyr_lv, s);
+            const int64_t nup = std::max<int64_t>(g->pyr_off[g->pyr_K] - g->pyr_off[1], 1);
+            if ((e = dalloc(&g->pyr_lv, (size_t)nup * (A.pyr.W + 2), s)) != cudaSuccess) {
+                g->pyr_lv_nc = 0;
+                return cuda_status(e);
+            }
+            g->pyr_lv_nc = A.pyr.W + 2;
+        }
         for (int k = 0; k <= g->pyr_K; ++k) A.pyr.off[k] = g->pyr_off[k];
         A.pyr.parent = g->pyr_parent;
         A.pyr.child_off = g->pyr_child_off;

@@ -822,16 +822,17 @@ __device__ __forceinline__ void wide_lane(const InstDev& I, int& P, int& nvc, in
     p = threadIdx.x - lv * P;
 }
 
-template <bool COMP, bool CO>
+template <bool COMP, bool CO, bool HIER = false>
 __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I, const VTile& vt,
                                            const float* __restrict__ dold,
                                            float* __restrict__ dnew, bool first, PhaseSmem& S,
                                            DF (&run)[4])
 {
+    // HIER: z = M_hier^-1 r read in place of M^-1 r (as apply_tile)
     int P, nvc, lv, p;
     wide_lane(I, P, nvc, lv, p);
     const int cb = 4 * p, Cp = I.Cp;
-    const float* __restrict__ rb = A.r + pass_base(I, cb);
+    const float* __restrict__ rb = (HIER ? A.pyr.z : A.r) + pass_base(I, cb);
     const float* __restrict__ ob = dold + pass_base(I, cb);
     float beta[4];
 #pragma unroll
@@ -848,14 +849,15 @@ __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I,
         load_neighbours(A, vs, nb);
         float rv[4], dv[4];
         ldw<4, CO>(rb + vs * Cp, rv);
+        const float mv = HIER ? 1.0f : nmv.y;
         if (first) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) dv[k] = nmv.y * rv[k];
+            for (int k = 0; k < 4; ++k) dv[k] = mv * rv[k];
         } else {
             float ov[4];
             ldw<4, CO>(ob + vs * Cp, ov);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) dv[k] = fmaf(beta[k], ov[k], nmv.y * rv[k]);
+            for (int k = 0; k < 4; ++k) dv[k] = fmaf(beta[k], ov[k], mv * rv[k]);
         }
         DF sacc[4];
 #pragma unroll
@@ -866,14 +868,15 @@ __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I,
             const float2 nmu = A.nm[u];
             float ru[4], du[4];
             ldw<4, CO>(rb + u * Cp, ru);
+            const float mu = HIER ? 1.0f : nmu.y;
             if (first) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) du[k] = nmu.y * ru[k];
+                for (int k = 0; k < 4; ++k) du[k] = mu * ru[k];
             } else {
                 float ou[4];
                 ldw<4, CO>(ob + u * Cp, ou);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) du[k] = fmaf(beta[k], ou[k], nmu.y * ru[k]);
+                for (int k = 0; k < 4; ++k) du[k] = fmaf(beta[k], ou[k], mu * ru[k]);
             }
             lap_acc<4, false>(sacc, nmu.x, dv, du);
         }
@@ -1068,7 +1071,7 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
         }
         if (WMAX == 4 && I.Cp > 4) {
             if (fetch) phase_scalars<PHASE, CO, 4>(A, I, in, it, S);
-            if (PHASE == 1) apply_wide<COMP, CO>(A, I, vt, dsrc, ddst, first, S, run);
+            if (PHASE == 1) apply_wide<COMP, CO, HIER>(A, I, vt, dsrc, ddst, first, S, run);
             else update_wide<COMP, CO>(A, I, vt, dsrc, S, run);
         } else if (PHASE == 1) {
             if (WMAX == 1 || I.Cp == 1)
@@ -1398,33 +1401,36 @@ pyr_gather0_kernel(SolveArgs A, const float* __restrict__ src, int nc, int scal)
     const int64_t np = P.off[2] - P.off[1];
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < np;
          p += (int64_t)gridDim.x * blockDim.x) {
-        DF acc[4], asc = {0.0f, 0.0f}, adg = {0.0f, 0.0f};
-#pragma unroll
-        for (int ch = 0; ch < 4; ++ch) acc[ch] = DF{0.0f, 0.0f};
         // a parent's children are grid vertices of its own image
         const InstDev& I = A.inst[P.vimg[P.off[1] + p]];
         const int cp = I.Cp;
         const float* base = src + I.vec_base - I.voff * cp;
-        const int32_t j1 = P.child_off[p + 1];
-#pragma unroll 4
-        for (int32_t j = P.child_off[p]; j < j1; ++j) {
-            const int64_t c = P.child_idx[j];
-            const float* x = base + c * cp;
-#pragma unroll
-            for (int ch = 0; ch < 4; ++ch)
-                if (ch < cp) acc[ch] = df_add_f(acc[ch], x[ch]);
-            if (scal) {
-                asc = df_add_f(asc, P.scv[c]);
-                adg = df_add_f(adg, P.dg[c]);
-            }
-        }
+        const int32_t j0 = P.child_off[p], j1 = P.child_off[p + 1];
         float2* dst = P.lv + p * nc;
+        for (int c0 = 0; c0 < W; c0 += 4) {          // 4 channels per walk of the children
+            DF acc[4], asc = {0.0f, 0.0f}, adg = {0.0f, 0.0f};
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch)
-            if (ch < W) pyr_st(dst + ch, acc[ch]);
-        if (scal) {
-            pyr_st(dst + W, asc);
-            pyr_st(dst + W + 1, adg);
+            for (int k = 0; k < 4; ++k) acc[k] = DF{0.0f, 0.0f};
+            const bool sc_here = scal && c0 == 0;
+#pragma unroll 4
+            for (int32_t j = j0; j < j1; ++j) {
+                const int64_t c = P.child_idx[j];
+                const float* x = base + c * cp + c0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (c0 + k < cp) acc[k] = df_add_f(acc[k], x[k]);
+                if (sc_here) {
+                    asc = df_add_f(asc, P.scv[c]);
+                    adg = df_add_f(adg, P.dg[c]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c0 + k < W) pyr_st(dst + c0 + k, acc[k]);
+            if (sc_here) {
+                pyr_st(dst + W, asc);
+                pyr_st(dst + W + 1, adg);
+            }
         }
     }
 }
@@ -1432,22 +1438,24 @@ pyr_gather0_kernel(SolveArgs A, const float* __restrict__ src, int nc, int scal)
 // one parent g (absolute, level k + 1 >= 2) sums its level-k children
 __device__ __forceinline__ void pyr_sum_children(const PyrDev& P, int k, int64_t g, int nc)
 {
-    DF acc[kPyrMaxNc];
-#pragma unroll
-    for (int ch = 0; ch < kPyrMaxNc; ++ch) acc[ch] = DF{0.0f, 0.0f};
     const int64_t gl = g - P.off[1];
-    const int32_t j1 = P.child_off[gl + 1];
+    const int32_t j0 = P.child_off[gl], j1 = P.child_off[gl + 1];
+    float2* dst = P.lv + gl * nc;
+    for (int c0 = 0; c0 < nc; c0 += kPyrMaxNc) {     // kPyrMaxNc values per walk
+        DF acc[kPyrMaxNc];
+#pragma unroll
+        for (int ch = 0; ch < kPyrMaxNc; ++ch) acc[ch] = DF{0.0f, 0.0f};
 #pragma unroll 4
-    for (int32_t j = P.child_off[gl]; j < j1; ++j) {
-        const float2* x = P.lv + (P.off[k] + P.child_idx[j] - P.off[1]) * nc;
+        for (int32_t j = j0; j < j1; ++j) {
+            const float2* x = P.lv + (P.off[k] + P.child_idx[j] - P.off[1]) * nc + c0;
+#pragma unroll
+            for (int ch = 0; ch < kPyrMaxNc; ++ch)
+                if (c0 + ch < nc) acc[ch] = df_add(acc[ch], pyr_ld(x + ch));
+        }
 #pragma unroll
         for (int ch = 0; ch < kPyrMaxNc; ++ch)
-            if (ch < nc) acc[ch] = df_add(acc[ch], pyr_ld(x + ch));
+            if (c0 + ch < nc) pyr_st(dst + c0 + ch, acc[ch]);
     }
-    float2* dst = P.lv + gl * nc;
-#pragma unroll
-    for (int ch = 0; ch < kPyrMaxNc; ++ch)
-        if (ch < nc) pyr_st(dst + ch, acc[ch]);
 }
 
 // Level k + 1 from level k, every image.
@@ -1491,12 +1499,10 @@ pyr_tail_kernel(SolveArgs A, int nc, int up, const float* __restrict__ wt)
                     const float2* u =
                         top ? nullptr : P.lv + (P.off[k + 1] + P.parent[g] - P.off[1]) * nc;
                     const float w = wt[g];
-#pragma unroll
-                    for (int ch = 0; ch < kPyrMaxNc; ++ch)
-                        if (ch < nc) {
-                            const DF xv = df_mul_f(pyr_ld(x + ch), w);
-                            pyr_st(x + ch, top ? xv : df_add(xv, pyr_ld(u + ch)));
-                        }
+                    for (int ch = 0; ch < nc; ++ch) {
+                        const DF xv = df_mul_f(pyr_ld(x + ch), w);
+                        pyr_st(x + ch, top ? xv : df_add(xv, pyr_ld(u + ch)));
+                    }
                 }
                 __syncthreads();
             }
@@ -1559,21 +1565,19 @@ pyr_down_low_kernel(SolveArgs A, int nc, const float* __restrict__ wt)
                 if (Ki > 4) l4 = P.lv + (P.off[4] + P.parent[g3] - P.off[1]) * nc;
             }
         }
-#pragma unroll
-        for (int ch = 0; ch < kPyrMaxNc; ++ch)
-            if (ch < nc) {
-                DF x = df_mul_f(pyr_ld(x1 + ch), w1);
-                if (Ki > 2) {
-                    DF x2 = df_mul_f(pyr_ld(l2 + ch), w2);
-                    if (Ki > 3) {
-                        DF x3 = df_mul_f(pyr_ld(l3 + ch), w3);
-                        if (Ki > 4) x3 = df_add(x3, pyr_ld(l4 + ch));
-                        x2 = df_add(x2, x3);
-                    }
-                    x = df_add(x, x2);
+        for (int ch = 0; ch < nc; ++ch) {
+            DF x = df_mul_f(pyr_ld(x1 + ch), w1);
+            if (Ki > 2) {
+                DF x2 = df_mul_f(pyr_ld(l2 + ch), w2);
+                if (Ki > 3) {
+                    DF x3 = df_mul_f(pyr_ld(l3 + ch), w3);
+                    if (Ki > 4) x3 = df_add(x3, pyr_ld(l4 + ch));
+                    x2 = df_add(x2, x3);
                 }
-                pyr_st(x1 + ch, x);
+                x = df_add(x, x2);
             }
+            pyr_st(x1 + ch, x);
+        }
     }
 }
 
@@ -1612,19 +1616,86 @@ __device__ __forceinline__ void pyr_precond_tile(const SolveArgs& A, const InstD
     store_partials<W>(acc, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst, out, S.red);
 }
 
+// Level 0 on a tile of a wide image (Cp > 4), in the wide phases' lane
+// layout (the Cp / 4 threads of a vertex take one float4 of its row each);
+// products r z accumulate in run[] over the block's run of the image's
+// tiles.
+__device__ __forceinline__ void pyr_precond_wide(const SolveArgs& A, const InstDev& I,
+                                                 const VTile& vt, DF (&run)[4])
+{
+    const PyrDev& P = A.pyr;
+    int Pn, nvc, lv, p;
+    wide_lane(I, Pn, nvc, lv, p);
+    const int cb = 4 * p, Cp = I.Cp;
+    const int64_t base = pass_base(I, cb);
+    const int nverts = (int)(vt.v1 - vt.v0);
+    for (int c0 = 0; c0 < nverts; c0 += nvc) {
+        const int v = (int)vt.v0 + c0 + lv;
+        const bool valid = lv < nvc && c0 + lv < nverts;
+        const int vs = valid ? v : (int)vt.v0;
+        float rv[4], zv[4], x[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        ldw<4, false>(A.r + base + (int64_t)vs * Cp, rv);
+        const float c0f = P.coef[vs];
+        if (P.K > 1) {
+            const float2* x1 = P.lv + (int64_t)P.parent[vs] * P.W + cb;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 t = x1[k];
+                x[k] = t.x + t.y;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            zv[k] = fmaf(c0f, rv[k], x[k]);
+            if (valid && cb + k < I.C) run[k] = df_add(run[k], df_mul_exact(rv[k], zv[k]));
+        }
+        if (valid) stw<4>(P.z + base + (int64_t)v * Cp, zv);
+    }
+}
+
 __global__ void __launch_bounds__(kVTile)
 pyr_precond0_kernel(SolveArgs A, float2* out)
 {
     __shared__ PhaseSmem S;
+    __shared__ WideSmem Wd;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
+    // wide images: one partial per run of the block's tiles of an image,
+    // stored in the run's first slot, the run's other slots zero (as in the
+    // phase kernels)
+    int cur = -1, run_tile = 0, run_C = 0, run_Cp = 8, run_ntiles = 0;
+    int64_t run_base = 0;
+    DF run[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) run[k] = {0.0f, 0.0f};
     for (int tile = t0; tile < t1; ++tile) {
         const VTile vt = A.vt[tile];
         const InstDev I = A.inst[vt.inst];
+        if (I.Cp > 4) {
+            if (vt.inst != cur) {
+                if (cur >= 0) flush_wide(run, run_Cp, run_C, run_ntiles, run_base, run_tile, out, Wd);
+                cur = vt.inst;
+                run_tile = vt.t_in_inst;
+                run_C = I.C;
+                run_Cp = I.Cp;
+                run_ntiles = I.ntiles;
+                run_base = I.part_base;
+            } else if ((int)threadIdx.x < I.C) {
+                out[I.part_base + (int64_t)threadIdx.x * I.ntiles + vt.t_in_inst] =
+                    make_float2(0.0f, 0.0f);
+            }
+            pyr_precond_wide(A, I, vt, run);
+            continue;
+        }
+        if (cur >= 0) {
+            flush_wide(run, run_Cp, run_C, run_ntiles, run_base, run_tile, out, Wd);
+            cur = -1;
+        }
         if (I.Cp == 1) pyr_precond_tile<1>(A, I, vt, out, S);
         else if (I.Cp == 2) pyr_precond_tile<2>(A, I, vt, out, S);
         else pyr_precond_tile<4>(A, I, vt, out, S);
     }
+    if (cur >= 0) flush_wide(run, run_Cp, run_C, run_ntiles, run_base, run_tile, out, Wd);
 }
 
 // Level 0 of the initialisation: y = (cinit b + x1_b) / (cinit S c + x1_Sc),

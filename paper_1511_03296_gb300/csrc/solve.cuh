@@ -6,7 +6,7 @@
 namespace fbs {
 
 constexpr int kMaxLevels = 16;     // bilateral-space pyramid levels (12-bit fields: at most 13)
-constexpr int kPyrMaxNc = 6;       // level-vector values per vertex: 4 channels, S c, diag A
+constexpr int kPyrMaxNc = 6;       // level-vector values per chunk of a pyramid sum
 constexpr int kPyrTailThreads = 1024;
 
 // The bilateral-space pyramid of a grid (supplement) and the per-solve
@@ -15,7 +15,7 @@ constexpr int kPyrTailThreads = 1024;
 // the grid's vertices.  Values of levels >= 1 live in buf (W per vertex).
 struct PyrDev {
     int K;                     // levels of the deepest image's pyramid (level 0 = the grid)
-    int W;                     // channels of a level vector: the widest image's Cp (<= 4)
+    int W;                     // channels of a level vector: the widest image's Cp
     int64_t off[kMaxLevels + 1];
     const int64_t* ioff;       // [K * (n_images + 1)]: image i's vertices on level k are
                                //   [ioff[k (n+1) + i], ioff[k (n+1) + i + 1]) (absolute)
@@ -31,8 +31,8 @@ struct PyrDev {
     float* coef;               // [off[K]]: preconditioner scale w(k) P(1) / P(diag A) (per solve)
     float* dg;                 // [off[1]]: diag(A) (per solve)
     float* scv;                // [off[1]]: S c (per solve)
-    float2* lv;                // [(off[K] - off[1]) * (W + 2)]: level values (double-float
-                               //   hi, lo), nc per vertex
+    float2* lv;                // [(off[K] - off[1]) * nc]: level values (double-float hi,
+                               //   lo), nc = W (+ 2 in the set-up) per vertex
     float* z;                  // CG vector layout: z = M_hier^-1 r
 };
 

@@ -1,8 +1,8 @@
 """Parity of the hierarchical preconditioner and initialisation (Sec. 4, the
 bilateral-space pyramid of the supplement) on the GPU with the oracle's
 hierarchical mode, at equal iteration counts (rel-L2 1e-5 on y and x).
-Solves it does not cover (an image of more than 4 channels) use Jacobi and
-are compared with the Jacobi oracle."""
+Images of any channel count are covered (Cp > 4 in the wide phases' lane
+layout)."""
 import numpy as np
 import pytest
 
@@ -132,10 +132,36 @@ def test_hier_batched_mixed_channel_counts():
     _check(insts)
 
 
-def test_hier_falls_back_for_wide_channels():
-    _check([_inst(96, 40, 56, (8.0, 4.0, 3.0), C=5)], hier=False)
-    _check([_inst(97, 40, 56, (8.0, 4.0, 3.0), C=1), _inst(98, 40, 56, (8.0, 4.0, 3.0), C=6)],
-           hier=False)
+@pytest.mark.parametrize("C", [5, 8, 21])
+def test_hier_wide_images(C):
+    # Cp > 4: the wide phases' lane layout, level vectors of Cp channels
+    _check([_inst(96 + C, 40, 56, (8.0, 4.0, 3.0), C=C, npoly=5)])
+
+
+def test_hier_batched_narrow_and_wide():
+    insts = [_inst(97, 40, 56, (8.0, 4.0, 3.0), C=1), _inst(98, 47, 61, (8.0, 4.0, 3.0), C=5),
+             _inst(99, 33, 70, (3.3, 5.0, 7.7), C=21), _inst(100, 52, 44, (8.0, 4.0, 3.0), C=2)]
+    _check(insts)
+
+
+def test_hier_backward_wide():
+    import torch
+    from paper_1511_03296_gb300 import fbs
+    inst = _inst(104, 40, 56, (8.0, 4.0, 3.0), C=6, npoly=5)
+    g = gpu_grid([inst], 2)
+    t, c = to_dev(inst.t), to_dev(inst.c)
+    og = oracle_grid(inst, 2)
+    with oracle.hierarchical(og):
+        oy, _ = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
+        yh = oy.astype(np.float32)
+        dx = np.random.default_rng(11).normal(size=inst.t.shape).astype(np.float32)
+        odt, odc = oracle.backward(og, inst.t, inst.c, inst.lam, 25, yh.astype(np.float64),
+                                   dx.reshape(6, -1))
+    dt, dc = torch.empty_like(t), torch.empty_like(c)
+    fbs.solve_backward(g, [t], [c], inst.lam, [to_dev(yh)], [to_dev(dx)], [dt], [dc], 25)
+    fbs.grid_sync(g)
+    assert rel_l2(dt.cpu().numpy().reshape(6, -1), odt) <= REL_L2_TOL
+    assert rel_l2(dc.cpu().numpy().reshape(-1), odc) <= REL_L2_TOL
 
 
 def test_hier_converges_faster_than_jacobi_on_the_gpu():
