@@ -317,8 +317,8 @@ def time_steps(step, steps, warmup, flush, stream):
 # captured and the traffic is scaled by its ratio to the algorithmic bytes
 # (below 1: the gathers read 16-bit packed neighbour offsets, not the 32-bit
 # ids the algorithmic count assumes).
-PCG_TRAFFIC_1080P = 6.887680e6 + 7.725056e6
-PCG_TRAFFIC_RATIO_BATCHED = (108.822784e6 + 10.850560e6 + 66.430208e6 + 0.663552e6) / 235835472
+PCG_TRAFFIC_1080P = 6.887936e6 + 7.725312e6
+PCG_TRAFFIC_RATIO_BATCHED = (108.809728e6 + 11.157760e6 + 66.430208e6 + 0.708096e6) / 235835472
 
 
 def pcg_roofline(regions, solves_per_step, steps, bytes_per_iter, peak):
