@@ -438,3 +438,14 @@ def bilateral_solve(t, c, grid: Grid, lam: float, pcg_iters: int = 25):
     if _BS is None:
         _BS = _autograd_function()
     return _BS.apply(t, c, grid, lam, pcg_iters)
+
+
+def __getattr__(name):
+    # fbs.BilateralSolve (the torch.autograd.Function), built on first access
+    # so that importing the binding does not import torch
+    global _BS
+    if name == "BilateralSolve":
+        if _BS is None:
+            _BS = _autograd_function()
+        return _BS
+    raise AttributeError(f"module {__name__!r} has no attribute {name!r}")

@@ -90,6 +90,11 @@ def test_argument_errors_need_no_gpu(lib):
         assert lib.fbs_domain_transform(*args, None) == 1, args
 
 
+def test_autograd_function_is_exposed():
+    torch = pytest.importorskip("torch")
+    assert issubclass(fbs.BilateralSolve, torch.autograd.Function)
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     with pytest.raises(RuntimeError, match="not built"):
         fbs._lib = None
