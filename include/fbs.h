@@ -120,8 +120,9 @@ fbs_status fbs_solve(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iters, 
  * ties in pivot order) and the fewest leading rows whose mass reaches
  * (1 - eps) of |B|_F^2 are kept (t of them, the image's rank); the reduced
  * system A Y~ = Q~ (the kept columns of Q) is solved with `pcg_iters`
- * Jacobi-PCG iterations per column, exactly as fbs_solve solves a t-channel
- * target, and x = S^T (Y~ R~) with R~ the kept rows.  R and P are formed on
+ * PCG iterations per column, exactly as fbs_solve solves a t-channel target
+ * (with the grid's preconditioner option), and x = S^T (Y~ R~) with R~ the
+ * kept rows.  R and P are formed on
  * the host from the pivoted Cholesky factorisation of the Gram matrix
  * B^T B (accumulated on the GPU with FP64 accuracy); a pivot at or below
  * 1e-13 of the largest column mass ends the factorisation (numerically
