@@ -711,6 +711,9 @@ def run_ours(args, dist):
         line["batched"] = run_extra_batched(dist, flush, stream, peak, xs, 3)
         line["fwd_bwd"] = run_extra_fwd_bwd(dist, flush, stream, peak, xs, 3)
         line["robust"] = run_extra_robust(dist, flush, stream, peak, max(3, xs // 2), 3)
+        line["batched_hierarchical"] = run_extra_batched(dist, flush, stream, peak,
+                                                         max(3, xs // 2), 3, sequential=False,
+                                                         precond="hierarchical")
         line["lowrank"] = run_extra_lowrank(dist, flush, stream, max(3, xs // 2), 3)
         line["domain_transform"] = run_extra_dt(dist, flush, stream, xs, 3)
     if dist.rank == 0 and not args.no_cpu_baseline:
