@@ -237,37 +237,63 @@ static double dot(int64_t V, const double* x, const double* y)
     return s;
 }
 
-/* Preconditioned CG, supplement Alg. 2 (Shewchuk B3), fixed iteration
- * count, one right-hand side.  y holds the initial state on entry.
- * The paper's lambda_new / lambda_old are named delta here. */
-int fbso_pcg(int64_t V, const int32_t* nbr, const double* n, const double* a,
-             const double* minv, double lam, const double* b, double* y, int iters)
+/* Preconditioned conjugate gradients (supplement, Algorithm 2; the
+ * Hestenes-Stiefel recurrences with a preconditioner), fixed iteration
+ * count, one right-hand side.  The preconditioner is a callback so the
+ * Jacobi and the hierarchical solves share one loop.  Per iteration:
+ *     q = A p;  alpha = rho / p'q;  y += alpha p;  r -= alpha q;
+ *     z = M^-1 r;  rho' = r'z;  beta = rho' / rho;  p = z + beta p.
+ * The y, r update, z and r'z are one pass over the vertices (z overwrites
+ * q, which is no longer needed); rho is the paper's lambda (renamed: the
+ * smoothness weight is lambda).  y holds the initial state on entry. */
+typedef void (*precond_fn)(const void* ctx, const double* r, double* z);
+
+struct jacobi_ctx { int64_t V; const double* minv; };
+
+static void jacobi_precond(const void* ctx, const double* r, double* z)
+{
+    const struct jacobi_ctx* J = (const struct jacobi_ctx*)ctx;
+    for (int64_t v = 0; v < J->V; ++v) z[v] = J->minv[v] * r[v];
+}
+
+static int pcg_core(int64_t V, const int32_t* nbr, const double* n, const double* a, double lam,
+                    precond_fn M, const void* mctx, const double* b, double* y, int iters)
 {
     size_t sz = (size_t)(V > 0 ? V : 1) * sizeof(double);
     double* r = (double*)malloc(sz);
-    double* d = (double*)malloc(sz);
+    double* p = (double*)malloc(sz);
     double* q = (double*)malloc(sz);
-    double* s = (double*)malloc(sz);
-    if (!r || !d || !q || !s) { free(r); free(d); free(q); free(s); return FBSO_ERR_OOM; }
+    if (!r || !p || !q) { free(r); free(p); free(q); return FBSO_ERR_OOM; }
 
+    /* r = b - A y, p = M^-1 r, rho = r'p */
     fbso_apply_A(V, nbr, n, a, lam, y, q);
     for (int64_t v = 0; v < V; ++v) r[v] = b[v] - q[v];
-    for (int64_t v = 0; v < V; ++v) d[v] = minv[v] * r[v];
-    double delta = dot(V, r, d);
-    for (int i = 0; i < iters; ++i) {
-        fbso_apply_A(V, nbr, n, a, lam, d, q);
-        double dq = dot(V, d, q);
-        double alpha = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
-        for (int64_t v = 0; v < V; ++v) y[v] += alpha * d[v];
-        for (int64_t v = 0; v < V; ++v) r[v] -= alpha * q[v];
-        for (int64_t v = 0; v < V; ++v) s[v] = minv[v] * r[v];
-        double delta_old = delta;
-        delta = dot(V, r, s);
-        double beta = delta_old != 0.0 ? delta / delta_old : 0.0;
-        for (int64_t v = 0; v < V; ++v) d[v] = s[v] + beta * d[v];
+    M(mctx, r, p);
+    double rho = dot(V, r, p);
+    for (int it = 0; it < iters; ++it) {
+        fbso_apply_A(V, nbr, n, a, lam, p, q);
+        const double pq = dot(V, p, q);
+        const double alpha = (pq > 0.0 && rho != 0.0) ? rho / pq : 0.0;
+        for (int64_t v = 0; v < V; ++v) {
+            y[v] += alpha * p[v];
+            r[v] -= alpha * q[v];
+        }
+        M(mctx, r, q);                               /* q now holds z = M^-1 r */
+        const double rho_next = dot(V, r, q);
+        const double beta = rho != 0.0 ? rho_next / rho : 0.0;
+        for (int64_t v = 0; v < V; ++v) p[v] = q[v] + beta * p[v];
+        rho = rho_next;
     }
-    free(r); free(d); free(q); free(s);
+    free(r); free(p); free(q);
     return FBSO_OK;
+}
+
+/* Jacobi PCG: M^-1 = 1 / diag(A) (0 where diag(A) <= 0) */
+int fbso_pcg(int64_t V, const int32_t* nbr, const double* n, const double* a,
+             const double* minv, double lam, const double* b, double* y, int iters)
+{
+    struct jacobi_ctx J = {V, minv};
+    return pcg_core(V, nbr, n, a, lam, jacobi_precond, &J, b, y, iters);
 }
 
 /* slice (Eq. (8)): x = S^T y */
@@ -517,38 +543,27 @@ static int hier_init(const double* b, const double* sc, double* y)
     return FBSO_OK;
 }
 
-/* Alg. 2 with M^-1 = M_hier^-1. */
+/* PCG with M^-1 = M_hier^-1 (the preconditioner of Sec. 4) */
+struct hier_ctx { const double* coef; double* work; };
+
+static void hier_precond_cb(const void* ctx, const double* r, double* z)
+{
+    const struct hier_ctx* H = (const struct hier_ctx*)ctx;
+    hier_apply(H->coef, r, z, H->work);
+}
+
 static int pcg_hier(int64_t V, const int32_t* nbr, const double* n, const double* a, double lam,
                     const double* b, double* y, int iters)
 {
     const int64_t T = pyr_total();
-    size_t sz = (size_t)(V > 0 ? V : 1) * sizeof(double);
-    double* r = (double*)malloc(sz);
-    double* d = (double*)malloc(sz);
-    double* q = (double*)malloc(sz);
-    double* s = (double*)malloc(sz);
     double* coef = (double*)malloc((size_t)T * sizeof(double));
     double* work = (double*)malloc((size_t)T * sizeof(double));
-    int st = (!r || !d || !q || !s || !coef || !work) ? FBSO_ERR_OOM : hier_coef(a, coef);
+    int st = (!coef || !work) ? FBSO_ERR_OOM : hier_coef(a, coef);
     if (!st) {
-        fbso_apply_A(V, nbr, n, a, lam, y, q);
-        for (int64_t v = 0; v < V; ++v) r[v] = b[v] - q[v];
-        hier_apply(coef, r, d, work);
-        double delta = dot(V, r, d);
-        for (int i = 0; i < iters; ++i) {
-            fbso_apply_A(V, nbr, n, a, lam, d, q);
-            double dq = dot(V, d, q);
-            double alpha = (dq > 0.0 && delta != 0.0) ? delta / dq : 0.0;
-            for (int64_t v = 0; v < V; ++v) y[v] += alpha * d[v];
-            for (int64_t v = 0; v < V; ++v) r[v] -= alpha * q[v];
-            hier_apply(coef, r, s, work);
-            double delta_old = delta;
-            delta = dot(V, r, s);
-            double beta = delta_old != 0.0 ? delta / delta_old : 0.0;
-            for (int64_t v = 0; v < V; ++v) d[v] = s[v] + beta * d[v];
-        }
+        struct hier_ctx H = {coef, work};
+        st = pcg_core(V, nbr, n, a, lam, hier_precond_cb, &H, b, y, iters);
     }
-    free(r); free(d); free(q); free(s); free(coef); free(work);
+    free(coef); free(work);
     return st;
 }
 
@@ -572,7 +587,8 @@ int fbso_hier_init(const double* b, const double* sc, double* y)
     return hier_init(b, sc, y);
 }
 
-/* Which form the solves below use: 0 = Alg. 2 as printed (fbso_pcg),
+/* Which form the solves below use: 0 = the two-reduction Jacobi PCG of
+ * Algorithm 2 (fbso_pcg),
  * 1 = the single-reduction form (fbso_pcg_single).  Process-wide; the test
  * suite sets it around the calls that need it. */
 static int g_pcg_form = 0;

@@ -7,6 +7,7 @@ index or a transposed operand in ``oracle/fbs_oracle.c`` fails one of them.
 """
 import json
 import os
+import types
 
 import numpy as np
 import pytest
@@ -656,3 +657,91 @@ def test_domain_transform_stops_at_an_edge():
     assert np.allclose(out[:, :, :k + 1], left, rtol=0, atol=1e-12)
     assert np.allclose(out[:, :, k + 1:], right, rtol=0, atol=1e-12)
     assert not np.allclose(out, x)
+
+
+# ---- hierarchical preconditioner and initialisation, hand-computed (Sec. 4) ----
+
+def _hand_pyramid():
+    # five vertices along x (x = 0, 1, 2, 3 and a second colour at x = 3):
+    # halving x gives level 1 = {x=0: vertices 0, 1; x=1: vertices 2, 3, 4},
+    # halving again gives the single top vertex, so P(1) = (1,1,1,1,1 | 2, 3 | 5)
+    sh = {"x": 36, "y": 48, "l": 24, "u": 12, "v": 0}
+
+    def key(**f):
+        return sum(int(v) << sh[k] for k, v in f.items())
+
+    vkey = np.array([key(x=0), key(x=1), key(x=2), key(x=3), key(x=3, l=1)], np.uint64)
+    return types.SimpleNamespace(vkey=vkey)
+
+
+def test_hand_pyramid_levels():
+    sizes, parent = oracle.pyramid(_hand_pyramid().vkey)
+    assert sizes.tolist() == [5, 2, 1]
+    assert parent.tolist() == [0, 0, 1, 1, 1, 0, 0]
+
+
+def test_hier_preconditioner_hand_computed():
+    # M_hier^-1 = P^T(z_weight o P(1) o P(.) / P(diag A)) with (alpha, beta) =
+    # (2, 5): z_weight = 1, 2^-6, 2^-7 on levels 0, 1, 2.  With diag(A) =
+    # (1, 2, 3, 4, 5): P(diag A) = (3, 12) on level 1 and 15 on level 2, so
+    # the level scalings are 1/a_v; 2^-6 * 2/3 = 1/96 and 2^-6 * 3/12 = 1/256;
+    # 2^-7 * 5/15 = 1/384.  Dropping P(1), or weighting by alpha^-(beta k),
+    # changes every coarse entry.
+    a = np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+    expect = np.diag(1.0 / a)
+    expect[:2, :2] += 1.0 / 96.0
+    expect[2:, 2:] += 1.0 / 256.0
+    expect += 1.0 / 384.0
+    with oracle.hierarchical(_hand_pyramid(), prec=(2.0, 5.0)) as H:
+        M = np.stack([H.precond(a, e) for e in np.eye(5)], axis=1)
+    assert np.allclose(M, expect, rtol=1e-14, atol=0)
+
+
+def test_hier_init_hand_computed():
+    # y_hier = P^T(z_weight o P(b) / P(1)) / P^T(z_weight o P(Sc) / P(1)) with
+    # (alpha, beta) = (4, 0): z_weight = 1, 1/4, 1/16.  b = (3, 0, 2, 5, 0),
+    # Sc = (1, 0, 2, 1, 0):
+    #   numerator   level 1: (3/2, 7/3)/4 = (3/8, 7/12); level 2: (10/5)/16 = 1/8
+    #               -> (7/2, 1/2, 65/24, 137/24, 17/24)
+    #   denominator level 1: (1/2, 3/3)/4 = (1/8, 1/4); level 2: (4/5)/16 = 1/20
+    #               -> (47/40, 7/40, 23/10, 13/10, 3/10)
+    b = np.array([3.0, 0.0, 2.0, 5.0, 0.0])
+    sc = np.array([1.0, 0.0, 2.0, 1.0, 0.0])
+    expect = np.array([140 / 47, 20 / 7, 325 / 276, 685 / 156, 85 / 36])
+    with oracle.hierarchical(_hand_pyramid(), init=(4.0, 0.0)) as H:
+        y = H.init(b, sc)
+    assert np.allclose(y, expect, rtol=1e-14, atol=0)
+
+
+# ---- domain transform: the iterations' sigma schedule (Gastal and Oliveira) ----
+
+def _dt_three_samples(a):
+    # one iteration on a 3-sample line with a flat guide (every step has
+    # length 1, weight a): the forward pass is lower triangular, the backward
+    # pass upper triangular, written out by hand from the recursion
+    fwd = np.array([[1.0, 0.0, 0.0],
+                    [a, 1.0 - a, 0.0],
+                    [a * a, a * (1.0 - a), 1.0 - a]])
+    bwd = np.array([[1.0 - a, a * (1.0 - a), a * a],
+                    [0.0, 1.0 - a, a],
+                    [0.0, 0.0, 1.0]])
+    return bwd @ fwd
+
+
+@pytest.mark.parametrize("iters", [2, 3])
+def test_domain_transform_sigma_schedule(iters):
+    # The cascade's per-iteration sigmas halve from one iteration to the next,
+    # starting large, and their squares add up to sigma_s^2: for 2 iterations
+    # (2, 1) sigma_s / sqrt(5), for 3 (4, 2, 1) sigma_s / sqrt(21).  On a
+    # 3-sample line the iterations do not commute (the ends), so the order is
+    # checked too; a reversed schedule moves the result by ~0.1.
+    sig_s = 3.0
+    sig = {2: [2 / 5 ** 0.5, 1 / 5 ** 0.5],
+           3: [4 / 21 ** 0.5, 2 / 21 ** 0.5, 1 / 21 ** 0.5]}[iters]
+    x = np.array([1.0, -2.0, 5.0])
+    expect = x.copy()
+    for s in sig:
+        expect = _dt_three_samples(np.exp(-np.sqrt(2.0) / (s * sig_s))) @ expect
+    guide = np.zeros((3, 1, 3), np.float32)
+    out = oracle.domain_transform(guide, x.reshape(1, 1, 3), sig_s, 10.0, iters)[0, 0]
+    assert np.allclose(out, expect, rtol=1e-14, atol=1e-15)
