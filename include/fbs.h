@@ -293,9 +293,22 @@ fbs_status fbs_autotune(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iter
  * (FBS_OPT_PRECONDITIONER and FBS_OPT_PCG_FORM do not apply: the pyramid
  * needs its own device arrays).
  *
- * Limits and sharing: the array holds 6 float vectors of sum_k C_k V_k
- * entries plus per-vertex and per-tile terms; a problem that does not fit
- * returns FBS_ERR_ARG.  Every GPU that loads the library holds the array
+ * Launch options set on the grid (FBS_OPT_PCG_LAUNCH, FBS_OPT_PHASE_BLOCKS,
+ * or fbs_autotune's choice) apply as they do to fbs_solve.
+ *
+ * Limits and sharing: the array is 64 MiB (67,108,864 bytes).  A problem
+ * needs, with V_k the vertex count and C_k the channel count of image k,
+ * Cp_k = C_k for C_k <= 2 and C_k rounded up to a multiple of 4 otherwise,
+ * and T_k = ceil(V_k / 256) vertex tiles:
+ *     32 B x sum_k roundup32(Cp_k V_k)    eight CG vectors (y, r, r_lo, two
+ *                                         search directions, q, two spares)
+ *   + 12 B x sum_k V_k                    diag(A) remainder and {n, M^-1}
+ *   + 32 B x sum_k C_k T_k                inner-product partials
+ *   + 144 B per image + 56 B per (image, channel) + 4,224 B of barrier words,
+ * each of these seven pieces rounded up to 256 bytes.  (One 3-channel image
+ * fits up to about 478,000 vertices, a 1-channel image about 1.5 million.)
+ * A problem that does not fit returns FBS_ERR_ARG before any device work.
+ * Every GPU that loads the library holds the array
  * until the process exits.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress) -- make that first call
  * before any stream capture.  All calls share the array and it keeps the

@@ -1607,6 +1607,8 @@ bool grid_view(const fbs_grid* g, GridView* out)
     out->bistoch_iters = g->bistoch_iters;
     out->precision = g->precision;
     out->persistent = g->persistent;
+    out->force_persistent = g->force_persistent;
+    out->phase_blocks = g->phase_blocks;
     out->img = g->img.data();
     out->voff = g->voff.data();
     out->vt0 = g->vt0.data();

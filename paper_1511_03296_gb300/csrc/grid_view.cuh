@@ -14,6 +14,8 @@ struct GridView {
     int bistoch_iters;
     int precision;             // FBS_VECTORS_*
     int persistent;            // 1: persistent PCG loop allowed
+    int force_persistent;      // 1: persistent loop even where per-phase launches are preferred
+    int phase_blocks;          // per-phase launch size, x (SMs x resident blocks)
     const ImgDev* img;         // host, n_images
     const int64_t* voff;       // host, n_images + 1
     const int* vt0;            // host, n_images

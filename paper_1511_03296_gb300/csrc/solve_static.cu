@@ -209,7 +209,10 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
     cudaStreamIsCapturing(s, &cs);
     P.persistent = G.persistent && cs == cudaStreamCaptureStatusNone ? 1 : 0;
     P.barrier = reinterpret_cast<unsigned*>(base + L.barrier);
-    if (P.persistent && !resident_preferred(A, P)) P.persistent = 0;
+    // the grid's launch options (fbs_set_option, fbs_autotune) as fbs_solve uses them
+    P.block_mult = G.phase_blocks;
+    P.force_persistent = G.force_persistent;
+    if (P.persistent && !P.force_persistent && !resident_preferred(A, P)) P.persistent = 0;
 
     e = launch_segment(A, P, kSegSetup, kSplatConfidence, s);
     if (e == cudaSuccess) e = launch_segment(A, P, kSegLoop, kSplatConfidence, s);

@@ -395,11 +395,35 @@ def profile_read():
 
 # ------------------------------------------------------------- autograd ---
 
-def _autograd_function():
+def _forward_batch(grid, ts, cs, lam, pcg_iters):
+    """One fbs_solve over every image of the grid; returns (xs, ys)."""
+    import torch
+    ts = [t.contiguous() for t in ts]
+    cs = [c.contiguous() for c in cs]
+    xs = [torch.empty_like(t) for t in ts]
+    ys = [torch.empty((int(t.shape[0]), grid.vertex_counts[k]), device=t.device,
+                      dtype=torch.float32) for k, t in enumerate(ts)]
+    solve(grid, ts, cs, lam, pcg_iters, x=xs, y=ys)
+    return ts, cs, xs, ys
+
+
+def _backward_batch(grid, ts, cs, ys, gxs, lam, pcg_iters):
+    """One fbs_solve_backward over every image of the grid; an output that
+    took no part in the loss (gradient None) contributes zeros."""
+    import torch
+    gxs = [torch.zeros_like(t) if g is None else g.contiguous() for g, t in zip(gxs, ts)]
+    dts = [torch.empty_like(t) for t in ts]
+    dcs = [torch.empty_like(c) for c in cs]
+    solve_backward(grid, ts, cs, lam, ys, gxs, dts, dcs, pcg_iters)
+    return dts, dcs
+
+
+def _autograd_functions():
     import torch
 
     class BilateralSolve(torch.autograd.Function):
-        """x = solve(t, c) on a prebuilt, bistochastised grid of ONE image.
+        """x = solve(t, c) on a prebuilt, bistochastised grid of ONE image:
+        ``BilateralSolve.apply(t, c, grid, lam, pcg_iters)``.
 
         forward saves only the bilateral-space solution y (C x V), as Sec. 3
         notes; backward runs a second PCG with the same A (fbs_solve_backward)
@@ -407,45 +431,76 @@ def _autograd_function():
 
         @staticmethod
         def forward(ctx, t, c, grid, lam, pcg_iters):
-            t = t.contiguous()
-            c = c.contiguous()
-            C, H, W = t.shape
-            x = torch.empty_like(t)
-            y = torch.empty((C, grid.vertex_counts[0]), device=t.device, dtype=torch.float32)
-            solve(grid, [t], [c], lam, pcg_iters, x=[x], y=[y])
-            ctx.save_for_backward(t, c, y)
+            if grid.n_images != 1:
+                raise ValueError("BilateralSolve takes a one-image grid; use "
+                                 "BilateralSolveBatch (bilateral_solve with lists) for a batch")
+            ts, cs, xs, ys = _forward_batch(grid, [t], [c], lam, pcg_iters)
+            ctx.save_for_backward(ts[0], cs[0], ys[0])
             ctx.grid, ctx.lam, ctx.iters = grid, lam, pcg_iters
-            return x
+            return xs[0]
 
         @staticmethod
         def backward(ctx, gx):
             t, c, y = ctx.saved_tensors
-            gx = gx.contiguous()
-            dt = torch.empty_like(t)
-            dc = torch.empty_like(c)
-            solve_backward(ctx.grid, [t], [c], ctx.lam, [y], [gx], [dt], [dc], ctx.iters)
-            return dt, dc, None, None, None
+            dts, dcs = _backward_batch(ctx.grid, [t], [c], [y], [gx], ctx.lam, ctx.iters)
+            return dts[0], dcs[0], None, None, None
 
-    return BilateralSolve
+    class BilateralSolveBatch(torch.autograd.Function):
+        """Every image of a batched grid in one forward launch sequence and one
+        backward: ``BilateralSolveBatch.apply(grid, lam, pcg_iters, t_0, ..,
+        t_{n-1}, c_0, .., c_{n-1})`` returns (x_0, .., x_{n-1}).  lam is one
+        value or one per image.  forward saves the targets, confidences and
+        the solutions y_k only; backward is one fbs_solve_backward call for
+        the whole batch."""
+
+        @staticmethod
+        def forward(ctx, grid, lam, pcg_iters, *tc):
+            n = grid.n_images
+            if len(tc) != 2 * n:
+                raise ValueError(f"expected {n} targets and {n} confidences")
+            ts, cs, xs, ys = _forward_batch(grid, tc[:n], tc[n:], lam, pcg_iters)
+            ctx.save_for_backward(*ts, *cs, *ys)
+            ctx.grid, ctx.lam, ctx.iters, ctx.n = grid, lam, pcg_iters, n
+            return tuple(xs)
+
+        @staticmethod
+        def backward(ctx, *gxs):
+            n = ctx.n
+            saved = ctx.saved_tensors
+            ts, cs, ys = saved[:n], saved[n:2 * n], saved[2 * n:]
+            dts, dcs = _backward_batch(ctx.grid, ts, cs, ys, gxs, ctx.lam, ctx.iters)
+            return (None, None, None, *dts, *dcs)
+
+    return BilateralSolve, BilateralSolveBatch
 
 
-_BS = None
+_FUNCS = None
 
 
-def bilateral_solve(t, c, grid: Grid, lam: float, pcg_iters: int = 25):
-    """Differentiable solve of one image (see BilateralSolve)."""
-    global _BS
-    if _BS is None:
-        _BS = _autograd_function()
-    return _BS.apply(t, c, grid, lam, pcg_iters)
+def _functions():
+    global _FUNCS
+    if _FUNCS is None:
+        _FUNCS = _autograd_functions()
+    return _FUNCS
+
+
+def bilateral_solve(t, c, grid: Grid, lam, pcg_iters: int = 25):
+    """Differentiable solve.  t, c tensors: one image (BilateralSolve), x
+    returned.  t, c lists with one entry per image of the grid: the whole
+    batch (BilateralSolveBatch), a list of x returned."""
+    if isinstance(t, (list, tuple)):
+        if not isinstance(c, (list, tuple)) or len(t) != len(c):
+            raise ValueError("lists of targets and confidences of equal length")
+        return list(_functions()[1].apply(grid, lam, pcg_iters, *t, *c))
+    return _functions()[0].apply(t, c, grid, lam, pcg_iters)
 
 
 def __getattr__(name):
-    # fbs.BilateralSolve (the torch.autograd.Function), built on first access
-    # so that importing the binding does not import torch
-    global _BS
+    # fbs.BilateralSolve / fbs.BilateralSolveBatch (torch.autograd.Function
+    # classes), built on first access so that importing the binding does not
+    # import torch
     if name == "BilateralSolve":
-        if _BS is None:
-            _BS = _autograd_function()
-        return _BS
+        return _functions()[0]
+    if name == "BilateralSolveBatch":
+        return _functions()[1]
     raise AttributeError(f"module {__name__!r} has no attribute {name!r}")

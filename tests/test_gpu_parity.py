@@ -306,6 +306,11 @@ def test_forward_both_vector_precisions(precision):
 
 
 def test_autograd_function_matches_backward():
+    # The gradient of c goes through t - S^T y-hat, which cancels where the
+    # solve reproduces the target, so the FP32 rounding of the forward y-hat
+    # is amplified there.  The oracle's backward is therefore given the GPU's
+    # own y-hat and dL/dx (the forward x is checked on its own), and the
+    # comparison holds the backward to the stated bar.
     import torch
     from paper_1511_03296_gb300 import fbs
     inst = _inst(14, 40, 60, (8.0, 4.0, 3.0), C=3, lam=16.0)
@@ -316,12 +321,19 @@ def test_autograd_function_matches_backward():
     label = to_dev(np.random.default_rng(0).random(inst.t.shape).astype(np.float32))
     loss = ((x - label) ** 2).mean()
     loss.backward()
+    yh = torch.empty((3, g.vertex_counts[0]), device="cuda")
+    x2 = torch.empty_like(x)
+    fbs.solve(g, [t.detach()], [c.detach()], inst.lam, 25, x=[x2], y=[yh])
+    fbs.grid_sync(g)
+    assert torch.equal(x2, x.detach())
     og = oracle_grid(inst, 2)
-    oy, ox = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
-    dx = 2.0 * (ox - label.cpu().numpy().reshape(3, -1).astype(np.float64)) / ox.size
-    odt, odc = oracle.backward(og, inst.t, inst.c, inst.lam, 25, oy, dx)
-    assert rel_l2(t.grad.cpu().numpy().reshape(3, -1), odt) <= REL_L2_TOL * 10
-    assert rel_l2(c.grad.cpu().numpy().reshape(-1), odc) <= REL_L2_TOL * 10
+    _, ox = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
+    assert rel_l2(x.detach().cpu().numpy().reshape(3, -1), ox) <= REL_L2_TOL
+    dx = (2.0 * (x.detach() - label) / x.numel()).cpu().numpy().reshape(3, -1)
+    odt, odc = oracle.backward(og, inst.t, inst.c, inst.lam, 25,
+                               yh.cpu().numpy().astype(np.float64), dx.astype(np.float64))
+    assert rel_l2(t.grad.cpu().numpy().reshape(3, -1), odt) <= REL_L2_TOL
+    assert rel_l2(c.grad.cpu().numpy().reshape(-1), odc) <= REL_L2_TOL
 
 
 # ------------------------------------------------------------ errors -------

@@ -63,11 +63,38 @@ def test_static_solve_1080p_matches_fbs_solve():
         assert rel_l2(x_st, x_ref) <= REL_L2_TOL and rel_l2(y_st, y_ref) <= REL_L2_TOL, call
 
 
-def test_static_solve_rejects_problems_above_the_array():
+STATIC_ARRAY_BYTES = 64 << 20
+
+
+def static_bytes(vertex_counts, channels):
+    """Scratch a problem needs, by the formula the header states."""
+    a256 = lambda x: (x + 255) // 256 * 256
+    cp = [c if c <= 2 else (c + 3) // 4 * 4 for c in channels]
+    cv = sum((p * v + 31) // 32 * 32 for p, v in zip(cp, vertex_counts))
+    cpart = sum(c * ((v + 255) // 256) for c, v in zip(channels, vertex_counts))
+    n, vt = len(channels), sum(vertex_counts)
+    return (a256(144 * n) + a256(32 * cv) + a256(4 * vt) + a256(8 * vt) + a256(56 * sum(channels))
+            + a256(32 * cpart) + a256(4224))
+
+
+def test_static_solve_limit_is_the_documented_one():
+    # the widest target that fits by the stated formula solves; the next
+    # wider one, whose padded width crosses the limit, is rejected
+    import torch
     from paper_1511_03296_gb300 import fbs
     rng = np.random.Generator(np.random.PCG64(12))
-    inst = synth.depth_instance(rng, 480, 640, 20, (2.0, 2.0, 2.0), 8.0, channels=64)
+    inst = synth.depth_instance(rng, 480, 640, 20, (2.0, 2.0, 2.0), 8.0, channels=1)
     g = gpu_grid([inst], 2)
-    assert 6 * 64 * g.vertex_counts[0] * 4 > 64 << 20
+    V = g.vertex_counts[0]
+    fits = [C for C in range(1, 65) if static_bytes([V], [C]) <= STATIC_ARRAY_BYTES]
+    c_ok = max(fits)
+    c_big = c_ok + 1
+    assert c_big <= 64 and static_bytes([V], [c_big]) > STATIC_ARRAY_BYTES, (V, c_ok)
+    c = to_dev(inst.c)
+    t_ok = to_dev(np.repeat(inst.t, c_ok, axis=0))
+    x = torch.empty_like(t_ok)
+    fbs.solve_static(g, [t_ok], [c], inst.lam, 5, x=[x])
+    fbs.grid_sync(g)
+    assert torch.isfinite(x).all()
     with pytest.raises(fbs.FbsError, match="ARG"):
-        fbs.solve_static(g, [to_dev(inst.t)], [to_dev(inst.c)], inst.lam, 5)
+        fbs.solve_static(g, [to_dev(np.repeat(inst.t, c_big, axis=0))], [c], inst.lam, 5)
