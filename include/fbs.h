@@ -304,7 +304,7 @@ fbs_status fbs_autotune(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iter
  *                                         search directions, q, two spares)
  *   + 12 B x sum_k V_k                    diag(A) remainder and {n, M^-1}
  *   + 32 B x sum_k C_k T_k                inner-product partials
- *   + 144 B per image + 56 B per (image, channel) + 4,224 B of barrier words,
+ *   + 144 B per image + 72 B per (image, channel) + 4,224 B of barrier words,
  * each of these seven pieces rounded up to 256 bytes.  (One 3-channel image
  * fits up to about 478,000 vertices, a 1-channel image about 1.5 million.)
  * A problem that does not fit returns FBS_ERR_ARG before any device work.

@@ -958,6 +958,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.aux[0] = g->vec + 6 * g->cap_vec;
     A.aux[1] = g->vec + 7 * g->cap_vec;
     A.scal = g->scal;
+    A.nscal = pc;
     plan.barrier = g->barrier;
     A.part_rs[0] = g->part;
     A.part_rs[1] = g->part + g->cap_part;
@@ -1002,6 +1003,9 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     // AUTO: the resident loop for small batches; per-phase (graph) otherwise
     if (plan.persistent && !plan.force_persistent && !resident_preferred(A, plan))
         plan.persistent = 0;
+    // the resident loop finalises each phase's scalars in its barrier; the
+    // initial residual then finalises delta_0 the same way
+    A.fin = plan.persistent && resident_fits(A, plan) ? 1 : 0;
     return run_segments(g, A, plan, s);
 }
 

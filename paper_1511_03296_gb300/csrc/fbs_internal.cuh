@@ -97,6 +97,10 @@ struct Scal {
     double delta[2];
     double delta0;          // r_0^T M^-1 r_0 (both forms): the stall test's scale
     double gam[2], alp[2];  // single-reduction form: gamma_i and alpha_i by iteration parity
+    double alpha;           // finalised scalars (standard form, Jacobi): alpha of the
+    float beta;             //   current iteration, beta of the next phase 1
+    unsigned done;          // tiles of the image whose partials are stored (first
+                            //   channel's entry only; 0 between phases)
 };
 
 // FP32-vector safeguard of the CG scalars: a channel whose r^T M^-1 r has

@@ -118,6 +118,7 @@ struct PhaseSmem {
     double sd2[kMaxChannels];    // second inner product (single-reduction form)
     float sf[kMaxChannels];      // beta (phase 1)
     double sa[kMaxChannels];     // alpha (phase 2)
+    int last;                    // this block completed an image's partials
 };
 
 // scratch of the per-channel reduction of wide images (Cp > 4)
@@ -214,6 +215,74 @@ __device__ void reduce_partials_all(const float2* __restrict__ part, const InstD
         DF t = red[k][0];
         for (int j = 1; j < nw; ++j) t = df_add(t, red[k][j]);
         out[k] = df_to_double(t);
+    }
+    __syncthreads();
+}
+
+// Finalised CG scalars (A.fin): the block that completes an image's tile
+// partials of a phase reduces them -- in the same fixed order as any block
+// would -- and stores the scalars the next phase needs, so the blocks of the
+// next phase read a few words instead of each reducing every partial of the
+// image.  kind 0: the partials are r^T M^-1 r of iteration `it` (initial
+// residual, or phase 2 of iteration it - 1): delta_it and beta_it.  kind 1:
+// d^T A d of iteration `it` (phase 1): alpha_it.  `ntiles`: the image's tiles
+// whose partials this block has stored since its last call.  The counter is
+// the image's first Scal entry; the completing block resets it.  Whole block.
+__device__ void finish_image(const SolveArgs& A, const InstDev& I, int ntiles,
+                             const float2* __restrict__ part, int kind, int it, PhaseSmem& S)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned old = atomicAdd(&A.scal[I.pc].done, (unsigned)ntiles);
+        const int last = old + (unsigned)ntiles == (unsigned)I.ntiles;
+        if (last) __threadfence();
+        S.last = last;
+    }
+    __syncthreads();
+    if (!S.last) return;
+    if (I.Cp == 1) reduce_partials_all<1, 8>(part, I, S.sd, S.red);
+    else if (I.Cp == 2) reduce_partials_all<2, 4>(part, I, S.sd, S.red);
+    else if (I.Cp == 4) reduce_partials_all<4, 2>(part, I, S.sd, S.red);
+    else {
+        reduce_instance_partials(part, I, S.sd);
+        __syncthreads();
+    }
+    for (int ch = threadIdx.x; ch < I.C; ch += blockDim.x) {
+        Scal* sc = &A.scal[I.pc + ch];
+        const double d0 = __ldcg(&sc->delta0);
+        if (kind == 0) {
+            const int slot = it & 1;
+            const double dnow = S.sd[ch];
+            double beta = 0.0;
+            if (it > 0) {
+                const double dprev = __ldcg(&sc->delta[slot ^ 1]);
+                beta = dprev != 0.0 && !cg_stalled(dnow, d0) ? dnow / dprev : 0.0;
+            } else {
+                sc->delta0 = dnow;
+            }
+            sc->delta[slot] = dnow;
+            sc->beta = (float)beta;
+        } else {
+            const double delta = __ldcg(&sc->delta[it & 1]);
+            const double dq = S.sd[ch];
+            sc->alpha = (dq > 0.0 && !cg_stalled(delta, d0)) ? delta / dq : 0.0;
+        }
+    }
+    if (threadIdx.x == 0) A.scal[I.pc].done = 0u;
+    __syncthreads();
+}
+
+// The finalised scalars of image I for a phase (A.fin): beta (phase 1) or
+// alpha (phase 2); padding channels 0.  Whole block; ends with a barrier.
+template <int PHASE>
+__device__ __forceinline__ void load_scalars(const SolveArgs& A, const InstDev& I, PhaseSmem& S)
+{
+    __syncthreads();
+    for (int ch = threadIdx.x; ch < I.Cp; ch += blockDim.x) {
+        const bool on = ch < I.C;
+        if (PHASE == 1) S.sf[ch] = on ? __ldcg(&A.scal[I.pc + ch].beta) : 0.0f;
+        else S.sa[ch] = on ? __ldcg(&A.scal[I.pc + ch].alpha) : 0.0;
     }
     __syncthreads();
 }
@@ -627,6 +696,7 @@ residual_kernel(SolveArgs A)
         if (I.Cp == 1) residual_tile<1, COMP>(A, I, vt, S);
         else if (I.Cp == 2) residual_tile<2, COMP>(A, I, vt, S);
         else residual_tile<4, COMP>(A, I, vt, S);
+        if (A.fin) finish_image(A, I, 1, A.part_rs[0], 0, 0, S);
     }
 }
 
@@ -1790,52 +1860,160 @@ cudaError_t pyr_setup(const SolveArgs& A, cudaStream_t s)
 }
 
 // ------------------------------------------------- persistent PCG loop ---
-// Grid barrier for a cooperative launch.  Thread 0 of each block arrives on
-// its group's counter (groups of consecutive blocks, each counter on its own
-// 128-byte line); the last arrival of a group arrives on the top counter;
-// the last group to arrive resets the top counter and advances the
-// generation word that every block polls.  Layout of `bar` (words): [0] top
-// counter, [1] generation, [32 g] counter of group g.  Every wait is
-// bounded: on time-out the block records kErrTimeout and false is returned.
-__device__ bool grid_barrier(unsigned* bar, uint32_t* err)
+// Grid barrier for a cooperative launch: one arrival counter that only
+// grows.  Thread 0 of each block publishes the block's writes (fence), adds
+// 1, and polls the counter with acquire loads until it reaches (epoch + 1) x
+// gridDim.x, the arrivals of every block at this barrier; `epoch` counts
+// the block's barriers (it starts at 0 with the counter).  The comparison is
+// of the signed difference, so a counter preset to 2^31 (the failure-path
+// test) is never reached.  Every wait is bounded: on time-out the block
+// records kErrTimeout and false is returned.  Layout of `bar`: word 0.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool grid_barrier(unsigned* bar, unsigned& epoch, uint32_t* err)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned* top = bar;
-        unsigned* gen = bar + 1;
-        const unsigned gsize = (gridDim.x + kBarrierGroups - 1) / kBarrierGroups;
-        const unsigned ngroups = (gridDim.x + gsize - 1) / gsize;
-        const unsigned grp = blockIdx.x / gsize;
-        const unsigned members = min(gsize, gridDim.x - grp * gsize);
-        unsigned* gcount = bar + 32 * (grp + 1);
-        const unsigned g = *(volatile unsigned*)gen;
+        const unsigned target = (epoch + 1u) * gridDim.x;
         __threadfence();
-        bool released = false;
-        if (atomicAdd(gcount, 1u) == members - 1) {
-            *(volatile unsigned*)gcount = 0u;
-            if (atomicAdd(top, 1u) == ngroups - 1) {
-                *(volatile unsigned*)top = 0u;
-                __threadfence();
-                atomicAdd(gen, 1u);
-                released = true;
+        atomicAdd(bar, 1u);
+        unsigned spins = 0;
+        while ((int)(ld_acquire_gpu(bar) - target) < 0) {
+            if (++spins > kBarrierSpinLimit) {
+                atomicOr(err, kErrTimeout);
+                ok = 0;
+                break;
             }
-        }
-        if (!released) {
-            unsigned spins = 0;
-            while (*(volatile unsigned*)gen == g) {
-                if (++spins > kBarrierSpinLimit) {
-                    atomicOr(err, kErrTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
-            }
+            __nanosleep(32);
         }
         __threadfence();
         s_ok = ok;
     }
+    ++epoch;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Store the scalars that follow a reduced inner product of one (image,
+// channel): kind 0, sum = r^T M^-1 r of iteration `it` -> delta_it, beta_it;
+// kind 1, sum = d^T A d of iteration `it` -> alpha_it (as phase_scalars).
+__device__ __forceinline__ void set_scalars(Scal* sc, int kind, int it, double sum)
+{
+    const double d0 = __ldcg(&sc->delta0);
+    if (kind == 0) {
+        double beta = 0.0;
+        if (it > 0) {
+            const double dprev = __ldcg(&sc->delta[(it & 1) ^ 1]);
+            beta = dprev != 0.0 && !cg_stalled(sum, d0) ? sum / dprev : 0.0;
+        } else {
+            sc->delta0 = sum;
+        }
+        sc->delta[it & 1] = sum;
+        sc->beta = (float)beta;
+    } else {
+        const double delta = __ldcg(&sc->delta[it & 1]);
+        sc->alpha = (sum > 0.0 && !cg_stalled(delta, d0)) ? delta / sum : 0.0;
+    }
+}
+
+// The scalars of every (image, channel) after a phase of the resident loop
+// (kind and it as in set_scalars), by the block that completed the phase.
+// Each sum is formed in the order of reduce_partials_all (thread t of the
+// block takes slots t, t + kVTile, ...; warp trees; warps in order), so every
+// launch style reaches the same scalar.  An image of at most 32 tiles is one
+// warp tree (the other warps' sums are exact zeros), so such images are
+// taken by the warps in turn; a larger image by the whole block.  `own` is
+// the block's own image, used when the batch has one image.  Whole block.
+__device__ void finalise_all(const SolveArgs& A, const InstDev& own, const float2* __restrict__ part,
+                             int kind, int it, PhaseSmem& S)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < A.ninst; ++k) {
+        const InstDev I = A.ninst == 1 ? own : A.inst[k];
+        if (I.ntiles <= 32) continue;
+        if (I.Cp == 1) reduce_partials_all<1, 8>(part, I, S.sd, S.red);
+        else if (I.Cp == 2) reduce_partials_all<2, 4>(part, I, S.sd, S.red);
+        else if (I.Cp == 4) reduce_partials_all<4, 2>(part, I, S.sd, S.red);
+        else {
+            reduce_instance_partials(part, I, S.sd);
+            __syncthreads();
+        }
+        for (int ch = threadIdx.x; ch < I.C; ch += blockDim.x)
+            set_scalars(&A.scal[I.pc + ch], kind, it, S.sd[ch]);
+        __syncthreads();
+    }
+    int pair = 0;
+    for (int k = 0; k < A.ninst; ++k) {
+        const int ntiles = A.ninst == 1 ? own.ntiles : A.inst[k].ntiles;
+        if (ntiles > 32) continue;
+        const InstDev& I = A.ninst == 1 ? own : A.inst[k];
+        for (int ch = 0; ch < I.C; ++ch, ++pair) {
+            if (pair % nw != w) continue;
+            const float2 v = lane < ntiles ? __ldcg(part + I.part_base + (int64_t)ch * ntiles + lane)
+                                           : make_float2(0.0f, 0.0f);
+            DF acc = {0.0f, 0.0f};
+            acc = df_add(acc, DF{v.x, v.y});
+            const DF t = df_warp_sum(acc);
+            if (lane == 0) set_scalars(&A.scal[I.pc + ch], kind, it, df_to_double(t));
+        }
+    }
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid barrier of the resident loop that also finalises the phase: every
+// block has stored its tile partials; the block whose arrival completes the
+// count reduces all (image, channel) partials, stores the next phase's
+// scalars and then releases the others through the release word (bar[32],
+// its own 128-byte line), which holds the number of barriers passed.  The
+// arrival count only grows (as in grid_barrier); a counter preset to 2^31
+// (the failure-path test) completes no barrier, and every wait is bounded:
+// on time-out the block records kErrTimeout and false is returned.
+__device__ bool reduce_barrier(const SolveArgs& A, const InstDev& own, unsigned* bar,
+                               unsigned& epoch, const float2* __restrict__ part, int kind, int it,
+                               PhaseSmem& S)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned target = (epoch + 1u) * gridDim.x;
+        __threadfence();
+        const unsigned old = atomicAdd(bar, 1u);
+        S.last = old == target - 1u;
+        if (S.last) __threadfence();
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (S.last) {
+        finalise_all(A, own, part, kind, it, S);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release_gpu(bar + 32, epoch + 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        unsigned spins = 0;
+        while ((int)(ld_acquire_gpu(bar + 32) - (epoch + 1u)) < 0) {
+            if (++spins > kBarrierSpinLimit) {
+                atomicOr(A.err, kErrTimeout);
+                s_ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+    }
+    ++epoch;
     __syncthreads();
     return s_ok != 0;
 }
@@ -1850,13 +2028,14 @@ pcg_loop_kernel(SolveArgs A, int iters, unsigned* bar)
     __shared__ WideSmem Wd;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
+    unsigned epoch = 0;
     for (int it = 0; it < iters; ++it) {
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
         phase_run<1, COMP, true, WMAX>(A, dold, dnew, it, t0, t1, S, Wd);
-        if (!grid_barrier(bar, A.err)) return;
+        if (!grid_barrier(bar, epoch, A.err)) return;
         phase_run<2, COMP, true, WMAX>(A, dnew, nullptr, it, t0, t1, S, Wd);
-        if (!grid_barrier(bar, A.err)) return;
+        if (!grid_barrier(bar, epoch, A.err)) return;
     }
 }
 
@@ -1904,6 +2083,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
         q[k] = 0.0f;
         if (!COMP) rlo[k] = 0.0f;
     }
+    unsigned epoch = 0;
     for (int it = 0; it < iters; ++it) {
         const int slot = it & 1;
         const float* dold = A.d[(it + 1) & 1];
@@ -1934,23 +2114,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
                     }
                 }
                 if (g0 == 0) {
-                    reduce_partials_all<W>(A.part_rs[slot], I, S.sd, S.red);
-                    if (tx < W) {
-                        double beta = 0.0;
-                        if (tx < I.C) {
-                            if (it > 0) {
-                                const double dprev = __ldcg(&A.scal[I.pc + tx].delta[slot ^ 1]);
-                                const double d0 = __ldcg(&A.scal[I.pc + tx].delta0);
-                                beta = dprev != 0.0 && !cg_stalled(S.sd[tx], d0) ? S.sd[tx] / dprev
-                                                                                 : 0.0;
-                            } else {
-                                A.scal[I.pc + tx].delta0 = S.sd[tx];
-                            }
-                            A.scal[I.pc + tx].delta[slot] = S.sd[tx];
-                        }
-                        S.sf[tx] = (float)beta;
-                    }
-                    __syncthreads();
+                    load_scalars<1>(A, I, S);
 #pragma unroll
                     for (int k = 0; k < W; ++k) {
                         beta[k] = S.sf[k];
@@ -1979,7 +2143,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
             if (valid) stw<W>(dnew + base + v * I.Cp, dv);
             store_partials<W>(acc, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst, A.part_dq, S.red);
         }
-        if (!grid_barrier(bar, A.err)) return;
+        if (!reduce_barrier(A, I, bar, epoch, A.part_dq, 1, it, S)) return;
         // ---- phase 2
         {
             DF s[W];
@@ -1996,20 +2160,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
                         ldw<W, true>(dnew + base + u * I.Cp, dn[j]);
                     }
                 }
-                if (g0 == 0) {
-                    reduce_partials_all<W>(A.part_dq, I, S.sd, S.red);
-                    if (tx < W) {
-                        double alpha = 0.0;
-                        if (tx < I.C) {
-                            const double delta = __ldcg(&A.scal[I.pc + tx].delta[slot]);
-                            const double d0 = __ldcg(&A.scal[I.pc + tx].delta0);
-                            const double dq = S.sd[tx];
-                            alpha = (dq > 0.0 && !cg_stalled(delta, d0)) ? delta / dq : 0.0;
-                        }
-                        S.sa[tx] = alpha;
-                    }
-                    __syncthreads();
-                }
+                if (g0 == 0) load_scalars<2>(A, I, S);
                 if (COMP) {
 #pragma unroll
                     for (int j = 0; j < NG; ++j) lap_acc<W, true>(s, s_nmu[g0 + j][tx].x, d, dn[j]);
@@ -2037,7 +2188,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
             store_partials<W>(acc, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst,
                               A.part_rs[slot ^ 1], S.red);
         }
-        if (!grid_barrier(bar, A.err)) return;
+        if (!reduce_barrier(A, I, bar, epoch, A.part_rs[slot ^ 1], 0, it + 1, S)) return;
     }
     if (valid) {
         stw<W>(A.y + base + v * I.Cp, y);
@@ -2157,8 +2308,8 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
             // barrier words zero (or, for the failure-path test, a top counter
             // that the last arrival can never match)
             cudaError_t e = cudaMemsetAsync(P.barrier, 0, kBarrierWords * sizeof(unsigned), s);
-            if (e == cudaSuccess && P.inject_timeout)   // top counter = 0x40000000 (little-endian)
-                e = cudaMemsetAsync(reinterpret_cast<unsigned char*>(P.barrier) + 3, 0x40, 1, s);
+            if (e == cudaSuccess && P.inject_timeout)   // counter = 2^31 (little-endian)
+                e = cudaMemsetAsync(reinterpret_cast<unsigned char*>(P.barrier) + 3, 0x80, 1, s);
             if (e != cudaSuccess) return e;
             SolveArgs a = A;
             int iters = P.pcg_iters;
@@ -2272,6 +2423,9 @@ cudaError_t launch_segment(const SolveArgs& A, const SolvePlan& P, int seg, int 
     static const int occ_rt = occupancy((const void*)residual_kernel<true>);
     cudaError_t e = cudaSuccess;
     if (seg == kSegSetup) {
+        // CG scalars and the images' completion counters start at zero
+        if ((e = cudaMemsetAsync(A.scal, 0, sizeof(Scal) * (size_t)A.nscal, s)) != cudaSuccess)
+            return e;
         prof_begin(f_splat, s);
         switch (P.chan_block) {
             case 1: e = launch_splat<1>(A, P, mode, s); break;

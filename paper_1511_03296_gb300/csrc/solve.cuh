@@ -62,6 +62,11 @@ struct SolveArgs {
     float* aux[2];             // single-reduction form: s = A p by iteration parity
     // reductions
     Scal* scal;                // sum_k C_k
+    int nscal;                 // entries of scal
+    int fin;                   // 1: finalised scalars (the resident loop) -- the block
+                               //    that completes a phase's partials reduces them once
+                               //    and stores the next phase's scalars; 0: every block
+                               //    reduces an image's partials when it starts on it
     float2* part_rs[2];        // sum_k C_k * ntiles_k double-float tile partials of r^T M^-1 r
     float2* part_dq;           // ... of d^T A d
     float2* part_mu[2];        // single-reduction form: partials of w^T u by parity

@@ -186,6 +186,7 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
     A.aux[0] = vec + 6 * cv;
     A.aux[1] = vec + 7 * cv;
     A.scal = reinterpret_cast<Scal*>(base + L.scal);
+    A.nscal = pc;
     A.part_rs[0] = part;
     A.part_rs[1] = part + cpart;
     A.part_dq = part + 2 * cpart;
@@ -213,6 +214,7 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
     P.block_mult = G.phase_blocks;
     P.force_persistent = G.force_persistent;
     if (P.persistent && !P.force_persistent && !resident_preferred(A, P)) P.persistent = 0;
+    A.fin = P.persistent && resident_fits(A, P) ? 1 : 0;
 
     e = launch_segment(A, P, kSegSetup, kSplatConfidence, s);
     if (e == cudaSuccess) e = launch_segment(A, P, kSegLoop, kSplatConfidence, s);

@@ -73,7 +73,7 @@ def static_bytes(vertex_counts, channels):
     cv = sum((p * v + 31) // 32 * 32 for p, v in zip(cp, vertex_counts))
     cpart = sum(c * ((v + 255) // 256) for c, v in zip(channels, vertex_counts))
     n, vt = len(channels), sum(vertex_counts)
-    return (a256(144 * n) + a256(32 * cv) + a256(4 * vt) + a256(8 * vt) + a256(56 * sum(channels))
+    return (a256(144 * n) + a256(32 * cv) + a256(4 * vt) + a256(8 * vt) + a256(72 * sum(channels))
             + a256(32 * cpart) + a256(4224))
 
 
