@@ -200,7 +200,8 @@ def _robust_parity(inst, sigma_gm, irls, pcg, tol):
     og = oracle_grid(inst, 2)
     oy, ox = oracle.solve_robust(og, inst.t, inst.c, inst.lam, sigma_gm, irls, pcg)
     ey, ex = rel_l2(y.cpu().numpy(), oy), rel_l2(x.cpu().numpy().reshape(1, -1), ox)
-    assert ey <= tol and ex <= tol, (ey, ex)
+    tol_y, tol_x = tol if isinstance(tol, tuple) else (tol, tol)
+    assert ey <= tol_y and ex <= tol_x, (ey, ex, tol_y, tol_x)
     return ey, ex
 
 
@@ -211,20 +212,28 @@ def test_robust_small(pcg_launch):
 
 
 def robust_tolerance(irls):
-    """max(1e-5, 4 x the FP64 loop's own deviation when its state is stored in
-    float32), from tests/golden/robust_sensitivity.json (written by the oracle)."""
+    """Bounds on y and x after `irls` IRLS iterations: max(1e-5, the largest
+    deviation of the FP64 loop when everything an FP32-vector solver keeps
+    in float32 carries a float32-sized representation error -- rounded to
+    nearest, or moved by seeded uniform amounts within half an ulp).  The
+    IRLS loop amplifies such errors about fourfold per iteration from the
+    seventh on; the values come from tests/golden/robust_sensitivity.json,
+    written by the oracle alone."""
     import json
     import os
     sens = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
                                        "robust_sensitivity.json")))
-    return max(REL_L2_TOL, 4.0 * max(sens["y"][irls - 1], sens["b"][irls - 1]))
+    k = irls - 1
+    tol_y = max([sens["store32"][k]] + [d[k] for d in sens["store32_draws"]])
+    tol_x = max([sens["store32_x"][k]] + [d[k] for d in sens["store32_draws_x"]])
+    return max(REL_L2_TOL, tol_y), max(REL_L2_TOL, tol_x)
 
 
 @pytest.mark.parametrize("irls", [3, 10])
 def test_robust_1400x1000(irls):
     inst = synth.robust_1400x1000().instances[0]
     tol = robust_tolerance(irls)
-    print(f"robust 1400x1000, {irls} IRLS, tol {tol:.2e}, rel-L2 (y, x):",
+    print(f"robust 1400x1000, {irls} IRLS, tol (y, x) ({tol[0]:.2e}, {tol[1]:.2e}), rel-L2 (y, x):",
           _robust_parity(inst, 1.0, irls, 25, tol))
 
 
