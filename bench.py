@@ -34,8 +34,15 @@ if ROOT not in sys.path:
 METRIC = "solved Mpix/s (25-iter PCG, 1080p & batched), fwd+bwd Mpix/s; % HBM peak"
 WORKLOAD = ("plain solve, 1920x1080 reference, C=3 piecewise-planar target, c~U[0,1], "
             "sigma=(16,8,8), lambda=128, 2 bistochastisation sweeps, 25 Jacobi-PCG iterations")
+L2_NOTE = ("GPU arm: L2 flushed between steps by a 256 MiB write outside the step events; "
+           "CPU oracle arm: host memory, no flush")
 BISTOCH_ITERS = 2
 PCG_ITERS = 25
+
+
+def bench_config():
+    """The config object both arms print (same keys and values)."""
+    return {"workload": WORKLOAD, "l2": L2_NOTE}
 
 
 def parse_args():
@@ -266,7 +273,8 @@ def run_reference(args, dist):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * total / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pixels_per_step": sample.n_pixels},
+            "config": bench_config(),
+            "sample_pixels_per_step": sample.n_pixels,
             "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": 1, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
@@ -390,9 +398,15 @@ def run_extra_batched(dist, flush, stream, peak, steps, warmup, n_images=64, seq
             "phase_share": {k: round(v[1] / max(1e-9, sum(w[1] for w in regions.values())), 4)
                             for k, v in regions.items() if v[0]},
             "pcg_roofline": dict(pcg_roofline(regions, 1, steps, bytes_iter, peak) or {},
-                                 traffic=PCG_TRAFFIC_RATIO_BATCHED * bytes_iter,
+                                 traffic=PCG_TRAFFIC_RATIO_BATCHED * bytes_iter
+                                 if precond == "jacobi" else None,
                                  traffic_source="ncu of the first 16 images, scaled by "
-                                                "traffic / algorithmic bytes")}
+                                                "traffic / algorithmic bytes"
+                                 if precond == "jacobi" else None,
+                                 bytes_basis="Jacobi PCG iteration, 48 + 40 C per vertex"
+                                 if precond == "jacobi" else
+                                 "Jacobi-byte equivalent: 48 + 40 C per vertex; the pyramid "
+                                 "sweeps' bytes are not counted, their time is")}
 
 
 def run_extra_robust(dist, flush, stream, peak, steps, warmup):
@@ -582,6 +596,27 @@ def run_only(args, dist):
         print(json.dumps({"only": args.only, **out}), flush=True)
 
 
+def summary(line):
+    """The headline figures of every workload, compact, last on the line."""
+    frac = lambda rec: round(rec.get("pcg_roofline", {}).get("frac", float("nan")), 3)
+    b, f, r = line["batched"], line["fwd_bwd"], line["robust"]
+    h, lr = line["batched_hierarchical"], line["lowrank"]
+    return {
+        "1080p_mpix_s": round(line["value"], 1),
+        "1080p_pcg_frac": round(line["roofline"].get("frac", float("nan")), 3),
+        "batched_mpix_s": round(b["batched_mpix_s"], 1),
+        "one_at_a_time_mpix_s": round(b["one_at_a_time_mpix_s"], 1),
+        "batched_speedup": round(b["batched_mpix_s"] / b["one_at_a_time_mpix_s"], 2),
+        "batched_pcg_frac": frac(b),
+        "fwd_bwd_mpix_s": round(f["fwd_bwd_mpix_s"], 1), "fwd_bwd_pcg_frac": frac(f),
+        "robust_mpix_s": round(r["robust_mpix_s"], 1), "robust_pcg_frac": frac(r),
+        "hierarchical_batched_mpix_s": round(h["batched_mpix_s"], 1),
+        "lowrank_speedup": round(lr["speedup"], 2),
+        "domain_transform_mpix_s": round(line["domain_transform"]["mpix_s"], 1),
+        "cpu_oracle_1core_mpix_s": round(line.get("cpu_baseline", {}).get("value", float("nan")), 2),
+    }
+
+
 def run_ours(args, dist):
     import torch
 
@@ -687,12 +722,12 @@ def run_ours(args, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pixels_per_gpu": inst.n_pixels, "vertices": V,
-                   "channels": inst.channels, "parallelism": f"replicas x{dist.world}",
-                   "l2": "flushed between steps (256 MiB write outside the step events)",
-                   "precision": "FP32 vectors, FP64-accurate CG dot products, FP64 "
-                                "bistochastisation",
-                   "tuning": tuning},
+        "config": bench_config(),
+        "details": {"pixels_per_gpu": inst.n_pixels, "vertices": V, "channels": inst.channels,
+                    "parallelism": f"replicas x{dist.world}",
+                    "precision": "FP32 vectors, FP64-accurate CG dot products, FP64 "
+                                 "bistochastisation",
+                    "tuning": tuning, "phase_share": None, "kernel_share": None},
         "clocks": clk.summary(),
         "e2e": {"value": whole_job_mpix(dist.world, inst.n_pixels, e2e_ms), "unit": "Mpix/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -703,22 +738,31 @@ def run_ours(args, dist):
                          peak_source="measured" if peaks else "fallback",
                          note="working set L2-resident at this size; see batched / fwd_bwd "
                               "for the HBM-bound sizes"),
-        "phase_share": region_share,
-        "kernel_share": shares,
     }
+    line["details"]["phase_share"] = region_share
+    line["details"]["kernel_share"] = shares
     if not args.no_extra:
         xs = max(3, min(args.steps // 10, 20))
-        line["batched"] = run_extra_batched(dist, flush, stream, peak, xs, 3)
-        line["fwd_bwd"] = run_extra_fwd_bwd(dist, flush, stream, peak, xs, 3)
-        line["robust"] = run_extra_robust(dist, flush, stream, peak, max(3, xs // 2), 3)
-        line["batched_hierarchical"] = run_extra_batched(dist, flush, stream, peak,
-                                                         max(3, xs // 2), 3, sequential=False,
-                                                         precond="hierarchical")
-        line["lowrank"] = run_extra_lowrank(dist, flush, stream, max(3, xs // 2), 3)
-        line["domain_transform"] = run_extra_dt(dist, flush, stream, xs, 3)
+        extra = {
+            "batched": run_extra_batched(dist, flush, stream, peak, xs, 3),
+            "fwd_bwd": run_extra_fwd_bwd(dist, flush, stream, peak, xs, 3),
+            "robust": run_extra_robust(dist, flush, stream, peak, max(3, xs // 2), 3),
+            "batched_hierarchical": run_extra_batched(dist, flush, stream, peak,
+                                                      max(3, xs // 2), 3, sequential=False,
+                                                      precond="hierarchical"),
+            "lowrank": run_extra_lowrank(dist, flush, stream, max(3, xs // 2), 3),
+            "domain_transform": run_extra_dt(dist, flush, stream, xs, 3),
+        }
+        # long per-workload records (phase shares, tuning) go to details, so the
+        # results themselves stay near the end of the line
+        for name, rec in extra.items():
+            line["details"][name] = {k: rec.pop(k) for k in ("phase_share", "tuning") if k in rec}
+        line.update(extra)
     if dist.rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(synth.plain_1080p().instances[0], args.cpu_seconds)
         line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.cpu_seconds / 2)
+    if not args.no_extra:
+        line["summary"] = summary(line)
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
 
