@@ -102,10 +102,12 @@ class Dist:
 
 def tune(fbs, yuv, sig, t, c, lam, x):
     """The library's autotuner on one grid of the workload (its choice is then
-    set on every step's grid; tuning happens outside the timed region)."""
+    set on every step's grid; tuning happens outside the timed region).  Every
+    step builds a new grid and solves it once, so the tuner times first solves
+    on a grid (no graph replay)."""
     g = fbs.grid_build(yuv, *sig)
     fbs.bistochastize(g, BISTOCH_ITERS)
-    r = fbs.autotune(g, t, c, lam, PCG_ITERS, x=x)
+    r = fbs.autotune(g, t, c, lam, PCG_ITERS, x=x, single_solve=True)
     g.destroy()
     return r
 

@@ -241,9 +241,16 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *   loop start with its barrier counter preset so that no barrier can
  *   complete; every block waits out its bounded spin, latches
  *   FBS_ERR_TIMEOUT and returns (a test of the failure path; one-shot).
+ * FBS_OPT_TUNE_SINGLE_SOLVE: 0 (default) or 1 -- what fbs_autotune times.
+ *   0: repeated solves on this grid, whose per-phase launches are replayed
+ *   from a CUDA graph captured on the second solve of a shape.  1: the
+ *   first solve on a grid (the graphs are dropped before every timed
+ *   solve, so per-phase launches go out one by one), for callers that
+ *   build a new grid for every solve.
  */
 enum { FBS_OPT_VECTOR_PRECISION = 1, FBS_OPT_PCG_LAUNCH = 2, FBS_OPT_INJECT_BARRIER_TIMEOUT = 3,
-       FBS_OPT_PCG_FORM = 4, FBS_OPT_PHASE_BLOCKS = 5, FBS_OPT_PRECONDITIONER = 6 };
+       FBS_OPT_PCG_FORM = 4, FBS_OPT_PHASE_BLOCKS = 5, FBS_OPT_PRECONDITIONER = 6,
+       FBS_OPT_TUNE_SINGLE_SOLVE = 7 };
 enum { FBS_PRECOND_JACOBI = 0, FBS_PRECOND_HIERARCHICAL = 1 };
 enum { FBS_VECTORS_AUTO = 0, FBS_VECTORS_FP32 = 1, FBS_VECTORS_COMPENSATED = 2 };
 enum { FBS_PCG_AUTO = 0, FBS_PCG_PERSISTENT = 1, FBS_PCG_PER_PHASE = 2 };
@@ -260,8 +267,9 @@ fbs_status fbs_set_option(fbs_grid* g, int option, int value);
  * (per-phase launches, or the persistent loop where its cooperative launch
  * fits), PCG form (standard or single-reduction) and the per-phase block
  * count (FBS_OPT_PHASE_BLOCKS 1, 2, 4) -- each warmed up twice (so graph
- * replay is what gets timed) and timed over three solves with CUDA events on
- * `stream`, then leaves the fastest set on the grid (fbs_set_option values)
+ * replay is what gets timed; with FBS_OPT_TUNE_SINGLE_SOLVE set, the graphs
+ * are dropped before each solve instead) and timed over three solves with
+ * CUDA events on `stream`, then leaves the fastest set on the grid (fbs_set_option values)
  * and solves once more with it, so the output buffers in probs hold that
  * configuration's result.  *out, if not null, receives the choice and its
  * median solve time.  Synchronises `stream`.  Errors: as fbs_solve;

@@ -265,6 +265,7 @@ struct fbs_grid {
     int force_persistent = 0;
     int pcg_form = FBS_PCG_FORM_STANDARD;
     int phase_blocks = 1;
+    int tune_single = 0;       // fbs_autotune times first solves (graphs dropped)
     int precond = FBS_PRECOND_JACOBI;
     // bilateral-space pyramid (built on the first hierarchical solve)
     int pyr_K = 0;
@@ -1354,6 +1355,11 @@ fbs_status fbs_set_option(fbs_grid* g, int option, int value)
         g->phase_blocks = value;
         return FBS_OK;
     }
+    if (option == FBS_OPT_TUNE_SINGLE_SOLVE) {
+        if (value != 0 && value != 1) return FBS_ERR_ARG;
+        g->tune_single = value;
+        return FBS_OK;
+    }
     if (option == FBS_OPT_PCG_FORM) {
         if (value != FBS_PCG_FORM_STANDARD && value != FBS_PCG_FORM_SINGLE) return FBS_ERR_ARG;
         g->pcg_form = value;
@@ -1399,9 +1405,20 @@ fbs_status fbs_autotune(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iter
         g->force_persistent = cands[c].launch == FBS_PCG_PERSISTENT ? 1 : 0;
         g->pcg_form = cands[c].form;
         g->phase_blocks = cands[c].blocks;
-        for (int w = 0; w < 2 && !st; ++w) st = fbs_solve(g, probs, pcg_iters, stream);
+        // single-solve timing: drop the graphs (after the work that may use
+        // them has finished) so that each solve is a grid's first
+        auto drop_graphs = [&]() {
+            if (!g->tune_single) return;
+            if (cudaStreamSynchronize(s) != cudaSuccess) st = FBS_ERR_CUDA;
+            free_graphs(g);
+        };
+        for (int w = 0; w < 2 && !st; ++w) {
+            drop_graphs();
+            if (!st) st = fbs_solve(g, probs, pcg_iters, stream);
+        }
         float t[3] = {0.0f, 0.0f, 0.0f};
         for (int r = 0; r < 3 && !st; ++r) {
+            drop_graphs();
             if (cudaEventRecord(ev[0], s) != cudaSuccess) st = FBS_ERR_CUDA;
             if (!st) st = fbs_solve(g, probs, pcg_iters, stream);
             if (!st && cudaEventRecord(ev[1], s) != cudaSuccess) st = FBS_ERR_CUDA;

@@ -28,7 +28,7 @@ EXPORTED = ["fbs_grid_build", "fbs_bistochastize", "fbs_solve", "fbs_solve_robus
             "fbs_domain_transform", "fbs_pyramid_export"]
 
 OPT_VECTOR_PRECISION, OPT_PCG_LAUNCH, OPT_INJECT_BARRIER_TIMEOUT, OPT_PCG_FORM = 1, 2, 3, 4
-OPT_PHASE_BLOCKS, OPT_PRECONDITIONER = 5, 6
+OPT_PHASE_BLOCKS, OPT_PRECONDITIONER, OPT_TUNE_SINGLE_SOLVE = 5, 6, 7
 PRECOND_JACOBI, PRECOND_HIERARCHICAL = 0, 1
 VECTORS_AUTO, VECTORS_FP32, VECTORS_COMPENSATED = 0, 1, 2
 PCG_AUTO, PCG_PERSISTENT, PCG_PER_PHASE = 0, 1, 2
@@ -217,18 +217,79 @@ class _TuneResult(ctypes.Structure):
                 ("candidates", ctypes.c_int)]
 
 
+def tuning_key(grid: Grid, t: List, device_name: Optional[str] = None) -> str:
+    """The autotuner cache's key of a problem: the GPU's name and the
+    problem's shape class -- the image count and the total vertex count
+    (each in powers of two) and the widest padded channel row."""
+    import math
+    if device_name is None:
+        import torch
+        device_name = torch.cuda.get_device_name(t[0].device)
+    n = grid.n_images
+    v = max(1, sum(grid.vertex_counts))
+    cmax = max(int(tt.shape[0]) for tt in t)
+    row = cmax if cmax <= 2 else (cmax + 3) // 4 * 4
+    return (f"{device_name}|images~2^{math.ceil(math.log2(n)) if n > 1 else 0}"
+            f"|vertices~2^{round(math.log2(v))}|row={row}")
+
+
+def _cache_read(path: str) -> dict:
+    import json
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("entries", {}) if isinstance(d, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def _cache_write(path: str, key: str, tuning: dict) -> None:
+    import json
+    entries = _cache_read(path)
+    entries[key] = {k: tuning[k] for k in ("pcg_launch", "pcg_form", "phase_blocks", "solve_ms")}
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump({"format": "fbs autotune cache 1", "entries": entries}, f, indent=1,
+                  sort_keys=True)
+    os.replace(tmp, path)
+
+
 def autotune(grid: Grid, t: List, c: List, lam, pcg_iters: int = 25, x: Optional[List] = None,
-             y: Optional[List] = None, stream=None) -> dict:
+             y: Optional[List] = None, stream=None, cache: Optional[str] = None,
+             single_solve: bool = False) -> dict:
     """fbs_autotune: times the PCG launch configurations on this problem, leaves
     the fastest set on the grid and returns it (the outputs hold its result).
     The same settings can be applied to another grid of the same shape with
-    ``apply_tuning``."""
+    ``apply_tuning``.
+
+    cache: a JSON file of earlier choices keyed by ``tuning_key`` (GPU name
+    and shape class).  On a hit the stored choice is set on the grid and one
+    solve fills the outputs, with no timing ("cached": True in the result);
+    on a miss the problem is tuned and the choice stored.
+
+    single_solve: time each configuration as the first solve on a grid
+    (OPT_TUNE_SINGLE_SOLVE), for callers that build a new grid per solve;
+    otherwise repeated solves on the grid (graph replay) are timed."""
+    key = None
+    if cache is not None:
+        key = tuning_key(grid, t) + ("|single-solve" if single_solve else "|repeated")
+    if cache is not None:
+        hit = _cache_read(cache).get(key)
+        if hit is not None:
+            apply_tuning(grid, hit)
+            solve(grid, t, c, lam, pcg_iters, x=x, y=y, stream=stream)
+            return dict(hit, candidates=0, cached=True, key=key)
     probs = _problems(grid, t, c, lam, x, y)
     r = _TuneResult()
+    set_option(grid, OPT_TUNE_SINGLE_SOLVE, 1 if single_solve else 0)
     _check(load().fbs_autotune(grid.handle, probs, int(pcg_iters), _stream_ptr(stream),
                                ctypes.byref(r)), "fbs_autotune")
-    return {"pcg_launch": r.pcg_launch, "pcg_form": r.pcg_form, "phase_blocks": r.phase_blocks,
-            "solve_ms": r.solve_ms, "candidates": r.candidates}
+    out = {"pcg_launch": r.pcg_launch, "pcg_form": r.pcg_form, "phase_blocks": r.phase_blocks,
+           "solve_ms": r.solve_ms, "candidates": r.candidates}
+    if cache is not None:
+        _cache_write(cache, key, out)
+        out.update(cached=False, key=key)
+    return out
 
 
 def apply_tuning(grid: Grid, tuning: dict) -> None:

@@ -451,3 +451,53 @@ def test_autotune_picks_a_configuration_and_keeps_parity():
     xs, ys = gpu_solve(g2, insts, 25)
     for k in range(2):
         assert np.array_equal(xs[k], x[k].cpu().numpy())
+
+
+def test_autotune_cache_reapplies_the_choice(tmp_path):
+    # the first grid is tuned and its choice stored under the GPU name and the
+    # shape class; a second grid of the same shape takes it from the cache
+    # without timing and solves to the same result, within the bar of the oracle
+    import torch
+    from paper_1511_03296_gb300 import fbs
+    insts = [_inst(61, 180, 240, (8.0, 4.0, 3.0), C=1, npoly=8),
+             _inst(62, 150, 200, (16.0, 8.0, 8.0), C=2, npoly=6)]
+    path = str(tmp_path / "tune.json")
+    runs = []
+    for _ in range(2):
+        g = gpu_grid(insts, 2)
+        t = [to_dev(i.t) for i in insts]
+        c = [to_dev(i.c) for i in insts]
+        x = [torch.empty_like(tt) for tt in t]
+        r = fbs.autotune(g, t, c, [i.lam for i in insts], 25, x=x, cache=path)
+        fbs.grid_sync(g)
+        runs.append((r, [xx.cpu().numpy() for xx in x]))
+    (r1, x1), (r2, x2) = runs
+    assert r1["cached"] is False and r2["cached"] is True and r1["key"] == r2["key"]
+    assert {k: r1[k] for k in ("pcg_launch", "pcg_form", "phase_blocks")} == \
+        {k: r2[k] for k in ("pcg_launch", "pcg_form", "phase_blocks")}
+    for k, inst in enumerate(insts):
+        assert np.array_equal(x1[k], x2[k])
+        og = oracle_grid(inst, 2)
+        form = "single" if r2["pcg_form"] == fbs.PCG_FORM_SINGLE else "standard"
+        with oracle.pcg_form(form):
+            _, ox = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
+        assert rel_l2(x2[k].reshape(inst.channels, -1), ox) <= REL_L2_TOL
+
+
+def test_autotune_single_solve_keeps_parity():
+    # timing first solves on the grid (graphs dropped before each) picks a
+    # valid configuration, and the solve it leaves behind keeps parity
+    import torch
+    from paper_1511_03296_gb300 import fbs
+    inst = _inst(63, 240, 320, (16.0, 8.0, 8.0), C=3, npoly=10)
+    g = gpu_grid([inst], 2)
+    t, c = to_dev(inst.t), to_dev(inst.c)
+    x = torch.empty_like(t)
+    r = fbs.autotune(g, [t], [c], inst.lam, 25, x=[x], single_solve=True)
+    fbs.grid_sync(g)
+    assert r["pcg_launch"] in (fbs.PCG_PER_PHASE, fbs.PCG_PERSISTENT)
+    og = oracle_grid(inst, 2)
+    form = "single" if r["pcg_form"] == fbs.PCG_FORM_SINGLE else "standard"
+    with oracle.pcg_form(form):
+        _, ox = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
+    assert rel_l2(x.cpu().numpy().reshape(3, -1), ox) <= REL_L2_TOL
