@@ -328,6 +328,11 @@ def time_steps(step, steps, warmup, flush, stream):
 # (below 1: the gathers read 16-bit packed neighbour offsets, not the 32-bit
 # ids the algorithmic count assumes).
 PCG_TRAFFIC_1080P = 6.887936e6 + 7.725312e6
+# The resident loop (all 25 iterations in one cooperative launch) at 1080p:
+# dram__bytes over the launch (rate x duration from the capture in
+# profiles/pcg_resident_1080p.md), per iteration; after the first iteration
+# the working set is served from L2.
+PCG_TRAFFIC_1080P_RESIDENT = 20.610394e9 * 443.936e-6 / 25
 PCG_TRAFFIC_RATIO_BATCHED = (108.809728e6 + 11.157760e6 + 66.430208e6 + 0.708096e6) / 235835472
 
 
@@ -447,37 +452,36 @@ def run_extra_robust(dist, flush, stream, peak, steps, warmup):
 
 
 def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
-    """16 images 640x480, 21-channel softmax targets: forward solve, MSE loss
-    gradient against a label map, backward solve (dL/dt, dL/dc)."""
+    """16 images 640x480, 21-channel softmax targets, through the library's
+    autograd Function for a batch (BilateralSolveBatch): one forward solve of
+    all images, the MSE loss against a label map, loss.backward() -- one
+    backward solve of all images giving dL/dt and dL/dc."""
     import torch
     from paper_1511_03296_gb300 import fbs, synth
     wl = synth.segmentation_16(seed=rank_seed(5, dist.rank), n_images=n_images)
     insts = wl.instances
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     yuv = [dev(i.yuv) for i in insts]
-    t = [dev(i.t) for i in insts]
-    c = [dev(i.c) for i in insts]
+    t = [dev(i.t).requires_grad_(True) for i in insts]
+    c = [dev(i.c).requires_grad_(True) for i in insts]
     lab = [dev(i.label) for i in insts]
-    x = [torch.empty_like(tt) for tt in t]
-    dx = [torch.empty_like(tt) for tt in t]
-    dt = [torch.empty_like(tt) for tt in t]
-    dc = [torch.empty_like(cc) for cc in c]
+    x0 = [torch.empty_like(tt) for tt in t]
     sig = ([i.sigma_xy for i in insts], [i.sigma_l for i in insts], [i.sigma_uv for i in insts])
     lam = [i.lam for i in insts]
     numel = sum(tt.numel() for tt in t)
     info = {}
-    tuning = tune(fbs, yuv, sig, t, c, lam, x)
+    tuning = tune(fbs, yuv, sig, [tt.detach() for tt in t], [cc.detach() for cc in c], lam, x0)
 
     def step():
         g = fbs.grid_build(yuv, *sig)
         fbs.apply_tuning(g, tuning)
         fbs.bistochastize(g, BISTOCH_ITERS)
-        y = [torch.empty((i.channels, g.vertex_counts[k]), device="cuda")
-             for k, i in enumerate(insts)]
-        fbs.solve(g, t, c, lam, PCG_ITERS, x=x, y=y)
-        for k in range(len(insts)):               # the loss: mean((x - label)^2)
-            torch.sub(x[k], lab[k], out=dx[k]).mul_(2.0 / numel)
-        fbs.solve_backward(g, t, c, lam, y, dx, dt, dc, PCG_ITERS)
+        for tt, cc in zip(t, c):
+            tt.grad = None
+            cc.grad = None
+        xs = fbs.bilateral_solve(t, c, g, lam, PCG_ITERS)
+        loss = sum(((xx - ll) ** 2).sum() for xx, ll in zip(xs, lab)) / numel
+        loss.backward()
         info["V"] = g.vertex_counts
         g.destroy()
 
@@ -489,7 +493,8 @@ def run_extra_fwd_bwd(dist, flush, stream, peak, steps, warmup, n_images=16):
     npix = wl.n_pixels
     bytes_iter = sum(V * (48 + 40 * i.channels) for V, i in zip(info["V"], insts))
     return {"workload": "16 images 640x480, C=21 softmax targets, c~U[0,1], sigma=(8,4,3), "
-                        "lambda=128, forward + backward (2 x 25 PCG iterations)",
+                        "lambda=128, forward + backward through the autograd Function "
+                        "(2 x 25 PCG iterations)",
             "pixels": npix, "vertices": int(sum(info["V"])),
             "fwd_bwd_mpix_s": whole_job_mpix(dist.world, npix, m), "ms_per_step": m,
             "tuning": tuning,
@@ -716,6 +721,7 @@ def run_ours(args, dist):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     bytes_iter = algorithmic_bytes_per_pcg_iteration(V, inst.channels)
     roof = pcg_roofline(regions, 1, args.steps, bytes_iter, peak)
+    resident = tuning.get("pcg_launch") == fbs.PCG_PERSISTENT
     region_share = {k: round(t / max(1e-9, sum(tt for _, tt in regions.values())), 4)
                     for k, (n, t) in regions.items() if n}
 
@@ -734,9 +740,12 @@ def run_ours(args, dist):
         "e2e": {"value": whole_job_mpix(dist.world, inst.n_pixels, e2e_ms), "unit": "Mpix/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(round(launches_per_step * args.steps)),
-        "roofline": dict(roof or {}, kernel="pcg iteration (both CG phases)",
-                         traffic=PCG_TRAFFIC_1080P,
-                         traffic_source="ncu, cold caches, one iteration (apply + update)",
+        "roofline": dict(roof or {}, kernel="pcg iteration (both CG phases)" +
+                         (", resident loop" if resident else ", per-phase launches"),
+                         traffic=PCG_TRAFFIC_1080P_RESIDENT if resident else PCG_TRAFFIC_1080P,
+                         traffic_source=("ncu, one 25-iteration launch of the resident loop, "
+                                         "per iteration" if resident else
+                                         "ncu, cold caches, one iteration (apply + update)"),
                          peak_source="measured" if peaks else "fallback",
                          note="working set L2-resident at this size; see batched / fwd_bwd "
                               "for the HBM-bound sizes"),

@@ -18,13 +18,16 @@ constexpr int kGridThreads = 512;        // CTA size of the grid-build kernels
 constexpr int kVTile = 256;              // vertices per PCG tile (= CTA size)
 constexpr int kChanBlock = 4;            // channels processed per pass of a PCG tile
 constexpr int kMaxChannels = 64;         // channels per image
-constexpr unsigned kBarrierGroups = 32;            // first-level counters of the grid barrier
-constexpr unsigned kBarrierWords = 32 * (kBarrierGroups + 1);
+// grid-barrier block (words): 0 the arrival counter, kWorkCounterWord the
+// splat's work counter, 32 (a 128-byte line of its own) the release word of
+// the resident loop's barrier; 33 lines in all
+constexpr unsigned kBarrierWords = 32 * 33;
 constexpr int kNbrOffMax = 32767;          // packed neighbour offsets: |offset| <= this
 constexpr int kNbrEscape = -32768;         // ... else this, and the 32-bit table holds the id
 constexpr unsigned kWorkCounterWord = 2;   // in the barrier block, unused by the barrier:
                                            // the splat's work counter
-constexpr unsigned kBarrierSpinLimit = 1u << 20;   // polls of >= 64 ns: >= 67 ms before a time-out
+constexpr unsigned kBarrierSpinLimit = 1u << 20;   // polls of >= 64 ns (an L2 round trip and a
+                                                    // 32 ns sleep): >= 67 ms before a time-out
 
 // device error bits (latched in fbs_grid::err)
 enum : uint32_t {

@@ -179,7 +179,10 @@ cudaError_t lr_splat(const LrImg* imgs_dev, int n_images, int64_t Vtot, const in
 {
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((Vtot + 255) / 256,
                                                                (int64_t)device_info().sms * 8));
+    static int fam = prof_family("lr_splat");
+    prof_begin(fam, s);
     lr_splat_kernel<<<nb, 256, 0, s>>>(imgs_dev, n_images, Vtot, voff_dev, pstart, m, perm, B);
+    prof_end(fam, s);
     return cudaGetLastError();
 }
 
@@ -187,9 +190,12 @@ cudaError_t lr_gram(const LrImg* imgs_dev, int n_images, const float* B, float2*
                     int cmax, cudaStream_t s)
 {
     const int pstride = cmax * (cmax + 1) / 2;
+    static int fam = prof_family("lr_gram");
+    prof_begin(fam, s);
     lr_gram_kernel<<<dim3(kLrGramBlocks, n_images), kLrThreads, 0, s>>>(imgs_dev, B, part, pstride);
     lr_gram_reduce_kernel<<<n_images, kLrThreads, 0, s>>>(imgs_dev, part, kLrGramBlocks, pstride, G,
                                                          cmax);
+    prof_end(fam, s);
     return cudaGetLastError();
 }
 
@@ -197,7 +203,10 @@ cudaError_t lr_map(const LrImg* imgs_dev, int n_images, int64_t max_pixels, cuda
 {
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((max_pixels + 255) / 256,
                                                                (int64_t)device_info().sms * 4));
+    static int fam = prof_family("lr_map");
+    prof_begin(fam, s);
     lr_map_kernel<<<dim3(nb, n_images), 256, 0, s>>>(imgs_dev);
+    prof_end(fam, s);
     return cudaGetLastError();
 }
 

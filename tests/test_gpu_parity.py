@@ -123,28 +123,26 @@ def test_batched_uneven_images(pcg_launch):
     _check_solve(insts)
 
 
-def test_batched_64_full_size_sampled():
+def test_batched_64_full_size():
     # the batched workload at full size (64 images, ~44 Mpx) in one grid and one
-    # solve; three seeded images are compared with the oracle in full, and every
-    # image satisfies properties that hold at any size
+    # solve; every image's grid is bit-exact and its y and x within the bar of
+    # the oracle
     from paper_1511_03296_gb300 import fbs
     insts = synth.batched_64().instances
     g = gpu_grid(insts, 2)
     xs, ys = gpu_solve(g, insts, 25)
+    worst = (0.0, -1)
     for k, inst in enumerate(insts):
         keys, vid, m, nbr, n = fbs.grid_export(g, k)
         assert int(m.sum()) == inst.n_pixels                  # S S^T = D_m: sum m = N
-        assert np.all(np.diff(keys.astype(np.int64)) > 0)      # canonical ascending keys
         assert np.isfinite(xs[k]).all() and np.isfinite(ys[k]).all()
-    rng = np.random.default_rng(4)
-    for k in sorted(rng.choice(len(insts), 3, replace=False)):
-        inst = insts[k]
         og = oracle_grid(inst, 2)
         assert_grid_bit_exact(g, k, og)
         oy, ox = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
         ey, ex = rel_l2(ys[k], oy), rel_l2(xs[k].reshape(inst.channels, -1), ox)
-        print(f"batched image {k} ({inst.width}x{inst.height}, C={inst.channels}) rel-L2", ey, ex)
-        assert ey <= REL_L2_TOL and ex <= REL_L2_TOL
+        assert ey <= REL_L2_TOL and ex <= REL_L2_TOL, (k, ey, ex)
+        worst = max(worst, (max(ey, ex), k))
+    print("batched 64 images: largest rel-L2 (y or x) %.2e on image %d" % worst)
 
 
 def test_full_1080p_parity(pcg_launch):
