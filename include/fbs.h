@@ -193,6 +193,11 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *                            (the FP32 A d of the first phase only enters
  *                            d^T q, i.e. the step length).  Same vector bytes
  *                            per channel, one more neighbour-table pass per
+ *                            iteration.  In
+ *                            fbs_solve_robust y and the diagonal remainder of
+ *                            A are double-float pairs too (the IRLS loop
+ *                            amplifies their float32 rounding): 4 more bytes
+ *                            per vertex and 8 per vertex and channel moved per
  *                            iteration.
  *   FBS_VECTORS_AUTO         (default) compensated for fbs_solve_backward,
  *                            FP32 for fbs_solve and fbs_solve_robust.

@@ -287,6 +287,7 @@ struct fbs_grid {
     int pyr_lv_nc = 0;                  // level-vector values per vertex pyr_lv holds
     int inject_timeout = 0;
     float* a = nullptr;
+    float* alo = nullptr;      // low part of a' (robust solver, compensated precision)
     float2* nm = nullptr;
     size_t cap_scal = 0, cap_part = 0;
     Scal* scal = nullptr;
@@ -325,7 +326,8 @@ void free_grid_memory(fbs_grid* g, cudaStream_t s)
     dfree(g->m, s); dfree(g->nbr, s); dfree(g->nbrp, s); dfree(g->n64, s); dfree(g->n64b, s); dfree(g->nf, s);
     dfree(g->cell_voff, s); dfree(g->cell_nv, s); dfree(g->err, s); dfree(g->vt, s);
     dfree(g->gt, s); dfree(g->gt_voff, s);
-    dfree(g->vec, s); dfree(g->a, s); dfree(g->nm, s); dfree(g->scal, s); dfree(g->part, s);
+    dfree(g->vec, s); dfree(g->a, s); dfree(g->alo, s); dfree(g->nm, s); dfree(g->scal, s);
+    dfree(g->part, s);
     dfree(g->inst, s); dfree(g->barrier, s);
     dfree(g->pyr_parent, s); dfree(g->pyr_child_off, s); dfree(g->pyr_child_idx, s);
     dfree(g->pyr_vimg, s); dfree(g->pyr_ioff, s); dfree(g->pyr_kimg, s); dfree(g->pyr_key, s);
@@ -894,6 +896,9 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     if (g->precision == FBS_VECTORS_FP32) plan.comp = 0;
     else if (g->precision == FBS_VECTORS_COMPENSATED) plan.comp = 1;
     else plan.comp = plan.mode == kSplatBackward ? 1 : 0;
+    // the robust solver in compensated precision also keeps y and a' as
+    // double-float pairs: its IRLS loop amplifies their float32 rounding
+    plan.dfy = plan.comp && plan.mode == kSplatRobust ? 1 : 0;
     // the whole PCG loop as one cooperative launch, except inside a caller's
     // stream capture (per-phase launches are captured instead)
     // the single-reduction form for FP32 vectors and images of at most 4
@@ -958,6 +963,12 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.q = g->vec + 5 * g->cap_vec;
     A.aux[0] = g->vec + 6 * g->cap_vec;
     A.aux[1] = g->vec + 7 * g->cap_vec;
+    if (plan.dfy && !g->alo) {
+        if (cap) return FBS_ERR_STATE;
+        if ((e = dalloc(&g->alo, g->Vtot, s)) != cudaSuccess) return cuda_status(e);
+    }
+    A.alo = plan.dfy ? g->alo : nullptr;
+    A.ylo = plan.dfy ? A.aux[1] : nullptr;
     A.scal = g->scal;
     A.nscal = pc;
     plan.barrier = g->barrier;

@@ -361,7 +361,13 @@ __device__ __forceinline__ void vertex_epilogue(const SolveArgs& A, const InstDe
     const double lam = (double)I.lam;
     const double rem = has_nbr ? lam * ((double)cnt - nv * (10.0 * nv + sum_n)) : 0.0;
     const double diag = has_nbr ? lam * ((double)cnt - 10.0 * nv * nv) + scd : scd;
-    A.a[v] = (float)(rem + scd);
+    if (A.alo) {                        // a' as a double-float pair
+        const DF ap = df_from_double(rem + scd);
+        A.a[v] = ap.hi;
+        A.alo[v] = ap.lo;
+    } else {
+        A.a[v] = (float)(rem + scd);
+    }
     A.nm[v] = make_float2((float)nv, diag > 0.0 ? (float)(1.0 / diag) : 0.0f);
     if (A.pyr.K > 0) {                  // hierarchical preconditioner: diag(A) and S c
         A.pyr.dg[v] = (float)diag;
@@ -371,12 +377,13 @@ __device__ __forceinline__ void vertex_epilogue(const SolveArgs& A, const InstDe
 
 // Splat weight and value of one pixel (index i within its image) for channel
 // ch: robust weights are Geman-McClure of the residual against the vertex's
-// current solution yv.
+// current solution yv (+ ylo, its low part when y is a double-float pair:
+// yv - t is exact when they are close, so the residual keeps y's accuracy).
 __device__ __forceinline__ float splat_weight(const InstDev& I, int mode, int64_t i, float yv,
-                                              float s2)
+                                              float ylo, float s2)
 {
     if (mode == kSplatRobust) {
-        const float e = yv - I.t[i];
+        const float e = (yv - I.t[i]) + ylo;
         const float den = s2 + e * e;
         return (2.0f * s2) / (den * den);
     }
@@ -414,6 +421,7 @@ __device__ __forceinline__ void splat_store(const SolveArgs& A, const InstDev& I
                 A.r[idx] = b;
             }
             A.y[idx] = scf > 0.0f ? b / scf : 0.0f;
+            if (A.ylo) A.ylo[idx] = 0.0f;
         }
     }
 }
@@ -452,8 +460,12 @@ __device__ __forceinline__ void splat_unit(const SolveArgs& A, const InstDev& I,
     const uint32_t p0 = valid ? A.pstart[v] : 0u, cnt = valid ? A.m[v] : 0u;
     const bool big = cnt > kSplatWarpMin;
     const uint32_t own = big ? 0u : cnt;
-    float yv = 0.0f;
-    if (mode == kSplatRobust && valid) yv = A.y[vec_index(I, 0, v)];
+    // robust weights: the robust solver has one channel (CB = 1)
+    float yv = 0.0f, ylv = 0.0f;
+    if (mode == kSplatRobust && valid) {
+        yv = A.y[vec_index(I, 0, v)];
+        if (CB == 1 && A.ylo) ylv = A.ylo[vec_index(I, 0, v)];
+    }
     DF sc = {0.0f, 0.0f};
     bool bad = false;
     for (int cb = 0; cb < I.C; cb += CB) {
@@ -469,7 +481,7 @@ __device__ __forceinline__ void splat_unit(const SolveArgs& A, const InstDev& I,
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int64_t i = ii[u] >= 0 ? ii[u] : 0;
-                wv[u] = splat_weight(I, mode, i, yv, s2);
+                wv[u] = splat_weight(I, mode, i, yv, ylv, s2);
 #pragma unroll
                 for (int k = 0; k < CB; ++k)
                     val[k][u] = splat_value(I, mode, min(cb + k, I.C - 1), i);
@@ -500,6 +512,7 @@ __device__ __forceinline__ void splat_unit(const SolveArgs& A, const InstDev& I,
             const uint32_t q0 = __shfl_sync(FULL, p0, owner);
             const uint32_t qn = __shfl_sync(FULL, cnt, owner);
             const float qy = __shfl_sync(FULL, yv, owner);
+            const float qyl = CB == 1 ? __shfl_sync(FULL, ylv, owner) : 0.0f;
             DF wacc[CB], wsc = {0.0f, 0.0f};
 #pragma unroll
             for (int k = 0; k < CB; ++k) wacc[k] = {0.0f, 0.0f};
@@ -515,7 +528,7 @@ __device__ __forceinline__ void splat_unit(const SolveArgs& A, const InstDev& I,
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int64_t i = ii[u] >= 0 ? ii[u] : 0;
-                    wv[u] = splat_weight(I, mode, i, qy, s2);
+                    wv[u] = splat_weight(I, mode, i, qy, qyl, s2);
 #pragma unroll
                     for (int k = 0; k < CB; ++k)
                         val[k][u] = splat_value(I, mode, min(cb + k, I.C - 1), i);
@@ -621,9 +634,11 @@ __device__ __forceinline__ void lap_acc(DF (&s)[W], float nu, const float (&zv)[
 
 // (A z)_v = a'_v z_v + lambda n_v s
 template <bool COMP>
-__device__ __forceinline__ DF lap_finish(float av, float lam_n, float zv, DF s)
+__device__ __forceinline__ DF lap_finish(float av, float lam_n, float zv, DF s, float alv = 0.0f)
 {
-    return COMP ? df_add(df_mul_exact(av, zv), df_mul_f(df_two_sum(s.hi, s.lo), lam_n))
+    // COMP: a' z exactly (plus alv z when a' is a double-float pair a' = av + alv)
+    return COMP ? df_add(df_add_f(df_mul_exact(av, zv), alv * zv),
+                         df_mul_f(df_two_sum(s.hi, s.lo), lam_n))
                 : DF{fmaf(av, zv, lam_n * s.hi), 0.0f};
 }
 
@@ -639,6 +654,7 @@ __device__ __forceinline__ void residual_tile(const SolveArgs& A, const InstDev&
     const int64_t vs = valid ? v : vt.v0;
     const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
     const float av = valid ? A.a[v] : 0.0f;
+    const float alv = COMP && A.alo && valid ? A.alo[v] : 0.0f;
     const float lam_n = I.lam * nmv.x;
     int32_t nb[10];
 #pragma unroll
@@ -665,7 +681,7 @@ __device__ __forceinline__ void residual_tile(const SolveArgs& A, const InstDev&
         DF acc[W];
 #pragma unroll
         for (int k = 0; k < W; ++k) {
-            const DF Ay = lap_finish<COMP>(av, lam_n, yv[k], s[k]);
+            const DF Ay = lap_finish<COMP>(av, lam_n, yv[k], s[k], alv);
             if (COMP) {
                 const DF r = df_add(DF{rv[k], rl[k]}, df_neg(Ay));
                 rv[k] = r.hi;
@@ -792,11 +808,16 @@ __device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I
     ldw<W, CO>(A.r + off + vs * W, rv);
     if (COMP) ldw<W, CO>(A.rlo + off + vs * W, rl);
     else ldw<W, CO>(A.q + off + vs * W, qv);
+    // COMP with a double-float y (A.ylo): y's low part, updated exactly
+    const bool ydf = COMP && A.ylo != nullptr;
+    float yl[W];
+    if (ydf) ldw<W, CO>(A.ylo + off + vs * W, yl);
     if (fetch) phase_scalars<2, CO, W>(A, I, in, it, S);
     DF sacc[W];
-    float av = 0.0f;
+    float av = 0.0f, alv = 0.0f;
     if (COMP) {
         av = valid ? A.a[v] : 0.0f;
+        alv = A.alo && valid ? A.alo[v] : 0.0f;
 #pragma unroll
         for (int k = 0; k < W; ++k) sacc[k] = {0.0f, 0.0f};
         int nb[10];
@@ -814,9 +835,15 @@ __device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I
 #pragma unroll
     for (int k = 0; k < W; ++k) {
         const double alpha = S.sa[k];
-        yv[k] = fmaf((float)alpha, dv[k], yv[k]);
+        if (ydf) {
+            const DF yy = df_add(DF{yv[k], yl[k]}, df_mul_f(df_from_double(alpha), dv[k]));
+            yv[k] = yy.hi;
+            yl[k] = yy.lo;
+        } else {
+            yv[k] = fmaf((float)alpha, dv[k], yv[k]);
+        }
         if (COMP) {
-            const DF q = lap_finish<true>(av, lam_n, dv[k], sacc[k]);
+            const DF q = lap_finish<true>(av, lam_n, dv[k], sacc[k], alv);
             const DF r = df_add(DF{rv[k], rl[k]}, df_neg(df_mul(df_from_double(alpha), q)));
             rv[k] = r.hi;
             rl[k] = r.lo;
@@ -829,6 +856,7 @@ __device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I
         stw<W>(A.y + off + v * W, yv);
         stw<W>(A.r + off + v * W, rv);
         if (COMP) stw<W>(A.rlo + off + v * W, rl);
+        if (ydf) stw<W>(A.ylo + off + v * W, yl);
     }
 }
 
@@ -983,14 +1011,17 @@ __device__ __forceinline__ void update_wide(const SolveArgs& A, const InstDev& I
         const bool valid = lv < nvc && c0 + lv < nverts;
         const int vs = valid ? v : (int)vt.v0;
         const float2 nmv = valid ? A.nm[v] : make_float2(0.0f, 0.0f);
-        float dv[4], yv[4], rv[4], rl[4], qv[4];
+        float dv[4], yv[4], rv[4], rl[4], qv[4], yl[4];
         ldw<4, CO>(d + base + vs * Cp, dv);
         ldw<4, CO>(A.y + base + vs * Cp, yv);
         ldw<4, CO>(A.r + base + vs * Cp, rv);
+        const bool ydf = COMP && A.ylo != nullptr;     // y as a double-float pair
+        if (ydf) ldw<4, CO>(A.ylo + base + vs * Cp, yl);
         DF sacc[4];
-        float av = 0.0f, lam_n = 0.0f;
+        float av = 0.0f, lam_n = 0.0f, alv = 0.0f;
         if (COMP) {
             av = valid ? A.a[v] : 0.0f;
+            alv = A.alo && valid ? A.alo[v] : 0.0f;
             lam_n = I.lam * nmv.x;
             ldw<4, CO>(A.rlo + base + vs * Cp, rl);
 #pragma unroll
@@ -1010,9 +1041,15 @@ __device__ __forceinline__ void update_wide(const SolveArgs& A, const InstDev& I
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            yv[k] = fmaf((float)alpha[k], dv[k], yv[k]);
+            if (ydf) {
+                const DF yy = df_add(DF{yv[k], yl[k]}, df_mul_f(df_from_double(alpha[k]), dv[k]));
+                yv[k] = yy.hi;
+                yl[k] = yy.lo;
+            } else {
+                yv[k] = fmaf((float)alpha[k], dv[k], yv[k]);
+            }
             if (COMP) {
-                const DF q = lap_finish<true>(av, lam_n, dv[k], sacc[k]);
+                const DF q = lap_finish<true>(av, lam_n, dv[k], sacc[k], alv);
                 const DF r = df_add(DF{rv[k], rl[k]}, df_neg(df_mul(df_from_double(alpha[k]), q)));
                 rv[k] = r.hi;
                 rl[k] = r.lo;
@@ -1025,6 +1062,7 @@ __device__ __forceinline__ void update_wide(const SolveArgs& A, const InstDev& I
             stw<4>(A.y + base + v * Cp, yv);
             stw<4>(A.r + base + v * Cp, rv);
             if (COMP) stw<4>(A.rlo + base + v * Cp, rl);
+            if (ydf) stw<4>(A.ylo + base + v * Cp, yl);
         }
     }
 }
@@ -2072,11 +2110,14 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
     const float lam_n = I.lam * nmv.x;
     const int64_t vs = valid ? v : vt.v0;   // safe gather index for absent neighbours
     const int64_t base = pass_base(I, 0);
-    // own state in registers
-    float r[W], rlo[W], y[W], d[W], q[W];
+    // own state in registers (y's low part too when y is a double-float pair)
+    const bool ydf = COMP && A.ylo != nullptr;
+    const float alv = COMP && A.alo && valid ? A.alo[v] : 0.0f;
+    float r[W], rlo[W], y[W], yl[W], d[W], q[W];
     ldw<W, false>(A.r + base + vs * I.Cp, r);
     ldw<W, false>(A.y + base + vs * I.Cp, y);
     if (COMP) ldw<W, false>(A.rlo + base + vs * I.Cp, rlo);
+    if (ydf) ldw<W, false>(A.ylo + base + vs * I.Cp, yl);
 #pragma unroll
     for (int k = 0; k < W; ++k) {
         d[k] = 0.0f;
@@ -2171,9 +2212,15 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
 #pragma unroll
             for (int k = 0; k < W; ++k) {
                 const double alpha = S.sa[k];
-                y[k] = fmaf((float)alpha, d[k], y[k]);
+                if (ydf) {
+                    const DF yy = df_add(DF{y[k], yl[k]}, df_mul_f(df_from_double(alpha), d[k]));
+                    y[k] = yy.hi;
+                    yl[k] = yy.lo;
+                } else {
+                    y[k] = fmaf((float)alpha, d[k], y[k]);
+                }
                 if (COMP) {
-                    const DF qq = lap_finish<true>(av, lam_n, d[k], s[k]);
+                    const DF qq = lap_finish<true>(av, lam_n, d[k], s[k], alv);
                     const DF rr = df_add(DF{r[k], rlo[k]},
                                          df_neg(df_mul(df_from_double(alpha), qq)));
                     r[k] = rr.hi;
@@ -2193,6 +2240,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
     if (valid) {
         stw<W>(A.y + base + v * I.Cp, y);
         if (COMP) stw<W>(A.rlo + base + v * I.Cp, rlo);
+        if (ydf) stw<W>(A.ylo + base + v * I.Cp, yl);
     }
 }
 
@@ -2225,7 +2273,9 @@ slice_kernel(SolveArgs A)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < I.N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t v = A.vid[I.pix_base + i];
-        for (int ch = 0; ch < I.C; ++ch) I.x[(int64_t)ch * I.N + i] = A.y[vec_index(I, ch, v)];
+        for (int ch = 0; ch < I.C; ++ch)
+            I.x[(int64_t)ch * I.N + i] =
+                A.y[vec_index(I, ch, v)] + (A.ylo ? A.ylo[vec_index(I, ch, v)] : 0.0f);
     }
 }
 
@@ -2242,7 +2292,7 @@ backward_slice_kernel(SolveArgs A)
         const float ci = I.c[i];
         float dc = 0.0f;
         for (int ch = 0; ch < I.C; ++ch) {
-            const float z = A.y[vec_index(I, ch, v)];
+            const float z = A.y[vec_index(I, ch, v)] + (A.ylo ? A.ylo[vec_index(I, ch, v)] : 0.0f);
             if (I.dt) I.dt[(int64_t)ch * I.N + i] = ci * z;
             const float yh = I.yhat[(int64_t)ch * I.V + (v - I.voff)];
             dc = fmaf(z, I.t[(int64_t)ch * I.N + i] - yh, dc);
@@ -2262,7 +2312,7 @@ export_y_kernel(SolveArgs A)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t ch = i / I.V, j = i - ch * I.V;
-        dst[i] = A.y[I.vec_base + j * I.Cp + ch];
+        dst[i] = A.y[I.vec_base + j * I.Cp + ch] + (A.ylo ? A.ylo[I.vec_base + j * I.Cp + ch] : 0.0f);
     }
 }
 

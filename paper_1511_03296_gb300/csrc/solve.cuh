@@ -52,6 +52,7 @@ struct SolveArgs {
     const uint32_t* vid;       // global pixel -> global vertex
     // per-vertex problem data
     float* a;                  // a' = lambda (m - n o Bbar n) + S c (Laplacian-form remainder)
+    float* alo;                // low part of a' as a double-float pair, or nullptr
     float2* nm;                // {n, M^-1}
     // vectors, all sum_k C_k V_k floats
     float* y;
@@ -60,6 +61,8 @@ struct SolveArgs {
     float* d[2];
     float* q;
     float* aux[2];             // single-reduction form: s = A p by iteration parity
+    float* ylo;                // low part of y as a double-float pair (aux[1]), or nullptr:
+                               //   the robust solver in compensated precision
     // reductions
     Scal* scal;                // sum_k C_k
     int nscal;                 // entries of scal
@@ -93,6 +96,8 @@ struct SolvePlan {
     int single;                // 1: single-reduction PCG form (FP32, Cp <= 4, per-phase)
     int block_mult;            // per-phase kernels: blocks = min(tiles, SMs x occupancy x this)
     int hier;                  // 1: hierarchical preconditioner and initialisation (per-phase)
+    int dfy;                   // 1: y and a' held as double-float pairs too (robust solver,
+                               //    compensated precision)
 };
 
 // A solve runs as segments: for each outer (IRLS) iteration a setup (splat,
