@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -184,6 +185,69 @@ __global__ void upload_kernel(unsigned char* dst, Chunk c, int n)
 {
     for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = c.b[i];
 }
+// Host-to-device copies of host-built tables (image descriptors, sort
+// tiles, vertex tiles) through a pinned staging ring: a copy from pageable
+// memory first waits for all earlier work on the stream, which would leave
+// the GPU idle between a caller's steps while the host prepares the next
+// grid.  A region of the ring is reused only after the copy that last read
+// it has completed (one event per copy).  Falls back to a plain copy inside
+// a stream capture (the ring's contents would be read at replay time) and
+// for copies larger than half the ring.
+cudaError_t pinned_upload(void* dst, const void* src, size_t bytes, cudaStream_t s)
+{
+    struct Use {
+        size_t lo, hi;
+        cudaEvent_t ev;
+    };
+    static std::mutex mu;
+    static unsigned char* ring = nullptr;
+    static size_t cap = 0, head = 0;
+    static std::deque<Use> inflight;
+    if (bytes == 0) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ring && cap == 0) {
+        cap = (size_t)16 << 20;
+        if (cudaMallocHost(&ring, cap) != cudaSuccess) {
+            cudaGetLastError();
+            ring = nullptr;
+            cap = 1;                                // do not try again
+        }
+    }
+    if (!ring || bytes > cap / 2 || capturing(s))
+        return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+    size_t lo = (head + 255) & ~(size_t)255;
+    if (lo + bytes > cap) lo = 0;
+    const size_t hi = lo + bytes;
+    cudaError_t e = cudaSuccess;
+    for (auto it = inflight.begin(); it != inflight.end();) {
+        const bool overlaps = it->lo < hi && lo < it->hi;
+        if (overlaps) {
+            e = cudaEventSynchronize(it->ev);
+            if (e != cudaSuccess) return e;
+        }
+        if (overlaps || cudaEventQuery(it->ev) == cudaSuccess) {
+            cudaEventDestroy(it->ev);
+            it = inflight.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    cudaGetLastError();                             // cudaEventQuery's cudaErrorNotReady
+    memcpy(ring + lo, src, bytes);
+    if ((e = cudaMemcpyAsync(dst, ring + lo, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ev, s)) != cudaSuccess) {
+        cudaEventSynchronize(ev);
+        cudaEventDestroy(ev);
+        return e;
+    }
+    inflight.push_back(Use{lo, hi, ev});
+    head = hi;
+    return cudaSuccess;
+}
+
 cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t s)
 {
     static int fam = prof_family("upload");
@@ -484,9 +548,8 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
     FBS_TRY(dalloc(&g->cell_voff, cells, s));
     FBS_TRY(dalloc(&g->cell_nv, cells, s));
     FBS_TRY(cudaMemsetAsync(g->err, 0, sizeof(uint32_t), s));
-    FBS_TRY(cudaMemcpyAsync(d_img, img.data(), img.size() * sizeof(ImgDev), cudaMemcpyHostToDevice, s));
-    FBS_TRY(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(GTile),
-                            cudaMemcpyHostToDevice, s));
+    FBS_TRY(pinned_upload(d_img, img.data(), img.size() * sizeof(ImgDev), s));
+    FBS_TRY(pinned_upload(d_tiles, tiles.data(), tiles.size() * sizeof(GTile), s));
     FBS_TRY(launch_grid_sort(d_tiles, ntiles, d_img, d_tile_nv, g->err, P2, max_cells, g->vid,
                              g->perm, d_tkey, d_tm, d_tps, g->cell_voff, g->cell_nv, s));
     FBS_TRY(launch_scan_tiles(d_tile_nv, d_tile_voff, ntiles, s));
@@ -543,8 +606,7 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
         }
         g->nvt = (int)vt.size();
         FBS_TRY(dalloc(&g->vt, vt.size(), s));
-        FBS_TRY(cudaMemcpyAsync(g->vt, vt.data(), vt.size() * sizeof(VTile),
-                                cudaMemcpyHostToDevice, s));
+        FBS_TRY(pinned_upload(g->vt, vt.data(), vt.size() * sizeof(VTile), s));
     }
     dfree(d_img, s);
     dfree(d_tile_nv, s);
