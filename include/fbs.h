@@ -217,16 +217,17 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *   FBS_PCG_PER_PHASE        two launches per iteration (replayed from a CUDA
  *                            graph when the same solve repeats).
  * FBS_OPT_PCG_FORM: which form of the Jacobi PCG (supplement Alg. 2) runs:
- *   FBS_PCG_FORM_STANDARD    (default) Alg. 2 as printed: two phases, two
- *                            global reductions per iteration.
+ *   FBS_PCG_FORM_STANDARD    (default) Alg. 2: two phases, two global
+ *                            reductions per iteration.
  *   FBS_PCG_FORM_SINGLE      the single-reduction (Chronopoulos-Gear) form,
  *                            with the same iterates in exact arithmetic: u =
  *                            M^-1 r, w = A u and s = A p are carried along and
  *                            both inner products of an iteration are taken
- *                            together, so an iteration is one launch.  Used
- *                            for FP32 vectors when no image has more than 4
- *                            channels (per-phase launches); other solves keep
- *                            the standard form.
+ *                            together, so an iteration is one launch, or,
+ *                            with the persistent style where every tile has a
+ *                            co-resident block, one grid barrier.  Used for
+ *                            FP32 vectors when no image has more than 4
+ *                            channels; other solves keep the standard form.
  * FBS_OPT_PRECONDITIONER: the preconditioner and initial state (Sec. 4):
  *   FBS_PRECOND_JACOBI        (default) M^-1 = diag(A)^-1 and the flat
  *                             initialisation y0 = S(c o t) / S c.
@@ -270,7 +271,8 @@ fbs_status fbs_set_option(fbs_grid* g, int option, int value);
  *
  * Runs fbs_solve(g, probs, pcg_iters) under each candidate -- launch style
  * (per-phase launches, or the persistent loop where its cooperative launch
- * fits), PCG form (standard or single-reduction) and the per-phase block
+ * fits; with the single-reduction form, the resident loop of that form),
+ * PCG form (standard or single-reduction) and the per-phase block
  * count (FBS_OPT_PHASE_BLOCKS 1, 2, 4) -- each warmed up twice (so graph
  * replay is what gets timed; with FBS_OPT_TUNE_SINGLE_SOLVE set, the graphs
  * are dropped before each solve instead) and timed over three solves with

@@ -969,7 +969,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     // hierarchical preconditioner: any channel count
     plan.hier = g->precond == FBS_PRECOND_HIERARCHICAL ? 1 : 0;
     if (plan.hier) plan.single = 0;
-    plan.persistent = g->persistent && !capturing(s) && !plan.single && !plan.hier ? 1 : 0;
+    plan.persistent = g->persistent && !capturing(s) && !plan.hier ? 1 : 0;
     plan.block_mult = g->phase_blocks;
     plan.force_persistent = g->force_persistent;
     plan.inject_timeout = plan.persistent ? g->inject_timeout : 0;
@@ -1464,7 +1464,8 @@ fbs_status fbs_autotune(fbs_grid* g, const fbs_problem_desc* probs, int pcg_iter
                           {FBS_PCG_PER_PHASE, FBS_PCG_FORM_STANDARD, 4},
                           {FBS_PCG_PER_PHASE, FBS_PCG_FORM_SINGLE, 1},
                           {FBS_PCG_PER_PHASE, FBS_PCG_FORM_SINGLE, 2},
-                          {FBS_PCG_PERSISTENT, FBS_PCG_FORM_STANDARD, 1}};
+                          {FBS_PCG_PERSISTENT, FBS_PCG_FORM_STANDARD, 1},
+                          {FBS_PCG_PERSISTENT, FBS_PCG_FORM_SINGLE, 1}};
     const int n = (int)(sizeof(cands) / sizeof(cands[0]));
     const int saved_persistent = g->persistent, saved_force = g->force_persistent,
               saved_form = g->pcg_form, saved_blocks = g->phase_blocks;

@@ -2004,6 +2004,76 @@ __device__ void finalise_all(const SolveArgs& A, const InstDev& own, const float
     }
 }
 
+// The single-reduction form's scalars of iteration `it` from gamma_it and
+// mu_it (cg_scalars' rules, with gamma and alpha of iteration it - 1 from
+// sc), stored for the next pass: beta and alpha to be read, gamma_it and
+// alpha_it by parity.
+__device__ __forceinline__ void single_scalars(Scal* sc, int it, double gamma, double mu)
+{
+    const int slot = it & 1;
+    double beta = 0.0, den = mu;
+    bool stalled = gamma == 0.0;
+    if (it > 0) {
+        const double gold = __ldcg(&sc->gam[slot ^ 1]);
+        const double aold = __ldcg(&sc->alp[slot ^ 1]);
+        stalled = cg_stalled(gamma, __ldcg(&sc->delta0));
+        beta = gold != 0.0 && !stalled ? gamma / gold : 0.0;
+        if (beta != 0.0 && aold != 0.0) den = mu - beta * gamma / aold;
+    } else {
+        sc->delta0 = gamma;
+    }
+    const double alpha = (!stalled && den > 0.0) ? gamma / den : 0.0;
+    sc->gam[slot] = gamma;
+    sc->alp[slot] = alpha;
+    sc->beta = (float)beta;
+    sc->alpha = alpha;
+}
+
+// finalise_all for the single-reduction form: the partials of gamma_it
+// (part_rs[it & 1]) and of mu_it (part_mu[it & 1]) of every (image, channel),
+// in the order of reduce_partials_all, then single_scalars.  Whole block.
+__device__ void finalise_single(const SolveArgs& A, const InstDev& own, int it, PhaseSmem& S)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float2* __restrict__ pg = A.part_rs[it & 1];
+    const float2* __restrict__ pm = A.part_mu[it & 1];
+    for (int k = 0; k < A.ninst; ++k) {
+        const InstDev I = A.ninst == 1 ? own : A.inst[k];
+        if (I.ntiles <= 32) continue;
+        if (I.Cp == 1) {
+            reduce_partials_all<1, 8>(pg, I, S.sd, S.red);
+            reduce_partials_all<1, 8>(pm, I, S.sd2, S.red);
+        } else if (I.Cp == 2) {
+            reduce_partials_all<2, 4>(pg, I, S.sd, S.red);
+            reduce_partials_all<2, 4>(pm, I, S.sd2, S.red);
+        } else {
+            reduce_partials_all<4, 2>(pg, I, S.sd, S.red);
+            reduce_partials_all<4, 2>(pm, I, S.sd2, S.red);
+        }
+        for (int ch = threadIdx.x; ch < I.C; ch += blockDim.x)
+            single_scalars(&A.scal[I.pc + ch], it, S.sd[ch], S.sd2[ch]);
+        __syncthreads();
+    }
+    int pair = 0;
+    for (int k = 0; k < A.ninst; ++k) {
+        const int ntiles = A.ninst == 1 ? own.ntiles : A.inst[k].ntiles;
+        if (ntiles > 32) continue;
+        const InstDev& I = A.ninst == 1 ? own : A.inst[k];
+        for (int ch = 0; ch < I.C; ++ch, ++pair) {
+            if (pair % nw != w) continue;
+            const int64_t o = I.part_base + (int64_t)ch * ntiles + lane;
+            const float2 g = lane < ntiles ? __ldcg(pg + o) : make_float2(0.0f, 0.0f);
+            const float2 m = lane < ntiles ? __ldcg(pm + o) : make_float2(0.0f, 0.0f);
+            DF ag = {0.0f, 0.0f}, am = {0.0f, 0.0f};
+            ag = df_add(ag, DF{g.x, g.y});
+            am = df_add(am, DF{m.x, m.y});
+            const DF tg = df_warp_sum(ag), tm = df_warp_sum(am);
+            if (lane == 0)
+                single_scalars(&A.scal[I.pc + ch], it, df_to_double(tg), df_to_double(tm));
+        }
+    }
+}
+
 __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -2016,7 +2086,9 @@ __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v)
 // its own 128-byte line), which holds the number of barriers passed.  The
 // arrival count only grows (as in grid_barrier); a counter preset to 2^31
 // (the failure-path test) completes no barrier, and every wait is bounded:
-// on time-out the block records kErrTimeout and false is returned.
+// on time-out the block records kErrTimeout and false is returned.  kind 0
+// and 1 as in finish_image; kind 2: the single-reduction form's gamma and
+// mu of iteration `it` (part is not used).
 __device__ bool reduce_barrier(const SolveArgs& A, const InstDev& own, unsigned* bar,
                                unsigned& epoch, const float2* __restrict__ part, int kind, int it,
                                PhaseSmem& S)
@@ -2033,7 +2105,8 @@ __device__ bool reduce_barrier(const SolveArgs& A, const InstDev& own, unsigned*
     }
     __syncthreads();
     if (S.last) {
-        finalise_all(A, own, part, kind, it, S);
+        if (kind == 2) finalise_single(A, own, it, S);    // single-reduction form
+        else finalise_all(A, own, part, kind, it, S);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -2260,6 +2333,161 @@ pcg_resident_kernel(SolveArgs A, int iters, unsigned* bar)
     else resident_loop<4, COMP>(A, I, vt, iters, bar, s_nb, s_nmu, S);
 }
 
+// ------------------------------- resident single-reduction PCG loop ---
+// The single-reduction form (see cg_tile) with all iterations in one
+// cooperative launch, one tile per block: one grid barrier per iteration
+// instead of two, the last block to reach it forming beta and alpha of the
+// next iteration from the partials of gamma and mu.  Each thread keeps its
+// vertex's r, w and s in registers (p and y stay in memory: read and
+// written once per iteration), gathers the neighbours' r_i, w_i and
+// s_(i-1) from the previous iteration's buffers (by parity, as cg_tile), and
+// writes its own for the next.  The set-up pass forms w_0 = A M^-1 r_0 and
+// the partials of mu_0 (gamma_0's come from the initial residual).  FP32
+// vectors, Cp <= 4; the same arithmetic per vertex as cg_tile.
+template <int W, int NG = (W == 4 ? 2 : 5)>
+__device__ void resident_single_loop(const SolveArgs& A, const InstDev& I, const VTile& vt,
+                                     int iters, unsigned* bar, int32_t (*s_nb)[kVTile],
+                                     float2 (*s_nmu)[kVTile], PhaseSmem& S)
+{
+    const int tx = threadIdx.x;
+    const int v = (int)vt.v0 + tx;
+    const bool valid = v < (int)vt.v1;
+    const int vs = valid ? v : (int)vt.v0;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        const int32_t u = valid ? A.nbr[(int64_t)k * A.Vtot + v] : -1;
+        s_nb[k][tx] = u;
+        s_nmu[k][tx] = u >= 0 ? A.nm[u] : make_float2(0.0f, 0.0f);
+    }
+    const float2 nmv = A.nm[vs];
+    const float av = A.a[vs];
+    const float lam_n = I.lam * nmv.x;
+    const int64_t off = I.vec_base - I.voff * W;
+    DF rg[W], rm[W];
+    float r[W], w[W], so[W];
+    unsigned epoch = 0;
+    // set-up: w_0 = A M^-1 r_0 (into d[0]) and the partials of mu_0
+    {
+        const float* __restrict__ rb = A.r + off;
+        float u0[W], lap[W];
+        ldw<W, false>(rb + vs * W, r);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            u0[k] = nmv.y * r[k];
+            lap[k] = 0.0f;
+        }
+        __syncthreads();                    // s_nb, s_nmu
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            const int32_t u0i = s_nb[j][tx];
+            const int u = u0i >= 0 ? u0i : vs;
+            const float2 nm = s_nmu[j][tx];
+            float ru[W];
+            ldw<W, false>(rb + u * W, ru);
+#pragma unroll
+            for (int k = 0; k < W; ++k) lap[k] = fmaf(nm.x, u0[k] - nm.y * ru[k], lap[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            w[k] = fmaf(av, u0[k], lam_n * lap[k]);
+            so[k] = 0.0f;
+            rm[k] = valid && k < I.C ? df_mul_exact(w[k], u0[k]) : DF{0.0f, 0.0f};
+        }
+        if (valid) stw<W>(A.d[0] + off + v * W, w);
+        store_partials<W>(rm, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst, A.part_mu[0], S.red);
+    }
+    if (!reduce_barrier(A, I, bar, epoch, nullptr, 2, 0, S)) return;
+    for (int it = 0; it < iters; ++it) {
+        const int cur = it & 1, nxt = cur ^ 1;
+        const bool first = it == 0, last = it == iters - 1;
+        __syncthreads();
+        for (int ch = tx; ch < I.Cp; ch += blockDim.x) {
+            const bool on = ch < I.C;
+            S.sf[ch] = on ? __ldcg(&A.scal[I.pc + ch].beta) : 0.0f;
+            S.sa[ch] = on ? __ldcg(&A.scal[I.pc + ch].alpha) : 0.0;
+        }
+        __syncthreads();
+        float beta[W], alpha[W], pv[W], yv[W], r1[W], u1[W];
+        if (!first) ldw<W, false>(A.q + off + vs * W, pv);
+        ldw<W, false>(A.y + off + vs * W, yv);
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            beta[k] = S.sf[k];
+            alpha[k] = (float)S.sa[k];
+            const float si = first ? w[k] : fmaf(beta[k], so[k], w[k]);
+            const float ui = nmv.y * r[k];
+            pv[k] = first ? ui : fmaf(beta[k], pv[k], ui);
+            yv[k] = fmaf(alpha[k], pv[k], yv[k]);
+            r1[k] = fmaf(-alpha[k], si, r[k]);
+            u1[k] = nmv.y * r1[k];
+            so[k] = si;
+        }
+        if (valid) {
+            stw<W>(A.y + off + v * W, yv);
+            stw<W>(A.q + off + v * W, pv);
+        }
+        if (last) break;
+        const float* __restrict__ rb = (cur ? A.rlo : A.r) + off;   // r_i
+        const float* __restrict__ wb = A.d[cur] + off;             // w_i
+        const float* __restrict__ sb = A.aux[nxt] + off;           // s_(i-1)
+        float lap[W];
+#pragma unroll
+        for (int k = 0; k < W; ++k) lap[k] = 0.0f;
+#pragma unroll
+        for (int g0 = 0; g0 < 10; g0 += NG) {
+            float ru[NG][W], wu[NG][W], su[NG][W];
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                const int32_t u0i = s_nb[g0 + j][tx];
+                const int u = u0i >= 0 ? u0i : vs;
+                ldw<W, false>(rb + u * W, ru[j]);
+                ldw<W, false>(wb + u * W, wu[j]);
+                if (!first) ldw<W, false>(sb + u * W, su[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < NG; ++j) {
+                const float2 nm = s_nmu[g0 + j][tx];
+#pragma unroll
+                for (int k = 0; k < W; ++k) {
+                    const float s_u = first ? wu[j][k] : fmaf(beta[k], su[j][k], wu[j][k]);
+                    const float u_u = nm.y * fmaf(-alpha[k], s_u, ru[j][k]);
+                    lap[k] = fmaf(nm.x, u1[k] - u_u, lap[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            w[k] = fmaf(av, u1[k], lam_n * lap[k]);
+            r[k] = r1[k];
+            const bool on = valid && k < I.C;
+            rg[k] = on ? df_mul_exact(r1[k], u1[k]) : DF{0.0f, 0.0f};
+            rm[k] = on ? df_mul_exact(w[k], u1[k]) : DF{0.0f, 0.0f};
+        }
+        if (valid) {
+            stw<W>(A.aux[cur] + off + v * W, so);
+            stw<W>((nxt ? A.rlo : A.r) + off + v * W, r1);
+            stw<W>(A.d[nxt] + off + v * W, w);
+        }
+        store_partials<W>(rg, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst, A.part_rs[nxt], S.red);
+        store_partials<W>(rm, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst, A.part_mu[nxt], S.red);
+        if (!reduce_barrier(A, I, bar, epoch, nullptr, 2, it + 1, S)) return;
+    }
+}
+
+template <int WMAX>
+__global__ void __launch_bounds__(kVTile, 3)
+pcg_resident_single_kernel(SolveArgs A, int iters, unsigned* bar)
+{
+    __shared__ int32_t s_nb[10][kVTile];
+    __shared__ float2 s_nmu[10][kVTile];
+    __shared__ PhaseSmem S;
+    const VTile vt = A.vt[blockIdx.x];
+    const InstDev I = A.inst[vt.inst];
+    if (WMAX == 1 || I.Cp == 1) resident_single_loop<1>(A, I, vt, iters, bar, s_nb, s_nmu, S);
+    else if (WMAX == 2 || I.Cp == 2) resident_single_loop<2>(A, I, vt, iters, bar, s_nb, s_nmu, S);
+    else resident_single_loop<4>(A, I, vt, iters, bar, s_nb, s_nmu, S);
+}
+
 // index of the widest pass: 0 (W = 1), 1 (W = 2), 2 (W = 4)
 int width_index(int cmax) { return cmax <= 1 ? 0 : cmax <= 2 ? 1 : 2; }
 
@@ -2352,7 +2580,31 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
     static const int occ_res[3] = {occupancy((const void*)pcg_resident_kernel<1, COMP>),
                                    occupancy((const void*)pcg_resident_kernel<2, COMP>),
                                    occupancy((const void*)pcg_resident_kernel<4, COMP>)};
-    if (P.persistent && P.pcg_iters > 0) {
+    static const int occ_res_single[3] = {occupancy((const void*)pcg_resident_single_kernel<1>),
+                                          occupancy((const void*)pcg_resident_single_kernel<2>),
+                                          occupancy((const void*)pcg_resident_single_kernel<4>)};
+    if (P.persistent && P.pcg_iters > 0 && P.single && !COMP && P.cmax <= 4 &&
+        A.nvt <= device_info().sms * occ_res_single[wi]) {
+        // the single-reduction form, resident: one barrier per iteration
+        static int f_res_single = prof_family("pcg_resident_single");
+        cudaError_t e = cudaMemsetAsync(P.barrier, 0, kBarrierWords * sizeof(unsigned), s);
+        if (e == cudaSuccess && P.inject_timeout)   // counter = 2^31 (little-endian)
+            e = cudaMemsetAsync(reinterpret_cast<unsigned char*>(P.barrier) + 3, 0x80, 1, s);
+        if (e != cudaSuccess) return e;
+        SolveArgs a = A;
+        int iters = P.pcg_iters;
+        unsigned* bar = P.barrier;
+        void* args[] = {&a, &iters, &bar};
+        const void* fn = wi == 0   ? (const void*)pcg_resident_single_kernel<1>
+                         : wi == 1 ? (const void*)pcg_resident_single_kernel<2>
+                                   : (const void*)pcg_resident_single_kernel<4>;
+        prof_begin(f_res_single, s);
+        e = cudaLaunchCooperativeKernel(fn, dim3(A.nvt), dim3(kVTile), args, 0, s);
+        prof_end(f_res_single, s);
+        if (e == cudaSuccess) return cudaGetLastError();
+        cudaGetLastError();   // clear, and fall back to per-phase launches
+    }
+    if (P.persistent && P.pcg_iters > 0 && !P.single) {
         const bool resident = P.cmax <= 4 && A.nvt <= device_info().sms * occ_res[wi];
         if (resident || P.force_persistent) {
             // barrier words zero (or, for the failure-path test, a top counter
@@ -2446,6 +2698,12 @@ cudaError_t launch_splat(const SolveArgs& A, const SolvePlan& P, int mode, cudaS
 
 bool resident_fits(const SolveArgs& A, const SolvePlan& P)
 {
+    static const int occ_single[3] = {occupancy((const void*)pcg_resident_single_kernel<1>),
+                                      occupancy((const void*)pcg_resident_single_kernel<2>),
+                                      occupancy((const void*)pcg_resident_single_kernel<4>)};
+    if (P.single)
+        return !P.comp && P.cmax <= 4 &&
+               A.nvt <= device_info().sms * occ_single[width_index(P.cmax)];
     static const int occ[2][3] = {{occupancy((const void*)pcg_resident_kernel<1, false>),
                                    occupancy((const void*)pcg_resident_kernel<2, false>),
                                    occupancy((const void*)pcg_resident_kernel<4, false>)},

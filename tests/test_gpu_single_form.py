@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 from paper_1511_03296_gb300 import synth
-from tests.gpu_util import PCG_FORM, REL_L2_TOL, gpu_grid, gpu_solve, oracle_grid, rel_l2, to_dev
+from tests.gpu_util import (PCG_FORM, PCG_LAUNCH, REL_L2_TOL, gpu_grid, gpu_solve, oracle_grid,
+                            rel_l2, to_dev)
 
 import oracle
 
@@ -44,12 +45,22 @@ def _check(insts, iters=25, tol=REL_L2_TOL, form="single"):
     return errs
 
 
-def test_single_plain_64x48():
+@pytest.fixture(params=["auto", "persistent", "per_phase"])
+def pcg_launch(request):
+    # persistent: the resident single-reduction loop where every tile has a
+    # co-resident block (one grid barrier per iteration); per_phase: one
+    # launch per iteration
+    PCG_LAUNCH["mode"] = {"auto": 0, "persistent": 1, "per_phase": 2}[request.param]
+    yield request.param
+    PCG_LAUNCH["mode"] = 0
+
+
+def test_single_plain_64x48(pcg_launch):
     _check(synth.plain_64x48().instances)
 
 
 @pytest.mark.parametrize("iters", [0, 1, 2, 5, 50])
-def test_single_iteration_counts(iters):
+def test_single_iteration_counts(iters, pcg_launch):
     _check([_inst(10, 70, 90, (8.0, 4.0, 3.0), C=2, npoly=6)], iters)
 
 
@@ -74,7 +85,7 @@ def test_single_zero_confidence_channels_and_vertices():
     _check([inst])
 
 
-def test_single_batched_uneven_images():
+def test_single_batched_uneven_images(pcg_launch):
     insts = [_inst(20, 37, 53, (3.3, 5.0, 7.7), C=1, lam=32.0),
              _inst(21, 120, 160, (8.0, 4.0, 3.0), C=2, lam=128.0, npoly=8),
              _inst(22, 9, 300, (16.0, 8.0, 8.0), C=3, lam=4.0),
@@ -83,12 +94,13 @@ def test_single_batched_uneven_images():
     _check(insts)
 
 
-def test_single_full_1080p():
+def test_single_full_1080p(pcg_launch):
+    # 414 tiles: the resident single-reduction loop fits (persistent)
     inst = synth.plain_1080p().instances[0]
-    print("single form 1080p rel-L2 (y, x):", _check([inst]))
+    print(f"single form 1080p ({pcg_launch}) rel-L2 (y, x):", _check([inst]))
 
 
-def test_single_deterministic():
+def test_single_deterministic(pcg_launch):
     inst = _inst(30, 120, 160, (8.0, 4.0, 3.0), C=2, npoly=8)
     g = gpu_grid([inst], 2)
     a = gpu_solve(g, [inst], 25)
@@ -118,3 +130,26 @@ def test_single_robust_small():
 def test_wide_images_fall_back_to_standard_form():
     # 5 channels (padded to 8): the single form does not cover it
     _check([_inst(40, 60, 80, (8.0, 4.0, 3.0), C=5, npoly=6)], form="standard")
+
+
+def test_single_resident_barrier_timeout_is_reported():
+    # the resident single-reduction loop's barrier, preset so that it can
+    # never complete: every block waits out its bounded spin and the
+    # time-out is latched; the grid keeps working afterwards
+    import torch
+    from paper_1511_03296_gb300 import fbs
+    inst = _inst(40, 64, 64, (8.0, 4.0, 3.0), C=1)
+    g = gpu_grid([inst], 2)
+    fbs.set_option(g, fbs.OPT_PCG_LAUNCH, fbs.PCG_PERSISTENT)
+    t, c = to_dev(inst.t), to_dev(inst.c)
+    x = torch.empty_like(t)
+    fbs.set_option(g, fbs.OPT_INJECT_BARRIER_TIMEOUT, 1)
+    fbs.solve(g, [t], [c], inst.lam, 5, x=[x])
+    with pytest.raises(fbs.FbsError, match="TIMEOUT"):
+        fbs.grid_sync(g)
+    fbs.solve(g, [t], [c], inst.lam, 25, x=[x])
+    fbs.grid_sync(g)
+    og = oracle_grid(inst, 2)
+    with oracle.pcg_form("single"):
+        _, ox = oracle.solve(og, inst.t, inst.c, inst.lam, 25)
+    assert rel_l2(x.cpu().numpy().reshape(1, -1), ox) <= REL_L2_TOL
