@@ -333,6 +333,9 @@ PCG_TRAFFIC_1080P = 6.887936e6 + 7.725312e6
 # profiles/pcg_resident_1080p.md), per iteration; after the first iteration
 # the working set is served from L2.
 PCG_TRAFFIC_1080P_RESIDENT = 20.610394e9 * 443.936e-6 / 25
+# The same for the resident loop of the single-reduction form
+# (profiles/pcg_resident_single_1080p.md).
+PCG_TRAFFIC_1080P_RESIDENT_SINGLE = 22.722101e9 * 409.472e-6 / 25
 PCG_TRAFFIC_RATIO_BATCHED = (108.809728e6 + 11.157760e6 + 66.430208e6 + 0.708096e6) / 235835472
 
 
@@ -781,6 +784,7 @@ def run_ours(args, dist):
     bytes_iter = algorithmic_bytes_per_pcg_iteration(V, inst.channels)
     roof = pcg_roofline(regions, 1, args.steps, bytes_iter, peak)
     resident = tuning.get("pcg_launch") == fbs.PCG_PERSISTENT
+    single = tuning.get("pcg_form") == fbs.PCG_FORM_SINGLE
     region_share = {k: round(t / max(1e-9, sum(tt for _, tt in regions.values())), 4)
                     for k, (n, t) in regions.items() if n}
 
@@ -807,9 +811,14 @@ def run_ours(args, dist):
                            "note": "copies and compute one after another, L2 flushed between "
                                    "steps outside the events"}},
         "gpu_launches": int(round(launches_per_step * args.steps)),
-        "roofline": dict(roof or {}, kernel="pcg iteration (both CG phases)" +
-                         (", resident loop" if resident else ", per-phase launches"),
-                         traffic=PCG_TRAFFIC_1080P_RESIDENT if resident else PCG_TRAFFIC_1080P,
+        "roofline": dict(roof or {}, kernel="pcg iteration" + (
+                             ", resident loop of the single-reduction form" if resident and single
+                             else ", resident loop" if resident else
+                             ", single-reduction form, per-iteration launches" if single else
+                             " (both CG phases), per-phase launches"),
+                         traffic=(PCG_TRAFFIC_1080P_RESIDENT_SINGLE if resident and single else
+                                  PCG_TRAFFIC_1080P_RESIDENT if resident else
+                                  None if single else PCG_TRAFFIC_1080P),
                          traffic_source=("ncu, one 25-iteration launch of the resident loop, "
                                          "per iteration" if resident else
                                          "ncu, cold caches, one iteration (apply + update)"),
