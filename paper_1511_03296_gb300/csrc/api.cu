@@ -25,12 +25,12 @@ cudaError_t launch_scan_tiles(const int*, int64_t*, int, cudaStream_t);
 cudaError_t launch_grid_finalize(const GTile*, int, const ImgDev*, const int64_t*, uint32_t*,
                                  const uint64_t*, const uint32_t*, const uint32_t*, uint64_t*,
                                  uint32_t*, uint32_t*, uint32_t*, cudaStream_t);
-cudaError_t launch_pack_neighbours(const int32_t*, uint32_t*, int64_t, cudaStream_t);
+cudaError_t launch_pack_neighbours(const int32_t*, int64_t, uint32_t*, int64_t, cudaStream_t);
 cudaError_t launch_grid_neighbours(const GTile*, int, const ImgDev*, const int64_t*,
                                    const uint64_t*, const uint32_t*, const uint32_t*, int32_t*,
                                    int64_t, cudaStream_t);
 cudaError_t launch_bistoch(const double*, double*, float*, const uint32_t*, const int32_t*,
-                           int64_t, int, int, cudaStream_t);
+                           int64_t, int64_t, int, int, cudaStream_t);
 
 // ----------------------------------------------------------- device info ---
 const DeviceInfo& device_info()
@@ -248,6 +248,30 @@ cudaError_t pinned_upload(void* dst, const void* src, size_t bytes, cudaStream_t
     return cudaSuccess;
 }
 
+// A pinned host buffer of this thread for device-to-host reads that the
+// host waits for before the call returns (copies into pageable memory are
+// synchronous: they would stop the host before the following launches).
+// Grows as needed; an earlier read has completed by the time a call asks
+// for it again.
+unsigned char* pinned_readback(size_t bytes)
+{
+    thread_local unsigned char* buf = nullptr;
+    thread_local size_t cap = 0;
+    if (bytes > cap) {
+        if (buf) cudaFreeHost(buf);
+        buf = nullptr;
+        cap = 0;
+        const size_t want = std::max<size_t>(bytes, (size_t)1 << 20);
+        if (cudaMallocHost(&buf, want) != cudaSuccess) {
+            cudaGetLastError();
+            buf = nullptr;
+            return nullptr;
+        }
+        cap = want;
+    }
+    return buf;
+}
+
 cudaError_t upload(void* dst, const void* src, size_t bytes, cudaStream_t s)
 {
     static int fam = prof_family("upload");
@@ -307,6 +331,8 @@ struct fbs_grid {
     uint32_t* pstart = nullptr;
     uint32_t* m = nullptr;
     int32_t* nbr = nullptr;
+    int64_t nbr_stride = 0;    // entries between the 10 rows of nbr (its vertex capacity)
+    cudaEvent_t ev_counts = nullptr;   // the grid build's vertex counts have reached the host
     uint32_t* nbrp = nullptr;           // 5 x Vtot packed 16-bit neighbour offsets
     double* n64 = nullptr;
     double* n64b = nullptr;
@@ -385,6 +411,10 @@ void free_grid_memory(fbs_grid* g, cudaStream_t s)
     if (g->cap_stream) {
         cudaStreamDestroy(g->cap_stream);
         g->cap_stream = nullptr;
+    }
+    if (g->ev_counts) {
+        cudaEventDestroy(g->ev_counts);
+        g->ev_counts = nullptr;
     }
     dfree(g->vkey, s); dfree(g->vid, s); dfree(g->perm, s); dfree(g->pstart, s);
     dfree(g->m, s); dfree(g->nbr, s); dfree(g->nbrp, s); dfree(g->n64, s); dfree(g->n64b, s); dfree(g->nf, s);
@@ -553,10 +583,46 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
     FBS_TRY(launch_grid_sort(d_tiles, ntiles, d_img, d_tile_nv, g->err, P2, max_cells, g->vid,
                              g->perm, d_tkey, d_tm, d_tps, g->cell_voff, g->cell_nv, s));
     FBS_TRY(launch_scan_tiles(d_tile_nv, d_tile_voff, ntiles, s));
-    FBS_TRY(cudaMemcpyAsync(tile_voff.data(), d_tile_voff, (ntiles + 1) * sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, s));
-    FBS_TRY(cudaMemcpyAsync(&err_bits, g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    FBS_TRY(cudaStreamSynchronize(s));
+    {
+        // The vertex counts come back to the host while the finalize and
+        // neighbour passes run: those write arrays sized by the pixel count
+        // (V <= N; the sort keeps its counts in range even when it latches an
+        // error), and the neighbour table's row stride is that capacity.
+        const size_t rb_bytes = (size_t)(ntiles + 1) * sizeof(int64_t) + sizeof(uint32_t);
+        unsigned char* rb = pinned_readback(rb_bytes);
+        uint32_t* rb_err = nullptr;
+        int64_t* rb_voff = nullptr;
+        if (rb) {
+            rb_voff = reinterpret_cast<int64_t*>(rb);
+            rb_err = reinterpret_cast<uint32_t*>(rb + (size_t)(ntiles + 1) * sizeof(int64_t));
+            FBS_TRY(cudaMemcpyAsync(rb_voff, d_tile_voff, (ntiles + 1) * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, s));
+            FBS_TRY(cudaMemcpyAsync(rb_err, g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+            if (!g->ev_counts) FBS_TRY(cudaEventCreateWithFlags(&g->ev_counts, cudaEventDisableTiming));
+            FBS_TRY(cudaEventRecord(g->ev_counts, s));
+        }
+        const int64_t Vcap = std::max<int64_t>(pix, 1);
+        g->nbr_stride = Vcap;
+        FBS_TRY(dalloc(&g->vkey, Vcap, s));
+        FBS_TRY(dalloc(&g->pstart, Vcap, s));
+        FBS_TRY(dalloc(&g->m, Vcap, s));
+        FBS_TRY(launch_grid_finalize(d_tiles, ntiles, d_img, d_tile_voff, g->vid, d_tkey, d_tm,
+                                     d_tps, g->vkey, g->m, g->pstart, g->cell_voff, s));
+        FBS_TRY(dalloc(&g->nbr, (size_t)Vcap * 10, s));
+        FBS_TRY(launch_grid_neighbours(d_tiles, ntiles, d_img, d_tile_voff, g->vkey, g->cell_voff,
+                                       g->cell_nv, g->nbr, Vcap, s));
+        if (rb) {
+            FBS_TRY(cudaEventSynchronize(g->ev_counts));
+            std::copy(rb_voff, rb_voff + ntiles + 1, tile_voff.begin());
+            err_bits = *rb_err;
+        } else {                            // no pinned memory: read synchronously
+            FBS_TRY(cudaMemcpyAsync(tile_voff.data(), d_tile_voff, (ntiles + 1) * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, s));
+            FBS_TRY(cudaMemcpyAsync(&err_bits, g->err, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                    s));
+            FBS_TRY(cudaStreamSynchronize(s));
+        }
+    }
     if (err_bits) {
         st = latched(err_bits);
         goto fail_status;
@@ -569,20 +635,9 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
             while (ti < ntiles && tiles[ti].img < k) ++ti;
             g->voff[k] = tile_voff[ti];
         }
-        // the GPU idles from the synchronisation until the next launch:
-        // allocate what the finalize pass writes, launch it, and do the rest
-        // of the host work while it runs
         const int64_t V = g->Vtot;
-        FBS_TRY(dalloc(&g->vkey, V, s));
-        FBS_TRY(dalloc(&g->pstart, V, s));
-        FBS_TRY(dalloc(&g->m, V, s));
-        FBS_TRY(launch_grid_finalize(d_tiles, ntiles, d_img, d_tile_voff, g->vid, d_tkey, d_tm,
-                                     d_tps, g->vkey, g->m, g->pstart, g->cell_voff, s));
-        FBS_TRY(dalloc(&g->nbr, (size_t)V * 10, s));
         FBS_TRY(dalloc(&g->nbrp, (size_t)V * 5, s));
-        FBS_TRY(launch_grid_neighbours(d_tiles, ntiles, d_img, d_tile_voff, g->vkey, g->cell_voff,
-                                       g->cell_nv, g->nbr, V, s));
-        FBS_TRY(launch_pack_neighbours(g->nbr, g->nbrp, V, s));
+        FBS_TRY(launch_pack_neighbours(g->nbr, g->nbr_stride, g->nbrp, V, s));
         FBS_TRY(dalloc(&g->n64, V, s));
         FBS_TRY(dalloc(&g->n64b, V, s));
         FBS_TRY(dalloc(&g->nf, V, s));
@@ -645,7 +700,8 @@ fbs_status fbs_bistochastize(fbs_grid* g, int iters, void* stream)
     for (int it = 0; it < iters; ++it) {
         const double* nold = g->n64;
         double* nnew = g->n64b;
-        cudaError_t e = launch_bistoch(nold, nnew, g->nf, g->m, g->nbr, g->Vtot, it == 0,
+        cudaError_t e = launch_bistoch(nold, nnew, g->nf, g->m, g->nbr, g->nbr_stride, g->Vtot,
+                                       it == 0,
                                        it == iters - 1, s);
         if (e != cudaSuccess) return cuda_status(e);
         std::swap(g->n64, g->n64b);
@@ -1008,6 +1064,7 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     A.inst = g->inst;
     A.ninst = g->n_images;
     A.nbr = g->nbr;
+    A.nbr_stride = g->nbr_stride;
     A.nbrp = g->nbrp;
     A.Vtot = g->Vtot;
     A.n64 = g->n64;
@@ -1558,7 +1615,7 @@ fbs_status fbs_grid_export(const fbs_grid* g, int image, void* stream, uint64_t*
     if (host_nbr && e == cudaSuccess) {
         soa.resize((size_t)V * 10);
         for (int k = 0; k < 10 && e == cudaSuccess; ++k)
-            e = cudaMemcpyAsync(soa.data() + (size_t)k * V, g->nbr + (size_t)k * g->Vtot + v0,
+            e = cudaMemcpyAsync(soa.data() + (size_t)k * V, g->nbr + (size_t)k * g->nbr_stride + v0,
                                 V * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     }
     if (host_n && e == cudaSuccess)
@@ -1710,6 +1767,7 @@ bool grid_view(const fbs_grid* g, GridView* out)
     out->nvt_img = g->nvt_img.data();
     out->vt = g->vt;
     out->nbr = g->nbr;
+    out->nbr_stride = g->nbr_stride;
     out->nbrp = g->nbrp;
     out->n64 = g->n64;
     out->m = g->m;

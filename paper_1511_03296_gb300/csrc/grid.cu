@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(256)
 grid_neighbours_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict__ imgs,
                        const int64_t* __restrict__ tile_voff, const uint64_t* __restrict__ vkey,
                        const uint32_t* __restrict__ cell_voff, const uint32_t* __restrict__ cell_nv,
-                       int32_t* __restrict__ nbr, int64_t Vtot)
+                       int32_t* __restrict__ nbr, int64_t nstride)
 {
     const GTile t = tiles[blockIdx.x];
     const ImgDev im = imgs[t.img];
@@ -438,7 +438,7 @@ grid_neighbours_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict
                     const uint64_t target = s ? key + unit : key - unit;
                     found = find_in_cell(vkey, cell_voff[c], cell_nv[c], target);
                 }
-                nbr[(int64_t)(2 * d + s) * Vtot + v] = found;
+                nbr[(int64_t)(2 * d + s) * nstride + v] = found;
             }
         }
     }
@@ -449,7 +449,7 @@ grid_neighbours_kernel(const GTile* __restrict__ tiles, const ImgDev* __restrict
 __global__ void __launch_bounds__(256)
 bistoch_kernel(const double* __restrict__ nold, double* __restrict__ nnew,
                float* __restrict__ nf, const uint32_t* __restrict__ m,
-               const int32_t* __restrict__ nbr, int64_t V, int first, int last)
+               const int32_t* __restrict__ nbr, int64_t nstride, int64_t V, int first, int last)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -457,7 +457,7 @@ bistoch_kernel(const double* __restrict__ nold, double* __restrict__ nnew,
         double bn = __dmul_rn(10.0, nv);
 #pragma unroll
         for (int k = 0; k < 10; ++k) {
-            const int32_t u = nbr[(int64_t)k * V + v];
+            const int32_t u = nbr[(int64_t)k * nstride + v];
             if (u >= 0) bn = __dadd_rn(bn, first ? 1.0 : nold[u]);
         }
         const double r = __dsqrt_rn(__ddiv_rn(__dmul_rn(nv, (double)m[v]), bn));
@@ -476,7 +476,8 @@ bistoch_kernel(const double* __restrict__ nold, double* __restrict__ nnew,
 // offsets small: l, u, v neighbours share the cell, x neighbours are in the
 // next cell, y neighbours one cell row away.
 __global__ void __launch_bounds__(256)
-pack_neighbours_kernel(const int32_t* __restrict__ nbr, uint32_t* __restrict__ nbrp, int64_t V)
+pack_neighbours_kernel(const int32_t* __restrict__ nbr, int64_t nstride, uint32_t* __restrict__ nbrp,
+                       int64_t V)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -485,7 +486,7 @@ pack_neighbours_kernel(const int32_t* __restrict__ nbr, uint32_t* __restrict__ n
             uint32_t w = 0;
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
-                const int32_t u = nbr[(int64_t)(2 * d + s) * V + v];
+                const int32_t u = nbr[(int64_t)(2 * d + s) * nstride + v];
                 const int64_t off = u >= 0 ? (int64_t)u - v : 0;
                 const int32_t h = (off >= -kNbrOffMax && off <= kNbrOffMax) ? (int32_t)off
                                                                              : kNbrEscape;
@@ -546,33 +547,35 @@ cudaError_t launch_grid_finalize(const GTile* tiles, int ntiles, const ImgDev* i
 cudaError_t launch_grid_neighbours(const GTile* tiles, int ntiles, const ImgDev* imgs,
                                    const int64_t* tile_voff, const uint64_t* vkey,
                                    const uint32_t* cell_voff, const uint32_t* cell_nv,
-                                   int32_t* nbr, int64_t Vtot, cudaStream_t s)
+                                   int32_t* nbr, int64_t nstride, cudaStream_t s)
 {
     static int fam = prof_family("grid_neighbours");
     prof_begin(fam, s);
     grid_neighbours_kernel<<<ntiles, 256, 0, s>>>(tiles, imgs, tile_voff, vkey, cell_voff, cell_nv,
-                                                  nbr, Vtot);
+                                                  nbr, nstride);
     prof_end(fam, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bistoch(const double* nold, double* nnew, float* nf, const uint32_t* m,
-                           const int32_t* nbr, int64_t V, int first, int last, cudaStream_t s)
+                           const int32_t* nbr, int64_t nstride, int64_t V, int first, int last,
+                           cudaStream_t s)
 {
     if (V == 0) return cudaSuccess;
     static int fam = prof_family("bistochastize");
     int blocks = (int)std::min<int64_t>((V + 255) / 256, (int64_t)device_info().sms * 8);
     prof_begin(fam, s);
-    bistoch_kernel<<<blocks, 256, 0, s>>>(nold, nnew, nf, m, nbr, V, first, last);
+    bistoch_kernel<<<blocks, 256, 0, s>>>(nold, nnew, nf, m, nbr, nstride, V, first, last);
     prof_end(fam, s);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_neighbours(const int32_t* nbr, uint32_t* nbrp, int64_t V, cudaStream_t s)
+cudaError_t launch_pack_neighbours(const int32_t* nbr, int64_t nstride, uint32_t* nbrp, int64_t V,
+                                   cudaStream_t s)
 {
     if (V == 0) return cudaSuccess;
     const int blocks = (int)std::min<int64_t>((V + 255) / 256, (int64_t)device_info().sms * 8);
-    pack_neighbours_kernel<<<blocks, 256, 0, s>>>(nbr, nbrp, V);
+    pack_neighbours_kernel<<<blocks, 256, 0, s>>>(nbr, nstride, nbrp, V);
     return cudaGetLastError();
 }
 

@@ -21,7 +21,8 @@ struct GridView {
     const int* vt0;            // host, n_images
     const int* nvt_img;        // host, n_images
     const VTile* vt;           // device
-    const int32_t* nbr;        // device
+    const int32_t* nbr;        // device, 10 rows of nbr_stride entries
+    int64_t nbr_stride;
     const uint32_t* nbrp;      // device, packed offsets
     const double* n64;
     const uint32_t* m;

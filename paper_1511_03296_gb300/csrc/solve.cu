@@ -106,7 +106,7 @@ __device__ __forceinline__ void load_neighbours(const SolveArgs& A, int v, int (
 #pragma unroll
         for (int j = 0; j < 10; ++j) {
             const int o = (int)(int16_t)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
-            if (o == kNbrEscape) nb[j] = A.nbr[(int64_t)j * A.Vtot + v];
+            if (o == kNbrEscape) nb[j] = A.nbr[(int64_t)j * A.nbr_stride + v];
         }
     }
 }
@@ -350,7 +350,7 @@ __device__ __forceinline__ void vertex_epilogue(const SolveArgs& A, const InstDe
     double sum_n = 0.0;
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
-        const int32_t u = A.nbr[(int64_t)k * A.Vtot + v];
+        const int32_t u = A.nbr[(int64_t)k * A.nbr_stride + v];
         if (u >= 0) {
             has_nbr = true;
             sum_n += A.n64[u];
@@ -658,7 +658,7 @@ __device__ __forceinline__ void residual_tile(const SolveArgs& A, const InstDev&
     const float lam_n = I.lam * nmv.x;
     int32_t nb[10];
 #pragma unroll
-    for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.Vtot + v] : -1;
+    for (int j = 0; j < 10; ++j) nb[j] = valid ? A.nbr[(int64_t)j * A.nbr_stride + v] : -1;
     for (int cb = 0; cb < I.C; cb += W) {
         const int64_t base = pass_base(I, cb);
         float yv[W];
@@ -1341,7 +1341,7 @@ __device__ __forceinline__ void cg_tile(const SolveArgs& A, const InstDev& I, co
     for (int k = 0; k < W; ++k) lap[k] = 0.0f;
 #pragma unroll
     for (int j = 0; j < 10; ++j) {
-        const int u0 = A.nbr[(int64_t)j * A.Vtot + vs];
+        const int u0 = A.nbr[(int64_t)j * A.nbr_stride + vs];
         const int u = u0 >= 0 ? u0 : vs;        // absent: the vertex itself, term 0
         const float2 nm = A.nm[u];
         float ru[W], wu[W], su[W];
@@ -1394,7 +1394,7 @@ __device__ __forceinline__ void cg_w0_tile(const SolveArgs& A, const InstDev& I,
     }
 #pragma unroll
     for (int j = 0; j < 10; ++j) {
-        const int u0i = A.nbr[(int64_t)j * A.Vtot + vs];
+        const int u0i = A.nbr[(int64_t)j * A.nbr_stride + vs];
         const int u = u0i >= 0 ? u0i : vs;
         const float2 nm = A.nm[u];
         float ru[W];
@@ -2172,7 +2172,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
     float2 nmv = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
-        const int32_t u = valid ? A.nbr[(int64_t)k * A.Vtot + v] : -1;
+        const int32_t u = valid ? A.nbr[(int64_t)k * A.nbr_stride + v] : -1;
         s_nb[k][tx] = u;
         s_nmu[k][tx] = u >= 0 ? A.nm[u] : make_float2(0.0f, 0.0f);
     }
@@ -2355,7 +2355,7 @@ __device__ void resident_single_loop(const SolveArgs& A, const InstDev& I, const
     const int vs = valid ? v : (int)vt.v0;
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
-        const int32_t u = valid ? A.nbr[(int64_t)k * A.Vtot + v] : -1;
+        const int32_t u = valid ? A.nbr[(int64_t)k * A.nbr_stride + v] : -1;
         s_nb[k][tx] = u;
         s_nmu[k][tx] = u >= 0 ? A.nm[u] : make_float2(0.0f, 0.0f);
     }

@@ -42,7 +42,8 @@ struct SolveArgs {
     const InstDev* inst;
     int ninst;
     // grid
-    const int32_t* nbr;        // 10 x Vtot, global vertex ids, -1 if absent
+    const int32_t* nbr;        // 10 rows of nbr_stride, global vertex ids, -1 if absent
+    int64_t nbr_stride;        // row stride of nbr (>= Vtot: the grid's vertex capacity)
     const uint32_t* nbrp;      // 5 x Vtot, packed 16-bit offsets (-1 and +1 per dimension)
     int64_t Vtot;
     const double* n64;         // bistochastisation vector n

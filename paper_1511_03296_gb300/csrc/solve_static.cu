@@ -168,6 +168,7 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
     A.inst = reinterpret_cast<const InstDev*>(base + L.inst);
     A.ninst = G.n_images;
     A.nbr = G.nbr;
+    A.nbr_stride = G.nbr_stride;
     A.nbrp = G.nbrp;
     A.Vtot = G.Vtot;
     A.n64 = G.n64;
