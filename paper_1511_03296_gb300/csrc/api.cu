@@ -1088,6 +1088,8 @@ fbs_status run(fbs_grid* g, std::vector<InstDev>& inst, SolvePlan plan, cudaStre
     }
     A.alo = plan.dfy ? g->alo : nullptr;
     A.ylo = plan.dfy ? A.aux[1] : nullptr;
+    A.zq = !plan.comp && !plan.hier && !plan.single ? A.aux[0] : nullptr;
+    A.nf = g->nf;
     A.scal = g->scal;
     A.nscal = pc;
     plan.barrier = g->barrier;
@@ -1770,6 +1772,7 @@ bool grid_view(const fbs_grid* g, GridView* out)
     out->nbr_stride = g->nbr_stride;
     out->nbrp = g->nbrp;
     out->n64 = g->n64;
+    out->nf = g->nf;
     out->m = g->m;
     out->pstart = g->pstart;
     out->perm = g->perm;

@@ -25,6 +25,7 @@ struct GridView {
     int64_t nbr_stride;
     const uint32_t* nbrp;      // device, packed offsets
     const double* n64;
+    const float* nf;           // n in FP32
     const uint32_t* m;
     const uint32_t* pstart;
     const uint32_t* perm;

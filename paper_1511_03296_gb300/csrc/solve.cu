@@ -725,12 +725,73 @@ residual_kernel(SolveArgs A)
 // (phase 2 recomputes it exactly from d).  With fetch (the tile starts the
 // block's run over an image) the CG scalars are formed first, after the
 // tile's neighbour ids and own values have been requested.
-template <int W, bool COMP, bool CO, bool HIER = false>
+// FP32 phase 1 of iterations >= 1 with the preconditioned residual
+// z = M^-1 r stored by the previous update: since d = z + beta d_old is
+// linear, A d = A z + beta q_old, so a neighbour contributes only n_u and z_u
+// (two dense gathers instead of {n, M^-1}, r and d_old) and the vertex's own
+// q_old is a streamed read.  d and d^T q are formed as in apply_tile; q
+// differs from A d by rounding only.  (Iteration 0 takes apply_tile's path,
+// whose q = A d = A z starts the recurrence.)
+template <int W, bool CO>
+__device__ __forceinline__ void apply_tile_z(const SolveArgs& A, const InstDev& I,
+                                             const VTile& vt, const float* __restrict__ dold,
+                                             float* __restrict__ dnew, PhaseSmem& S,
+                                             DF (&run)[4], bool fetch, const float2* in, int it)
+{
+    const int v = (int)vt.v0 + (int)threadIdx.x;
+    const bool valid = v < (int)vt.v1;
+    const int vs = valid ? v : (int)vt.v0;
+    const int64_t off = I.vec_base - I.voff * W;
+    const float* __restrict__ zb = A.zq + off;
+    int nb[10];
+    load_neighbours(A, vs, nb);
+    float zv[W], ov[W], qo[W];
+    ldw<W, CO>(zb + vs * W, zv);
+    ldw<W, CO>(dold + off + vs * W, ov);
+    ldw<W, CO>(A.q + off + vs * W, qo);
+    const float nv = valid ? A.nf[v] : 0.0f;
+    const float av = valid ? A.a[v] : 0.0f;
+    if (fetch) phase_scalars<1, CO, W>(A, I, in, it, S);
+    float sacc[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) sacc[k] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 10; ++j) {
+        const int u = nb[j];
+        const float nu = A.nf[u];
+        float zu[W];
+        ldw<W, CO>(zb + u * W, zu);
+#pragma unroll
+        for (int k = 0; k < W; ++k) sacc[k] = fmaf(nu, zv[k] - zu[k], sacc[k]);
+    }
+    const float lam_n = I.lam * nv;
+    float dv[W], qh[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const float beta = S.sf[k];
+        const float az = fmaf(av, zv[k], lam_n * sacc[k]);
+        dv[k] = fmaf(beta, ov[k], zv[k]);
+        qh[k] = fmaf(beta, qo[k], az);
+        if (valid && k < I.C) run[k] = df_add(run[k], df_mul_exact(dv[k], qh[k]));
+    }
+    if (valid) {
+        stw<W>(dnew + off + v * W, dv);
+        stw<W>(A.q + off + v * W, qh);
+    }
+}
+
+// Z: the z form (FP32, Jacobi, iterations >= 1; z stored by the last update)
+template <int W, bool COMP, bool CO, bool HIER = false, bool Z = false>
 __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
                                            const float* __restrict__ dold,
                                            float* __restrict__ dnew, bool first, PhaseSmem& S,
                                            DF (&run)[4], bool fetch, const float2* in, int it)
 {
+    static_assert(!Z || (!COMP && !HIER), "the z form is the FP32 Jacobi phase 1");
+    if (Z) {
+        apply_tile_z<W, CO>(A, I, vt, dold, dnew, S, run, fetch, in, it);
+        return;
+    }
     // HIER: the preconditioned residual z = M_hier^-1 r is a vector of its own
     // (the pyramid passes after each update), read in place of M^-1 r
     const int v = (int)vt.v0 + (int)threadIdx.x;
@@ -857,6 +918,12 @@ __device__ __forceinline__ void update_tile(const SolveArgs& A, const InstDev& I
         stw<W>(A.r + off + v * W, rv);
         if (COMP) stw<W>(A.rlo + off + v * W, rl);
         if (ydf) stw<W>(A.ylo + off + v * W, yl);
+        if (!COMP && A.zq) {
+            float zv[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) zv[k] = nmv.y * rv[k];
+            stw<W>(A.zq + off + v * W, zv);
+        }
     }
 }
 
@@ -901,6 +968,12 @@ __device__ __forceinline__ void update_pair(const SolveArgs& A, const InstDev& I
         if (valid[t]) {
             stw<W>(A.y + off + v[t] * W, yv[t]);
             stw<W>(A.r + off + v[t] * W, rv[t]);
+            if (A.zq) {
+                float zv[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) zv[k] = nmv[t].y * rv[t][k];
+                stw<W>(A.zq + off + v[t] * W, zv);
+            }
         }
     }
 }
@@ -920,12 +993,74 @@ __device__ __forceinline__ void wide_lane(const InstDev& I, int& P, int& nvc, in
     p = threadIdx.x - lv * P;
 }
 
-template <bool COMP, bool CO, bool HIER = false>
+// The z form of apply_tile_z for wide images: a neighbour contributes n_u
+// and its z row (one float4 per lane) in place of {n, M^-1}, r and d_old.
+template <bool CO>
+__device__ __forceinline__ void apply_wide_z(const SolveArgs& A, const InstDev& I,
+                                             const VTile& vt, const float* __restrict__ dold,
+                                             float* __restrict__ dnew, PhaseSmem& S,
+                                             DF (&run)[4])
+{
+    int P, nvc, lv, p;
+    wide_lane(I, P, nvc, lv, p);
+    const int cb = 4 * p, Cp = I.Cp;
+    const int64_t base = pass_base(I, cb);
+    const float* __restrict__ zb = A.zq + base;
+    float beta[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) beta[k] = S.sf[min(cb + k, kMaxChannels - 1)];
+    const int nverts = (int)(vt.v1 - vt.v0);
+    for (int c0 = 0; c0 < nverts; c0 += nvc) {
+        const int v = (int)vt.v0 + c0 + lv;
+        const bool valid = lv < nvc && c0 + lv < nverts;
+        const int vs = valid ? v : (int)vt.v0;
+        int nb[10];
+        load_neighbours(A, vs, nb);
+        float zv[4], ov[4], qo[4];
+        ldw<4, CO>(zb + vs * Cp, zv);
+        ldw<4, CO>(dold + base + vs * Cp, ov);
+        ldw<4, CO>(A.q + base + vs * Cp, qo);
+        const float nv = valid ? A.nf[v] : 0.0f;
+        const float av = valid ? A.a[v] : 0.0f;
+        float sacc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sacc[k] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+            const int u = nb[j];
+            const float nu = A.nf[u];
+            float zu[4];
+            ldw<4, CO>(zb + u * Cp, zu);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sacc[k] = fmaf(nu, zv[k] - zu[k], sacc[k]);
+        }
+        const float lam_n = I.lam * nv;
+        float dv[4], qh[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float az = fmaf(av, zv[k], lam_n * sacc[k]);
+            dv[k] = fmaf(beta[k], ov[k], zv[k]);
+            qh[k] = fmaf(beta[k], qo[k], az);
+            if (valid && cb + k < I.C) run[k] = df_add(run[k], df_mul_exact(dv[k], qh[k]));
+        }
+        if (valid) {
+            stw<4>(dnew + base + v * Cp, dv);
+            stw<4>(A.q + base + v * Cp, qh);
+        }
+    }
+}
+
+template <bool COMP, bool CO, bool HIER = false, bool Z = false>
 __device__ __forceinline__ void apply_wide(const SolveArgs& A, const InstDev& I, const VTile& vt,
                                            const float* __restrict__ dold,
                                            float* __restrict__ dnew, bool first, PhaseSmem& S,
                                            DF (&run)[4])
 {
+    static_assert(!Z || (!COMP && !HIER), "the z form is the FP32 Jacobi phase 1");
+    if (Z) {
+        apply_wide_z<CO>(A, I, vt, dold, dnew, S, run);
+        return;
+    }
     // HIER: z = M_hier^-1 r read in place of M^-1 r (as apply_tile)
     int P, nvc, lv, p;
     wide_lane(I, P, nvc, lv, p);
@@ -1063,6 +1198,12 @@ __device__ __forceinline__ void update_wide(const SolveArgs& A, const InstDev& I
             stw<4>(A.r + base + v * Cp, rv);
             if (COMP) stw<4>(A.rlo + base + v * Cp, rl);
             if (ydf) stw<4>(A.ylo + base + v * Cp, yl);
+            if (!COMP && A.zq) {
+                float zv[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) zv[k] = nmv.y * rv[k];
+                stw<4>(A.zq + base + v * Cp, zv);
+            }
         }
     }
 }
@@ -1123,7 +1264,7 @@ __device__ __forceinline__ void flush_run(DF (&run)[4], int W, int C, int ntiles
 // scalars (phase 1: delta_it and beta; phase 2: alpha), then dispatches each
 // tile on the image's pass width.  When an image's channels fit one pass the
 // products are accumulated over the run of its tiles in this chunk.
-template <int PHASE, bool COMP, bool CO, int WMAX, bool HIER = false>
+template <int PHASE, bool COMP, bool CO, int WMAX, bool HIER = false, bool Z = false>
 __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
                           float* __restrict__ ddst, int it, int t0, int t1, PhaseSmem& S,
                           WideSmem& Wd)
@@ -1179,15 +1320,15 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
         }
         if (WMAX == 4 && I.Cp > 4) {
             if (fetch) phase_scalars<PHASE, CO, 4>(A, I, in, it, S);
-            if (PHASE == 1) apply_wide<COMP, CO, HIER>(A, I, vt, dsrc, ddst, first, S, run);
+            if (PHASE == 1) apply_wide<COMP, CO, HIER, Z>(A, I, vt, dsrc, ddst, first, S, run);
             else update_wide<COMP, CO>(A, I, vt, dsrc, S, run);
         } else if (PHASE == 1) {
             if (WMAX == 1 || I.Cp == 1)
-                apply_tile<1, COMP, CO, HIER>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
+                apply_tile<1, COMP, CO, HIER, Z>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
             else if (WMAX == 2 || I.Cp == 2)
-                apply_tile<2, COMP, CO, HIER>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
+                apply_tile<2, COMP, CO, HIER, Z>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
             else
-                apply_tile<4, COMP, CO, HIER>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
+                apply_tile<4, COMP, CO, HIER, Z>(A, I, vt, dsrc, ddst, first, S, run, fetch, in, it);
         } else {
             if (WMAX == 1 || I.Cp == 1)
                 update_tile<1, COMP, CO>(A, I, vt, dsrc, S, run, fetch, in, it);
@@ -1215,7 +1356,7 @@ __device__ void phase_run(const SolveArgs& A, const float* __restrict__ dsrc,
 template <int WMAX>
 constexpr int phase_min_blocks() { return WMAX <= 2 ? 4 : 2; }
 
-template <int WMAX, bool COMP, bool HIER = false>
+template <int WMAX, bool COMP, bool HIER = false, bool Z = false>
 __global__ void __launch_bounds__(kVTile, phase_min_blocks<WMAX>())
 pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict__ dnew, int it)
 {
@@ -1223,7 +1364,7 @@ pcg_apply_kernel(SolveArgs A, const float* __restrict__ dold, float* __restrict_
     __shared__ WideSmem Wd;
     int t0, t1;
     block_chunk(A.nvt, t0, t1);
-    phase_run<1, COMP, false, WMAX, HIER>(A, dold, dnew, it, t0, t1, S, Wd);
+    phase_run<1, COMP, false, WMAX, HIER, Z>(A, dold, dnew, it, t0, t1, S, Wd);
 }
 
 template <int WMAX, bool COMP>
@@ -2143,7 +2284,10 @@ pcg_loop_kernel(SolveArgs A, int iters, unsigned* bar)
     for (int it = 0; it < iters; ++it) {
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
-        phase_run<1, COMP, true, WMAX>(A, dold, dnew, it, t0, t1, S, Wd);
+        if (!COMP && it > 0 && A.zq)
+            phase_run<1, COMP, true, WMAX, false, !COMP>(A, dold, dnew, it, t0, t1, S, Wd);
+        else
+            phase_run<1, COMP, true, WMAX>(A, dold, dnew, it, t0, t1, S, Wd);
         if (!grid_barrier(bar, epoch, A.err)) return;
         phase_run<2, COMP, true, WMAX>(A, dnew, nullptr, it, t0, t1, S, Wd);
         if (!grid_barrier(bar, epoch, A.err)) return;
@@ -2663,6 +2807,11 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
             if (wi == 0) pcg_apply_kernel<1, COMP, true><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
             else if (wi == 1) pcg_apply_kernel<2, COMP, true><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
             else pcg_apply_kernel<4, COMP, true><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+        } else if (!COMP && it > 0 && A.zq) {   // the z form
+            constexpr bool Z = !COMP;
+            if (wi == 0) pcg_apply_kernel<1, COMP, false, Z><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+            else if (wi == 1) pcg_apply_kernel<2, COMP, false, Z><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
+            else pcg_apply_kernel<4, COMP, false, Z><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
         } else {
             if (wi == 0) pcg_apply_kernel<1, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);
             else if (wi == 1) pcg_apply_kernel<2, COMP><<<nb_p, kVTile, 0, s>>>(A, dold, dnew, it);

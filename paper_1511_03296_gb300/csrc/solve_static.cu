@@ -207,6 +207,8 @@ extern "C" fbs_status fbs_solve_static(fbs_grid* g, const fbs_problem_desc* prob
     P.max_cv = max_cv;
     for (int k = 0; k < G.n_images; ++k) P.export_y |= probs[k].y != nullptr;
     P.comp = G.precision == FBS_VECTORS_COMPENSATED ? 1 : 0;
+    A.zq = P.comp ? nullptr : A.aux[0];
+    A.nf = G.nf;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cs);
     P.persistent = G.persistent && cs == cudaStreamCaptureStatusNone ? 1 : 0;
