@@ -2303,7 +2303,7 @@ pcg_loop_kernel(SolveArgs A, int iters, unsigned* bar)
 // gathers use a safe index (the vertex itself when a neighbour is absent) so
 // they issue together with the reduction of the previous phase's partials.
 
-template <int W, bool COMP, int NG = (W == 4 ? 5 : 10)>
+template <int W, bool COMP, int NG = (COMP && W == 4 ? 5 : 10)>
 __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile& vt, int iters,
                               unsigned* bar, int32_t (*s_nb)[kVTile], float2 (*s_nmu)[kVTile],
                               PhaseSmem& S)
@@ -2346,25 +2346,31 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
         const int slot = it & 1;
         const float* dold = A.d[(it + 1) & 1];
         float* dnew = A.d[it & 1];
-        // ---- phase 1: gathers first (they do not depend on beta), then the
-        // reduction of the previous phase's partials overlaps their latency.
-        // Neighbours are gathered in groups of NG (all ten when W <= 2; two
-        // groups of five for W = 4, to stay within the register budget of
-        // three resident blocks per SM).
+        // ---- phase 1.  FP32: the z form, q = A z + beta q_old (A d, since
+        // d = z + beta d_old is linear), so a neighbour contributes only its
+        // z = M^-1 r -- stored by the previous phase 2, or, in iteration 0,
+        // formed from the initial residual.  Compensated: a neighbour's d is
+        // formed from its gathered r and d_old and q = A d, the arithmetic of
+        // the per-phase kernels (whose results this loop reproduces
+        // bitwise).  Gathers first (they do not depend on beta), then the
+        // reduction of the previous phase's partials overlaps their latency;
+        // groups of NG neighbours.
         {
-            float dv[W], beta[W];
+            float zv[W], dv[W], beta[W];
+#pragma unroll
+            for (int k = 0; k < W; ++k) zv[k] = nmv.y * r[k];
             DF s[W];
 #pragma unroll
             for (int k = 0; k < W; ++k) s[k] = {0.0f, 0.0f};
 #pragma unroll
             for (int g0 = 0; g0 < 10; g0 += NG) {
-                float ru[NG][W], du[NG][W];
+                float zu[NG][W], du[NG][W];
 #pragma unroll
                 for (int j = 0; j < NG; ++j) {
                     const int32_t u0 = s_nb[g0 + j][tx];
                     const int64_t u = u0 >= 0 ? u0 : vs;
-                    ldw<W, true>(A.r + base + u * I.Cp, ru[j]);
-                    if (it > 0) {
+                    ldw<W, true>((!COMP && it > 0 ? A.zq : A.r) + base + u * I.Cp, zu[j]);
+                    if (COMP && it > 0) {
                         ldw<W, true>(dold + base + u * I.Cp, du[j]);
                     } else {
 #pragma unroll
@@ -2376,7 +2382,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
 #pragma unroll
                     for (int k = 0; k < W; ++k) {
                         beta[k] = S.sf[k];
-                        dv[k] = fmaf(beta[k], d[k], nmv.y * r[k]);
+                        dv[k] = fmaf(beta[k], d[k], zv[k]);
                     }
                 }
 #pragma unroll
@@ -2384,21 +2390,26 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
                     const float2 nm = s_nmu[g0 + j][tx];
                     float dz[W];
 #pragma unroll
-                    for (int k = 0; k < W; ++k) dz[k] = fmaf(beta[k], du[j][k], nm.y * ru[j][k]);
-                    lap_acc<W, false>(s, nm.x, dv, dz);
+                    for (int k = 0; k < W; ++k)
+                        dz[k] = COMP ? fmaf(beta[k], du[j][k], nm.y * zu[j][k])
+                                     : (it == 0 ? nm.y * zu[j][k] : zu[j][k]);
+                    lap_acc<W, false>(s, nm.x, COMP ? dv : zv, dz);
                 }
             }
             DF acc[W];
 #pragma unroll
             for (int k = 0; k < W; ++k) {
-                const DF qq = lap_finish<false>(av, lam_n, dv[k], s[k]);
+                if (COMP) {
+                    q[k] = lap_finish<false>(av, lam_n, dv[k], s[k]).hi;
+                } else {
+                    const DF az = lap_finish<false>(av, lam_n, zv[k], s[k]);
+                    q[k] = fmaf(beta[k], q[k], az.hi);      // q = 0 before iteration 0
+                }
                 d[k] = dv[k];
-                q[k] = qq.hi;
                 const bool on = valid && k < I.C;
-                acc[k] = !on ? DF{0.0f, 0.0f}
-                             : df_mul_exact(dv[k], qq.hi);
+                acc[k] = !on ? DF{0.0f, 0.0f} : df_mul_exact(dv[k], q[k]);
             }
-            if (valid) stw<W>(dnew + base + v * I.Cp, dv);
+            if (COMP && valid) stw<W>(dnew + base + v * I.Cp, dv);
             store_partials<W>(acc, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst, A.part_dq, S.red);
         }
         if (!reduce_barrier(A, I, bar, epoch, A.part_dq, 1, it, S)) return;
@@ -2448,7 +2459,14 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
                 const bool on = valid && k < I.C;
                 acc[k] = on ? df_mul_exact(r[k], nmv.y * r[k]) : DF{0.0f, 0.0f};
             }
-            if (valid) stw<W>(A.r + base + v * I.Cp, r);
+            if (valid && COMP) {
+                stw<W>(A.r + base + v * I.Cp, r);
+            } else if (valid) {          // z = M^-1 r for the neighbours' next phase 1
+                float zv[W];
+#pragma unroll
+                for (int k = 0; k < W; ++k) zv[k] = nmv.y * r[k];
+                stw<W>(A.zq + base + v * I.Cp, zv);
+            }
             store_partials<W>(acc, I.C, I.ntiles, I.part_base, 0, vt.t_in_inst,
                               A.part_rs[slot ^ 1], S.red);
         }
@@ -2456,6 +2474,7 @@ __device__ void resident_loop(const SolveArgs& A, const InstDev& I, const VTile&
     }
     if (valid) {
         stw<W>(A.y + base + v * I.Cp, y);
+        if (!COMP) stw<W>(A.r + base + v * I.Cp, r);
         if (COMP) stw<W>(A.rlo + base + v * I.Cp, rlo);
         if (ydf) stw<W>(A.ylo + base + v * I.Cp, yl);
     }
@@ -2749,7 +2768,8 @@ cudaError_t launch_loop(const SolveArgs& A, const SolvePlan& P, cudaStream_t s)
         cudaGetLastError();   // clear, and fall back to per-phase launches
     }
     if (P.persistent && P.pcg_iters > 0 && !P.single) {
-        const bool resident = P.cmax <= 4 && A.nvt <= device_info().sms * occ_res[wi];
+        const bool resident = P.cmax <= 4 && A.nvt <= device_info().sms * occ_res[wi] &&
+                              (COMP || A.zq);
         if (resident || P.force_persistent) {
             // barrier words zero (or, for the failure-path test, a top counter
             // that the last arrival can never match)
@@ -2859,7 +2879,7 @@ bool resident_fits(const SolveArgs& A, const SolvePlan& P)
                                   {occupancy((const void*)pcg_resident_kernel<1, true>),
                                    occupancy((const void*)pcg_resident_kernel<2, true>),
                                    occupancy((const void*)pcg_resident_kernel<4, true>)}};
-    if (P.cmax > 4) return false;
+    if (P.cmax > 4 || (!P.comp && !A.zq)) return false;   // FP32: the loop keeps z in zq
     return A.nvt <= device_info().sms * occ[P.comp ? 1 : 0][width_index(P.cmax)];
 }
 

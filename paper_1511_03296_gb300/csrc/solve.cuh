@@ -65,8 +65,9 @@ struct SolveArgs {
     float* ylo;                // low part of y as a double-float pair (aux[1]), or nullptr:
                                //   the robust solver in compensated precision
     float* zq;                 // z = M^-1 r (aux[0]) for the FP32 Jacobi phase 1, which
-                               //   forms A d as A z + beta q_old; nullptr in the other
-                               //   variants (compensated, hierarchical, single reduction)
+                               //   forms A d as A z + beta q_old (per-phase, persistent and
+                               //   resident launches); nullptr in the other variants
+                               //   (compensated, hierarchical, single reduction)
     const float* nf;           // n in FP32, dense (the neighbour weights of the z form)
     // reductions
     Scal* scal;                // sum_k C_k
