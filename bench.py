@@ -320,23 +320,22 @@ def time_steps(step, steps, warmup, flush, stream):
 
 # DRAM traffic of one PCG iteration (both phases) from one ncu capture of the
 # current kernels (dram__bytes_read.sum + dram__bytes_write.sum; the summaries
-# and commands are in profiles/pcg_1080p.md and profiles/pcg_*_batched16.md).
-# ncu flushes the caches before each captured launch, so at 1080p this is the
-# cold-start traffic of an L2-resident working set.  The 64-image batch is too
-# large to capture under the profiling size rule: its 16-image prefix was
-# captured and the traffic is scaled by its ratio to the algorithmic bytes
-# (below 1: the gathers read 16-bit packed neighbour offsets, not the 32-bit
-# ids the algorithmic count assumes).
-PCG_TRAFFIC_1080P = 6.887936e6 + 7.725312e6
-# The resident loop (all 25 iterations in one cooperative launch) at 1080p:
-# dram__bytes over the launch (rate x duration from the capture in
-# profiles/pcg_resident_1080p.md), per iteration; after the first iteration
-# the working set is served from L2.
-PCG_TRAFFIC_1080P_RESIDENT = 20.610394e9 * 443.936e-6 / 25
-# The same for the resident loop of the single-reduction form
-# (profiles/pcg_resident_single_1080p.md).
+# and commands are in profiles/pcg_*_batched16.md and
+# profiles/pcg_resident_single_1080p.md).  ncu flushes the caches before each
+# captured launch.  The 64-image batch is too large to capture under the
+# profiling size rule: its 16-image prefix was captured (the z-form apply of
+# an iteration >= 1 and the update, four launches each, averaged) and the
+# traffic is scaled by its ratio to the algorithmic bytes (below 1: the
+# gathers read 16-bit packed neighbour offsets, not the 32-bit ids the
+# algorithmic count assumes, and the updates' writes stay in L2 within the
+# captured launch).  None: the kernel changed since its last capture.
+PCG_TRAFFIC_1080P = None
+PCG_TRAFFIC_1080P_RESIDENT = None
+# The resident loop of the single-reduction form at 1080p (all 25 iterations
+# in one cooperative launch): dram__bytes over the launch (rate x duration),
+# per iteration; after the first iteration the working set is served from L2.
 PCG_TRAFFIC_1080P_RESIDENT_SINGLE = 22.722101e9 * 409.472e-6 / 25
-PCG_TRAFFIC_RATIO_BATCHED = (108.809728e6 + 11.157760e6 + 66.430208e6 + 0.708096e6) / 235835472
+PCG_TRAFFIC_RATIO_BATCHED = (106975552 + 6058368 + 66441280 + 408576) / 235835472
 
 
 def pcg_roofline(regions, solves_per_step, steps, bytes_per_iter, peak):
