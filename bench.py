@@ -62,6 +62,10 @@ def parse_args():
                    help="run one extra workload alone (for profiling) and print its line")
     p.add_argument("--images", type=int, default=None,
                    help="image count of the --only workload (default: its full size)")
+    p.add_argument("--tune-cache", default=None,
+                   help="JSON file of autotuner choices: read when it holds the workload's "
+                        "shape class, else written after timing (a profiled run then uses "
+                        "the choice of a plain run)")
     return p.parse_args()
 
 
@@ -100,6 +104,9 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+TUNE_CACHE = None     # --tune-cache
+
+
 def tune(fbs, yuv, sig, t, c, lam, x):
     """The library's autotuner on one grid of the workload (its choice is then
     set on every step's grid; tuning happens outside the timed region).  Every
@@ -107,7 +114,7 @@ def tune(fbs, yuv, sig, t, c, lam, x):
     on a grid (no graph replay)."""
     g = fbs.grid_build(yuv, *sig)
     fbs.bistochastize(g, BISTOCH_ITERS)
-    r = fbs.autotune(g, t, c, lam, PCG_ITERS, x=x, single_solve=True)
+    r = fbs.autotune(g, t, c, lam, PCG_ITERS, x=x, single_solve=True, cache=TUNE_CACHE)
     g.destroy()
     return r
 
@@ -854,7 +861,9 @@ def run_ours(args, dist):
 
 
 def main():
+    global TUNE_CACHE
     args = parse_args()
+    TUNE_CACHE = args.tune_cache
     dist = Dist()
     try:
         if args.impl == "reference":
