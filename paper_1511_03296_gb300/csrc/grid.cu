@@ -574,8 +574,11 @@ cudaError_t launch_pack_neighbours(const int32_t* nbr, int64_t nstride, uint32_t
                                    cudaStream_t s)
 {
     if (V == 0) return cudaSuccess;
+    static int fam = prof_family("pack_neighbours");
     const int blocks = (int)std::min<int64_t>((V + 255) / 256, (int64_t)device_info().sms * 8);
+    prof_begin(fam, s);
     pack_neighbours_kernel<<<blocks, 256, 0, s>>>(nbr, nstride, nbrp, V);
+    prof_end(fam, s);
     return cudaGetLastError();
 }
 
