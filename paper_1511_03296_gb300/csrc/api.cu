@@ -333,7 +333,7 @@ struct fbs_grid {
     int32_t* nbr = nullptr;
     int64_t nbr_stride = 0;    // entries between the 10 rows of nbr (its vertex capacity)
     cudaEvent_t ev_counts = nullptr;   // the grid build's vertex counts have reached the host
-    uint32_t* nbrp = nullptr;           // 5 x Vtot packed 16-bit neighbour offsets
+    uint32_t* nbrp = nullptr;           // kNbrWords x Vtot packed neighbour offsets
     double* n64 = nullptr;
     double* n64b = nullptr;
     float* nf = nullptr;
@@ -636,7 +636,7 @@ fbs_status fbs_grid_build(const fbs_image_desc* imgs, int n_images, void* stream
             g->voff[k] = tile_voff[ti];
         }
         const int64_t V = g->Vtot;
-        FBS_TRY(dalloc(&g->nbrp, (size_t)V * 5, s));
+        FBS_TRY(dalloc(&g->nbrp, (size_t)V * kNbrWords, s));
         FBS_TRY(launch_pack_neighbours(g->nbr, g->nbr_stride, g->nbrp, V, s));
         FBS_TRY(dalloc(&g->n64, V, s));
         FBS_TRY(dalloc(&g->n64b, V, s));

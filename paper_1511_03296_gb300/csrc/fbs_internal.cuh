@@ -22,8 +22,11 @@ constexpr int kMaxChannels = 64;         // channels per image
 // splat's work counter, 32 (a 128-byte line of its own) the release word of
 // the resident loop's barrier; 33 lines in all
 constexpr unsigned kBarrierWords = 32 * 33;
-constexpr int kNbrOffMax = 32767;          // packed neighbour offsets: |offset| <= this
+constexpr int kNbrOffMax = 32767;          // packed 16-bit neighbour offsets (y): |offset| <= this
 constexpr int kNbrEscape = -32768;         // ... else this, and the 32-bit table holds the id
+constexpr int kNbrOffMax8 = 127;           // packed 8-bit offsets (x, l, u, v): |offset| <= this
+constexpr int kNbrEscape8 = -128;          // ... else this (the 32-bit table holds the id)
+constexpr int kNbrWords = 3;               // packed words per vertex
 constexpr unsigned kWorkCounterWord = 2;   // in the barrier block, unused by the barrier:
                                            // the splat's work counter
 constexpr unsigned kBarrierSpinLimit = 1u << 20;   // polls of >= 64 ns (an L2 round trip and a

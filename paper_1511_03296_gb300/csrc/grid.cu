@@ -468,32 +468,43 @@ bistoch_kernel(const double* __restrict__ nold, double* __restrict__ nnew,
 
 }  // namespace
 
-// Packed neighbour table: for dimension d, one 32-bit word per vertex holding
-// the -1 and +1 neighbours as 16-bit signed offsets from the vertex (low and
-// high half); an absent neighbour is offset 0 (the vertex itself, whose
-// Laplacian term is exactly 0), and an offset outside [-32767, 32767] is the
-// escape value -32768 (read the 32-bit table instead).  Spatial order keeps
-// offsets small: l, u, v neighbours share the cell, x neighbours are in the
-// next cell, y neighbours one cell row away.
+// Packed neighbour table: three 32-bit words per vertex (rows of V words)
+// holding the ten neighbours as signed offsets from the vertex.  Spatial
+// order keeps them small: l, u, v neighbours share the cell and x neighbours
+// are in the next cell (8-bit offsets), y neighbours one cell row away
+// (16-bit).  Word 0: x-, x+, l-, l+ (bytes 0..3); word 1: u-, u+, v-, v+;
+// word 2: y- (low half), y+ (high half).  An absent neighbour is offset 0
+// (the vertex itself, whose Laplacian term is exactly 0); an offset out of
+// range is the escape value (-128, or -32768 for y): read the 32-bit table.
+__device__ __forceinline__ uint32_t pack8(int64_t off)
+{
+    const int32_t h = (off >= -kNbrOffMax8 && off <= kNbrOffMax8) ? (int32_t)off : kNbrEscape8;
+    return (uint32_t)h & 0xffu;
+}
+
+__device__ __forceinline__ uint32_t pack16(int64_t off)
+{
+    const int32_t h = (off >= -kNbrOffMax && off <= kNbrOffMax) ? (int32_t)off : kNbrEscape;
+    return (uint32_t)h & 0xffffu;
+}
+
 __global__ void __launch_bounds__(256)
 pack_neighbours_kernel(const int32_t* __restrict__ nbr, int64_t nstride, uint32_t* __restrict__ nbrp,
                        int64_t V)
 {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
          v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t off[10];
 #pragma unroll
-        for (int d = 0; d < 5; ++d) {
-            uint32_t w = 0;
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const int32_t u = nbr[(int64_t)(2 * d + s) * nstride + v];
-                const int64_t off = u >= 0 ? (int64_t)u - v : 0;
-                const int32_t h = (off >= -kNbrOffMax && off <= kNbrOffMax) ? (int32_t)off
-                                                                             : kNbrEscape;
-                w |= ((uint32_t)h & 0xffffu) << (16 * s);
-            }
-            nbrp[(int64_t)d * V + v] = w;
+        for (int j = 0; j < 10; ++j) {
+            const int32_t u = nbr[(int64_t)j * nstride + v];
+            off[j] = u >= 0 ? (int64_t)u - v : 0;
         }
+        // neighbour j = 2 d + s: d = 0 x, 1 y, 2 l, 3 u, 4 v; s = 0 (-1), 1 (+1)
+        nbrp[v] = pack8(off[0]) | pack8(off[1]) << 8 | pack8(off[4]) << 16 | pack8(off[5]) << 24;
+        nbrp[V + v] = pack8(off[6]) | pack8(off[7]) << 8 | pack8(off[8]) << 16 |
+                      pack8(off[9]) << 24;
+        nbrp[2 * V + v] = pack16(off[2]) | pack16(off[3]) << 16;
     }
 }
 

@@ -83,30 +83,41 @@ __device__ __forceinline__ void stw(float* p, const float (&v)[W])
     }
 }
 
-// The ten neighbours of vertex v (order: -1, +1 per dimension) from the
-// packed table (16-bit offsets; absent: v itself, whose Laplacian term is
-// exactly 0).  Escaped offsets are rare (more than 32767 vertices between a
-// vertex and its y neighbour): the 32-bit table is read only in a
-// warp-uniform branch when some lane of the warp has one, so the common
-// path has no load in the id chain.  All lanes of the warp must call it.
+// The ten neighbours of vertex v (order: -1, +1 per dimension x, y, l, u, v)
+// from the packed table (8-bit offsets for x, l, u, v and 16-bit for y;
+// absent: v itself, whose Laplacian term is exactly 0).  Escaped offsets are
+// rare (a cell with more than 127 vertices between neighbours, or more than
+// 32767 vertices between a vertex and its y neighbour): the 32-bit table is
+// read only in a warp-uniform branch when some lane of the warp has one, so
+// the common path has no load in the id chain.  All lanes of the warp must
+// call it.
 __device__ __forceinline__ void load_neighbours(const SolveArgs& A, int v, int (&nb)[10])
 {
-    uint32_t w[5];
+    const uint32_t w0 = A.nbrp[v];
+    const uint32_t w1 = A.nbrp[A.Vtot + v];
+    const uint32_t w2 = A.nbrp[2 * A.Vtot + v];
+    int o[10];
+    o[0] = (int)(int8_t)(w0 & 0xffu);
+    o[1] = (int)(int8_t)((w0 >> 8) & 0xffu);
+    o[4] = (int)(int8_t)((w0 >> 16) & 0xffu);
+    o[5] = (int)(int8_t)(w0 >> 24);
+    o[6] = (int)(int8_t)(w1 & 0xffu);
+    o[7] = (int)(int8_t)((w1 >> 8) & 0xffu);
+    o[8] = (int)(int8_t)((w1 >> 16) & 0xffu);
+    o[9] = (int)(int8_t)(w1 >> 24);
+    o[2] = (int)(int16_t)(w2 & 0xffffu);
+    o[3] = (int)(int16_t)(w2 >> 16);
+    bool esc = (o[2] == kNbrEscape) | (o[3] == kNbrEscape);
 #pragma unroll
-    for (int d = 0; d < 5; ++d) w[d] = A.nbrp[(int64_t)d * A.Vtot + v];
-    bool esc = false;
-#pragma unroll
-    for (int d = 0; d < 5; ++d) {
-        const int om = (int)(int16_t)(w[d] & 0xffffu), op = (int)(int16_t)(w[d] >> 16);
-        nb[2 * d] = v + om;
-        nb[2 * d + 1] = v + op;
-        esc |= (om == kNbrEscape) | (op == kNbrEscape);
+    for (int j = 0; j < 10; ++j) {
+        nb[j] = v + o[j];
+        if (j != 2 && j != 3) esc |= o[j] == kNbrEscape8;
     }
     if (__any_sync(0xffffffffu, esc)) {
 #pragma unroll
         for (int j = 0; j < 10; ++j) {
-            const int o = (int)(int16_t)((w[j >> 1] >> (16 * (j & 1))) & 0xffffu);
-            if (o == kNbrEscape) nb[j] = A.nbr[(int64_t)j * A.nbr_stride + v];
+            const bool e = (j == 2 || j == 3) ? o[j] == kNbrEscape : o[j] == kNbrEscape8;
+            if (e) nb[j] = A.nbr[(int64_t)j * A.nbr_stride + v];
         }
     }
 }

@@ -44,7 +44,7 @@ struct SolveArgs {
     // grid
     const int32_t* nbr;        // 10 rows of nbr_stride, global vertex ids, -1 if absent
     int64_t nbr_stride;        // row stride of nbr (>= Vtot: the grid's vertex capacity)
-    const uint32_t* nbrp;      // 5 x Vtot, packed 16-bit offsets (-1 and +1 per dimension)
+    const uint32_t* nbrp;      // 3 x Vtot, packed offsets (8-bit x, l, u, v; 16-bit y)
     int64_t Vtot;
     const double* n64;         // bistochastisation vector n
     const uint32_t* m;         // counts

@@ -443,6 +443,22 @@ def test_solve_with_escaped_neighbour_offsets():
     _check_solve([inst])
 
 
+def test_solve_with_escaped_8bit_neighbour_offsets(pcg_launch):
+    # 96 x 128 at sigma_xy = 32 with fine colour sigmas (4, 0.25): about a
+    # thousand vertices per cell, so x and l neighbours lie more than 127
+    # vertices away (beyond the packed table's 8-bit offsets) and the phase
+    # kernels read them from the 32-bit table (the resident loops load the
+    # 32-bit table once)
+    from paper_1511_03296_gb300 import fbs
+    inst = synth.make_tiny(44, 96, 128, 40, 1, (32.0, 4.0, 0.25), 128.0)
+    g = gpu_grid([inst], 2)
+    _, _, _, nbr, _ = fbs.grid_export(g, 0, with_n=False)
+    v = np.arange(nbr.shape[0])[:, None]
+    far = (nbr >= 0) & (np.abs(nbr.astype(np.int64) - v) > 127)
+    assert far[:, [0, 1]].sum() > 0 and far[:, [4, 5]].sum() > 0, far.sum(0)
+    _check_solve([inst])
+
+
 def test_autotune_picks_a_configuration_and_keeps_parity():
     # the tuned configuration is left on the grid and its result is in the
     # outputs; a later solve with it still matches the oracle
