@@ -333,16 +333,17 @@ def time_steps(step, steps, warmup, flush, stream):
 # profiling size rule: its 16-image prefix was captured (the z-form apply of
 # an iteration >= 1 and the update, four launches each, averaged) and the
 # traffic is scaled by its ratio to the algorithmic bytes (below 1: the
-# gathers read 16-bit packed neighbour offsets, not the 32-bit ids the
-# algorithmic count assumes, and the updates' writes stay in L2 within the
-# captured launch).  None: the kernel changed since its last capture.
+# gathers read 12 B of packed 8- and 16-bit neighbour offsets per vertex, not
+# the 40 B of 32-bit ids the algorithmic count assumes, and the updates'
+# writes stay in L2 within the captured launch).  None: the kernel changed
+# since its last capture.
 PCG_TRAFFIC_1080P = None
 PCG_TRAFFIC_1080P_RESIDENT = None
 # The resident loop of the single-reduction form at 1080p (all 25 iterations
 # in one cooperative launch): dram__bytes over the launch (rate x duration),
 # per iteration; after the first iteration the working set is served from L2.
 PCG_TRAFFIC_1080P_RESIDENT_SINGLE = 22.722101e9 * 409.472e-6 / 25
-PCG_TRAFFIC_RATIO_BATCHED = (106975552 + 6058368 + 66441280 + 408576) / 235835472
+PCG_TRAFFIC_RATIO_BATCHED = (85614656 + 2921600 + 66437824 + 509312) / 235835472
 
 
 def pcg_roofline(regions, solves_per_step, steps, bytes_per_iter, peak):
