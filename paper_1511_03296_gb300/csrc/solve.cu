@@ -2596,11 +2596,13 @@ __device__ void resident_single_loop(const SolveArgs& A, const InstDev& I, const
             u1[k] = nmv.y * r1[k];
             so[k] = si;
         }
-        if (valid) {
-            stw<W>(A.y + off + v * W, yv);
-            stw<W>(A.q + off + v * W, pv);
+        if (last) {
+            if (valid) {
+                stw<W>(A.y + off + v * W, yv);
+                stw<W>(A.q + off + v * W, pv);
+            }
+            break;
         }
-        if (last) break;
         const float* __restrict__ rb = (cur ? A.rlo : A.r) + off;   // r_i
         const float* __restrict__ wb = A.d[cur] + off;             // w_i
         const float* __restrict__ sb = A.aux[nxt] + off;           // s_(i-1)
@@ -2637,7 +2639,9 @@ __device__ void resident_single_loop(const SolveArgs& A, const InstDev& I, const
             rg[k] = on ? df_mul_exact(r1[k], u1[k]) : DF{0.0f, 0.0f};
             rm[k] = on ? df_mul_exact(w[k], u1[k]) : DF{0.0f, 0.0f};
         }
-        if (valid) {
+        if (valid) {                // every store after the last gather
+            stw<W>(A.y + off + v * W, yv);
+            stw<W>(A.q + off + v * W, pv);
             stw<W>(A.aux[cur] + off + v * W, so);
             stw<W>((nxt ? A.rlo : A.r) + off + v * W, r1);
             stw<W>(A.d[nxt] + off + v * W, w);
