@@ -342,7 +342,7 @@ PCG_TRAFFIC_1080P_RESIDENT = None
 # The resident loop of the single-reduction form at 1080p (all 25 iterations
 # in one cooperative launch): dram__bytes over the launch (rate x duration),
 # per iteration; after the first iteration the working set is served from L2.
-PCG_TRAFFIC_1080P_RESIDENT_SINGLE = 22.722101e9 * 409.472e-6 / 25
+PCG_TRAFFIC_1080P_RESIDENT_SINGLE = 23.025889e9 * 404.192e-6 / 25
 PCG_TRAFFIC_RATIO_BATCHED = (85614656 + 2921600 + 66437824 + 509312) / 235835472
 
 
