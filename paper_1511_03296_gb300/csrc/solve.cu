@@ -728,14 +728,6 @@ residual_kernel(SolveArgs A)
 }
 
 // -------------------------------------------------- PCG phase bodies ---
-// Phase 1 of iteration `it` on one tile of an image with Cp = W <= 4 (one
-// pass; the row stride is the compile-time W, and vertex ids are 32-bit):
-// d = M^-1 r + beta d_old (own vertex and, on the fly, its neighbours),
-// q = A d, products d q into run[].  q is formed in FP32 in both precisions:
-// here it only enters d^T q (the step length).  COMP: q is not stored
-// (phase 2 recomputes it exactly from d).  With fetch (the tile starts the
-// block's run over an image) the CG scalars are formed first, after the
-// tile's neighbour ids and own values have been requested.
 // FP32 phase 1 of iterations >= 1 with the preconditioned residual
 // z = M^-1 r stored by the previous update: since d = z + beta d_old is
 // linear, A d = A z + beta q_old, so a neighbour contributes only n_u and z_u
@@ -791,6 +783,14 @@ __device__ __forceinline__ void apply_tile_z(const SolveArgs& A, const InstDev& 
     }
 }
 
+// Phase 1 of iteration `it` on one tile of an image with Cp = W <= 4 (one
+// pass; the row stride is the compile-time W, and vertex ids are 32-bit):
+// d = M^-1 r + beta d_old (own vertex and, on the fly, its neighbours),
+// q = A d, products d q into run[].  q is formed in FP32 in both precisions;
+// FP32 stores it for phase 2, while COMP uses it only in d^T q (the step
+// length) and phase 2 recomputes it exactly from d.  With fetch (the tile starts the
+// block's run over an image) the CG scalars are formed first, after the
+// tile's neighbour ids and own values have been requested.
 // Z: the z form (FP32, Jacobi, iterations >= 1; z stored by the last update)
 template <int W, bool COMP, bool CO, bool HIER = false, bool Z = false>
 __device__ __forceinline__ void apply_tile(const SolveArgs& A, const InstDev& I, const VTile& vt,
