@@ -185,7 +185,10 @@ fbs_status fbs_solve_backward(fbs_grid* g, const fbs_problem_desc* probs,
  *
  * FBS_OPT_VECTOR_PRECISION: how the CG state is held (the paper fixes no
  * precision; every variant keeps the CG inner products FP64-accurate):
- *   FBS_VECTORS_FP32         y, r, d, q in FP32; A d computed in FP32.
+ *   FBS_VECTORS_FP32         y, r, d, q in FP32; A d computed in FP32 (with
+ *                            the Jacobi preconditioner, from the second PCG
+ *                            iteration as A z + beta q_old with z = M^-1 r,
+ *                            equal to A d up to rounding).
  *   FBS_VECTORS_COMPENSATED  y, d in FP32; the residual r as a pair of FP32
  *                            values (double-float) and q = A d recomputed in
  *                            the update phase with error-free products, so
