@@ -429,6 +429,46 @@ def test_pcg_single_equals_standard_iterates():
         assert np.allclose(y1, ys, rtol=1e-9, atol=1e-9 * np.abs(ys).max()), k
 
 
+def _pcg_zform_dense(A, minv, b, y0, iters):
+    """Jacobi PCG with the recurrence the GPU's FP32 phase 1 uses from the
+    second iteration: d = z + beta d_old is linear in z = M^-1 r, so
+    A d = A z + beta (A d_old); the product A d itself is formed only in
+    iteration 0.  Written here from that identity on a dense A, with the
+    oracle's guards (alpha = 0 unless d^T A d > 0 and rho != 0; beta = 0 when
+    rho = 0)."""
+    y = y0.copy()
+    r = b - A @ y
+    z = minv * r
+    rho = r @ z
+    d = z.copy()
+    q = A @ d
+    for it in range(iters):
+        if it > 0:
+            d = z + beta * d
+            q = A @ z + beta * q
+        dq = d @ q
+        alpha = rho / dq if (dq > 0.0 and rho != 0.0) else 0.0
+        y = y + alpha * d
+        r = r - alpha * q
+        z = minv * r
+        rho_next = r @ z
+        beta = rho_next / rho if rho != 0.0 else 0.0
+        rho = rho_next
+    return y
+
+
+def test_pcg_zform_recurrence_equals_standard_iterates():
+    # A d = A z + beta A d_old: the z form's iterates equal the standard
+    # form's (the oracle's) at every iteration count in exact arithmetic
+    inst, g, S, B, A, b, sc = _problem(iters=2, lam=16.0, C=1)
+    a, minv = oracle.diag(g.m, g.nbr, g.n, sc, inst.lam)
+    y0 = oracle.flat_init(b[0], sc)
+    for k in range(0, 16):
+        ys = oracle.pcg(g.nbr, g.n, a, minv, inst.lam, b[0], y0, k)
+        yz = _pcg_zform_dense(A, minv, b[0], y0, k)
+        assert np.allclose(yz, ys, rtol=1e-9, atol=1e-9 * np.abs(ys).max()), k
+
+
 def test_pcg_single_converged_matches_dense_solve():
     inst, g, S, B, A, b, sc = _problem(iters=2, lam=16.0)
     with oracle.pcg_form("single"):
